@@ -1,0 +1,241 @@
+"""Plain FP64 CPU oracle for the stochastic Richards' equation solve.
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only callers.  The product path never
+imports this package.  It shares no code with the CUDA library.
+
+The numerical core is ``richards_oracle.c`` (plain loops, -O2
+-ffp-contract=off); this module compiles it with gcc on first use and wraps
+it with ctypes.  The MLMC statistics of Sec. 5 (Eqs. MLMCestimator_ch6,
+MC_var_ch6, eq:MLMCVar, MLMCSAMP_ch6) are written here in numpy.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "richards_oracle.c")
+_HDR = os.path.join(_HERE, "richards_oracle.h")
+_LIB = os.path.join(_HERE, "liboracle_richards.so")
+
+OK, PICARD_MAXIT, MG_MAXIT, NONFINITE = 0, 1, 2, 3
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no multiply-add contraction)."""
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-std=c11", "-D_GNU_SOURCE", "-o", tmp, _SRC, "-lm", "-lpthread"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Problem(C.Structure):
+    _fields_ = [("nsteps", C.c_int32), ("dt", C.c_double), ("theta_r", C.c_double),
+                ("theta_s", C.c_double), ("p_top", C.c_double), ("p_bottom", C.c_double),
+                ("p_init", C.c_double), ("picard_tol", C.c_double), ("picard_maxit", C.c_int32),
+                ("mg_tol", C.c_double), ("mg_maxit", C.c_int32), ("nu1", C.c_int32),
+                ("nu2", C.c_int32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("picard_iters", C.c_int64), ("mg_cycles", C.c_int64),
+                ("max_picard", C.c_int32), ("max_mg", C.c_int32)]
+
+
+def make_problem(nsteps=10, dt=0.01, theta_r=0.1, theta_s=0.5, p_top=-0.5, p_bottom=-5.0,
+                 p_init=-5.0, picard_tol=1e-8, picard_maxit=50, mg_tol=1e-10, mg_maxit=100,
+                 nu1=2, nu2=2) -> Problem:
+    """Physics and solver settings of the configured instance (Gardner closure)."""
+    return Problem(nsteps, dt, theta_r, theta_s, p_top, p_bottom, p_init, picard_tol,
+                   picard_maxit, mg_tol, mg_maxit, nu1, nu2)
+
+
+_lib = None
+_dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_u32p = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(build())
+        L.orc_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
+        L.orc_white_noise.argtypes = [C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint32, C.c_int64, _dp]
+        L.orc_fft2.argtypes = [_dp, _dp, C.c_int32, C.c_int32, C.c_int32]
+        L.orc_fft2.restype = C.c_int
+        L.orc_fftma_spectrum.argtypes = [C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double,
+                                         _dp, C.POINTER(C.c_double)]
+        L.orc_torus_size.argtypes = [C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double,
+                                     C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+        L.orc_sample_fields.argtypes = [C.c_uint64, C.c_double, C.c_double, C.c_double, C.c_double,
+                                        C.c_int32, C.c_int32, C.c_uint32, C.c_int64, C.c_int32,
+                                        C.c_int32, _dp, _dp, C.c_int32]
+        L.orc_solve_one.argtypes = [C.POINTER(Problem), C.c_int32, C.c_int32, _dp, _dp, C.c_double,
+                                    C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
+                                    C.POINTER(Stats)]
+        L.orc_solve_batch.argtypes = [C.POINTER(Problem), C.c_int32, C.c_int32, C.c_int32, _dp, _dp,
+                                      C.c_double, C.c_void_p, _dp, _i32p, C.POINTER(Stats), C.c_int32]
+        L.orc_picard_system.argtypes = [C.POINTER(Problem), C.c_int32, C.c_int32, _dp, _dp, C.c_double,
+                                        _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+        L.orc_mg_solve.argtypes = [C.c_int32, C.c_int32, C.c_double, _dp, _dp, _dp, _dp, _dp, _dp,
+                                   C.c_double, C.c_int32, C.c_int32, C.c_int32, _dp,
+                                   C.POINTER(C.c_int32), C.c_void_p]
+        _lib = L
+    return _lib
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+# ---------------------------------------------------------------- random fields
+def philox4x32_10(ctr, key):
+    out = np.zeros(4, np.uint32)
+    lib().orc_philox4x32_10(np.asarray(ctr, np.uint32), np.asarray(key, np.uint32), out)
+    return out
+
+
+def white_noise(seed, level, sample, field, npts):
+    y = np.empty(npts, np.float64)
+    lib().orc_white_noise(seed, level, sample, field, npts, y)
+    return y
+
+
+def fft2(x, inverse=False):
+    """2-D DFT of a complex [nz, nx] array with the oracle's own radix-2 FFT."""
+    x = np.asarray(x, np.complex128)
+    re, im = _f64(x.real.copy()), _f64(x.imag.copy())
+    nz, nx = x.shape
+    rc = lib().orc_fft2(re, im, nx, nz, int(inverse))
+    if rc:
+        raise ValueError("sizes must be powers of two")
+    return re + 1j * im
+
+
+def torus_size(nx, nz, sigma2=1.0, corr_len=0.3):
+    px, pz = C.c_int32(), C.c_int32()
+    lib().orc_torus_size(nx, nz, 1.0 / nz, sigma2, corr_len, C.byref(px), C.byref(pz))
+    return px.value, pz.value
+
+
+def fftma_sqrt_spectrum(px, pz, h, sigma2=1.0, corr_len=0.3):
+    s = np.empty(px * pz, np.float64)
+    ratio = C.c_double()
+    lib().orc_fftma_spectrum(px, pz, h, sigma2, corr_len, s, C.byref(ratio))
+    return s.reshape(pz, px), ratio.value
+
+
+def sample_fields(nx, nz, nsamples, seed=0, level=0, first_sample=0, coarsen_times=0,
+                  sigma2=1.0, corr_len=0.3, alpha_lo=0.5, alpha_span=1.5, nthreads=None):
+    """ln Ks and alpha fields [S, nz>>c, nx>>c] drawn by FFT-MA on the nx x nz grid."""
+    nthreads = nthreads or os.cpu_count() or 1
+    nxo, nzo = nx >> coarsen_times, nz >> coarsen_times
+    lnKs = np.empty((nsamples, nzo, nxo), np.float64)
+    alpha = np.empty((nsamples, nzo, nxo), np.float64)
+    rc = lib().orc_sample_fields(seed, sigma2, corr_len, alpha_lo, alpha_span, nx, nz, level,
+                                 first_sample, nsamples, coarsen_times, lnKs.reshape(-1),
+                                 alpha.reshape(-1), nthreads)
+    if rc:
+        raise ValueError("invalid field arguments")
+    return lnKs, alpha
+
+
+# ---------------------------------------------------------------------- solver
+def solve_one(pb, lnKs, alpha, alpha_scale=1.0, src=None, p_init=None):
+    lnKs, alpha = _f64(lnKs), _f64(alpha)
+    nz, nx = lnKs.shape
+    src = None if src is None else _f64(src)
+    p_init = None if p_init is None else _f64(p_init)
+    p = np.empty((nz, nx), np.float64)
+    q = C.c_double()
+    st = Stats()
+    rc = lib().orc_solve_one(C.byref(pb), nx, nz, lnKs.reshape(-1), alpha.reshape(-1), alpha_scale,
+                             _ptr(src), _ptr(p_init), _ptr(p), C.byref(q), C.byref(st))
+    if rc < 0:
+        raise ValueError("invalid grid")
+    return p, q.value, rc, st
+
+
+def solve_batch(pb, lnKs, alpha, alpha_scale=1.0, want_p=True, nthreads=None):
+    """Solve every sample of lnKs/alpha [S, nz, nx]; returns (p, qoi, status, stats)."""
+    nthreads = nthreads or os.cpu_count() or 1
+    lnKs, alpha = _f64(lnKs), _f64(alpha)
+    S, nz, nx = lnKs.shape
+    p = np.empty((S, nz, nx), np.float64) if want_p else None
+    qoi = np.empty(S, np.float64)
+    status = np.zeros(S, np.int32)
+    st = Stats()
+    rc = lib().orc_solve_batch(C.byref(pb), nx, nz, S, lnKs.reshape(-1), alpha.reshape(-1),
+                               alpha_scale, _ptr(p), qoi, status, C.byref(st), nthreads)
+    if rc < 0:
+        raise ValueError("invalid grid")
+    return p, qoi, status, st
+
+
+def picard_system(pb, lnKs, alpha, p, p_old, alpha_scale=1.0):
+    """The Picard system at iterate p: (Tx, Tz, Tbt, Tbb, Cdt, f)."""
+    lnKs, alpha, p, p_old = _f64(lnKs), _f64(alpha), _f64(p), _f64(p_old)
+    nz, nx = lnKs.shape
+    Tx, Tz, Cdt, f = (np.empty((nz, nx)) for _ in range(4))
+    Tbt, Tbb = np.empty(nx), np.empty(nx)
+    lib().orc_picard_system(C.byref(pb), nx, nz, lnKs.reshape(-1), alpha.reshape(-1), alpha_scale,
+                            p.reshape(-1), p_old.reshape(-1), Tx.reshape(-1), Tz.reshape(-1),
+                            Tbt, Tbb, Cdt.reshape(-1), f.reshape(-1))
+    return Tx, Tz, Tbt, Tbb, Cdt, f
+
+
+def mg_solve(Tx, Tz, Tbt, Tbb, Cdt, f, tol=1e-10, maxit=100, nu1=2, nu2=2):
+    """CCMG V(nu1,nu2) solve from dp = 0; returns (dp, cycles, rc, residual history)."""
+    Tx, Tz, Cdt, f = _f64(Tx), _f64(Tz), _f64(Cdt), _f64(f)
+    nz, nx = f.shape
+    dp = np.empty((nz, nx))
+    cyc = C.c_int32()
+    hist = np.zeros(maxit + 1)
+    rc = lib().orc_mg_solve(nx, nz, 1.0 / nz, Tx.reshape(-1), Tz.reshape(-1), _f64(Tbt), _f64(Tbb),
+                            Cdt.reshape(-1), f.reshape(-1), tol, maxit, nu1, nu2, dp.reshape(-1),
+                            C.byref(cyc), _ptr(hist))
+    return dp, cyc.value, rc, hist[: cyc.value + 1]
+
+
+# ------------------------------------------------------------------------ MLMC
+@dataclass
+class LevelStats:
+    n: int            # N_l samples
+    mean: float       # E^MC_{N_l}[P_l - P_{l-1}]   (Eq. SMC_ch6)
+    var: float        # V_l, unbiased 1/(N_l - 1)   (Eqs. MC_var_ch6, level_var_ch6)
+    cost: float       # W_l, cost of one sample of the pair (seconds)
+
+
+def level_stats(y, cost_per_sample):
+    y = np.asarray(y, np.float64)
+    n = y.size
+    return LevelStats(n, float(y.mean()), float(y.var(ddof=1)) if n > 1 else float("nan"),
+                      float(cost_per_sample))
+
+
+def mlmc_combine(levels):
+    """Telescoping estimate (Eq. MLMCestimator_ch6), sampling RMSE (Eq. eq:MLMCVar),
+    optimal N_l (Eq. MLMCSAMP_ch6) and the cost W(eps) of the optimal allocation."""
+    est = sum(L.mean for L in levels)
+    rmse = float(np.sqrt(sum(L.var / L.n for L in levels)))
+    return est, rmse
+
+
+def optimal_samples(levels, eps):
+    s = sum(np.sqrt(L.var * L.cost) for L in levels)
+    n_opt = [eps ** -2 * s * np.sqrt(L.var / L.cost) for L in levels]
+    w = eps ** -2 * s * s
+    return n_opt, w

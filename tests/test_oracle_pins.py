@@ -1,0 +1,357 @@
+"""Pins of the FP64 CPU oracle against facts fixed by the paper and by mathematics.
+
+None of these tests re-types an oracle formula and compares: each one checks a
+closed form, an invariant, a brute-force or library computation, or a published
+known-answer vector, chosen so that a dropped term, a wrong sign or index, or a
+transposed operand in the oracle fails at least one of them.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from tests.inputs import PHYSICS, SOLVER
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def problem(**kw):
+    d = dict(PHYSICS)
+    d.update(SOLVER)
+    d.update(dict(nsteps=1, dt=0.01))
+    d.update(kw)
+    return O.make_problem(**d)
+
+
+# ------------------------------------------------------------------ generator
+def test_philox_known_answers():
+    """Philox4x32-10 reproduces its published known-answer vectors (SC'11)."""
+    rows = [l.split() for l in open(os.path.join(HERE, "golden", "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        w = [int(x, 16) for x in r]
+        out = O.philox4x32_10(w[0:4], w[4:6])
+        assert [int(v) for v in out] == w[6:10]
+
+
+def test_white_noise_is_standard_normal():
+    from scipy import stats
+    y = np.concatenate([O.white_noise(0, 0, s, f, 4096) for s in range(8) for f in range(2)])
+    assert abs(y.mean()) < 5 / np.sqrt(y.size)
+    assert abs(y.var() - 1) < 5 * np.sqrt(2 / y.size)
+    assert stats.kstest(y, "norm").pvalue > 1e-3
+    # distinct (sample, field, level) streams are uncorrelated
+    a, b = O.white_noise(0, 0, 1, 0, 8192), O.white_noise(0, 0, 1, 1, 8192)
+    c = O.white_noise(0, 1, 1, 0, 8192)
+    assert abs(np.corrcoef(a, b)[0, 1]) < 5 / np.sqrt(8192)
+    assert abs(np.corrcoef(a, c)[0, 1]) < 5 / np.sqrt(8192)
+
+
+# ------------------------------------------------------------------------ FFT
+@pytest.mark.parametrize("shape", [(8, 8), (16, 32), (64, 4), (1, 16)])
+def test_fft_matches_library(shape):
+    rng = np.random.default_rng(1)
+    x = rng.normal(size=shape) + 1j * rng.normal(size=shape)
+    X = O.fft2(x)
+    ref = np.fft.fft2(x)
+    assert np.abs(X - ref).max() < 1e-12 * np.abs(ref).max()
+    back = O.fft2(X, inverse=True)
+    assert np.abs(back - x).max() < 1e-13 * np.abs(x).max()
+
+
+# ------------------------------------------------------------- FFT-MA fields
+@pytest.mark.parametrize("px,pz,h,lam", [(16, 16, 1 / 8, 0.3), (32, 16, 1 / 8, 0.2)])
+def test_fftma_exact_covariance(px, pz, h, lam):
+    """The circular autocorrelation of s = F^-1 sqrt(F c) equals the torus
+    covariance c itself (Appendix A, Eqs. convol1, product1), computed here by
+    brute force over all lags."""
+    sq, ratio = O.fftma_sqrt_spectrum(px, pz, h, 1.0, lam)
+    assert ratio >= -1e-12
+    s = np.real(np.fft.ifft2(sq))
+    for b in range(pz):
+        for a in range(px):
+            acorr = np.sum(s * np.roll(np.roll(s, -b, axis=0), -a, axis=1))
+            dx, dz = min(a, px - a) * h, min(b, pz - b) * h
+            assert abs(acorr - np.exp(-np.hypot(dx, dz) / lam)) < 1e-12
+
+
+def test_fields_empirical_covariance_and_marginals():
+    """4096 fields on 16x16: ln Ks is zero-mean with Cov(r) = exp(-r/0.3) at
+    lags up to 8 cells (within 5 standard errors); alpha = 0.5 + 1.5 Phi(g) has
+    a uniform marginal on (0.5, 2) (the configured bounded field)."""
+    from scipy import stats
+    n, S, lam = 16, 4096, 0.3
+    lnks, alpha = O.sample_fields(n, n, S, seed=0)
+    h = 1.0 / n
+    assert abs(lnks.mean()) < 0.05
+    for field in (lnks, None):
+        z = lnks if field is not None else np.sqrt(2) * stats.norm.ppf((alpha - 0.5) / 1.5) / np.sqrt(2)
+        for axis in (1, 2):
+            for lag in range(0, 9):
+                a = np.take(z, np.arange(0, n - lag), axis=axis)
+                b = np.take(z, np.arange(lag, n), axis=axis)
+                per_sample = (a * b).mean(axis=(1, 2))
+                se = per_sample.std(ddof=1) / np.sqrt(S)
+                target = np.exp(-lag * h / lam)
+                assert abs(per_sample.mean() - target) < 5 * se + 1e-3, (axis, lag)
+    assert alpha.min() > 0.5 and alpha.max() < 2.0
+    u = (alpha[:, 5, 7] - 0.5) / 1.5
+    assert stats.kstest(u, "uniform").pvalue > 1e-3
+
+
+def test_fields_coarsening_is_2x2_mean():
+    """coarsen_times = 1 returns the 2x2 block means of the fine draw."""
+    lk, al = O.sample_fields(16, 16, 3, seed=5)
+    lc, ac = O.sample_fields(16, 16, 3, seed=5, coarsen_times=1)
+    blk = lambda x: x.reshape(3, 8, 2, 8, 2).mean(axis=(2, 4))
+    assert np.abs(lc - blk(lk)).max() < 1e-14
+    assert np.abs(ac - blk(al)).max() < 1e-14
+
+
+# ---------------------------------------------------------- linear limits
+def layered_head(ks_rows, p_top, p_bot):
+    """Exact steady head in a horizontally layered column with uniform K per
+    layer: Darcy flux q = -K d(p + z)/dz is constant, and the hydraulic head
+    p + z drops across each half cell by q times its resistance (h/2)/K."""
+    nz = ks_rows.size
+    h = 1.0 / nz
+    half = (h / 2) / ks_rows
+    r_centre = np.concatenate([[half[0]], half[0] + np.cumsum(half[:-1] + half[1:])])
+    r_total = r_centre[-1] + half[-1]
+    phi_bot, phi_top = p_bot + 0.0, p_top + 1.0
+    q = -(phi_top - phi_bot) / r_total
+    phi = phi_bot - q * r_centre
+    z = (np.arange(nz) + 0.5) * h
+    return phi - z
+
+
+@pytest.mark.parametrize("n", [8, 16, 32])
+def test_saturated_limit_layered_closed_form(n):
+    """alpha = 0 (K = Ks, C = 0): steady layered flow has a closed form that the
+    harmonic face means, the half-cell Dirichlet faces and the gravity term
+    reproduce exactly."""
+    z = (np.arange(n) + 0.5) / n
+    ks_rows = np.exp(0.8 * np.sin(2 * np.pi * z) + 0.5 * np.cos(5 * z) + 0.3 * z)
+    lnks = np.repeat(np.log(ks_rows)[:, None], n, axis=1)
+    alpha = np.zeros((n, n))
+    pb = problem(nsteps=2)
+    p, q, rc, st = O.solve_one(pb, lnks, alpha)
+    assert rc == 0
+    exact = layered_head(ks_rows, PHYSICS["p_top"], PHYSICS["p_bottom"])
+    assert np.abs(p - exact[:, None]).max() < 1e-9
+    # bottom-flux QoI equals the exact downward Darcy flux
+    phi_drop = (PHYSICS["p_top"] + 1.0) - PHYSICS["p_bottom"]
+    r_total = np.sum(1.0 / n / ks_rows)
+    assert abs(q - phi_drop / r_total) < 1e-9 * max(1.0, abs(q))
+
+
+def test_saturated_limit_columns_closed_form():
+    """Ks varying only across x: every column carries its own vertical flux
+    and the head is the same linear profile in each column (no lateral flow)."""
+    n = 16
+    rng = np.random.default_rng(3)
+    lnks = np.repeat(rng.normal(size=n)[None, :], n, axis=0)
+    p, q, rc, _ = O.solve_one(problem(), lnks, np.zeros((n, n)))
+    z = (np.arange(n) + 0.5) / n
+    exact = PHYSICS["p_bottom"] + (PHYSICS["p_top"] - PHYSICS["p_bottom"]) * z
+    assert rc == 0 and np.abs(p - exact[:, None]).max() < 1e-9
+
+
+def hydraulic_head_dense_solve(lnks):
+    """Steady saturated flow solved for the hydraulic head phi = p + z with a
+    dense direct solve of G^T diag(c) G phi = b phi_D, where G is the
+    face-cell incidence matrix, c the face conductances (inverse of the sum of
+    the two half-cell resistances) and b the Dirichlet half-cell conductances.
+    Gravity never appears: it is absorbed into phi."""
+    nz, nx = lnks.shape
+    h = 1.0 / nz
+    K = np.exp(lnks)
+    rhalf = h * h / (2.0 * K)          # half-cell resistance per unit area
+    idx = lambda i, j: j * nx + i
+    rows, cond = [], []
+    for j in range(nz):
+        for i in range(nx):
+            if i + 1 < nx:
+                rows.append((idx(i, j), idx(i + 1, j)))
+                cond.append(1.0 / (rhalf[j, i] + rhalf[j, i + 1]))
+            if j + 1 < nz:
+                rows.append((idx(i, j), idx(i, j + 1)))
+                cond.append(1.0 / (rhalf[j, i] + rhalf[j + 1, i]))
+    n = nx * nz
+    G = np.zeros((len(rows), n))
+    for k, (a, b) in enumerate(rows):
+        G[k, a], G[k, b] = 1.0, -1.0
+    A = G.T @ np.diag(cond) @ G
+    rhs = np.zeros(n)
+    for i in range(nx):
+        bt, bb = 1.0 / rhalf[nz - 1, i], 1.0 / rhalf[0, i]
+        A[idx(i, nz - 1), idx(i, nz - 1)] += bt
+        A[idx(i, 0), idx(i, 0)] += bb
+        rhs[idx(i, nz - 1)] += bt * (PHYSICS["p_top"] + 1.0)
+        rhs[idx(i, 0)] += bb * (PHYSICS["p_bottom"] + 0.0)
+    phi = np.linalg.solve(A, rhs).reshape(nz, nx)
+    z = (np.arange(nz) + 0.5) * h
+    return phi - z[:, None]
+
+
+@pytest.mark.parametrize("shape", [(8, 8), (8, 12), (16, 16)])
+def test_saturated_limit_dense_direct_solve(shape):
+    """8x8 (and two other shapes): heterogeneous saturated limit equals a dense
+    direct solve of the hydraulic-head system built from an incidence matrix."""
+    nz, nx = shape
+    rng = np.random.default_rng(7)
+    lnks = rng.normal(size=(nz, nx))
+    p, q, rc, st = O.solve_one(problem(nsteps=1), lnks, np.zeros((nz, nx)))
+    assert rc == 0
+    assert np.abs(p - hydraulic_head_dense_solve(lnks)).max() < 1e-9
+
+
+# ------------------------------------------------------------ multigrid
+@pytest.mark.parametrize("n", [8, 32, 64])
+def test_mg_poisson_matches_dense_and_contracts(n):
+    """Poisson special case (Ks = 1, alpha = 0, C = 0): CCMG converges to the
+    dense solution; the residual decreases monotonically."""
+    rng = np.random.default_rng(11)
+    lnks = np.zeros((n, n))
+    pb = problem()
+    Tx, Tz, Tbt, Tbb, Cdt, f0 = O.picard_system(pb, lnks, np.zeros((n, n)), np.full((n, n), -1.0),
+                                                np.full((n, n), -1.0))
+    f = rng.normal(size=(n, n))
+    dp, cyc, rc, hist = O.mg_solve(Tx, Tz, Tbt, Tbb, Cdt, f, tol=1e-13, maxit=200)
+    assert rc == 0
+    assert np.all(np.diff(hist) < 0)
+    rho = (hist[-1] / hist[0]) ** (1.0 / cyc)
+    assert rho < 0.5, rho
+    # dense reference: same operator from the incidence-matrix construction,
+    # with Dirichlet data zero (phi_D = 0 means p_D = -z_D) -- use linearity:
+    # A dp = f for the head correction.
+    h = 1.0 / n
+    A = np.zeros((n * n, n * n))
+    for j in range(n):
+        for i in range(n):
+            P = j * n + i
+            for (a, b, t) in ((i + 1, j, 1 / h ** 2), (i - 1, j, 1 / h ** 2),
+                              (i, j + 1, 1 / h ** 2), (i, j - 1, 1 / h ** 2)):
+                if 0 <= a < n and 0 <= b < n:
+                    A[P, P] += t
+                    A[P, b * n + a] -= t
+                elif 0 <= a < n:      # beyond top/bottom: Dirichlet at h/2
+                    A[P, P] += 2 / h ** 2
+    ref = np.linalg.solve(A, f.reshape(-1)).reshape(n, n)
+    assert np.abs(dp - ref).max() < 1e-10 * np.abs(ref).max()
+
+
+# ------------------------------------------------------------ nonlinear pins
+def _mms(M):
+    import sympy as sp
+    x, z = sp.symbols("x z")
+    p_bot, p_top, A = PHYSICS["p_bottom"], PHYSICS["p_top"], 0.5
+    pstar = p_bot + (p_top - p_bot) * z + A * sp.sin(sp.pi * z) * sp.cos(sp.pi * x)
+    lnks = 0.4 * sp.cos(sp.pi * x) * sp.sin(sp.pi * z) + 0.2 * z
+    al = 1.0 + 0.3 * sp.sin(sp.pi * x) * sp.cos(sp.pi * z)
+    K = sp.exp(lnks) * sp.exp(al * pstar)
+    qx = -K * sp.diff(pstar, x)
+    qz = -K * (sp.diff(pstar, z) + 1)
+    src = sp.diff(qx, x) + sp.diff(qz, z)       # steady: div q = f
+    fn = {k: sp.lambdify((x, z), e, "numpy") for k, e in
+          dict(p=pstar, lnks=lnks, al=al, src=src).items()}
+    c = (np.arange(M) + 0.5) / M
+    X, Z = np.meshgrid(c, c)
+    return {k: np.broadcast_to(f(X, Z), X.shape).astype(np.float64) for k, f in fn.items()}
+
+
+@pytest.mark.slow
+def test_mms_second_order():
+    """Manufactured steady solution p* with smooth Ks, alpha and the source
+    f = -div(K(p*)(grad p* + e_z)): the discrete error is O(h^2)."""
+    errs = []
+    Ms = [16, 32, 64, 128]
+    for M in Ms:
+        d = _mms(M)
+        pb = problem(nsteps=1, dt=1e10, picard_maxit=200)
+        p, q, rc, st = O.solve_one(pb, d["lnks"], d["al"], src=d["src"], p_init=d["p"])
+        assert rc == 0
+        errs.append(np.abs(p - d["p"]).max())
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(orders > 1.85), (errs, orders)
+
+
+def test_mass_balance_per_step():
+    """Mixed form conserves mass (Sec. 4.1): over one step the change of stored
+    water equals dt times the net boundary inflow at t^{n+1}, up to the Picard
+    residual; interior fluxes cancel in pairs."""
+    n = 32
+    lnks, alpha = O.sample_fields(n, n, 1, seed=3)
+    lnks, alpha = lnks[0], alpha[0]
+    pb = problem(nsteps=1, dt=0.01)
+    h = 1.0 / n
+    tr, ts = PHYSICS["theta_r"], PHYSICS["theta_s"]
+
+    def water(p):
+        E = np.where(p < 0, np.exp(alpha * np.minimum(p, 0)), 1.0)
+        return h * h * np.sum(tr + (ts - tr) * E)
+
+    def outflow(p):
+        Ks = np.exp(lnks)
+        kt = Ks[-1] * np.exp(alpha[-1] * min(PHYSICS["p_top"], 0))
+        kb = Ks[0] * np.exp(alpha[0] * min(PHYSICS["p_bottom"], 0))
+        q_top = -kt * ((PHYSICS["p_top"] - p[-1]) / (h / 2) + 1)      # outward +z
+        q_bot = kb * ((p[0] - PHYSICS["p_bottom"]) / (h / 2) + 1)      # outward -z
+        return h * (q_top.sum() + q_bot.sum())
+
+    p = np.full((n, n), PHYSICS["p_init"])
+    for step in range(4):
+        p1, q, rc, st = O.solve_one(pb, lnks, alpha, p_init=p)
+        if rc != 0:
+            pytest.skip("sample did not converge")
+        dW = water(p1) - water(p)
+        flux = pb.dt * outflow(p1)
+        scale = pb.dt * h * np.abs(np.exp(lnks[-1])).sum()
+        assert abs(dW + flux) < 1e-6 * scale, (step, dW, flux)
+        p = p1
+
+
+def test_failure_statuses():
+    n = 16
+    lnks, alpha = O.sample_fields(n, n, 1, seed=0)
+    p, q, rc, _ = O.solve_one(problem(picard_maxit=1), lnks[0], alpha[0])
+    assert rc == O.PICARD_MAXIT and np.isnan(q)
+    bad = lnks[0].copy()
+    bad[3, 4] = np.nan
+    p, q, rc, _ = O.solve_one(problem(), bad, alpha[0])
+    assert rc == O.NONFINITE
+    with pytest.raises(ValueError):
+        O.solve_one(problem(), np.zeros((9, 9)), np.zeros((9, 9)))
+
+
+# ------------------------------------------------------------------- MLMC
+def test_optimal_sample_allocation_is_the_constrained_minimum():
+    """Eq. MLMCSAMP_ch6 is the Lagrange minimiser of sum N_l W_l subject to
+    sum V_l / N_l = eps^2 (Eq. MLMCopt_ch6): it meets the constraint, its cost
+    is eps^-2 (sum sqrt(V W))^2, and random feasible reallocations cost more."""
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        L = rng.integers(2, 6)
+        V = rng.uniform(1e-4, 1.0, L)
+        W = rng.uniform(1e-3, 10.0, L)
+        eps = 10 ** rng.uniform(-3, -1)
+        levels = [O.LevelStats(10, 0.0, v, w) for v, w in zip(V, W)]
+        n_opt, cost = O.optimal_samples(levels, eps)
+        n_opt = np.array(n_opt)
+        assert abs(np.sum(V / n_opt) - eps ** 2) < 1e-12 * eps ** 2
+        assert abs(np.sum(n_opt * W) - cost) < 1e-9 * cost
+        for _ in range(50):
+            n_try = n_opt * np.exp(rng.normal(scale=0.3, size=L))
+            n_try *= np.sum(V / n_try) / eps ** 2        # rescale onto the constraint
+            assert np.sum(n_try * W) >= cost * (1 - 1e-12)
+
+
+def test_mlmc_combine_telescopes():
+    rng = np.random.default_rng(2)
+    ys = [rng.normal(loc=m, scale=s, size=n) for m, s, n in ((1.0, 1.0, 400), (0.1, 0.2, 100))]
+    levels = [O.level_stats(y, 1.0) for y in ys]
+    est, rmse = O.mlmc_combine(levels)
+    assert abs(est - (ys[0].mean() + ys[1].mean())) < 1e-14
+    assert abs(rmse ** 2 - (ys[0].var(ddof=1) / 400 + ys[1].var(ddof=1) / 100)) < 1e-14
