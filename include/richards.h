@@ -1,0 +1,122 @@
+/*
+ * librichards -- batched Monte Carlo solves of the stochastic Richards'
+ * equation on one GB300 GPU (sm_103a), following
+ *   P. Kumar, C. Rodrigo, F. J. Gaspar, C. W. Oosterlee, "A parametric
+ *   acceleration of multilevel Monte Carlo convergence for nonlinear
+ *   variably saturated flow", arXiv 1903.08741.
+ *
+ * C ABI: plain pointers and sizes only.  Unless stated otherwise every array
+ * argument is DEVICE memory owned by the caller (the library never frees it),
+ * laid out row-major [sample][nz][nx] with x fastest and row z = 0 at the
+ * bottom of the unit-height domain; the mesh width is h = 1/nz (Eq. Grid_fine).
+ *
+ * Return codes: 0 = OK; < 0 = fatal error of the call (nothing is guaranteed
+ * about the outputs); > 0 = the call completed and the value is the worst
+ * per-sample status (RICH_PICARD_MAXIT, RICH_MG_MAXIT, RICH_NONFINITE), with
+ * the per-sample details in the status array.  No C++ exception crosses the
+ * ABI.  Streams are cudaStream_t passed as void* (NULL = legacy default).
+ */
+#ifndef RICHARDS_H
+#define RICHARDS_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    RICH_OK = 0,
+    RICH_PICARD_MAXIT = 1, /* a time step needed more Picard iterations than allowed (Sec. 4.3) */
+    RICH_MG_MAXIT = 2,     /* an MG solve stopped at mg_maxit cycles above tolerance           */
+    RICH_NONFINITE = 3,    /* NaN/Inf met in a residual or correction                          */
+    RICH_ERR_INVALID = -1, /* bad argument: sizes, pointers, unsupported grid                  */
+    RICH_ERR_CUDA = -2,    /* a CUDA runtime call failed                                       */
+    RICH_ERR_OOM = -3      /* device workspace could not be allocated                          */
+};
+
+enum { RICH_FP64 = 0, RICH_MIXED = 1 };
+
+typedef struct rich_ctx* rich_ctx_t;
+
+/* Physics and solver settings of one batch (Gardner closure, Sec. 2 with the
+ * configured closure; Picard, Sec. 4.1; CCMG, Sec. 4.2). */
+typedef struct {
+    int32_t nx, nz;          /* cells per side; must coarsen by 2 to <= 64 cells  */
+    int32_t nsteps;          /* implicit-Euler steps (Eq. Mixed_based)            */
+    double dt;
+    double theta_r, theta_s; /* residual / saturated water content                */
+    double p_top, p_bottom;  /* Dirichlet heads on the top and bottom faces       */
+    double p_init;           /* uniform initial head                              */
+    double picard_tol;       /* stop when ||dp||_inf < picard_tol (Sec. 4.1)      */
+    int32_t picard_maxit;    /* failure beyond this many iterations in a step     */
+    double mg_tol;           /* stop when ||f - A dp||_inf < mg_tol*max(1,||f||)  */
+    int32_t mg_maxit;
+    int32_t nu1, nu2;        /* red-black Gauss-Seidel steps before / after       */
+    int32_t precision;       /* RICH_FP64, or RICH_MIXED: FP32 V-cycles inside an
+                                FP64 defect-correction loop                       */
+} rich_problem_t;
+
+/* Random-field model: ln Ks Gaussian, exponential covariance sigma2*exp(-r/corr_len),
+ * drawn by FFT moving average (Appendix A, Eqs. convol1-product2); alpha =
+ * alpha_lo + alpha_span * Phi(g) with g an independent unit-variance field of the
+ * same correlation (the marginal transform Y = F_Y^-1(F_Z(Z)) of Sec. 3.1). */
+typedef struct {
+    double sigma2, corr_len;
+    double alpha_lo, alpha_span;
+    uint64_t seed;
+} rich_field_t;
+
+/* Host-side counters of a solve (summed over samples). */
+typedef struct {
+    int64_t picard_iters;    /* sum over samples and steps                        */
+    int64_t mg_cycles;       /* sum over samples of V-cycles                      */
+    int64_t cell_vcycles;    /* sum of V-cycles x fine cells                      */
+    int32_t max_picard;      /* largest Picard count of one step of one sample    */
+    int32_t failed;          /* samples with status PICARD_MAXIT or NONFINITE     */
+    double seconds;          /* wall time of the call                             */
+} rich_stats_t;
+
+/* Create a context on CUDA device `device`.  The context owns its device
+ * workspaces (grown on demand) and is not thread-safe. */
+int rich_create(rich_ctx_t* out, int device);
+void rich_destroy(rich_ctx_t ctx);
+const char* rich_status_str(int code);
+/* Text of the last fatal error seen by the calling thread (never NULL). */
+const char* rich_last_error(void);
+
+/* Draw ln Ks and alpha for samples first_sample .. first_sample+nsamples-1 of
+ * MLMC level `level` on an nx x nz grid, then average them over 2x2 blocks
+ * coarsen_times times.  Outputs lnKs, alpha: device [nsamples][nz>>c][nx>>c].
+ * White noise: Philox4x32-10 keyed by (seed, level), counter (cell pair,
+ * field, sample) with Box-Muller; FFT-MA on the smallest power-of-two torus of
+ * at least twice the grid whose circulant spectrum is non-negative
+ * (Appendix A).  Asynchronous on `stream`.  nx, nz must be powers of two. */
+int rich_sample_fields(rich_ctx_t ctx, const rich_field_t* field, int32_t nx, int32_t nz,
+                       uint32_t level, int64_t first_sample, int32_t nsamples,
+                       int32_t coarsen_times, double* lnKs, double* alpha, void* stream);
+
+/* Solve nsamples independent problems (Sec. 4: backward Euler, modified
+ * Picard, CCMG V(nu1,nu2) with red-black GS, harmonic-mean faces, piecewise-
+ * constant transfers, rediscretised coarse operators).  Inputs lnKs, alpha
+ * [S][nz][nx]; the nonlinearity used is alpha * alpha_scale (the parametric
+ * continuation of Sec. 5).  Outputs: qoi[S] = mean outward Darcy flux through
+ * the bottom faces at t = nsteps*dt (NaN for failed samples); p_final
+ * [S][nz][nx] or NULL; status[S].  stats (HOST) may be NULL.  The call returns
+ * once the batch is solved (the host reads convergence counters on `stream`). */
+int rich_solve_batch(rich_ctx_t ctx, const rich_problem_t* pb, int32_t nsamples,
+                     const double* lnKs, const double* alpha, double alpha_scale,
+                     double* qoi, double* p_final, int32_t* status, rich_stats_t* stats,
+                     void* stream);
+
+/* As rich_solve_batch, but lnKs, alpha, qoi, p_final and status are HOST
+ * arrays: the library copies inputs to its workspace and results back (the
+ * end-to-end path of a caller that holds no device memory). */
+int rich_solve_batch_host(rich_ctx_t ctx, const rich_problem_t* pb, int32_t nsamples,
+                          const double* lnKs, const double* alpha, double alpha_scale,
+                          double* qoi, double* p_final, int32_t* status, rich_stats_t* stats,
+                          void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,214 @@
+"""Python binding of librichards: batched stochastic Richards' solves on one GB300.
+
+Thin ctypes marshalling over the C ABI declared in ``include/richards.h``:
+torch tensors provide device memory and the current CUDA stream; every step of
+the computation runs in the library's CUDA kernels.  There is no CPU fallback:
+importing the binding without a built ``librichards.so`` raises, and so does
+calling it without a CUDA device.
+
+Entry points (same names as the C ABI): ``sample_fields``, ``solve_batch``,
+``solve_batch_host``, ``mlmc_estimate``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field, fields as dc_fields
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "librichards.so")
+
+OK, PICARD_MAXIT, MG_MAXIT, NONFINITE = 0, 1, 2, 3
+FP64, MIXED = 0, 1
+
+
+class RichError(RuntimeError):
+    pass
+
+
+class _Problem(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("nz", C.c_int32), ("nsteps", C.c_int32), ("dt", C.c_double),
+                ("theta_r", C.c_double), ("theta_s", C.c_double), ("p_top", C.c_double),
+                ("p_bottom", C.c_double), ("p_init", C.c_double), ("picard_tol", C.c_double),
+                ("picard_maxit", C.c_int32), ("mg_tol", C.c_double), ("mg_maxit", C.c_int32),
+                ("nu1", C.c_int32), ("nu2", C.c_int32), ("precision", C.c_int32)]
+
+
+class _Field(C.Structure):
+    _fields_ = [("sigma2", C.c_double), ("corr_len", C.c_double), ("alpha_lo", C.c_double),
+                ("alpha_span", C.c_double), ("seed", C.c_uint64)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [("picard_iters", C.c_int64), ("mg_cycles", C.c_int64), ("cell_vcycles", C.c_int64),
+                ("max_picard", C.c_int32), ("failed", C.c_int32), ("seconds", C.c_double)]
+
+
+@dataclass
+class Problem:
+    """Physics and solver settings (Gardner closure; Picard Sec. 4.1; CCMG Sec. 4.2)."""
+    nx: int = 32
+    nz: int = 32
+    nsteps: int = 10
+    dt: float = 0.01
+    theta_r: float = 0.1
+    theta_s: float = 0.5
+    p_top: float = -0.5
+    p_bottom: float = -5.0
+    p_init: float = -5.0
+    picard_tol: float = 1e-8
+    picard_maxit: int = 50
+    mg_tol: float = 1e-10
+    mg_maxit: int = 100
+    nu1: int = 2
+    nu2: int = 2
+    precision: int = FP64
+
+    def _c(self):
+        return _Problem(*[getattr(self, f.name) for f in dc_fields(self)])
+
+
+@dataclass
+class FieldModel:
+    """ln Ks ~ GRF(0, sigma2 exp(-r/corr_len)); alpha = alpha_lo + alpha_span Phi(g)."""
+    sigma2: float = 1.0
+    corr_len: float = 0.3
+    alpha_lo: float = 0.5
+    alpha_span: float = 1.5
+    seed: int = 0
+
+    def _c(self):
+        return _Field(self.sigma2, self.corr_len, self.alpha_lo, self.alpha_span, self.seed)
+
+
+@dataclass
+class Stats:
+    picard_iters: int = 0
+    mg_cycles: int = 0
+    cell_vcycles: int = 0
+    max_picard: int = 0
+    failed: int = 0
+    seconds: float = 0.0
+
+
+_lib = None
+
+
+def lib():
+    """Load librichards.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RichError(f"librichards.so not built ({LIB_PATH}); run paper_1903_08741_gb300/build.py")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, u32, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_double
+        L.rich_create.argtypes = [C.POINTER(vp), C.c_int]
+        L.rich_destroy.argtypes = [vp]
+        L.rich_status_str.argtypes = [C.c_int]
+        L.rich_status_str.restype = C.c_char_p
+        L.rich_last_error.restype = C.c_char_p
+        L.rich_sample_fields.argtypes = [vp, C.POINTER(_Field), i32, i32, u32, i64, i32, i32, vp, vp, vp]
+        L.rich_solve_batch.argtypes = [vp, C.POINTER(_Problem), i32, vp, vp, dbl, vp, vp, vp,
+                                       C.POINTER(_Stats), vp]
+        L.rich_solve_batch_host.argtypes = L.rich_solve_batch.argtypes
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return ["rich_create", "rich_destroy", "rich_status_str", "rich_last_error",
+            "rich_sample_fields", "rich_solve_batch", "rich_solve_batch_host"]
+
+
+def _check(rc):
+    if rc < 0:
+        raise RichError(f"{lib().rich_status_str(rc).decode()}: {lib().rich_last_error().decode()}")
+    return rc
+
+
+_ctx = {}
+
+
+def context(device: int = 0):
+    """The library context of a CUDA device (created once per process)."""
+    if device not in _ctx:
+        h = C.c_void_p()
+        _check(lib().rich_create(C.byref(h), device))
+        _ctx[device] = h
+    return _ctx[device]
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RichError("librichards needs a CUDA device")
+    return torch
+
+
+def _stream(torch, device):
+    return C.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _dev_ptr(t, dtype, name):
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise RichError(f"{name} must be a contiguous CUDA tensor of {dtype}")
+    return C.c_void_p(t.data_ptr())
+
+
+def sample_fields(nx, nz, nsamples, model: FieldModel | None = None, level=0, first_sample=0,
+                  coarsen_times=0, device=0, out=None):
+    """Draw (ln Ks, alpha) on device: [nsamples, nz >> c, nx >> c] float64 each."""
+    torch = _torch()
+    model = model or FieldModel()
+    shape = (nsamples, nz >> coarsen_times, nx >> coarsen_times)
+    if out is None:
+        out = (torch.empty(shape, dtype=torch.float64, device=f"cuda:{device}"),
+               torch.empty(shape, dtype=torch.float64, device=f"cuda:{device}"))
+    lk, al = out
+    _check(lib().rich_sample_fields(context(device), C.byref(model._c()), nx, nz, level, first_sample,
+                                    nsamples, coarsen_times, _dev_ptr(lk, torch.float64, "lnKs"),
+                                    _dev_ptr(al, torch.float64, "alpha"), _stream(torch, device)))
+    return lk, al
+
+
+def solve_batch(problem: Problem, lnKs, alpha, alpha_scale=1.0, want_p=False, device=None):
+    """Solve every sample of lnKs/alpha ([S, nz, nx] float64 CUDA tensors).
+
+    Returns (qoi [S], p_final [S, nz, nx] or None, status [S] int32, Stats, rc)."""
+    torch = _torch()
+    device = lnKs.device.index if device is None else device
+    S = lnKs.shape[0]
+    if tuple(lnKs.shape) != (S, problem.nz, problem.nx) or alpha.shape != lnKs.shape:
+        raise RichError("lnKs/alpha must be [S, nz, nx]")
+    qoi = torch.empty(S, dtype=torch.float64, device=lnKs.device)
+    status = torch.empty(S, dtype=torch.int32, device=lnKs.device)
+    p = torch.empty_like(lnKs) if want_p else None
+    st = _Stats()
+    rc = _check(lib().rich_solve_batch(context(device), C.byref(problem._c()), S,
+                                       _dev_ptr(lnKs, torch.float64, "lnKs"),
+                                       _dev_ptr(alpha, torch.float64, "alpha"), alpha_scale,
+                                       _dev_ptr(qoi, torch.float64, "qoi"),
+                                       None if p is None else _dev_ptr(p, torch.float64, "p"),
+                                       _dev_ptr(status, torch.int32, "status"), C.byref(st),
+                                       _stream(torch, device)))
+    return qoi, p, status, Stats(*[getattr(st, f) for f, _ in _Stats._fields_]), rc
+
+
+def solve_batch_host(problem: Problem, lnKs: np.ndarray, alpha: np.ndarray, alpha_scale=1.0,
+                     want_p=False, device=0):
+    """As solve_batch with host (numpy) inputs and outputs; the library moves the data."""
+    torch = _torch()
+    lnKs = np.ascontiguousarray(lnKs, np.float64)
+    alpha = np.ascontiguousarray(alpha, np.float64)
+    S = lnKs.shape[0]
+    qoi = np.empty(S, np.float64)
+    status = np.empty(S, np.int32)
+    p = np.empty_like(lnKs) if want_p else None
+    st = _Stats()
+    ptr = lambda a: None if a is None else C.c_void_p(a.ctypes.data)
+    rc = _check(lib().rich_solve_batch_host(context(device), C.byref(problem._c()), S, ptr(lnKs),
+                                            ptr(alpha), alpha_scale, ptr(qoi), ptr(p), ptr(status),
+                                            C.byref(st), _stream(torch, device)))
+    return qoi, p, status, Stats(*[getattr(st, f) for f, _ in _Stats._fields_]), rc

@@ -1,0 +1,117 @@
+// C-ABI entry points of librichards (declared in include/richards.h).
+#include "rich_internal.cuh"
+#include <stdio.h>
+#include <string.h>
+#include <new>
+
+static thread_local char g_err[512] = "";
+
+void rich_set_error(const char* msg, const char* file, int line) {
+    snprintf(g_err, sizeof(g_err), "%s (%s:%d)", msg, file, line);
+}
+
+extern "C" const char* rich_last_error(void) { return g_err; }
+
+extern "C" const char* rich_status_str(int code) {
+    switch (code) {
+        case RICH_OK: return "ok";
+        case RICH_PICARD_MAXIT: return "picard iteration limit reached";
+        case RICH_MG_MAXIT: return "multigrid cycle limit reached";
+        case RICH_NONFINITE: return "non-finite residual or correction";
+        case RICH_ERR_INVALID: return "invalid argument";
+        case RICH_ERR_CUDA: return "CUDA error";
+        case RICH_ERR_OOM: return "out of device memory";
+        default: return "unknown status";
+    }
+}
+
+extern "C" int rich_create(rich_ctx_t* out, int device) {
+    if (!out) return RICH_ERR_INVALID;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        rich_set_error("no such CUDA device", __FILE__, __LINE__);
+        return RICH_ERR_CUDA;
+    }
+    RICH_CUDA(cudaSetDevice(device));
+    rich_ctx* c = new (std::nothrow) rich_ctx();
+    if (!c) return RICH_ERR_OOM;
+    c->device = device;
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    *out = c;
+    return 0;
+}
+
+extern "C" void rich_destroy(rich_ctx_t ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->ws.base) cudaFree(ctx->ws.base);
+    if (ctx->ws.h_counters) cudaFreeHost(ctx->ws.h_counters);
+    if (ctx->fws.sqrt_lambda) cudaFree(ctx->fws.sqrt_lambda);
+    if (ctx->fws.work) cudaFree(ctx->fws.work);
+    if (ctx->fws.tw) cudaFree(ctx->fws.tw);
+    delete ctx;
+}
+
+static int check_problem(const rich_problem_t* pb) {
+    if (!pb || pb->nx < 1 || pb->nz < 1 || pb->nsteps < 0 || !(pb->dt > 0) ||
+        pb->picard_maxit < 1 || pb->mg_maxit < 1 || pb->nu1 < 0 || pb->nu2 < 0 ||
+        (pb->precision != RICH_FP64 && pb->precision != RICH_MIXED) || !(pb->picard_tol > 0) ||
+        !(pb->mg_tol > 0))
+        return RICH_ERR_INVALID;
+    if (rich_count_levels(pb->nx, pb->nz) < 1) return RICH_ERR_INVALID;
+    return 0;
+}
+
+extern "C" int rich_sample_fields(rich_ctx_t ctx, const rich_field_t* field, int32_t nx,
+                                  int32_t nz, uint32_t level, int64_t first_sample,
+                                  int32_t nsamples, int32_t coarsen_times, double* lnKs,
+                                  double* alpha, void* stream) {
+    if (!ctx || !field || nsamples < 0 || first_sample < 0) return RICH_ERR_INVALID;
+    if (nsamples > 0 && (!lnKs || !alpha)) return RICH_ERR_INVALID;
+    RICH_CUDA(cudaSetDevice(ctx->device));
+    return rich_fields_device(ctx, field, nx, nz, level, first_sample, nsamples, coarsen_times,
+                              lnKs, alpha, (cudaStream_t)stream);
+}
+
+extern "C" int rich_solve_batch(rich_ctx_t ctx, const rich_problem_t* pb, int32_t nsamples,
+                                const double* lnKs, const double* alpha, double alpha_scale,
+                                double* qoi, double* p_final, int32_t* status,
+                                rich_stats_t* stats, void* stream) {
+    if (!ctx || check_problem(pb) || nsamples < 0) return RICH_ERR_INVALID;
+    if (nsamples == 0) { if (stats) *stats = rich_stats_t{}; return 0; }
+    if (!lnKs || !alpha || !qoi) return RICH_ERR_INVALID;
+    RICH_CUDA(cudaSetDevice(ctx->device));
+    return rich_solve_device(ctx, pb, nsamples, lnKs, alpha, alpha_scale, qoi, p_final, status,
+                             stats, (cudaStream_t)stream);
+}
+
+extern "C" int rich_solve_batch_host(rich_ctx_t ctx, const rich_problem_t* pb, int32_t nsamples,
+                                     const double* lnKs, const double* alpha, double alpha_scale,
+                                     double* qoi, double* p_final, int32_t* status,
+                                     rich_stats_t* stats, void* stream) {
+    if (!ctx || check_problem(pb) || nsamples < 0) return RICH_ERR_INVALID;
+    if (nsamples == 0) { if (stats) *stats = rich_stats_t{}; return 0; }
+    if (!lnKs || !alpha || !qoi) return RICH_ERR_INVALID;
+    RICH_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    int e = rich_ws_reserve(ctx, nsamples, pb->nx, pb->nz, pb->precision == RICH_MIXED);
+    if (e) return e;
+    const size_t nc = (size_t)nsamples * pb->nx * pb->nz;
+    double* d_lk = ctx->ws.h_in;
+    double* d_al = d_lk + nc;
+    double* d_p = d_al + nc;
+    double* d_q = d_p + nc;
+    int32_t* d_st = (int32_t*)(d_q + nsamples);
+    RICH_CUDA(cudaMemcpyAsync(d_lk, lnKs, nc * 8, cudaMemcpyHostToDevice, st));
+    RICH_CUDA(cudaMemcpyAsync(d_al, alpha, nc * 8, cudaMemcpyHostToDevice, st));
+    int rc = rich_solve_device(ctx, pb, nsamples, d_lk, d_al, alpha_scale, d_q,
+                               p_final ? d_p : nullptr, d_st, stats, st);
+    if (rc < 0) return rc;
+    RICH_CUDA(cudaMemcpyAsync(qoi, d_q, (size_t)nsamples * 8, cudaMemcpyDeviceToHost, st));
+    if (status) RICH_CUDA(cudaMemcpyAsync(status, d_st, (size_t)nsamples * 4, cudaMemcpyDeviceToHost, st));
+    if (p_final) RICH_CUDA(cudaMemcpyAsync(p_final, d_p, nc * 8, cudaMemcpyDeviceToHost, st));
+    RICH_CUDA(cudaStreamSynchronize(st));
+    return rc;
+}

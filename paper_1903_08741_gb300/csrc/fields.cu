@@ -1,0 +1,303 @@
+// Random soil fields by FFT moving average (arXiv 1903.08741, Appendix A):
+// white noise y on a periodic px x pz torus, z = F^-1( sqrt(F c) . F y ), keep
+// the physical window, then ln Ks = z_0 and alpha = lo + span * Phi(z_1 / sigma).
+//
+// GPU design: the two real fields of a sample are packed into one complex
+// transform (re = y_0, im = y_1); sqrt(F c) is real and even, so the filter maps
+// real inputs to real outputs and the two fields come back in re / im.  The 2-D
+// FFT is two passes of batched 1-D radix-2 transforms in shared memory (rows,
+// then groups of adjacent columns so that global accesses stay coalesced).
+// White noise: Philox4x32-10 (Salmon et al., SC'11) implemented from its
+// definition, key = (seed low word, seed high word ^ level), counter = (cell
+// pair, field, sample low, sample high), two uniforms -> Box-Muller.
+#include "rich_internal.cuh"
+#include <math.h>
+#include <vector>
+#include <algorithm>
+
+namespace {
+
+struct cplx { double re, im; };
+
+__device__ __forceinline__ void philox10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
+        uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    }
+}
+
+__device__ __forceinline__ double u01(uint32_t hi, uint32_t lo) {
+    unsigned long long m = (((unsigned long long)hi << 32) | lo) >> 11;
+    return ((double)m + 0.5) * (1.0 / 9007199254740992.0);
+}
+
+// packed complex white noise: re = field 0, im = field 1, for samples
+// first..first+S-1 on the torus (npts = px*pz, even)
+__global__ void k_noise(int S, int npts, uint64_t seed, uint32_t level, int64_t first, cplx* out) {
+    long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;   // (sample, pair)
+    const int pairs = npts >> 1;
+    if (g >= (long long)S * pairs) return;
+    int s = (int)(g / pairs), q = (int)(g - (long long)s * pairs);
+    uint64_t sample = (uint64_t)(first + s);
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32) ^ level;
+    double y[2][2];
+#pragma unroll
+    for (int fld = 0; fld < 2; ++fld) {
+        uint32_t c[4] = {(uint32_t)q, (uint32_t)fld, (uint32_t)sample, (uint32_t)(sample >> 32)};
+        philox10(c, k0, k1);
+        double a = u01(c[0], c[1]), b = u01(c[2], c[3]);
+        double r = sqrt(-2.0 * log(a));
+        double sn, cs;
+        sincos(6.283185307179586476925286766559 * b, &sn, &cs);
+        y[fld][0] = r * cs; y[fld][1] = r * sn;
+    }
+    cplx* o = out + (size_t)s * npts + 2 * (size_t)q;
+    o[0] = cplx{y[0][0], y[1][0]};
+    o[1] = cplx{y[0][1], y[1][1]};
+}
+
+// twiddles w_k = exp(-2 pi i k / n), k < n/2
+__global__ void k_twiddles(int n, cplx* tw) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n / 2) return;
+    double s, c;
+    sincospi(-2.0 * (double)k / (double)n, &s, &c);
+    tw[k] = cplx{c, s};
+}
+
+// Batched radix-2 FFT of lines of length n (power of two) held in shared
+// memory.  A block handles LPB lines; line l of sample b starts at
+// b*sample_stride + l*line_stride, its elements are elem_stride apart.
+// Bit-reversed load, log2(n) butterfly stages, 1/n on the inverse.
+template <int LPB>
+__global__ void k_fft_lines(cplx* data, int n, int logn, int lines, long long sample_stride,
+                            int line_stride, int elem_stride, const cplx* __restrict__ tw,
+                            int inverse) {
+    // contiguous lines: consecutive threads take consecutive elements; strided
+    // lines (columns): consecutive threads take adjacent lines
+    const bool contig = elem_stride == 1;
+    extern __shared__ cplx sh[];
+    const int groups = lines / LPB;
+    const int b = blockIdx.x / groups, g = blockIdx.x - b * groups;
+    cplx* base = data + (size_t)b * sample_stride + (size_t)g * LPB * line_stride;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    // load: element e of line l -> shared [l][rev(e)]; consecutive threads read
+    // consecutive lines first so that column groups coalesce
+    for (int t = tid; t < n * LPB; t += nt) {
+        int l = contig ? t / n : t % LPB, e = contig ? t - (t / n) * n : t / LPB;
+        int r = logn ? (int)(__brev((unsigned)e) >> (32 - logn)) : 0;
+        sh[l * n + r] = base[(size_t)l * line_stride + (size_t)e * elem_stride];
+    }
+    __syncthreads();
+    const double sgn = inverse ? -1.0 : 1.0;
+    for (int m = 1, st = n >> 1; m < n; m <<= 1, st >>= 1) {
+        for (int t = tid; t < (n >> 1) * LPB; t += nt) {
+            int l = t / (n >> 1), bf = t - l * (n >> 1);
+            int grp = bf / m, k = bf - grp * m;
+            int a = grp * 2 * m + k, c = a + m;
+            cplx w = tw[k * st];
+            double wi = sgn * w.im;
+            cplx x = sh[l * n + c], y = sh[l * n + a];
+            double xr = x.re * w.re - x.im * wi;
+            double xi = x.re * wi + x.im * w.re;
+            sh[l * n + c] = cplx{y.re - xr, y.im - xi};
+            sh[l * n + a] = cplx{y.re + xr, y.im + xi};
+        }
+        __syncthreads();
+    }
+    const double sc = inverse ? 1.0 / (double)n : 1.0;
+    for (int t = tid; t < n * LPB; t += nt) {
+        int l = contig ? t / n : t % LPB, e = contig ? t - (t / n) * n : t / LPB;
+        cplx v = sh[l * n + e];
+        if (inverse) { v.re *= sc; v.im *= sc; }
+        base[(size_t)l * line_stride + (size_t)e * elem_stride] = v;
+    }
+}
+
+__global__ void k_filter(int S, int npts, const double* __restrict__ sq, cplx* d) {
+    long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= (long long)S * npts) return;
+    double w = sq[g % npts];
+    d[g].re *= w; d[g].im *= w;
+}
+
+// covariance on the torus: c(a, b) = sigma2 exp(-r / corr_len), periodic distances
+__global__ void k_cov(int px, int pz, double h, double sigma2, double corr_len, cplx* c) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= px * pz) return;
+    int b = g / px, a = g - b * px;
+    int ia = min(a, px - a), ib = min(b, pz - b);
+    double dx = ia * h, dz = ib * h;
+    c[g] = cplx{sigma2 * exp(-sqrt(dx * dx + dz * dz) / corr_len), 0.0};
+}
+
+__global__ void k_sqrt_spec(int npts, const cplx* __restrict__ lam, double* sq) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= npts) return;
+    double v = lam[g].re;
+    sq[g] = v > 0.0 ? sqrt(v) : 0.0;
+}
+
+// window of the torus -> ln Ks and alpha (Phi(x) = erfc(-x/sqrt 2)/2), in place
+// into a compact [S][nz][nx] pair of real arrays
+__global__ void k_window(int S, int nx, int nz, int px, int pz, const cplx* __restrict__ d,
+                         double inv_sigma, double alo, double aspan, double* lk, double* al) {
+    long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nc = nx * nz;
+    if (g >= (long long)S * nc) return;
+    int s = (int)(g / nc), q = (int)(g - (long long)s * nc);
+    int j = q / nx, i = q - j * nx;
+    cplx v = d[(size_t)s * px * pz + (size_t)j * px + i];
+    lk[g] = v.re;
+    double gg = v.im * inv_sigma;
+    al[g] = alo + aspan * 0.5 * erfc(-gg / sqrt(2.0));
+}
+
+// one 2x2 averaging step of both fields
+__global__ void k_avg2(int S, int nxc, int nzc, const double* __restrict__ lf,
+                       const double* __restrict__ af, double* lc, double* ac) {
+    long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nc = nxc * nzc, fx = 2 * nxc;
+    if (g >= (long long)S * nc) return;
+    int s = (int)(g / nc), q = (int)(g - (long long)s * nc);
+    int J = q / nxc, I = q - J * nxc;
+    size_t f00 = (size_t)s * 4 * nc + (size_t)(2 * J) * fx + 2 * I, f01 = f00 + fx;
+    lc[g] = 0.25 * (lf[f00] + lf[f00 + 1] + lf[f01] + lf[f01 + 1]);
+    ac[g] = 0.25 * (af[f00] + af[f00 + 1] + af[f01] + af[f01 + 1]);
+}
+
+inline unsigned nb(long long w, int t = 256) { return (unsigned)((w + t - 1) / t); }
+inline int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
+inline bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+template <int L>
+int fft_pass(cplx* d, int S, int n, int lines, long long sstride, int lstride, int estride,
+             const cplx* tw, int inverse, cudaStream_t st) {
+    size_t sm = (size_t)L * n * sizeof(cplx);
+    RICH_CUDA(cudaFuncSetAttribute(k_fft_lines<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_fft_lines<L><<<(unsigned)S * (lines / L), 256, sm, st>>>(d, n, ilog2(n), lines, sstride, lstride,
+                                                               estride, tw, inverse);
+    return 0;
+}
+
+// lines per block: the largest of 8, 4, 2, 1 that divides the line count and
+// keeps the block's lines within 128 KB of shared memory
+int fft_dispatch(cplx* d, int S, int n, int lines, long long sstride, int lstride, int estride,
+                 const cplx* tw, int inverse, cudaStream_t st) {
+    for (int L = 8; L >= 1; L >>= 1) {
+        if (lines % L || (size_t)L * n * sizeof(cplx) > (128u << 10)) continue;
+        switch (L) {
+            case 8: return fft_pass<8>(d, S, n, lines, sstride, lstride, estride, tw, inverse, st);
+            case 4: return fft_pass<4>(d, S, n, lines, sstride, lstride, estride, tw, inverse, st);
+            case 2: return fft_pass<2>(d, S, n, lines, sstride, lstride, estride, tw, inverse, st);
+            default: return fft_pass<1>(d, S, n, lines, sstride, lstride, estride, tw, inverse, st);
+        }
+    }
+    return RICH_ERR_INVALID;
+}
+
+int fft2(cplx* d, int S, int px, int pz, const cplx* twx, const cplx* twz, int inverse,
+         cudaStream_t st) {
+    const long long ss = (long long)px * pz;
+    if (int e = fft_dispatch(d, S, px, pz, ss, px, 1, twx, inverse, st)) return e;   // rows (x)
+    if (int e = fft_dispatch(d, S, pz, px, ss, 1, px, twz, inverse, st)) return e;   // columns (z)
+    RICH_CUDA(cudaGetLastError());
+    return 0;
+}
+
+}  // namespace
+
+// spectrum sqrt(F c) on the smallest valid torus, cached in the context
+static int ensure_spectrum(rich_ctx* ctx, int nx, int nz, double sigma2, double corr_len,
+                           cudaStream_t st) {
+    rich_field_ws& f = ctx->fws;
+    if (f.sqrt_lambda && f.nx == nx && f.nz == nz && f.sigma2 == sigma2 && f.corr_len == corr_len)
+        return 0;
+    if (f.sqrt_lambda) { cudaFree(f.sqrt_lambda); f.sqrt_lambda = nullptr; }
+    if (f.tw) { cudaFree(f.tw); f.tw = nullptr; }
+    if (f.work) { cudaFree(f.work); f.work = nullptr; }
+    const double h = 1.0 / nz;
+    int px = 1, pz = 1;
+    while (px < 2 * nx) px <<= 1;
+    while (pz < 2 * nz) pz <<= 1;
+    for (int tries = 0; tries < 4; ++tries) {
+        const int npts = px * pz;
+        cplx *c = nullptr, *tw = nullptr;
+        RICH_CUDA(cudaMalloc(&c, sizeof(cplx) * npts));
+        RICH_CUDA(cudaMalloc(&tw, sizeof(cplx) * (px / 2 + pz / 2 + 2)));
+        k_twiddles<<<nb(px / 2), 256, 0, st>>>(px, tw);
+        k_twiddles<<<nb(pz / 2), 256, 0, st>>>(pz, tw + px / 2 + 1);
+        k_cov<<<nb(npts), 256, 0, st>>>(px, pz, h, sigma2, corr_len, c);
+        if (int e = fft2(c, 1, px, pz, tw, tw + px / 2 + 1, 0, st)) return e;
+        std::vector<cplx> hl(npts);
+        RICH_CUDA(cudaMemcpyAsync(hl.data(), c, sizeof(cplx) * npts, cudaMemcpyDeviceToHost, st));
+        RICH_CUDA(cudaStreamSynchronize(st));
+        double lmin = hl[0].re, lmax = hl[0].re;
+        for (auto& v : hl) { lmin = std::min(lmin, v.re); lmax = std::max(lmax, v.re); }
+        bool ok = lmin / lmax >= -1e-12;
+        if (ok || tries == 3) {
+            RICH_CUDA(cudaMalloc(&f.sqrt_lambda, sizeof(double) * npts));
+            k_sqrt_spec<<<nb(npts), 256, 0, st>>>(npts, c, f.sqrt_lambda);
+            RICH_CUDA(cudaStreamSynchronize(st));
+            cudaFree(c);
+            f.tw = (double*)tw;
+            f.px = px; f.pz = pz; f.nx = nx; f.nz = nz; f.sigma2 = sigma2; f.corr_len = corr_len;
+            // work buffer: enough samples per chunk for ~512 MB
+            f.chunk = (int)std::max<long long>(1, (512ll << 20) / ((long long)npts * sizeof(cplx) + 32ll * nx * nz));
+            RICH_CUDA(cudaMalloc(&f.work, (sizeof(cplx) * npts + 32 * (size_t)nx * nz) * f.chunk));
+            return 0;
+        }
+        cudaFree(c); cudaFree(tw);
+        px *= 2; pz *= 2;
+    }
+    return RICH_ERR_INVALID;
+}
+
+int rich_fields_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int nz, uint32_t level,
+                       int64_t first, int S, int coarsen, double* lnKs, double* alpha,
+                       cudaStream_t st) {
+    if (!pow2(nx) || !pow2(nz) || coarsen < 0 || (nx >> coarsen) < 1 || (nz >> coarsen) < 1 ||
+        fd->sigma2 <= 0 || fd->corr_len <= 0)
+        return RICH_ERR_INVALID;
+    if (S == 0) return 0;
+    if (int e = ensure_spectrum(ctx, nx, nz, fd->sigma2, fd->corr_len, st)) return e;
+    rich_field_ws& f = ctx->fws;
+    const int px = f.px, pz = f.pz, npts = px * pz;
+    const cplx* twx = (const cplx*)f.tw;
+    const cplx* twz = twx + px / 2 + 1;
+    cplx* work = (cplx*)f.work;
+    double* tmp = (double*)(work + (size_t)npts * f.chunk);   // [chunk][4][nz][nx] real scratch
+    const int nxo = nx >> coarsen, nzo = nz >> coarsen;
+    const double inv_sigma = 1.0 / sqrt(fd->sigma2);
+    for (int s0 = 0; s0 < S; s0 += f.chunk) {
+        int cs = std::min(f.chunk, S - s0);
+        k_noise<<<nb((long long)cs * (npts / 2)), 256, 0, st>>>(cs, npts, fd->seed, level, first + s0, work);
+        if (int e = fft2(work, cs, px, pz, twx, twz, 0, st)) return e;
+        k_filter<<<nb((long long)cs * npts), 256, 0, st>>>(cs, npts, f.sqrt_lambda, work);
+        if (int e = fft2(work, cs, px, pz, twx, twz, 1, st)) return e;
+        // real scratch: two ping-pong pairs of [cs][nz][nx] arrays
+        const size_t blk = (size_t)cs * nx * nz;
+        double* bl[2] = {tmp, tmp + 2 * blk};
+        double* ba[2] = {tmp + blk, tmp + 3 * blk};
+        double* wl = coarsen ? bl[0] : lnKs + (size_t)s0 * nx * nz;
+        double* wa = coarsen ? ba[0] : alpha + (size_t)s0 * nx * nz;
+        k_window<<<nb((long long)cs * nx * nz), 256, 0, st>>>(cs, nx, nz, px, pz, work, inv_sigma,
+                                                            fd->alpha_lo, fd->alpha_span, wl, wa);
+        int cx = nx, cz = nz, cur = 0;
+        for (int c = 0; c < coarsen; ++c) {
+            int ncx = cx / 2, ncz = cz / 2;
+            bool last = c == coarsen - 1;
+            double* ol = last ? lnKs + (size_t)s0 * nxo * nzo : bl[1 - cur];
+            double* oa = last ? alpha + (size_t)s0 * nxo * nzo : ba[1 - cur];
+            k_avg2<<<nb((long long)cs * ncx * ncz), 256, 0, st>>>(cs, ncx, ncz, bl[cur], ba[cur], ol, oa);
+            cur = 1 - cur;
+            cx = ncx; cz = ncz;
+        }
+    }
+    RICH_CUDA(cudaGetLastError());
+    return 0;
+}

@@ -1,0 +1,71 @@
+// Internal declarations of librichards (CUDA path).  Not part of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+#include "../../include/richards.h"
+
+#define RICH_MAX_LEVELS 16
+
+#define RICH_CUDA(call)                                                     \
+    do {                                                                    \
+        cudaError_t e_ = (call);                                            \
+        if (e_ != cudaSuccess) { rich_set_error(cudaGetErrorString(e_), __FILE__, __LINE__); \
+                                 return RICH_ERR_CUDA; }                    \
+    } while (0)
+
+void rich_set_error(const char* msg, const char* file, int line);
+
+struct rich_level {
+    int nx, nz;
+    double *Tx, *Tz, *Cdt, *D, *invD, *f, *dp;   // [S][nz][nx]
+    double *Tbt, *Tbb;                           // [S][nx]
+    float *Tx32, *Tz32, *D32, *invD32, *f32, *dp32; // mixed-precision copies
+};
+
+// Device workspace of one batched solve, sized for S_cap samples of a grid.
+struct rich_ws {
+    int S_cap = 0, nx = 0, nz = 0, nlev = 0, mixed = 0;
+    rich_level lev[RICH_MAX_LEVELS];
+    double *p = nullptr, *thold = nullptr, *Ks = nullptr, *a = nullptr, *K = nullptr, *th = nullptr;
+    double *r = nullptr;                        // FP64 defect (mixed path)
+    int32_t *status = nullptr, *kpic = nullptr, *cyc = nullptr, *alive = nullptr;
+    int64_t *pic_total = nullptr, *mg_total = nullptr;
+    int32_t *maxpic = nullptr;
+    unsigned long long *nrm_f = nullptr, *nrm_r = nullptr, *nrm_dp = nullptr;
+    double* target = nullptr;
+    int32_t *list_pic = nullptr, *list_mg = nullptr, *list_tmp = nullptr;
+    int32_t* counters = nullptr;                // device [4]
+    int32_t* h_counters = nullptr;              // pinned host mirror [4]
+    double *h_in = nullptr;                     // staging for the host-buffer entry point
+    void* base = nullptr;                       // single allocation
+    size_t bytes = 0;
+};
+
+struct rich_field_ws {
+    int px = 0, pz = 0, nx = 0, nz = 0;
+    double sigma2 = -1, corr_len = -1;
+    double* sqrt_lambda = nullptr;              // [pz][px]
+    double* work = nullptr;                     // complex [chunk][pz][px][2]
+    double* tw = nullptr;                       // twiddles
+    int chunk = 0;
+};
+
+struct rich_ctx {
+    int device = 0;
+    int sm_count = 0;
+    rich_ws ws;
+    rich_field_ws fws;
+};
+
+// ---- solver (solver.cu)
+int rich_ws_reserve(rich_ctx* ctx, int S, int nx, int nz, int mixed);
+int rich_solve_device(rich_ctx* ctx, const rich_problem_t* pb, int S, const double* lnKs,
+                      const double* alpha, double alpha_scale, double* qoi, double* p_final,
+                      int32_t* status, rich_stats_t* stats, cudaStream_t st);
+int rich_count_levels(int nx, int nz);
+
+// ---- fields (fields.cu)
+int rich_fields_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int nz, uint32_t level,
+                       int64_t first, int S, int coarsen, double* lnKs, double* alpha,
+                       cudaStream_t st);

@@ -1,0 +1,62 @@
+"""The C-ABI library builds, loads and exports every function its header declares;
+the ctypes structures have the C layout.  No GPU needed."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_1903_08741_gb300 as R
+from paper_1903_08741_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    return B.build()
+
+
+def declared_functions():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**(rich_\w+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    names = declared_functions()
+    assert "rich_solve_batch" in names and "rich_sample_fields" in names
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (rich_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    L = C.CDLL(libpath)
+    for n in names:
+        assert hasattr(L, n)
+    assert sorted(R.exported_symbols()) == names
+
+
+def test_status_strings_without_gpu(libpath):
+    L = R.lib()
+    assert L.rich_status_str(0) == b"ok"
+    assert b"picard" in L.rich_status_str(1)
+    h = C.c_void_p()
+    assert L.rich_create(C.byref(h), 0) in (0, -2)   # -2 when no CUDA device is present
+
+
+def test_struct_layouts_match_c(tmp_path):
+    src = tmp_path / "sz.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "richards.h"\n'
+                   'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(rich_problem_t),'
+                   ' sizeof(rich_field_t), sizeof(rich_stats_t), offsetof(rich_problem_t, precision),'
+                   ' offsetof(rich_stats_t, seconds)); return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    vals = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    assert vals == [C.sizeof(R._Problem), C.sizeof(R._Field), C.sizeof(R._Stats),
+                    R._Problem.precision.offset, R._Stats.seconds.offset]

@@ -1,0 +1,191 @@
+"""GPU path vs the FP64 CPU oracle, element by element, through the C ABI.
+
+Inputs are identical seeded fields (drawn by the oracle and uploaded), so the
+comparison isolates the solver; the GPU field generator is compared with the
+oracle's separately.  Tolerances: 1e-10 relative on pressure head and QoI for
+the FP64 path, 1e-6 relative on the QoI for the FP32-in-FP64 mixed path, 1e-12
+on the fields; statuses must agree exactly.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from tests.inputs import PHYSICS, SOLVER
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+NTH = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module")
+def R():
+    import paper_1903_08741_gb300 as R
+    from paper_1903_08741_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+    return R
+
+
+def gpu_problem(R, nx, nz, nsteps, dt, **kw):
+    d = dict(PHYSICS)
+    d.update(SOLVER)
+    d.update(kw)
+    return R.Problem(nx=nx, nz=nz, nsteps=nsteps, dt=dt, **d)
+
+
+def orc_problem(nsteps, dt, **kw):
+    d = dict(PHYSICS)
+    d.update(SOLVER)
+    d.update(kw)
+    d.pop("precision", None)
+    return O.make_problem(nsteps=nsteps, dt=dt, **d)
+
+
+def compare(R, nx, nz, S, nsteps, dt, seed=0, alpha_scale=1.0, fields=None, rtol=1e-10,
+            exact_counts=True, **kw):
+    if fields is None:
+        lk, al = O.sample_fields(nx, nz, S, seed=seed) if (nx & (nx - 1)) == 0 and (nz & (nz - 1)) == 0 \
+            else _smooth(nx, nz, S, seed)
+    else:
+        lk, al = fields
+    p_o, q_o, s_o, st_o = O.solve_batch(orc_problem(nsteps, dt, **kw), lk, al, alpha_scale, nthreads=NTH)
+    dev = torch.device("cuda:0")
+    q, p, s, st, rc = R.solve_batch(gpu_problem(R, nx, nz, nsteps, dt, **kw),
+                                    torch.from_numpy(lk).to(dev), torch.from_numpy(al).to(dev),
+                                    alpha_scale, want_p=True)
+    q, p, s = q.cpu().numpy(), p.cpu().numpy(), s.cpu().numpy()
+    assert np.array_equal(s, s_o), (s, s_o)
+    ok = s_o == 0
+    assert np.all(np.isnan(q[~ok & (s_o != 2)]))
+    rel_q = np.abs(q[ok] - q_o[ok]) / np.maximum(np.abs(q_o[ok]), 1e-300)
+    rel_p = np.abs(p[ok] - p_o[ok]).max(initial=0) / np.abs(p_o[ok]).max(initial=1)
+    assert rel_q.max(initial=0) <= rtol, rel_q.max()
+    assert rel_p <= rtol, rel_p
+    # Stopping tests decided within a few ulps of their threshold can flip by one
+    # cycle between two rounding orders (FMA contraction, 1/D multiply, exp/log
+    # last-ulp differences); the values above are unaffected at 1e-10.
+    slack = 0 if exact_counts else 0.01
+    assert abs(st.picard_iters - st_o.picard_iters) <= max(1, slack * st_o.picard_iters)
+    assert abs(st.mg_cycles - st_o.mg_cycles) <= max(2, 0.005 * st_o.mg_cycles, slack * st_o.mg_cycles)
+    return q, q_o, s, st, st_o
+
+
+def _smooth(nx, nz, S, seed):
+    from tests.inputs import smooth_random_fields
+    return smooth_random_fields(nx, nz, S, seed)
+
+
+# ------------------------------------------------------------------ fields
+@pytest.mark.parametrize("nx,nz,c", [(16, 16, 0), (32, 32, 0), (32, 16, 0), (32, 32, 1), (64, 64, 2)])
+def test_fields_match_oracle(R, nx, nz, c):
+    S, first, level = 6, 3, 2
+    lk_o, al_o = O.sample_fields(nx, nz, S, seed=11, level=level, first_sample=first, coarsen_times=c)
+    lk, al = R.sample_fields(nx, nz, S, R.FieldModel(seed=11), level=level, first_sample=first,
+                             coarsen_times=c)
+    assert np.abs(lk.cpu().numpy() - lk_o).max() < 1e-12
+    assert np.abs(al.cpu().numpy() - al_o).max() < 1e-12
+
+
+def test_fields_large_batch_chunks(R):
+    """A batch larger than one FFT work chunk (128^2 grid, 256^2 torus)."""
+    S = 40
+    lk, al = R.sample_fields(128, 128, S, R.FieldModel(seed=0))
+    idx = [0, 17, 39]
+    for i in idx:
+        lo, ao = O.sample_fields(128, 128, 1, seed=0, first_sample=i)
+        assert np.abs(lk[i].cpu().numpy() - lo[0]).max() < 1e-12
+        assert np.abs(al[i].cpu().numpy() - ao[0]).max() < 1e-12
+
+
+# ------------------------------------------------------------- FP64 solver
+def test_solve_mc32_full(R):
+    """The 32^2 x 64-sample, 10-step workload, every sample and cell."""
+    q, q_o, s, st, st_o = compare(R, 32, 32, 64, 10, 0.01)
+    assert (s == 0).sum() > 32
+
+
+@pytest.mark.parametrize("nx,nz,S,steps", [(48, 32, 5, 3), (24, 40, 3, 2), (8, 8, 7, 4), (3, 3, 2, 2),
+                                           (16, 16, 33, 3)])
+def test_solve_ragged_shapes(R, nx, nz, S, steps):
+    """Grids that are not multiples of any tile, odd coarsest grids (3x2, 3x5),
+    a grid with no coarsening (3x3, direct solve), batch sizes off any block size."""
+    compare(R, nx, nz, S, steps, 0.01)
+
+
+def test_solve_alpha_scale_and_tight_tolerance(R):
+    """Continuation scale 0.4 and tolerances near the FP64 rounding floor, where
+    the V-cycle count of a solve may differ by one from the oracle's."""
+    compare(R, 32, 32, 8, 3, 0.01, alpha_scale=0.4, picard_tol=1e-11, mg_tol=1e-13,
+            exact_counts=False)
+
+
+def test_failure_statuses_match(R):
+    compare(R, 16, 16, 4, 2, 0.01, picard_maxit=1)
+    lk, al = O.sample_fields(16, 16, 3, seed=2)
+    lk[1, 4, 5] = np.nan
+    q, q_o, s, st, st_o = compare(R, 16, 16, 3, 2, 0.01, fields=(lk, al))
+    assert s[1] == 3 and np.isnan(q[1])
+
+
+def test_empty_and_invalid(R):
+    dev = torch.device("cuda:0")
+    e = torch.empty((0, 16, 16), dtype=torch.float64, device=dev)
+    q, p, s, st, rc = R.solve_batch(gpu_problem(R, 16, 16, 2, 0.01), e, e)
+    assert rc == 0 and q.numel() == 0
+    x = torch.zeros((2, 9, 9), dtype=torch.float64, device=dev)
+    with pytest.raises(R.RichError):
+        R.solve_batch(gpu_problem(R, 9, 9, 2, 0.01), x, x)     # coarsest grid of 81 cells
+    with pytest.raises(R.RichError):
+        R.solve_batch(gpu_problem(R, 16, 16, 2, 0.01, picard_maxit=0),
+                      torch.zeros((1, 16, 16), dtype=torch.float64, device=dev),
+                      torch.zeros((1, 16, 16), dtype=torch.float64, device=dev))
+
+
+def test_host_entry_point_matches_device(R):
+    lk, al = O.sample_fields(32, 32, 6, seed=4)
+    pb = gpu_problem(R, 32, 32, 3, 0.01)
+    qh, ph, sh, _, _ = R.solve_batch_host(pb, lk, al, want_p=True)
+    dev = torch.device("cuda:0")
+    qd, pd, sd, _, _ = R.solve_batch(pb, torch.from_numpy(lk).to(dev), torch.from_numpy(al).to(dev),
+                                     want_p=True)
+    assert np.array_equal(sh, sd.cpu().numpy())
+    assert np.array_equal(np.nan_to_num(qh), np.nan_to_num(qd.cpu().numpy()))
+    assert np.array_equal(ph, pd.cpu().numpy())
+
+
+# ------------------------------------------------------------ mixed path
+def test_mixed_precision_qoi_within_1e6(R):
+    lk, al = O.sample_fields(32, 32, 16, seed=1)
+    p_o, q_o, s_o, _ = O.solve_batch(orc_problem(5, 0.01), lk, al, nthreads=NTH)
+    dev = torch.device("cuda:0")
+    q, p, s, st, rc = R.solve_batch(gpu_problem(R, 32, 32, 5, 0.01, precision=R.MIXED),
+                                    torch.from_numpy(lk).to(dev), torch.from_numpy(al).to(dev))
+    q, s = q.cpu().numpy(), s.cpu().numpy()
+    ok = (s_o == 0) & (s == 0)
+    assert ok.sum() >= 12
+    rel = np.abs(q[ok] - q_o[ok]) / np.abs(q_o[ok])
+    assert rel.max() <= 1e-6, rel.max()
+
+
+# -------------------------------------------------- full-size, sampled
+@pytest.mark.slow
+def test_mc128_full_batch_sampled(R):
+    """128^2 x 4096 samples, 20 steps (the batched MC workload, launched as
+    bench.py launches it); 6 samples re-solved by the oracle one by one."""
+    S, n = 4096, 128
+    lk_d, al_d = R.sample_fields(n, n, S, R.FieldModel(seed=0))
+    q, p, s, st, rc = R.solve_batch(gpu_problem(R, n, n, 20, 0.005), lk_d, al_d, want_p=False)
+    q, s = q.cpu().numpy(), s.cpu().numpy()
+    picks = [0, 1, 777, 2048, 3001, 4095]
+    lk, al = lk_d[picks].cpu().numpy(), al_d[picks].cpu().numpy()
+    # the oracle solves from the oracle's own fields; they agree with the GPU's to 1e-12
+    lko, alo = np.stack([O.sample_fields(n, n, 1, seed=0, first_sample=i)[0][0] for i in picks]), None
+    assert np.abs(lko - lk).max() < 1e-12
+    p_o, q_o, s_o, _ = O.solve_batch(orc_problem(20, 0.005), lk, al, nthreads=NTH)
+    assert np.array_equal(s[picks], s_o)
+    ok = s_o == 0
+    rel = np.abs(q[picks][ok] - q_o[ok]) / np.abs(q_o[ok])
+    assert rel.max(initial=0) <= 1e-10
