@@ -1,0 +1,314 @@
+"""Benchmark: batched Monte Carlo Picard/CCMG solves of the stochastic Richards'
+equation on GB300 (one JSON line on rank 0).
+
+Default workload (N = 1): 4096 samples on a 128 x 128 grid, 20 implicit-Euler
+steps of dt = 0.005, FP64, fields by FFT-MA from seed 0 (ln Ks: exp. covariance,
+sigma^2 = 1, corr. length 0.3; alpha = 0.5 + 1.5 Phi(g)).  One bench step =
+sample the batch's fields on the GPU + solve every sample + accumulate the MC
+sums of the QoI (mean bottom flux) in FP64 on the GPU.  Inputs (~1.07 GB of
+fields per step) exceed L2, and every step draws fresh samples.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload mc128|mc32] [--precision fp64|mixed]
+
+Under torchrun (N > 1) every rank solves its own batch (weak scaling) and the
+per-step MC sums are all-reduced (8 doubles, the estimator's one exchange).
+``--impl reference`` times the FP64 CPU oracle on the host cores instead
+(rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (grid side, samples per GPU, steps, dt)
+    "mc128": (128, 4096, 20, 0.005),
+    "mc32": (32, 64, 10, 0.01),
+}
+PHYS = dict(theta_r=0.1, theta_s=0.5, p_top=-0.5, p_bottom=-5.0, p_init=-5.0,
+            picard_tol=1e-8, picard_maxit=50, mg_tol=1e-10, mg_maxit=100, nu1=2, nu2=2)
+FP64_TFLOPS_NOMINAL = 1.25      # GB300 FP64 (non-tensor) peak: 152 SMs x 2 FMA/clk x 2070 MHz x 2
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows if len(r) >= 9
+                          for k in range(4) if r[5 + k].lower() == "active"})
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+        pg = dist
+    return ws, rank, local, pg
+
+
+def cpu_baseline(n, nsamples, steps, dt, seed=0):
+    """The FP64 oracle as it stands, on every host core: fields + solves of a
+    bounded sample of the workload.  Returns (solves/s, cores, seconds)."""
+    import oracle as O
+    cores = os.cpu_count() or 1
+    O.build()
+    t0 = time.perf_counter()
+    lk, al = O.sample_fields(n, n, nsamples, seed=seed, first_sample=10_000_000, nthreads=cores)
+    pb = O.make_problem(nsteps=steps, dt=dt, **PHYS)
+    O.solve_batch(pb, lk, al, nthreads=cores, want_p=False)
+    dt_s = time.perf_counter() - t0
+    return nsamples / dt_s, cores, dt_s
+
+
+def run_reference(args):
+    ws, rank, local, pg = dist_setup(args)
+    n, S, steps, dt = WORKLOADS[args.workload]
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    per_step = max(cores, args.ref_samples or cores)
+    for _ in range(args.warmup):
+        cpu_baseline(n, per_step, steps, dt)
+    t = 0.0
+    for _ in range(args.steps):
+        _, _, s = cpu_baseline(n, per_step, steps, dt)
+        t += s
+    value = per_step * args.steps / t
+    sample = f"{per_step} samples per step of the {n}x{n}, {steps}-step workload"
+    print(json.dumps({
+        "impl": "reference", "metric": "Picard-MG solves/s", "value": value, "unit": "solves/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"mc{n}: {n}x{n} grid, {S} samples, {steps} steps dt={dt}, FP64",
+                   "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import paper_1903_08741_gb300 as R
+    from paper_1903_08741_gb300 import build as B
+
+    ws, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    if rank == 0 or not os.path.exists(B.LIB):
+        B.build()
+    if pg is not None:
+        pg.barrier()
+    dev = torch.device(f"cuda:{local}")
+    n, S, steps, dt = WORKLOADS[args.workload]
+    prec = R.MIXED if args.precision == "mixed" else R.FP64
+    pb = R.Problem(nx=n, nz=n, nsteps=steps, dt=dt, precision=prec, **PHYS)
+    model = R.FieldModel(seed=0)
+    lk = torch.empty((S, n, n), dtype=torch.float64, device=dev)
+    al = torch.empty_like(lk)
+    acc = torch.zeros(8, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sample_base = rank * 1_000_000
+
+    def step(k):
+        R.sample_fields(n, n, S, model, level=0, first_sample=sample_base + k * S, device=local,
+                        out=(lk, al))
+        q, _, st, stats, rc = R.solve_batch(pb, lk, al, device=local)
+        R.mlmc_accumulate(acc, q, st)
+        if pg is not None:
+            pg.all_reduce(acc)
+        return stats
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize(dev)
+    if pg is not None:
+        pg.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    R.profile(True, device=local)
+    l0 = R.launch_count()
+    acc.zero_()
+    torch.cuda.synchronize(dev)
+    if pg is not None:
+        pg.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    tot = R.Stats()
+    for k in range(args.steps):
+        st = step(args.warmup + k)
+        for f in ("picard_iters", "mg_cycles", "cell_vcycles", "failed"):
+            setattr(tot, f, getattr(tot, f) + getattr(st, f))
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if pg is not None:
+        pg.barrier()
+    ms = e0.elapsed_time(e1)
+    launches = R.launch_count() - l0
+    kms, klaunch, kbytes, kflops = R.profile_read(device=local)
+    R.profile(False, device=local)
+    clk = clocks.stop()
+    if pg is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    total = S * args.steps * ws
+    value = total / (ms / 1e3)
+    a = acc.cpu().numpy()
+
+    # end to end through the host-buffer entry point: H2D of the fields, solve,
+    # D2H of QoI and status, every step inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        R.sample_fields(n, n, S, model, level=0, first_sample=sample_base + 9_000_000, device=local,
+                        out=(lk, al))
+        hl = torch.empty((S, n, n), dtype=torch.float64, pin_memory=True)
+        ha = torch.empty_like(hl, pin_memory=True)
+        hl.copy_(lk)
+        ha.copy_(al)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            qh, _, sh, _, _ = R.solve_batch_host(pb, hl.numpy(), ha.numpy(), device=local)
+        t_e2e = time.perf_counter() - t0
+        if pg is not None:
+            t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        e2e = {"value": S * ws * args.e2e_steps / t_e2e, "unit": "solves/s",
+               "h2d_bytes_per_step": 2 * S * n * n * 8, "d2h_bytes_per_step": S * 8 + S * 4}
+
+    if rank != 0:
+        return
+    hbm_peak, peak_kind = load_peaks()
+    k_gbs = kbytes / (kms / 1e3) / 1e9 if kms > 0 else 0.0
+    k_tflops = kflops / (kms / 1e3) / 1e12 if kms > 0 else 0.0
+    frac_hbm = k_gbs / hbm_peak
+    frac_alu = k_tflops / FP64_TFLOPS_NOMINAL if prec == R.FP64 else 0.0
+    per_launch_bytes = kbytes / max(klaunch, 1)
+    if prec == R.FP64 and frac_alu > frac_hbm:
+        roof = {"bound": "alu", "achieved": k_tflops, "peak": FP64_TFLOPS_NOMINAL, "unit": "TFLOP/s",
+                "frac": frac_alu, "traffic": None,
+                "kernel": "k_rbgs<double> (finest level, one colour)",
+                "peak_kind": "FP64 nominal (152 SMs x 2 FMA/clk x 2.07 GHz)",
+                "hbm": {"achieved": k_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": frac_hbm,
+                        "peak_kind": peak_kind}}
+    else:
+        roof = {"bound": "hbm", "achieved": k_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": frac_hbm,
+                "traffic": None, "peak_kind": peak_kind,
+                "kernel": f"k_rbgs<{'double' if prec == R.FP64 else 'float'}> (finest level, one colour)"}
+    roof.update({"launches": klaunch, "alg_bytes_per_launch": per_launch_bytes,
+                 "avg_launch_us": 1e3 * kms / max(klaunch, 1), "kernel_ms_total": kms})
+    out = {
+        "metric": "Picard-MG solves/s", "value": value, "unit": "solves/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == R.FP64 else "f32-in-f64", "data": "synthetic",
+        "config": {"workload": f"mc{n}: {n}x{n} grid, {S} samples/GPU, {steps} steps dt={dt}, "
+                               f"{'FP64' if prec == R.FP64 else 'FP32 V-cycles in FP64 defect correction'}",
+                   "global_batch": S * ws, "grid": [n, n], "time_steps": steps,
+                   "l2": "inputs larger than L2 (2 x %.0f MB fields per step, fresh samples each step)"
+                         % (S * n * n * 8 / 1e6)},
+        "clocks": clk, "gpu_launches": launches, "roofline": roof,
+        "cell_updates_per_s": total * n * n * steps / (ms / 1e3),
+        "cell_vcycles_per_s": tot.cell_vcycles * ws / (ms / 1e3),
+        "picard_iters_per_sample": tot.picard_iters / (S * args.steps),
+        "vcycles_per_sample": tot.mg_cycles / (S * args.steps),
+        "failed_samples": tot.failed,
+        "mc_estimate": {"mean_qoi": a[0] / max(a[2], 1), "n": int(a[2]), "failed": int(a[3])},
+    }
+    if e2e:
+        out["e2e"] = e2e
+    if not args.no_cpu and ws == 1:
+        cores = os.cpu_count() or 1
+        ns = args.cpu_samples or cores
+        v, c, secs = cpu_baseline(n, ns, steps, dt)
+        out["cpu_baseline"] = {"value": v, "unit": "solves/s", "cores": c, "kind": "oracle",
+                               "sample": f"{ns} samples of the {n}x{n}, {steps}-step workload "
+                                         f"(fields + solves), {secs:.1f} s"}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="mc128")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-samples", type=int, default=0)
+    ap.add_argument("--ref-samples", type=int, default=0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -116,6 +116,29 @@ int rich_solve_batch_host(rich_ctx_t ctx, const rich_problem_t* pb, int32_t nsam
                           double* qoi, double* p_final, int32_t* status, rich_stats_t* stats,
                           void* stream);
 
+/* MC / MLMC level accumulation in FP64 on the device (Sec. 5, Eqs. SMC_ch6,
+ * MC_var_ch6, ML_var_ch6): for i < n with Y_i = qoi_fine[i] - qoi_coarse[i]
+ * (qoi_coarse NULL: Y_i = qoi_fine[i], the plain MC or level-0 term), adds to
+ * the DEVICE array acc[8]:
+ *   acc[0] += sum Y, acc[1] += sum Y^2, acc[2] += count, acc[3] += failed,
+ *   acc[4] += sum Qf, acc[5] += sum Qf^2, acc[6] += sum Qc, acc[7] += sum Qc^2.
+ * A sample is failed (counted, excluded from the sums) when either status is
+ * RICH_PICARD_MAXIT or RICH_NONFINITE or a QoI is not finite; statuses may be
+ * NULL.  Deterministic summation order.  Asynchronous on `stream`. */
+int rich_mlmc_accumulate(rich_ctx_t ctx, const double* qoi_fine, const double* qoi_coarse,
+                         const int32_t* status_fine, const int32_t* status_coarse, int32_t n,
+                         double* acc, void* stream);
+
+/* Measurement hooks.  rich_profile(ctx, 1) starts recording CUDA events around
+ * every finest-level smoothing launch (the dominant kernel) on its stream and
+ * resets the totals; rich_profile_read returns the summed event time (ms), the
+ * number of launches and their algorithmic bytes and FLOPs.  rich_launch_count
+ * returns the number of kernels this library has launched in the process. */
+int rich_profile(rich_ctx_t ctx, int enable);
+int rich_profile_read(rich_ctx_t ctx, double* ms, int64_t* launches, double* alg_bytes,
+                      double* alg_flops);
+int64_t rich_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

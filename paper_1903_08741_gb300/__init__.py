@@ -113,13 +113,18 @@ def lib():
         L.rich_solve_batch.argtypes = [vp, C.POINTER(_Problem), i32, vp, vp, dbl, vp, vp, vp,
                                        C.POINTER(_Stats), vp]
         L.rich_solve_batch_host.argtypes = L.rich_solve_batch.argtypes
+        L.rich_mlmc_accumulate.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp]
+        L.rich_profile.argtypes = [vp, C.c_int]
+        L.rich_profile_read.argtypes = [vp, C.POINTER(dbl), C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl)]
+        L.rich_launch_count.restype = i64
         _lib = L
     return _lib
 
 
 def exported_symbols():
     return ["rich_create", "rich_destroy", "rich_status_str", "rich_last_error",
-            "rich_sample_fields", "rich_solve_batch", "rich_solve_batch_host"]
+            "rich_sample_fields", "rich_solve_batch", "rich_solve_batch_host",
+            "rich_mlmc_accumulate", "rich_profile", "rich_profile_read", "rich_launch_count"]
 
 
 def _check(rc):
@@ -212,3 +217,35 @@ def solve_batch_host(problem: Problem, lnKs: np.ndarray, alpha: np.ndarray, alph
                                             ptr(alpha), alpha_scale, ptr(qoi), ptr(p), ptr(status),
                                             C.byref(st), _stream(torch, device)))
     return qoi, p, status, Stats(*[getattr(st, f) for f, _ in _Stats._fields_]), rc
+
+
+def mlmc_accumulate(acc, qoi_fine, status_fine=None, qoi_coarse=None, status_coarse=None):
+    """Add one batch of level differences to the device FP64 accumulator acc[8]
+    (sum Y, sum Y^2, count, failed, sum Qf, sum Qf^2, sum Qc, sum Qc^2)."""
+    torch = _torch()
+    dev = qoi_fine.device.index
+    ptr = lambda t, dt, n: None if t is None else _dev_ptr(t, dt, n)
+    _check(lib().rich_mlmc_accumulate(context(dev), ptr(qoi_fine, torch.float64, "qoi_fine"),
+                                      ptr(qoi_coarse, torch.float64, "qoi_coarse"),
+                                      ptr(status_fine, torch.int32, "status_fine"),
+                                      ptr(status_coarse, torch.int32, "status_coarse"),
+                                      qoi_fine.numel(), _dev_ptr(acc, torch.float64, "acc"),
+                                      _stream(torch, dev)))
+    return acc
+
+
+def profile(enable=True, device=0):
+    """Start (reset) or stop live event timing of the finest-level smoothing launches."""
+    _check(lib().rich_profile(context(device), int(enable)))
+
+
+def profile_read(device=0):
+    """(milliseconds, launches, algorithmic bytes, algorithmic FLOPs) since profile(True)."""
+    ms, n, b, f = C.c_double(), C.c_int64(), C.c_double(), C.c_double()
+    _check(lib().rich_profile_read(context(device), C.byref(ms), C.byref(n), C.byref(b), C.byref(f)))
+    return ms.value, n.value, b.value, f.value
+
+
+def launch_count():
+    """Kernels launched by librichards in this process so far."""
+    return int(lib().rich_launch_count())

@@ -3,8 +3,73 @@
 #include <stdio.h>
 #include <string.h>
 #include <new>
+#include <algorithm>
+
+#include <atomic>
 
 static thread_local char g_err[512] = "";
+static std::atomic<long long> g_launches{0};
+
+void rich_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+extern "C" int64_t rich_launch_count(void) { return g_launches.load(); }
+
+int rich_prof_begin(rich_ctx* ctx, cudaStream_t st) {
+    rich_prof& P = ctx->prof;
+    if (!P.enabled) return 0;
+    if (P.ev.size() < 2 * (P.used + 1)) {
+        size_t old = P.ev.size();
+        P.ev.resize(std::max<size_t>(64, 2 * old));
+        for (size_t k = old; k < P.ev.size(); ++k) RICH_CUDA(cudaEventCreate(&P.ev[k]));
+        P.pend_bytes.resize(P.ev.size() / 2);
+        P.pend_flops.resize(P.ev.size() / 2);
+    }
+    RICH_CUDA(cudaEventRecord(P.ev[2 * P.used], st));
+    return 0;
+}
+
+int rich_prof_end(rich_ctx* ctx, cudaStream_t st, double bytes, double flops) {
+    rich_prof& P = ctx->prof;
+    if (!P.enabled) return 0;
+    RICH_CUDA(cudaEventRecord(P.ev[2 * P.used + 1], st));
+    P.pend_bytes[P.used] = bytes;
+    P.pend_flops[P.used] = flops;
+    ++P.used;
+    return 0;
+}
+
+// all recorded events have completed (the caller synchronised their stream)
+int rich_prof_harvest(rich_ctx* ctx) {
+    rich_prof& P = ctx->prof;
+    for (size_t k = 0; k < P.used; ++k) {
+        float ms = 0;
+        RICH_CUDA(cudaEventElapsedTime(&ms, P.ev[2 * k], P.ev[2 * k + 1]));
+        P.ms += ms; P.bytes += P.pend_bytes[k]; P.flops += P.pend_flops[k]; ++P.launches;
+    }
+    P.used = 0;
+    return 0;
+}
+
+extern "C" int rich_profile(rich_ctx_t ctx, int enable) {
+    if (!ctx) return RICH_ERR_INVALID;
+    if (int e = rich_prof_harvest(ctx)) return e;
+    ctx->prof.enabled = enable;
+    ctx->prof.ms = ctx->prof.bytes = ctx->prof.flops = 0;
+    ctx->prof.launches = 0;
+    return 0;
+}
+
+extern "C" int rich_profile_read(rich_ctx_t ctx, double* ms, int64_t* launches, double* alg_bytes,
+                                 double* alg_flops) {
+    if (!ctx) return RICH_ERR_INVALID;
+    RICH_CUDA(cudaDeviceSynchronize());
+    if (int e = rich_prof_harvest(ctx)) return e;
+    if (ms) *ms = ctx->prof.ms;
+    if (launches) *launches = ctx->prof.launches;
+    if (alg_bytes) *alg_bytes = ctx->prof.bytes;
+    if (alg_flops) *alg_flops = ctx->prof.flops;
+    return 0;
+}
 
 void rich_set_error(const char* msg, const char* file, int line) {
     snprintf(g_err, sizeof(g_err), "%s (%s:%d)", msg, file, line);
@@ -51,6 +116,7 @@ extern "C" void rich_destroy(rich_ctx_t ctx) {
     if (ctx->fws.sqrt_lambda) cudaFree(ctx->fws.sqrt_lambda);
     if (ctx->fws.work) cudaFree(ctx->fws.work);
     if (ctx->fws.tw) cudaFree(ctx->fws.tw);
+    for (auto e : ctx->prof.ev) cudaEventDestroy(e);
     delete ctx;
 }
 

@@ -179,6 +179,7 @@ int fft_pass(cplx* d, int S, int n, int lines, long long sstride, int lstride, i
              const cplx* tw, int inverse, cudaStream_t st) {
     size_t sm = (size_t)L * n * sizeof(cplx);
     RICH_CUDA(cudaFuncSetAttribute(k_fft_lines<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    rich_count_launch();
     k_fft_lines<L><<<(unsigned)S * (lines / L), 256, sm, st>>>(d, n, ilog2(n), lines, sstride, lstride,
                                                                estride, tw, inverse);
     return 0;
@@ -229,9 +230,9 @@ static int ensure_spectrum(rich_ctx* ctx, int nx, int nz, double sigma2, double 
         cplx *c = nullptr, *tw = nullptr;
         RICH_CUDA(cudaMalloc(&c, sizeof(cplx) * npts));
         RICH_CUDA(cudaMalloc(&tw, sizeof(cplx) * (px / 2 + pz / 2 + 2)));
-        k_twiddles<<<nb(px / 2), 256, 0, st>>>(px, tw);
-        k_twiddles<<<nb(pz / 2), 256, 0, st>>>(pz, tw + px / 2 + 1);
-        k_cov<<<nb(npts), 256, 0, st>>>(px, pz, h, sigma2, corr_len, c);
+        rich_count_launch(); k_twiddles<<<nb(px / 2), 256, 0, st>>>(px, tw);
+        rich_count_launch(); k_twiddles<<<nb(pz / 2), 256, 0, st>>>(pz, tw + px / 2 + 1);
+        rich_count_launch(); k_cov<<<nb(npts), 256, 0, st>>>(px, pz, h, sigma2, corr_len, c);
         if (int e = fft2(c, 1, px, pz, tw, tw + px / 2 + 1, 0, st)) return e;
         std::vector<cplx> hl(npts);
         RICH_CUDA(cudaMemcpyAsync(hl.data(), c, sizeof(cplx) * npts, cudaMemcpyDeviceToHost, st));
@@ -241,7 +242,7 @@ static int ensure_spectrum(rich_ctx* ctx, int nx, int nz, double sigma2, double 
         bool ok = lmin / lmax >= -1e-12;
         if (ok || tries == 3) {
             RICH_CUDA(cudaMalloc(&f.sqrt_lambda, sizeof(double) * npts));
-            k_sqrt_spec<<<nb(npts), 256, 0, st>>>(npts, c, f.sqrt_lambda);
+            rich_count_launch(); k_sqrt_spec<<<nb(npts), 256, 0, st>>>(npts, c, f.sqrt_lambda);
             RICH_CUDA(cudaStreamSynchronize(st));
             cudaFree(c);
             f.tw = (double*)tw;
@@ -275,9 +276,9 @@ int rich_fields_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int nz, ui
     const double inv_sigma = 1.0 / sqrt(fd->sigma2);
     for (int s0 = 0; s0 < S; s0 += f.chunk) {
         int cs = std::min(f.chunk, S - s0);
-        k_noise<<<nb((long long)cs * (npts / 2)), 256, 0, st>>>(cs, npts, fd->seed, level, first + s0, work);
+        rich_count_launch(); k_noise<<<nb((long long)cs * (npts / 2)), 256, 0, st>>>(cs, npts, fd->seed, level, first + s0, work);
         if (int e = fft2(work, cs, px, pz, twx, twz, 0, st)) return e;
-        k_filter<<<nb((long long)cs * npts), 256, 0, st>>>(cs, npts, f.sqrt_lambda, work);
+        rich_count_launch(); k_filter<<<nb((long long)cs * npts), 256, 0, st>>>(cs, npts, f.sqrt_lambda, work);
         if (int e = fft2(work, cs, px, pz, twx, twz, 1, st)) return e;
         // real scratch: two ping-pong pairs of [cs][nz][nx] arrays
         const size_t blk = (size_t)cs * nx * nz;
@@ -285,7 +286,7 @@ int rich_fields_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int nz, ui
         double* ba[2] = {tmp + blk, tmp + 3 * blk};
         double* wl = coarsen ? bl[0] : lnKs + (size_t)s0 * nx * nz;
         double* wa = coarsen ? ba[0] : alpha + (size_t)s0 * nx * nz;
-        k_window<<<nb((long long)cs * nx * nz), 256, 0, st>>>(cs, nx, nz, px, pz, work, inv_sigma,
+        rich_count_launch(); k_window<<<nb((long long)cs * nx * nz), 256, 0, st>>>(cs, nx, nz, px, pz, work, inv_sigma,
                                                             fd->alpha_lo, fd->alpha_span, wl, wa);
         int cx = nx, cz = nz, cur = 0;
         for (int c = 0; c < coarsen; ++c) {
@@ -293,7 +294,7 @@ int rich_fields_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int nz, ui
             bool last = c == coarsen - 1;
             double* ol = last ? lnKs + (size_t)s0 * nxo * nzo : bl[1 - cur];
             double* oa = last ? alpha + (size_t)s0 * nxo * nzo : ba[1 - cur];
-            k_avg2<<<nb((long long)cs * ncx * ncz), 256, 0, st>>>(cs, ncx, ncz, bl[cur], ba[cur], ol, oa);
+            rich_count_launch(); k_avg2<<<nb((long long)cs * ncx * ncz), 256, 0, st>>>(cs, ncx, ncz, bl[cur], ba[cur], ol, oa);
             cur = 1 - cur;
             cx = ncx; cz = ncz;
         }

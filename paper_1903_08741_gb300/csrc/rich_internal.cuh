@@ -4,6 +4,7 @@
 #include <stdint.h>
 #include <stddef.h>
 #include "../../include/richards.h"
+#include <vector>
 
 #define RICH_MAX_LEVELS 16
 
@@ -51,12 +52,30 @@ struct rich_field_ws {
     int chunk = 0;
 };
 
+// Live timing of the finest-level smoothing launches (the dominant kernel):
+// CUDA events around each launch on the launching stream, harvested whenever
+// the host synchronises that stream anyway.
+struct rich_prof {
+    int enabled = 0;
+    std::vector<cudaEvent_t> ev;                   // 2 per pending launch
+    std::vector<double> pend_bytes, pend_flops;
+    size_t used = 0;
+    double ms = 0, bytes = 0, flops = 0;
+    int64_t launches = 0;
+};
+
 struct rich_ctx {
     int device = 0;
     int sm_count = 0;
     rich_ws ws;
     rich_field_ws fws;
+    rich_prof prof;
 };
+
+void rich_count_launch();
+int rich_prof_begin(rich_ctx* ctx, cudaStream_t st);
+int rich_prof_end(rich_ctx* ctx, cudaStream_t st, double bytes, double flops);
+int rich_prof_harvest(rich_ctx* ctx);
 
 // ---- solver (solver.cu)
 int rich_ws_reserve(rich_ctx* ctx, int S, int nx, int nz, int mixed);

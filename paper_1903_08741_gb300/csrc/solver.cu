@@ -581,7 +581,10 @@ int rich_ws_reserve(rich_ctx* ctx, int S, int nx, int nz, int mixed) {
 
 namespace {
 
+#define KL(...) (rich_count_launch(), __VA_ARGS__)
+
 struct Solver {
+    rich_ctx* ctx;
     rich_ws& w;
     const rich_problem_t& pb;
     cudaStream_t st;
@@ -592,7 +595,7 @@ struct Solver {
                                   cudaMemcpyDeviceToHost, st));
         RICH_CUDA(cudaStreamSynchronize(st));
         *out = w.h_counters[k];
-        return 0;
+        return rich_prof_harvest(ctx);
     }
     int zero_counter(int k) {
         RICH_CUDA(cudaMemsetAsync(w.counters + k, 0, sizeof(int32_t), st));
@@ -612,23 +615,31 @@ struct Solver {
         if (l == w.nlev - 1) {
             int nn = L.nx * L.nz;
             size_t sm = (size_t)nn * (nn + 1) * sizeof(T);
-            k_coarse_solve<T><<<n, 32, sm, st>>>(list, L.nx, L.nz, Tx, Tz, D, f, dp);
+            KL(k_coarse_solve<T><<<n, 32, sm, st>>>(list, L.nx, L.nz, Tx, Tz, D, f, dp));
             return;
         }
         const long long wpair = (long long)n * (L.nx / 2) * L.nz;
-        for (int it = 0; it < pb.nu1; ++it)
-            for (int c = 0; c < 2; ++c)
-                k_rbgs<T><<<nblk(wpair), TPB, 0, st>>>(list, n, L.nx, L.nz, c, Tx, Tz, invD, f, dp);
+        // algorithmic traffic of one colour pass: f, 1/D and the write of the
+        // updated half, both face arrays, the other colour's dp once
+        const double pb_bytes = (double)n * L.nx * L.nz * 4.0 * sizeof(T);
+        const double pb_flops = (double)wpair * 9.0;
+        auto smooth = [&](int nsweeps) {
+            for (int it = 0; it < nsweeps; ++it)
+                for (int c = 0; c < 2; ++c) {
+                    if (l == 0) rich_prof_begin(ctx, st);
+                    KL(k_rbgs<T><<<nblk(wpair), TPB, 0, st>>>(list, n, L.nx, L.nz, c, Tx, Tz, invD, f, dp));
+                    if (l == 0) rich_prof_end(ctx, st, pb_bytes, pb_flops);
+                }
+        };
+        smooth(pb.nu1);
         rich_level& Cl = w.lev[l + 1];
         T* fc = mixed ? (T*)Cl.f32 : (T*)Cl.f;
         T* dpc = mixed ? (T*)Cl.dp32 : (T*)Cl.dp;
         const long long wc = (long long)n * Cl.nx * Cl.nz;
-        k_resid_restrict<T><<<nblk(wc), TPB, 0, st>>>(list, n, Cl.nx, Cl.nz, Tx, Tz, D, f, dp, fc, dpc);
+        KL(k_resid_restrict<T><<<nblk(wc), TPB, 0, st>>>(list, n, Cl.nx, Cl.nz, Tx, Tz, D, f, dp, fc, dpc));
         vcycle<T>(l + 1, list, n, mixed);
-        k_prolong<T><<<nblk(wc), TPB, 0, st>>>(list, n, Cl.nx, Cl.nz, dpc, dp);
-        for (int it = 0; it < pb.nu2; ++it)
-            for (int c = 0; c < 2; ++c)
-                k_rbgs<T><<<nblk(wpair), TPB, 0, st>>>(list, n, L.nx, L.nz, c, Tx, Tz, invD, f, dp);
+        KL(k_prolong<T><<<nblk(wc), TPB, 0, st>>>(list, n, Cl.nx, Cl.nz, dpc, dp));
+        smooth(pb.nu2);
     }
 
     int run(const double* lnKs, const double* alpha, double alpha_scale, double* qoi,
@@ -637,95 +648,95 @@ struct Solver {
         const double h = 1.0 / nz, h2 = h * h, two_over_h2 = 2.0 / h2;
         const bool mixed = pb.precision == RICH_MIXED;
         const int bps = (ncell + RED_CHUNK - 1) / RED_CHUNK;
-        k_setup<<<nblk((long long)S * ncell), TPB, 0, st>>>(S, ncell, lnKs, alpha, alpha_scale,
-                                                          pb.p_init, w.Ks, w.a, w.p);
-        k_setup_samples<<<nblk(S), TPB, 0, st>>>(S, w.status, w.alive, w.pic_total, w.mg_total,
-                                                 w.maxpic, w.nrm_f, w.nrm_r, w.nrm_dp);
-        k_boundary_fine<<<nblk((long long)S * nx), TPB, 0, st>>>(S, nx, nz, w.Ks, w.a, two_over_h2,
+        KL(k_setup<<<nblk((long long)S * ncell), TPB, 0, st>>>(S, ncell, lnKs, alpha, alpha_scale,
+                                                          pb.p_init, w.Ks, w.a, w.p));
+        KL(k_setup_samples<<<nblk(S), TPB, 0, st>>>(S, w.status, w.alive, w.pic_total, w.mg_total,
+                                                 w.maxpic, w.nrm_f, w.nrm_r, w.nrm_dp));
+        KL(k_boundary_fine<<<nblk((long long)S * nx), TPB, 0, st>>>(S, nx, nz, w.Ks, w.a, two_over_h2,
                                                                 pb.p_top, pb.p_bottom,
-                                                                w.lev[0].Tbt, w.lev[0].Tbb);
+                                                                w.lev[0].Tbt, w.lev[0].Tbb));
         for (int l = 1; l < nlev; ++l)
-            k_boundary_coarsen<<<nblk((long long)S * w.lev[l].nx), TPB, 0, st>>>(
-                S, w.lev[l].nx, w.lev[l - 1].Tbt, w.lev[l - 1].Tbb, w.lev[l].Tbt, w.lev[l].Tbb);
+            KL(k_boundary_coarsen<<<nblk((long long)S * w.lev[l].nx), TPB, 0, st>>>(
+                S, w.lev[l].nx, w.lev[l - 1].Tbt, w.lev[l - 1].Tbb, w.lev[l].Tbt, w.lev[l].Tbb));
         RICH_CUDA(cudaGetLastError());
         rich_level& L0 = w.lev[0];
         for (int step = 0; step < pb.nsteps; ++step) {
             int np = 0;
             if (int e = zero_counter(0)) return e;
-            k_list_alive<<<nblk(S), TPB, 0, st>>>(S, w.alive, w.kpic, w.list_pic, w.counters + 0);
+            KL(k_list_alive<<<nblk(S), TPB, 0, st>>>(S, w.alive, w.kpic, w.list_pic, w.counters + 0));
             if (int e = read_counter(0, &np)) return e;
             if (np == 0) break;
-            k_theta_old<<<nblk((long long)np * ncell), TPB, 0, st>>>(w.list_pic, np, ncell, w.a, w.p,
-                                                                    pb.theta_r, pb.theta_s, w.thold);
+            KL(k_theta_old<<<nblk((long long)np * ncell), TPB, 0, st>>>(w.list_pic, np, ncell, w.a, w.p,
+                                                                    pb.theta_r, pb.theta_s, w.thold));
             for (int it = 0; it < pb.picard_maxit && np > 0; ++it) {
                 const long long wc = (long long)np * ncell;
-                k_conductivity<<<nblk(wc), TPB, 0, st>>>(w.list_pic, np, ncell, w.Ks, w.a, w.p,
-                                                         pb.theta_r, pb.theta_s, pb.dt, w.K, w.th, L0.Cdt);
-                k_faces<<<nblk(wc), TPB, 0, st>>>(w.list_pic, np, nx, nz, w.K, two_over_h2, L0.Tx, L0.Tz);
-                k_rhs<<<(unsigned)np * bps, RED_TPB, 0, st>>>(w.list_pic, bps, nx, nz, w.p, w.th, w.thold,
+                KL(k_conductivity<<<nblk(wc), TPB, 0, st>>>(w.list_pic, np, ncell, w.Ks, w.a, w.p,
+                                                         pb.theta_r, pb.theta_s, pb.dt, w.K, w.th, L0.Cdt));
+                KL(k_faces<<<nblk(wc), TPB, 0, st>>>(w.list_pic, np, nx, nz, w.K, two_over_h2, L0.Tx, L0.Tz));
+                KL(k_rhs<<<(unsigned)np * bps, RED_TPB, 0, st>>>(w.list_pic, bps, nx, nz, w.p, w.th, w.thold,
                                                              L0.Tx, L0.Tz, L0.Tbt, L0.Tbb, L0.Cdt, pb.dt,
                                                              h, pb.p_top, pb.p_bottom, L0.f, L0.D,
-                                                             L0.invD, w.nrm_f);
+                                                             L0.invD, w.nrm_f));
                 for (int l = 1; l < nlev; ++l) {
                     rich_level& F = w.lev[l - 1];
                     rich_level& Cl = w.lev[l];
-                    k_coarsen<<<nblk((long long)np * Cl.nx * Cl.nz), TPB, 0, st>>>(
+                    KL(k_coarsen<<<nblk((long long)np * Cl.nx * Cl.nz), TPB, 0, st>>>(
                         w.list_pic, np, Cl.nx, Cl.nz, F.Tx, F.Tz, F.Cdt, Cl.Tbt, Cl.Tbb, Cl.Tx, Cl.Tz,
-                        Cl.Cdt, Cl.D, Cl.invD);
+                        Cl.Cdt, Cl.D, Cl.invD));
                 }
                 if (mixed)
                     for (int l = 0; l < nlev; ++l) {
                         rich_level& Lv = w.lev[l];
-                        k_to_f32_op<<<nblk((long long)np * Lv.nx * Lv.nz), TPB, 0, st>>>(
+                        KL(k_to_f32_op<<<nblk((long long)np * Lv.nx * Lv.nz), TPB, 0, st>>>(
                             w.list_pic, np, Lv.nx * Lv.nz, Lv.Tx, Lv.Tz, Lv.D, Lv.Tx32, Lv.Tz32,
-                            Lv.D32, Lv.invD32);
+                            Lv.D32, Lv.invD32));
                     }
-                k_zero<<<nblk(wc), TPB, 0, st>>>(w.list_pic, np, ncell, L0.dp);
+                KL(k_zero<<<nblk(wc), TPB, 0, st>>>(w.list_pic, np, ncell, L0.dp));
                 int nm = 0;
                 if (int e = zero_counter(1)) return e;
-                k_mg_start<<<nblk(np), TPB, 0, st>>>(w.list_pic, np, pb.mg_tol, w.nrm_f, w.target, w.cyc,
-                                                     w.status, w.alive, w.list_mg, w.counters + 1);
+                KL(k_mg_start<<<nblk(np), TPB, 0, st>>>(w.list_pic, np, pb.mg_tol, w.nrm_f, w.target, w.cyc,
+                                                     w.status, w.alive, w.list_mg, w.counters + 1));
                 if (int e = read_counter(1, &nm)) return e;
                 if (mixed && nm > 0)   // first FP32 right-hand side: the defect of dp = 0 is f
-                    k_defect<<<(unsigned)nm * bps, RED_TPB, 0, st>>>(
+                    KL(k_defect<<<(unsigned)nm * bps, RED_TPB, 0, st>>>(
                         w.list_mg, bps, nx, nz, L0.Tx, L0.Tz, L0.D, L0.f, L0.dp, L0.f32, L0.dp32,
-                        w.nrm_dp);
+                        w.nrm_dp));
                 for (int c = 0; c < pb.mg_maxit && nm > 0; ++c) {
                     if (!mixed) {
                         vcycle<double>(0, w.list_mg, nm, false);
-                        k_resid_norm<double><<<(unsigned)nm * bps, RED_TPB, 0, st>>>(
-                            w.list_mg, bps, nx, nz, L0.Tx, L0.Tz, L0.D, L0.f, L0.dp, w.nrm_r);
+                        KL(k_resid_norm<double><<<(unsigned)nm * bps, RED_TPB, 0, st>>>(
+                            w.list_mg, bps, nx, nz, L0.Tx, L0.Tz, L0.D, L0.f, L0.dp, w.nrm_r));
                     } else {
                         // FP32 V-cycle on the FP32 defect, FP64 correction, then the FP64
                         // defect (stopping norm and the next FP32 right-hand side)
                         vcycle<float>(0, w.list_mg, nm, true);
-                        k_add_correction<<<nblk((long long)nm * ncell), TPB, 0, st>>>(
-                            w.list_mg, nm, ncell, L0.dp32, L0.dp);
-                        k_defect<<<(unsigned)nm * bps, RED_TPB, 0, st>>>(
+                        KL(k_add_correction<<<nblk((long long)nm * ncell), TPB, 0, st>>>(
+                            w.list_mg, nm, ncell, L0.dp32, L0.dp));
+                        KL(k_defect<<<(unsigned)nm * bps, RED_TPB, 0, st>>>(
                             w.list_mg, bps, nx, nz, L0.Tx, L0.Tz, L0.D, L0.f, L0.dp, L0.f32, L0.dp32,
-                            w.nrm_r);
+                            w.nrm_r));
                     }
                     if (int e = zero_counter(2)) return e;
-                    k_mg_decide<<<nblk(nm), TPB, 0, st>>>(w.list_mg, nm, pb.mg_maxit, w.nrm_r, w.target,
+                    KL(k_mg_decide<<<nblk(nm), TPB, 0, st>>>(w.list_mg, nm, pb.mg_maxit, w.nrm_r, w.target,
                                                           w.cyc, w.mg_total, w.status, w.alive,
-                                                          w.list_tmp, w.counters + 2);
+                                                          w.list_tmp, w.counters + 2));
                     if (int e = read_counter(2, &nm)) return e;
                     std::swap(w.list_mg, w.list_tmp);
                 }
                 if (mixed) {   // the defect norm slot doubles as scratch in the mixed loop
                     RICH_CUDA(cudaMemsetAsync(w.nrm_dp, 0, sizeof(unsigned long long) * S, st));
                 }
-                k_update_p<<<(unsigned)np * bps, RED_TPB, 0, st>>>(w.list_pic, bps, ncell, w.alive,
-                                                                   L0.dp, w.p, w.nrm_dp);
+                KL(k_update_p<<<(unsigned)np * bps, RED_TPB, 0, st>>>(w.list_pic, bps, ncell, w.alive,
+                                                                   L0.dp, w.p, w.nrm_dp));
                 if (int e = zero_counter(2)) return e;
-                k_picard_decide<<<nblk(np), TPB, 0, st>>>(w.list_pic, np, pb.picard_maxit, pb.picard_tol,
+                KL(k_picard_decide<<<nblk(np), TPB, 0, st>>>(w.list_pic, np, pb.picard_maxit, pb.picard_tol,
                                                           w.nrm_dp, w.kpic, w.pic_total, w.maxpic,
-                                                          w.status, w.alive, w.list_tmp, w.counters + 2);
+                                                          w.status, w.alive, w.list_tmp, w.counters + 2));
                 if (int e = read_counter(2, &np)) return e;
                 std::swap(w.list_pic, w.list_tmp);
             }
         }
-        k_qoi<<<S, 32, 0, st>>>(S, nx, nz, w.Ks, w.a, w.p, pb.p_bottom, h, w.alive, qoi);
+        KL(k_qoi<<<S, 32, 0, st>>>(S, nx, nz, w.Ks, w.a, w.p, pb.p_bottom, h, w.alive, qoi));
         if (p_final)
             RICH_CUDA(cudaMemcpyAsync(p_final, w.p, sizeof(double) * (size_t)S * ncell,
                                       cudaMemcpyDeviceToDevice, st));
@@ -747,7 +758,7 @@ int rich_solve_device(rich_ctx* ctx, const rich_problem_t* pb, int S, const doub
     if (e) return e;
     rich_ws& w = ctx->ws;
     if (w.lev[w.nlev - 1].nx * w.lev[w.nlev - 1].nz > 64) return RICH_ERR_INVALID;
-    Solver sv{w, *pb, st, S};
+    Solver sv{ctx, w, *pb, st, S};
     e = sv.run(lnKs, alpha, alpha_scale, qoi, p_final, status);
     if (e) return e;
     // worst status and counters (host)
