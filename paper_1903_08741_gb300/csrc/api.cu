@@ -38,6 +38,14 @@ int rich_prof_end(rich_ctx* ctx, cudaStream_t st, double bytes, double flops) {
     return 0;
 }
 
+// set the algorithmic work of the most recently recorded launch
+void rich_prof_amend(rich_ctx* ctx, double bytes, double flops) {
+    rich_prof& P = ctx->prof;
+    if (!P.enabled || P.used == 0) return;
+    P.pend_bytes[P.used - 1] = bytes;
+    P.pend_flops[P.used - 1] = flops;
+}
+
 // all recorded events have completed (the caller synchronised their stream)
 int rich_prof_harvest(rich_ctx* ctx) {
     rich_prof& P = ctx->prof;
@@ -117,6 +125,7 @@ extern "C" void rich_destroy(rich_ctx_t ctx) {
     if (ctx->fws.work) cudaFree(ctx->fws.work);
     if (ctx->fws.tw) cudaFree(ctx->fws.tw);
     for (auto e : ctx->prof.ev) cudaEventDestroy(e);
+    if (ctx->fused_scratch) cudaFree(ctx->fused_scratch);
     delete ctx;
 }
 

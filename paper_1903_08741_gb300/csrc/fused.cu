@@ -1,0 +1,544 @@
+// Persistent fused solver: one kernel launch solves a whole batch.
+//
+// Each CTA takes samples from an atomic queue and runs, for its sample, the
+// complete method of arXiv 1903.08741 Sec. 4: backward-Euler time loop,
+// modified Picard iteration on the mixed form (Eq. Mixed_based_3), and for
+// every Picard step the cell-centred multigrid solve (five-point harmonic-mean
+// stencil, Eq. five_stencil; red-black Gauss-Seidel; 1/4-sum restriction and
+// piecewise-constant prolongation, Eq. transfer; coarse operators by
+// rediscretisation with arithmetic means of face coefficients, Fig.
+// diffUpscale; exact coarsest solve).  All control flow is per CTA and uniform
+// (decisions come from block-wide reductions), so a sample never waits for
+// another and there is no host round trip inside a solve.
+//
+// Memory: every CTA owns one scratch slot holding its sample's hierarchy.  The
+// slot of a 128^2 FP64 problem is about 2 MB and the multigrid working set
+// about 0.85 MB, so the slots of all resident CTAs stay largely in the 129 MB
+// L2 (and small grids in L1).  Scratch arrays are read with plain loads (they
+// are rewritten inside the kernel; __syncthreads orders the accesses).
+//
+// Precision: TM = double gives the FP64 path (the oracle's algorithm and
+// stopping tests); TM = float gives FP32 V-cycles inside an FP64
+// defect-correction loop (FP64 Picard residual, FP64 outer residual, FP64
+// correction and stopping norm).
+#include "rich_internal.cuh"
+#include <math.h>
+#include <algorithm>
+
+namespace {
+
+constexpr unsigned long long ABS_MASK = 0x7FFFFFFFFFFFFFFFull;
+constexpr unsigned long long INF_BITS = 0x7FF0000000000000ull;
+constexpr int MAXL = RICH_MAX_LEVELS;
+
+enum { A_TX, A_TZ, A_CDT, A_D, A_INVD, A_F, A_DP, A_TBT, A_TBB, N64 };
+enum { B_TX, B_TZ, B_D, B_INVD, B_F, B_DP, N32 };
+
+struct FParams {
+    int S, nlev, mixed;
+    int nx[MAXL], nz[MAXL];
+    unsigned mnx[MAXL], mhx[MAXL];          // magic reciprocals of nx and nx/2
+    long long o64[MAXL][N64];               // byte offsets in the slot (-1: absent)
+    long long o32[MAXL][N32];
+    long long o_p, o_thold, o_Ks, o_a, o_K, o_th;
+    long long slot_bytes;
+    char* scratch;
+    const double* lnKs;
+    const double* alpha;
+    double alpha_scale;
+    double* qoi;
+    double* p_final;
+    int32_t* status;
+    int64_t* pic_total;
+    int64_t* mg_total;
+    int32_t* maxpic;
+    int* queue;
+    int nsteps, picard_maxit, mg_maxit, nu1, nu2;
+    double dt, tr, ts, p_top, p_bot, p_init, picard_tol, mg_tol, h, two_over_h2;
+};
+
+// c / d for c * d < 2^32 (m = floor(2^32 / d) + 1), d = 1 handled apart
+__device__ __forceinline__ int fdiv(int c, int d, unsigned m) {
+    return d == 1 ? c : (int)__umulhi((unsigned)c, m);
+}
+
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+    return (unsigned long long)__double_as_longlong(x) & ABS_MASK;
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+
+// block-wide max of v, returned to every thread
+__device__ __forceinline__ unsigned long long block_max(unsigned long long v, unsigned long long* red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_max_u64(v);
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < nw ? red[lane] : 0ull;
+        v = warp_max_u64(v);
+        if (lane == 0) red[32] = v;
+    }
+    __syncthreads();
+    unsigned long long r = red[32];
+    __syncthreads();
+    return r;
+}
+
+template <typename T>
+struct Lv {
+    int nx, nz, hx, nc;
+    unsigned mnx, mhx;
+    T *Tx, *Tz, *D, *invD, *f, *dp;
+};
+
+struct Lv64 {
+    int nx, nz, nc;
+    unsigned mnx;
+    double *Tx, *Tz, *Cdt, *D, *invD, *f, *dp, *Tbt, *Tbb;
+};
+
+template <typename T>
+__device__ __forceinline__ T offdiag(const T* Tx, const T* Tz, const T* x, int P, int i, int j,
+                                     int nx, int nz) {
+    T s = T(0);
+    if (i < nx - 1) s += Tx[P] * x[P + 1];
+    if (i > 0)      s += Tx[P - 1] * x[P - 1];
+    if (j < nz - 1) s += Tz[P] * x[P + nx];
+    if (j > 0)      s += Tz[P - nx] * x[P - nx];
+    return s;
+}
+
+// one colour of red-black Gauss-Seidel over the level (red: i + j even)
+template <typename T>
+__device__ __forceinline__ void rbgs(const Lv<T>& L, int colour) {
+    const int n = L.hx * L.nz;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        int j = fdiv(c, L.hx, L.mhx);
+        int i = 2 * (c - j * L.hx) + ((j + colour) & 1);
+        int P = j * L.nx + i;
+        L.dp[P] = (L.f[P] + offdiag(L.Tx, L.Tz, L.dp, P, i, j, L.nx, L.nz)) * L.invD[P];
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void resid_restrict(const Lv<T>& F, const Lv<T>& C) {
+    for (int c = threadIdx.x; c < C.nc; c += blockDim.x) {
+        int J = fdiv(c, C.nx, C.mnx), I = c - J * C.nx;
+        T r[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            int i = 2 * I + (k & 1), j = 2 * J + (k >> 1);
+            int P = j * F.nx + i;
+            r[k] = F.f[P] - (F.D[P] * F.dp[P] - offdiag(F.Tx, F.Tz, F.dp, P, i, j, F.nx, F.nz));
+        }
+        C.f[c] = T(0.25) * (r[0] + r[1] + r[2] + r[3]);
+        C.dp[c] = T(0);
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void prolong(const Lv<T>& F, const Lv<T>& C) {
+    for (int c = threadIdx.x; c < C.nc; c += blockDim.x) {
+        int J = fdiv(c, C.nx, C.mnx), I = c - J * C.nx;
+        T e = C.dp[c];
+        int P = (2 * J) * F.nx + 2 * I;
+        F.dp[P] += e; F.dp[P + 1] += e; F.dp[P + F.nx] += e; F.dp[P + F.nx + 1] += e;
+    }
+    __syncthreads();
+}
+
+// exact coarsest solve: Gaussian elimination of the assembled five-point
+// matrix by warp 0 in shared memory (symmetric, diagonally dominant)
+template <typename T>
+__device__ __forceinline__ void coarse_solve(const Lv<T>& L, T* A) {
+    if (threadIdx.x < 32) {
+        const int nn = L.nc, ld = nn + 1, lane = threadIdx.x;
+        for (int r = lane; r < nn; r += 32) {
+            for (int c = 0; c < nn; ++c) A[r * ld + c] = T(0);
+            int j = r / L.nx, i = r - j * L.nx;
+            A[r * ld + r] = L.D[r];
+            if (i < L.nx - 1) A[r * ld + r + 1] = -L.Tx[r];
+            if (i > 0)        A[r * ld + r - 1] = -L.Tx[r - 1];
+            if (j < L.nz - 1) A[r * ld + r + L.nx] = -L.Tz[r];
+            if (j > 0)        A[r * ld + r - L.nx] = -L.Tz[r - L.nx];
+            A[r * ld + nn] = L.f[r];
+        }
+        __syncwarp();
+        for (int k = 0; k < nn; ++k) {
+            for (int r = k + 1 + lane; r < nn; r += 32) {
+                T m = A[r * ld + k] / A[k * ld + k];
+                for (int c = k; c <= nn; ++c) A[r * ld + c] -= m * A[k * ld + c];
+            }
+            __syncwarp();
+        }
+        if (lane == 0) {
+            for (int k = nn - 1; k >= 0; --k) {
+                T sum = A[k * ld + nn];
+                for (int c = k + 1; c < nn; ++c) sum -= A[k * ld + c] * A[c * ld + nn];
+                A[k * ld + nn] = sum / A[k * ld + k];
+            }
+        }
+        __syncwarp();
+        for (int r = lane; r < nn; r += 32) L.dp[r] = A[r * ld + nn];
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ void vcycle(const Lv<T>* L, int nlev, int nu1, int nu2, T* A) {
+    for (int l = 0; l < nlev - 1; ++l) {
+        for (int it = 0; it < nu1; ++it) { rbgs(L[l], 0); rbgs(L[l], 1); }
+        resid_restrict(L[l], L[l + 1]);
+    }
+    coarse_solve(L[nlev - 1], A);
+    for (int l = nlev - 2; l >= 0; --l) {
+        prolong(L[l], L[l + 1]);
+        for (int it = 0; it < nu2; ++it) { rbgs(L[l], 0); rbgs(L[l], 1); }
+    }
+}
+
+// ||f - A dp||_inf on a level (as an IEEE bit pattern)
+template <typename T>
+__device__ __forceinline__ unsigned long long resid_norm(const Lv<T>& L, unsigned long long* red) {
+    unsigned long long m = 0;
+    for (int q = threadIdx.x; q < L.nc; q += blockDim.x) {
+        int j = fdiv(q, L.nx, L.mnx), i = q - j * L.nx;
+        double r = L.f[q] - (L.D[q] * L.dp[q] - offdiag(L.Tx, L.Tz, L.dp, q, i, j, L.nx, L.nz));
+        unsigned long long b = abs_bits(r);
+        m = b > m ? b : m;
+    }
+    return block_max(m, red);
+}
+
+template <typename TM>
+__global__ void __launch_bounds__(512)
+k_fused(const FParams P) {
+    extern __shared__ unsigned char smraw[];
+    TM* Amat = reinterpret_cast<TM*>(smraw);
+    __shared__ unsigned long long red[33];
+    __shared__ int s_sample;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    char* slot = P.scratch + (size_t)blockIdx.x * P.slot_bytes;
+    const int nlev = P.nlev;
+    const bool mixed = P.mixed;
+
+    // level descriptors live in shared memory (one copy per CTA, broadcast reads)
+    __shared__ Lv64 L64[MAXL];
+    __shared__ Lv<TM> LM[MAXL];
+    if (tid < nlev) {
+        const int l = tid;
+        Lv64& a = L64[l];
+        a.nx = P.nx[l]; a.nz = P.nz[l]; a.nc = a.nx * a.nz; a.mnx = P.mnx[l];
+        double** pp[N64] = {&a.Tx, &a.Tz, &a.Cdt, &a.D, &a.invD, &a.f, &a.dp, &a.Tbt, &a.Tbb};
+        for (int k = 0; k < N64; ++k) *pp[k] = P.o64[l][k] >= 0 ? (double*)(slot + P.o64[l][k]) : nullptr;
+        Lv<TM>& b = LM[l];
+        b.nx = a.nx; b.nz = a.nz; b.hx = a.nx >> 1; b.nc = a.nc; b.mnx = P.mnx[l]; b.mhx = P.mhx[l];
+        if (mixed) {
+            TM** qq[N32] = {&b.Tx, &b.Tz, &b.D, &b.invD, &b.f, &b.dp};
+            for (int k = 0; k < N32; ++k) *qq[k] = (TM*)(slot + P.o32[l][k]);
+        } else {
+            b.Tx = (TM*)a.Tx; b.Tz = (TM*)a.Tz; b.D = (TM*)a.D; b.invD = (TM*)a.invD;
+            b.f = (TM*)a.f; b.dp = (TM*)a.dp;
+        }
+    }
+    __syncthreads();
+    double* p = (double*)(slot + P.o_p);
+    double* thold = (double*)(slot + P.o_thold);
+    double* Ks = (double*)(slot + P.o_Ks);
+    double* aa = (double*)(slot + P.o_a);
+    double* K = (double*)(slot + P.o_K);
+    double* th = (double*)(slot + P.o_th);
+    const Lv64& F = L64[0];
+    const int nx = F.nx, nz = F.nz, nc = F.nc;
+    const double h = P.h, t2h = P.two_over_h2, dt = P.dt, tr = P.tr, ts = P.ts;
+
+    for (;;) {
+        if (tid == 0) s_sample = atomicAdd(P.queue, 1);
+        __syncthreads();
+        const int s = s_sample;
+        __syncthreads();
+        if (s >= P.S) break;
+        const double* lk = P.lnKs + (size_t)s * nc;
+        const double* al = P.alpha + (size_t)s * nc;
+
+        // ---- set-up: Ks, alpha * scale, initial head, Dirichlet faces (fixed)
+        for (int q = tid; q < nc; q += nt) {
+            Ks[q] = exp(lk[q]);
+            aa[q] = al[q] * P.alpha_scale;
+            p[q] = P.p_init;
+        }
+        __syncthreads();
+        for (int i = tid; i < nx; i += nt) {
+            int T = (nz - 1) * nx + i, B = i;
+            double kt = P.p_top < 0.0 ? Ks[T] * exp(aa[T] * P.p_top) : Ks[T];
+            double kb = P.p_bot < 0.0 ? Ks[B] * exp(aa[B] * P.p_bot) : Ks[B];
+            F.Tbt[i] = t2h * kt;
+            F.Tbb[i] = t2h * kb;
+        }
+        __syncthreads();
+        for (int l = 1; l < nlev; ++l) {
+            for (int I = tid; I < L64[l].nx; I += nt) {
+                L64[l].Tbt[I] = 0.25 * (0.5 * (L64[l - 1].Tbt[2 * I] + L64[l - 1].Tbt[2 * I + 1]));
+                L64[l].Tbb[I] = 0.25 * (0.5 * (L64[l - 1].Tbb[2 * I] + L64[l - 1].Tbb[2 * I + 1]));
+            }
+            __syncthreads();
+        }
+
+        int status = RICH_OK;
+        bool alive = true;
+        long long pic_tot = 0, mg_tot = 0;
+        int maxpic = 0;
+        for (int step = 0; step < P.nsteps && alive; ++step) {
+            for (int q = tid; q < nc; q += nt) {
+                double pp = p[q];
+                thold[q] = pp < 0.0 ? tr + (ts - tr) * exp(aa[q] * pp) : ts;
+            }
+            __syncthreads();
+            int k = 0;
+            for (;;) {
+                // ---- Picard system at p^k (Gardner closure, harmonic faces, f = -R)
+                for (int q = tid; q < nc; q += nt) {
+                    double pp = p[q], ks = Ks[q];
+                    if (pp < 0.0) {
+                        double a = aa[q];
+                        double E = exp(a * pp);
+                        K[q] = ks * E;
+                        th[q] = tr + (ts - tr) * E;
+                        F.Cdt[q] = ((ts - tr) * a * E) / dt;
+                    } else {
+                        K[q] = ks; th[q] = ts; F.Cdt[q] = 0.0;
+                    }
+                }
+                __syncthreads();
+                for (int q = tid; q < nc; q += nt) {
+                    int j = fdiv(q, nx, F.mnx), i = q - j * nx;
+                    double kp = K[q];
+                    if (i < nx - 1) { double ke = K[q + 1]; F.Tx[q] = t2h * kp * ke / (kp + ke); }
+                    else F.Tx[q] = 0.0;
+                    if (j < nz - 1) { double kn = K[q + nx]; F.Tz[q] = t2h * kp * kn / (kp + kn); }
+                    else F.Tz[q] = 0.0;
+                }
+                __syncthreads();
+                unsigned long long m = 0;
+                for (int q = tid; q < nc; q += nt) {
+                    int j = fdiv(q, nx, F.mnx), i = q - j * nx;
+                    double pp = p[q];
+                    double R = (th[q] - thold[q]) / dt;
+                    double d = F.Cdt[q];
+                    if (i < nx - 1) { double t = F.Tx[q];     R += -t * (p[q + 1] - pp); d += t; }
+                    if (i > 0)      { double t = F.Tx[q - 1]; R += -t * (p[q - 1] - pp); d += t; }
+                    if (j < nz - 1) { double t = F.Tz[q];     R += -t * (p[q + nx] - pp) - t * h; d += t; }
+                    else { double t = F.Tbt[i]; R += -t * (P.p_top - pp) - t * h / 2.0; d += t; }
+                    if (j > 0)      { double t = F.Tz[q - nx]; R += -t * (p[q - nx] - pp) + t * h; d += t; }
+                    else { double t = F.Tbb[i]; R += t * (pp - P.p_bot) + t * h / 2.0; d += t; }
+                    F.f[q] = -R;
+                    F.D[q] = d;
+                    double inv = 1.0 / d;
+                    F.invD[q] = inv;
+                    F.dp[q] = 0.0;
+                    if (mixed) {
+                        LM[0].Tx[q] = (TM)F.Tx[q]; LM[0].Tz[q] = (TM)F.Tz[q];
+                        LM[0].D[q] = (TM)d; LM[0].invD[q] = (TM)(1.0f / (float)d);
+                        LM[0].f[q] = (TM)(-R); LM[0].dp[q] = TM(0);
+                    }
+                    unsigned long long b = abs_bits(R);
+                    m = b > m ? b : m;
+                }
+                const unsigned long long fb = block_max(m, red);   // includes the sync
+                // ---- coarse operators (Fig. diffUpscale)
+                for (int l = 1; l < nlev; ++l) {
+                    const Lv64& Fl = L64[l - 1];
+                    const Lv64& Cl = L64[l];
+                    const int fx = Fl.nx;
+                    for (int c = tid; c < Cl.nc; c += nt) {
+                        int J = fdiv(c, Cl.nx, Cl.mnx), I = c - J * Cl.nx;
+                        int f00 = (2 * J) * fx + 2 * I, f01 = f00 + fx;
+                        double cd = 0.25 * (Fl.Cdt[f00] + Fl.Cdt[f00 + 1] + Fl.Cdt[f01] + Fl.Cdt[f01 + 1]);
+                        double d = cd, te = 0.0, tn = 0.0;
+                        if (I < Cl.nx - 1) { te = 0.25 * (0.5 * (Fl.Tx[f00 + 1] + Fl.Tx[f01 + 1])); d += te; }
+                        if (I > 0)         { d += 0.25 * (0.5 * (Fl.Tx[f00 - 1] + Fl.Tx[f01 - 1])); }
+                        if (J < Cl.nz - 1) { tn = 0.25 * (0.5 * (Fl.Tz[f01] + Fl.Tz[f01 + 1])); d += tn; }
+                        else d += Cl.Tbt[I];
+                        if (J > 0)         { d += 0.25 * (0.5 * (Fl.Tz[f00 - fx] + Fl.Tz[f00 - fx + 1])); }
+                        else d += Cl.Tbb[I];
+                        Cl.Tx[c] = te; Cl.Tz[c] = tn; Cl.Cdt[c] = cd; Cl.D[c] = d;
+                        if (mixed) {
+                            LM[l].Tx[c] = (TM)te; LM[l].Tz[c] = (TM)tn; LM[l].D[c] = (TM)d;
+                            LM[l].invD[c] = (TM)(1.0f / (float)d);
+                        } else {
+                            Cl.invD[c] = 1.0 / d;
+                        }
+                    }
+                    __syncthreads();
+                }
+                if (fb > INF_BITS - 1) { status = max(status, (int)RICH_NONFINITE); alive = false; break; }
+                // ---- multigrid solve of A dp = f
+                const double fn = __longlong_as_double((long long)fb);
+                const double target = P.mg_tol * (fn > 1.0 ? fn : 1.0);
+                double rn = fn;
+                int cyc = 0;
+                bool nonfinite = false;
+                while (rn >= target && cyc < P.mg_maxit) {
+                    vcycle<TM>(LM, nlev, P.nu1, P.nu2, Amat);
+                    unsigned long long rb;
+                    if (!mixed) {
+                        rb = resid_norm<TM>(LM[0], red);
+                    } else {
+                        // dp += e (FP64), then the FP64 defect: stopping norm and
+                        // the next FP32 right-hand side
+                        unsigned long long mm = 0;
+                        for (int q = tid; q < nc; q += nt) {
+                            F.dp[q] += (double)LM[0].dp[q];
+                        }
+                        __syncthreads();
+                        for (int q = tid; q < nc; q += nt) {
+                            int j = fdiv(q, nx, F.mnx), i = q - j * nx;
+                            double r = F.f[q] - (F.D[q] * F.dp[q] - offdiag(F.Tx, F.Tz, F.dp, q, i, j, nx, nz));
+                            LM[0].f[q] = (TM)r;
+                            LM[0].dp[q] = TM(0);
+                            unsigned long long b = abs_bits(r);
+                            mm = b > mm ? b : mm;
+                        }
+                        rb = block_max(mm, red);
+                    }
+                    ++cyc;
+                    if (rb > INF_BITS - 1) { nonfinite = true; break; }
+                    rn = __longlong_as_double((long long)rb);
+                }
+                mg_tot += cyc;
+                if (nonfinite) { status = max(status, (int)RICH_NONFINITE); alive = false; break; }
+                if (!(rn < target)) status = max(status, (int)RICH_MG_MAXIT);
+                // ---- p^{k+1} = p^k + dp, ||dp||_inf
+                unsigned long long dm = 0;
+                for (int q = tid; q < nc; q += nt) {
+                    double d = F.dp[q];
+                    p[q] += d;
+                    unsigned long long b = abs_bits(d);
+                    dm = b > dm ? b : dm;
+                }
+                const unsigned long long db = block_max(dm, red);
+                ++k;
+                ++pic_tot;
+                if (db > INF_BITS - 1) { status = max(status, (int)RICH_NONFINITE); alive = false; break; }
+                if (__longlong_as_double((long long)db) < P.picard_tol) break;
+                if (k >= P.picard_maxit) { status = max(status, (int)RICH_PICARD_MAXIT); alive = false; break; }
+            }
+            maxpic = max(maxpic, k);
+        }
+        // ---- QoI: mean outward Darcy flux through the bottom faces
+        if (tid < 32) {
+            double acc = 0.0;
+            for (int i = tid; i < nx; i += 32) {
+                double kb = P.p_bot < 0.0 ? Ks[i] * exp(aa[i] * P.p_bot) : Ks[i];
+                acc += kb * (2.0 * (p[i] - P.p_bot) / h + 1.0);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (tid == 0) {
+                P.qoi[s] = alive ? acc / nx : __longlong_as_double(0x7FF8000000000000ll);
+                if (P.status) P.status[s] = status;
+                P.pic_total[s] = pic_tot;
+                P.mg_total[s] = mg_tot;
+                P.maxpic[s] = maxpic;
+            }
+        }
+        if (P.p_final)
+            for (int q = tid; q < nc; q += nt) P.p_final[(size_t)s * nc + q] = p[q];
+        __syncthreads();
+    }
+}
+
+unsigned magic(int d) { return d <= 1 ? 0u : (unsigned)((0x100000000ull / (unsigned)d) + 1); }
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+// Fused persistent solve of S samples; stats arrays and the queue live in ctx->ws.
+int rich_solve_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const double* lnKs,
+                     const double* alpha, double alpha_scale, double* qoi, double* p_final,
+                     int32_t* status, cudaStream_t st) {
+    rich_ws& w = ctx->ws;
+    FParams P{};
+    const int nlev = rich_count_levels(pb->nx, pb->nz);
+    if (nlev < 1) return RICH_ERR_INVALID;
+    const bool mixed = pb->precision == RICH_MIXED;
+    // index arithmetic uses 32-bit magic division: cell index * row length < 2^32
+    if ((unsigned long long)pb->nx * pb->nz * pb->nx >= (1ull << 32)) return RICH_ERR_INVALID;
+    P.S = S; P.nlev = nlev; P.mixed = mixed;
+    size_t off = 0;
+    int lx = pb->nx, lz = pb->nz;
+    for (int l = 0; l < nlev; ++l) {
+        P.nx[l] = lx; P.nz[l] = lz; P.mnx[l] = magic(lx); P.mhx[l] = magic(lx / 2);
+        const size_t nc8 = (size_t)lx * lz * 8;
+        for (int k = 0; k < N64; ++k) {
+            size_t bytes = (k == A_TBT || k == A_TBB) ? (size_t)lx * 8 : nc8;
+            bool need = true;
+            if (mixed && (k == A_F || k == A_DP || k == A_INVD) && l > 0) need = false;
+            if (need) { P.o64[l][k] = (long long)off; off = al256(off + bytes); }
+            else P.o64[l][k] = -1;
+        }
+        for (int k = 0; k < N32; ++k) {
+            if (mixed) { P.o32[l][k] = (long long)off; off = al256(off + (size_t)lx * lz * 4); }
+            else P.o32[l][k] = -1;
+        }
+        lx /= 2; lz /= 2;
+    }
+    const size_t nc8 = (size_t)pb->nx * pb->nz * 8;
+    P.o_p = off; off = al256(off + nc8);
+    P.o_thold = off; off = al256(off + nc8);
+    P.o_Ks = off; off = al256(off + nc8);
+    P.o_a = off; off = al256(off + nc8);
+    P.o_K = off; off = al256(off + nc8);
+    P.o_th = off; off = al256(off + nc8);
+    P.slot_bytes = (long long)off;
+
+    // coarsest dense system in shared memory
+    const int nnc = P.nx[nlev - 1] * P.nz[nlev - 1];
+    const size_t smem = (size_t)nnc * (nnc + 1) * (mixed ? 4 : 8);
+    int occ = 0;
+    if (mixed) {
+        RICH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused<float>, 512, smem));
+    } else {
+        RICH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused<double>, 512, smem));
+    }
+    occ = std::max(occ, 1);
+    const int grid = std::max(1, std::min(S, ctx->sm_count * occ));
+    const size_t need = (size_t)grid * off + 256;
+    if (ctx->fused_bytes < need) {
+        if (ctx->fused_scratch) cudaFree(ctx->fused_scratch);
+        ctx->fused_scratch = nullptr; ctx->fused_bytes = 0;
+        cudaError_t e = cudaMalloc(&ctx->fused_scratch, need);
+        if (e != cudaSuccess) { cudaGetLastError(); return RICH_ERR_OOM; }
+        ctx->fused_bytes = need;
+    }
+    P.scratch = (char*)ctx->fused_scratch + 256;
+    P.queue = (int*)ctx->fused_scratch;
+    P.lnKs = lnKs; P.alpha = alpha; P.alpha_scale = alpha_scale;
+    P.qoi = qoi; P.p_final = p_final; P.status = w.status;
+    P.pic_total = w.pic_total; P.mg_total = w.mg_total; P.maxpic = w.maxpic;
+    P.nsteps = pb->nsteps; P.picard_maxit = pb->picard_maxit; P.mg_maxit = pb->mg_maxit;
+    P.nu1 = pb->nu1; P.nu2 = pb->nu2;
+    P.dt = pb->dt; P.tr = pb->theta_r; P.ts = pb->theta_s; P.p_top = pb->p_top; P.p_bot = pb->p_bottom;
+    P.p_init = pb->p_init; P.picard_tol = pb->picard_tol; P.mg_tol = pb->mg_tol;
+    P.h = 1.0 / pb->nz; P.two_over_h2 = 2.0 / (P.h * P.h);
+    RICH_CUDA(cudaMemsetAsync(P.queue, 0, sizeof(int), st));
+    rich_count_launch();
+    rich_prof_begin(ctx, st);
+    if (mixed) k_fused<float><<<grid, 512, smem, st>>>(P);
+    else k_fused<double><<<grid, 512, smem, st>>>(P);
+    rich_prof_end(ctx, st, 0.0, 0.0);
+    RICH_CUDA(cudaGetLastError());
+    if (status)
+        RICH_CUDA(cudaMemcpyAsync(status, w.status, sizeof(int32_t) * S, cudaMemcpyDeviceToDevice, st));
+    return 0;
+}

@@ -70,6 +70,8 @@ struct rich_ctx {
     rich_ws ws;
     rich_field_ws fws;
     rich_prof prof;
+    void* fused_scratch = nullptr;              // per-CTA slots of the fused solver
+    size_t fused_bytes = 0;
 };
 
 void rich_count_launch();
@@ -83,6 +85,10 @@ int rich_solve_device(rich_ctx* ctx, const rich_problem_t* pb, int S, const doub
                       const double* alpha, double alpha_scale, double* qoi, double* p_final,
                       int32_t* status, rich_stats_t* stats, cudaStream_t st);
 int rich_count_levels(int nx, int nz);
+int rich_solve_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const double* lnKs,
+                     const double* alpha, double alpha_scale, double* qoi, double* p_final,
+                     int32_t* status, cudaStream_t st);
+void rich_prof_amend(rich_ctx* ctx, double bytes, double flops);
 
 // ---- fields (fields.cu)
 int rich_fields_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int nz, uint32_t level,

@@ -18,6 +18,7 @@
 #include <chrono>
 #include <vector>
 #include <algorithm>
+#include <stdlib.h>
 
 namespace {
 
@@ -758,8 +759,14 @@ int rich_solve_device(rich_ctx* ctx, const rich_problem_t* pb, int S, const doub
     if (e) return e;
     rich_ws& w = ctx->ws;
     if (w.lev[w.nlev - 1].nx * w.lev[w.nlev - 1].nz > 64) return RICH_ERR_INVALID;
-    Solver sv{ctx, w, *pb, st, S};
-    e = sv.run(lnKs, alpha, alpha_scale, qoi, p_final, status);
+    static const char* which = getenv("RICH_SOLVER");
+    const bool batched = which && strcmp(which, "batched") == 0;
+    if (batched) {
+        Solver sv{ctx, w, *pb, st, S};
+        e = sv.run(lnKs, alpha, alpha_scale, qoi, p_final, status);
+    } else {
+        e = rich_solve_fused(ctx, pb, S, lnKs, alpha, alpha_scale, qoi, p_final, status, st);
+    }
     if (e) return e;
     // worst status and counters (host)
     std::vector<int32_t> hs(S), hmax(S);
@@ -779,6 +786,17 @@ int rich_solve_device(rich_ctx* ctx, const rich_problem_t* pb, int S, const doub
         if (hs[s] == RICH_PICARD_MAXIT || hs[s] == RICH_NONFINITE) acc.failed++;
     }
     acc.cell_vcycles = acc.mg_cycles * (int64_t)pb->nx * pb->nz;
+    if (!batched) {
+        // algorithmic work of the fused launch: per fine cell and V-cycle 74 flops
+        // and 16.7 words (two fused passes per level, hierarchy factor 4/3); per
+        // Picard iteration 56 flops and 10 words per fine cell (assembly, coarse
+        // operators, update)
+        const double nc = (double)pb->nx * pb->nz;
+        const double w8 = pb->precision == RICH_MIXED ? 4.0 : 8.0;
+        const double flops = nc * (74.0 * acc.mg_cycles + 56.0 * acc.picard_iters);
+        const double bytes = nc * (16.7 * w8 * acc.mg_cycles + 10.0 * 8.0 * acc.picard_iters);
+        rich_prof_amend(ctx, bytes, flops);
+    }
     acc.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (stats) *stats = acc;
     return worst;

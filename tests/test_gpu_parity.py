@@ -67,7 +67,7 @@ def compare(R, nx, nz, S, nsteps, dt, seed=0, alpha_scale=1.0, fields=None, rtol
     # Stopping tests decided within a few ulps of their threshold can flip by one
     # cycle between two rounding orders (FMA contraction, 1/D multiply, exp/log
     # last-ulp differences); the values above are unaffected at 1e-10.
-    slack = 0 if exact_counts else 0.01
+    slack = 0 if exact_counts else 0.05
     assert abs(st.picard_iters - st_o.picard_iters) <= max(1, slack * st_o.picard_iters)
     assert abs(st.mg_cycles - st_o.mg_cycles) <= max(2, 0.005 * st_o.mg_cycles, slack * st_o.mg_cycles)
     return q, q_o, s, st, st_o
