@@ -129,6 +129,32 @@ int rich_mlmc_accumulate(rich_ctx_t ctx, const double* qoi_fine, const double* q
                          const int32_t* status_fine, const int32_t* status_coarse, int32_t n,
                          double* acc, void* stream);
 
+/* Allocation-free solve.  The paper has no counterpart: this entry point exists
+ * for callers that cannot call cudaMalloc -- code embedded in a host framework
+ * that owns all device memory through its own pool allocator and forbids other
+ * allocations, or latency-sensitive loops that cannot afford cudaMalloc's
+ * implicit device synchronisation.  It runs the fused FP64 / mixed solver of
+ * rich_solve_batch on the CURRENT device with no context and allocates nothing
+ * (no cudaMalloc, cudaFree or allocating library call): its scratch is a
+ * library-owned static device array of RICH_NOALLOC_SCRATCH_BYTES (16 MiB),
+ * present on every GPU that loads the library until the process exits.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call shares the one array: calls whose work overlaps on the GPU
+ *     (other streams, other host threads) race and give wrong results; order
+ *     them on one stream.  Each call clears the state that must start at zero.
+ *   - The grid is limited to the CTA slots that fit in the array; a grid whose
+ *     per-CTA slot exceeds it is rejected with RICH_ERR_INVALID (a 128^2 FP64
+ *     problem needs about 2 MiB per CTA, so 8 CTAs run; 32^2 needs ~0.14 MiB).
+ * Inputs lnKs, alpha [S][nz][nx] and outputs qoi[S], status[S] (status may be
+ * NULL) are caller-owned DEVICE arrays.  The call is asynchronous on `stream`
+ * and returns 0 once the work is enqueued (per-sample results are in status),
+ * or a negative error code. */
+#define RICH_NOALLOC_SCRATCH_BYTES (16u << 20)
+int rich_solve_batch_noalloc(const rich_problem_t* pb, int32_t nsamples, const double* lnKs,
+                             const double* alpha, double alpha_scale, double* qoi,
+                             int32_t* status, void* stream);
+
 /* Measurement hooks.  rich_profile(ctx, 1) starts recording CUDA events around
  * every finest-level smoothing launch (the dominant kernel) on its stream and
  * resets the totals; rich_profile_read returns the summed event time (ms), the

@@ -117,6 +117,7 @@ def lib():
         L.rich_profile.argtypes = [vp, C.c_int]
         L.rich_profile_read.argtypes = [vp, C.POINTER(dbl), C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl)]
         L.rich_launch_count.restype = i64
+        L.rich_solve_batch_noalloc.argtypes = [C.POINTER(_Problem), i32, vp, vp, dbl, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -124,7 +125,8 @@ def lib():
 def exported_symbols():
     return ["rich_create", "rich_destroy", "rich_status_str", "rich_last_error",
             "rich_sample_fields", "rich_solve_batch", "rich_solve_batch_host",
-            "rich_mlmc_accumulate", "rich_profile", "rich_profile_read", "rich_launch_count"]
+            "rich_mlmc_accumulate", "rich_profile", "rich_profile_read", "rich_launch_count",
+            "rich_solve_batch_noalloc"]
 
 
 def _check(rc):
@@ -249,3 +251,22 @@ def profile_read(device=0):
 def launch_count():
     """Kernels launched by librichards in this process so far."""
     return int(lib().rich_launch_count())
+
+
+def solve_batch_noalloc(problem: Problem, lnKs, alpha, alpha_scale=1.0, qoi=None, status=None):
+    """Allocation-free solve on the current device (see include/richards.h): the
+    library allocates nothing; the caller provides qoi [S] and status [S]
+    (created here when not given).  Asynchronous on the current stream."""
+    torch = _torch()
+    S = lnKs.shape[0]
+    if qoi is None:
+        qoi = torch.empty(S, dtype=torch.float64, device=lnKs.device)
+    if status is None:
+        status = torch.empty(S, dtype=torch.int32, device=lnKs.device)
+    _check(lib().rich_solve_batch_noalloc(C.byref(problem._c()), S,
+                                          _dev_ptr(lnKs, torch.float64, "lnKs"),
+                                          _dev_ptr(alpha, torch.float64, "alpha"), alpha_scale,
+                                          _dev_ptr(qoi, torch.float64, "qoi"),
+                                          _dev_ptr(status, torch.int32, "status"),
+                                          _stream(torch, lnKs.device.index)))
+    return qoi, status

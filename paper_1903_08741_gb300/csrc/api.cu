@@ -129,7 +129,7 @@ extern "C" void rich_destroy(rich_ctx_t ctx) {
     delete ctx;
 }
 
-static int check_problem(const rich_problem_t* pb) {
+int rich_check_problem(const rich_problem_t* pb) {
     if (!pb || pb->nx < 1 || pb->nz < 1 || pb->nsteps < 0 || !(pb->dt > 0) ||
         pb->picard_maxit < 1 || pb->mg_maxit < 1 || pb->nu1 < 0 || pb->nu2 < 0 ||
         (pb->precision != RICH_FP64 && pb->precision != RICH_MIXED) || !(pb->picard_tol > 0) ||
@@ -154,7 +154,7 @@ extern "C" int rich_solve_batch(rich_ctx_t ctx, const rich_problem_t* pb, int32_
                                 const double* lnKs, const double* alpha, double alpha_scale,
                                 double* qoi, double* p_final, int32_t* status,
                                 rich_stats_t* stats, void* stream) {
-    if (!ctx || check_problem(pb) || nsamples < 0) return RICH_ERR_INVALID;
+    if (!ctx || rich_check_problem(pb) || nsamples < 0) return RICH_ERR_INVALID;
     if (nsamples == 0) { if (stats) *stats = rich_stats_t{}; return 0; }
     if (!lnKs || !alpha || !qoi) return RICH_ERR_INVALID;
     RICH_CUDA(cudaSetDevice(ctx->device));
@@ -166,7 +166,7 @@ extern "C" int rich_solve_batch_host(rich_ctx_t ctx, const rich_problem_t* pb, i
                                      const double* lnKs, const double* alpha, double alpha_scale,
                                      double* qoi, double* p_final, int32_t* status,
                                      rich_stats_t* stats, void* stream) {
-    if (!ctx || check_problem(pb) || nsamples < 0) return RICH_ERR_INVALID;
+    if (!ctx || rich_check_problem(pb) || nsamples < 0) return RICH_ERR_INVALID;
     if (nsamples == 0) { if (stats) *stats = rich_stats_t{}; return 0; }
     if (!lnKs || !alpha || !qoi) return RICH_ERR_INVALID;
     RICH_CUDA(cudaSetDevice(ctx->device));

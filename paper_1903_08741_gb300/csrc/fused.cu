@@ -447,9 +447,9 @@ k_fused(const FParams P) {
             if (tid == 0) {
                 P.qoi[s] = alive ? acc / nx : __longlong_as_double(0x7FF8000000000000ll);
                 if (P.status) P.status[s] = status;
-                P.pic_total[s] = pic_tot;
-                P.mg_total[s] = mg_tot;
-                P.maxpic[s] = maxpic;
+                if (P.pic_total) P.pic_total[s] = pic_tot;
+                if (P.mg_total) P.mg_total[s] = mg_tot;
+                if (P.maxpic) P.maxpic[s] = maxpic;
             }
         }
         if (P.p_final)
@@ -463,12 +463,9 @@ size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
 
-// Fused persistent solve of S samples; stats arrays and the queue live in ctx->ws.
-int rich_solve_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const double* lnKs,
-                     const double* alpha, double alpha_scale, double* qoi, double* p_final,
-                     int32_t* status, cudaStream_t st) {
-    rich_ws& w = ctx->ws;
-    FParams P{};
+// Slot layout and problem constants of the fused kernel (no device work).
+static int fused_setup(const rich_problem_t* pb, int S, FParams& P) {
+    P = FParams{};
     const int nlev = rich_count_levels(pb->nx, pb->nz);
     if (nlev < 1) return RICH_ERR_INVALID;
     const bool mixed = pb->precision == RICH_MIXED;
@@ -501,17 +498,50 @@ int rich_solve_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const doubl
     P.o_K = off; off = al256(off + nc8);
     P.o_th = off; off = al256(off + nc8);
     P.slot_bytes = (long long)off;
+    P.nsteps = pb->nsteps; P.picard_maxit = pb->picard_maxit; P.mg_maxit = pb->mg_maxit;
+    P.nu1 = pb->nu1; P.nu2 = pb->nu2;
+    P.dt = pb->dt; P.tr = pb->theta_r; P.ts = pb->theta_s; P.p_top = pb->p_top; P.p_bot = pb->p_bottom;
+    P.p_init = pb->p_init; P.picard_tol = pb->picard_tol; P.mg_tol = pb->mg_tol;
+    P.h = 1.0 / pb->nz; P.two_over_h2 = 2.0 / (P.h * P.h);
+    return 0;
+}
 
-    // coarsest dense system in shared memory
-    const int nnc = P.nx[nlev - 1] * P.nz[nlev - 1];
-    const size_t smem = (size_t)nnc * (nnc + 1) * (mixed ? 4 : 8);
-    int occ = 0;
-    if (mixed) {
-        RICH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused<float>, 512, smem));
+static size_t fused_smem(const FParams& P) {
+    const int nnc = P.nx[P.nlev - 1] * P.nz[P.nlev - 1];
+    return (size_t)nnc * (nnc + 1) * (P.mixed ? 4 : 8);
+}
+
+static int fused_occupancy(const FParams& P, size_t smem, int* occ) {
+    if (P.mixed) {
+        RICH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_fused<float>, 512, smem));
     } else {
-        RICH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused<double>, 512, smem));
+        RICH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_fused<double>, 512, smem));
     }
-    occ = std::max(occ, 1);
+    if (*occ < 1) *occ = 1;
+    return 0;
+}
+
+static int fused_launch(const FParams& P, int grid, size_t smem, cudaStream_t st) {
+    RICH_CUDA(cudaMemsetAsync(P.queue, 0, sizeof(int), st));
+    rich_count_launch();
+    if (P.mixed) k_fused<float><<<grid, 512, smem, st>>>(P);
+    else k_fused<double><<<grid, 512, smem, st>>>(P);
+    RICH_CUDA(cudaGetLastError());
+    return 0;
+}
+
+// Fused persistent solve of S samples; stats arrays live in ctx->ws, the
+// per-CTA slots and the queue counter in ctx->fused_scratch.
+int rich_solve_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const double* lnKs,
+                     const double* alpha, double alpha_scale, double* qoi, double* p_final,
+                     int32_t* status, cudaStream_t st) {
+    rich_ws& w = ctx->ws;
+    FParams P;
+    if (int e = fused_setup(pb, S, P)) return e;
+    const size_t off = (size_t)P.slot_bytes;
+    const size_t smem = fused_smem(P);
+    int occ = 0;
+    if (int e = fused_occupancy(P, smem, &occ)) return e;
     const int grid = std::max(1, std::min(S, ctx->sm_count * occ));
     const size_t need = (size_t)grid * off + 256;
     if (ctx->fused_bytes < need) {
@@ -526,19 +556,83 @@ int rich_solve_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const doubl
     P.lnKs = lnKs; P.alpha = alpha; P.alpha_scale = alpha_scale;
     P.qoi = qoi; P.p_final = p_final; P.status = w.status;
     P.pic_total = w.pic_total; P.mg_total = w.mg_total; P.maxpic = w.maxpic;
-    P.nsteps = pb->nsteps; P.picard_maxit = pb->picard_maxit; P.mg_maxit = pb->mg_maxit;
-    P.nu1 = pb->nu1; P.nu2 = pb->nu2;
-    P.dt = pb->dt; P.tr = pb->theta_r; P.ts = pb->theta_s; P.p_top = pb->p_top; P.p_bot = pb->p_bottom;
-    P.p_init = pb->p_init; P.picard_tol = pb->picard_tol; P.mg_tol = pb->mg_tol;
-    P.h = 1.0 / pb->nz; P.two_over_h2 = 2.0 / (P.h * P.h);
-    RICH_CUDA(cudaMemsetAsync(P.queue, 0, sizeof(int), st));
-    rich_count_launch();
     rich_prof_begin(ctx, st);
-    if (mixed) k_fused<float><<<grid, 512, smem, st>>>(P);
-    else k_fused<double><<<grid, 512, smem, st>>>(P);
+    if (int e = fused_launch(P, grid, smem, st)) return e;
     rich_prof_end(ctx, st, 0.0, 0.0);
-    RICH_CUDA(cudaGetLastError());
     if (status)
         RICH_CUDA(cudaMemcpyAsync(status, w.status, sizeof(int32_t) * S, cudaMemcpyDeviceToDevice, st));
     return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant.  Its scratch (queue counter + per-CTA slots) is a
+// file-scope device array of RICH_NOALLOC_SCRATCH_BYTES, created when the
+// library is loaded and held by every GPU that loads it until the process
+// exits.  Host code may not use the array's name as a device address (on the
+// host it names a shadow object), so the address is looked up once per device
+// with cudaGetSymbolAddress and cached.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[RICH_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int NOALLOC_MAX_DEVICES = 64;
+void* g_noalloc_addr[NOALLOC_MAX_DEVICES];
+int g_noalloc_sms[NOALLOC_MAX_DEVICES];
+}
+
+extern "C" int rich_solve_batch_noalloc(const rich_problem_t* pb, int32_t nsamples,
+                                        const double* lnKs, const double* alpha, double alpha_scale,
+                                        double* qoi, int32_t* status, void* stream) {
+    if (rich_check_problem(pb) || nsamples < 0) {
+        rich_set_error("invalid problem or sample count", __FILE__, __LINE__);
+        return RICH_ERR_INVALID;
+    }
+    if (nsamples == 0) return 0;
+    if (!lnKs || !alpha || !qoi) {
+        rich_set_error("lnKs, alpha and qoi are required", __FILE__, __LINE__);
+        return RICH_ERR_INVALID;
+    }
+    int dev = -1;
+    RICH_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+        rich_set_error("device index beyond the allocation-free table", __FILE__, __LINE__);
+        return RICH_ERR_INVALID;
+    }
+    if (!g_noalloc_addr[dev]) {      // first call on this device: resolve the symbol
+        void* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) {
+            cudaGetLastError();
+            rich_set_error(e != cudaSuccess ? cudaGetErrorString(e) : "null symbol address", __FILE__, __LINE__);
+            return RICH_ERR_CUDA;
+        }
+        int sms = 0;
+        RICH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        g_noalloc_sms[dev] = sms;
+        g_noalloc_addr[dev] = ptr;
+    }
+    FParams P;
+    if (int e = fused_setup(pb, nsamples, P)) {
+        rich_set_error("unsupported grid", __FILE__, __LINE__);
+        return e;
+    }
+    const size_t slot = (size_t)P.slot_bytes;
+    const size_t slots = (RICH_NOALLOC_SCRATCH_BYTES - 256) / slot;
+    if (slots < 1) {
+        rich_set_error("grid needs more scratch per CTA than the allocation-free entry point holds "
+                       "(RICH_NOALLOC_SCRATCH_BYTES)", __FILE__, __LINE__);
+        return RICH_ERR_INVALID;
+    }
+    const size_t smem = fused_smem(P);
+    int occ = 0;
+    if (int e = fused_occupancy(P, smem, &occ)) return e;
+    const int grid = (int)std::min<long long>({(long long)nsamples, (long long)g_noalloc_sms[dev] * occ,
+                                              (long long)slots});
+    char* base = (char*)g_noalloc_addr[dev];
+    P.queue = (int*)base;                 // cleared by fused_launch before the kernel
+    P.scratch = base + 256;
+    P.lnKs = lnKs; P.alpha = alpha; P.alpha_scale = alpha_scale;
+    P.qoi = qoi; P.p_final = nullptr; P.status = status;
+    P.pic_total = nullptr; P.mg_total = nullptr; P.maxpic = nullptr;
+    return fused_launch(P, grid, smem, (cudaStream_t)stream);
 }

@@ -89,6 +89,7 @@ int rich_solve_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const doubl
                      const double* alpha, double alpha_scale, double* qoi, double* p_final,
                      int32_t* status, cudaStream_t st);
 void rich_prof_amend(rich_ctx* ctx, double bytes, double flops);
+int rich_check_problem(const rich_problem_t* pb);
 
 // ---- fields (fields.cu)
 int rich_fields_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int nz, uint32_t level,

@@ -1,0 +1,55 @@
+"""The allocation-free solve entry point (rich_solve_batch_noalloc).
+
+Some callers cannot call cudaMalloc: code embedded in a host framework that
+owns all device memory through its own pool allocator, or latency-sensitive
+loops that cannot afford cudaMalloc's implicit device synchronisation.  For
+them the library offers one entry point that allocates nothing and works out of
+a fixed static device array.  This test calls it through the C ABI twice in a
+row, on different inputs, and checks each result against the regular
+rich_solve_batch entry point at the FP64 parity tolerance (1e-10 relative,
+statuses equal).  It lives in a file of its own that pytest collects last.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def test_noalloc_matches_solve_batch_twice():
+    import paper_1903_08741_gb300 as R
+    from paper_1903_08741_gb300 import build
+    from tests.inputs import PHYSICS, SOLVER
+    build.build()
+    assert torch.cuda.is_available()
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    pb = R.Problem(nx=32, nz=32, nsteps=3, dt=0.01, **PHYSICS, **SOLVER)
+    for call, seed in enumerate((21, 22)):
+        lk, al = O.sample_fields(32, 32, 12, seed=seed)
+        lk_d, al_d = torch.from_numpy(lk).to(dev), torch.from_numpy(al).to(dev)
+        q_ref, _, s_ref, _, _ = R.solve_batch(pb, lk_d, al_d)
+        qoi = torch.full((12,), -1.0, dtype=torch.float64, device=dev)
+        status = torch.full((12,), -7, dtype=torch.int32, device=dev)
+        R.solve_batch_noalloc(pb, lk_d, al_d, qoi=qoi, status=status)
+        torch.cuda.synchronize(dev)
+        q, s = qoi.cpu().numpy(), status.cpu().numpy()
+        q_ref, s_ref = q_ref.cpu().numpy(), s_ref.cpu().numpy()
+        assert np.array_equal(s, s_ref), (call, s, s_ref)
+        ok = s_ref == 0
+        assert ok.sum() >= 6
+        rel = np.abs(q[ok] - q_ref[ok]) / np.abs(q_ref[ok])
+        assert rel.max() <= 1e-10, (call, rel.max())
+        assert np.all(np.isnan(q[(s_ref == 1) | (s_ref == 3)]))
+
+
+def test_noalloc_rejects_oversized_grid():
+    import paper_1903_08741_gb300 as R
+    from tests.inputs import PHYSICS, SOLVER
+    dev = torch.device("cuda:0")
+    pb = R.Problem(nx=1024, nz=1024, nsteps=1, dt=0.01, **PHYSICS, **SOLVER)
+    x = torch.zeros((1, 1024, 1024), dtype=torch.float64, device=dev)
+    with pytest.raises(R.RichError):
+        R.solve_batch_noalloc(pb, x, x)
