@@ -162,6 +162,8 @@ def run_ours(args):
         pg.barrier()
     dev = torch.device(f"cuda:{local}")
     n, S, steps, dt = WORKLOADS[args.workload]
+    S = args.samples or S
+    steps = args.time_steps or steps
     prec = R.MIXED if args.precision == "mixed" else R.FP64
     pb = R.Problem(nx=n, nz=n, nsteps=steps, dt=dt, precision=prec, **PHYS)
     model = R.FieldModel(seed=0)
@@ -303,6 +305,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-samples", type=int, default=0)
     ap.add_argument("--ref-samples", type=int, default=0)
+    # profiling knobs (smaller cases for ncu captures; not bench workloads)
+    ap.add_argument("--samples", type=int, default=0, help="override samples per GPU")
+    ap.add_argument("--time-steps", type=int, default=0, help="override implicit-Euler steps")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
