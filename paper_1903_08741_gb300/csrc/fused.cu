@@ -11,16 +11,28 @@
 // (decisions come from block-wide reductions), so a sample never waits for
 // another and there is no host round trip inside a solve.
 //
-// Memory: every CTA owns one scratch slot holding its sample's hierarchy.  The
-// slot of a 128^2 FP64 problem is about 2 MB and the multigrid working set
-// about 0.85 MB, so the slots of all resident CTAs stay largely in the 129 MB
-// L2 (and small grids in L1).  Scratch arrays are read with plain loads (they
-// are rewritten inside the kernel; __syncthreads orders the accesses).
+// Memory: every CTA owns one scratch slot holding its sample's hierarchy; the
+// slots of the resident CTAs are largely L2 (small grids: L1) resident.
+// Scratch arrays are read with plain loads (they are rewritten inside the
+// kernel; __syncthreads orders the accesses).
 //
-// Precision: TM = double gives the FP64 path (the oracle's algorithm and
-// stopping tests); TM = float gives FP32 V-cycles inside an FP64
-// defect-correction loop (FP64 Picard residual, FP64 outer residual, FP64
-// correction and stopping norm).
+// Precision and instruction budget.  GB300 issues 2 FP64 FMAs per SM and
+// clock (1/64 of its FP32 rate), so the FP64 V-cycle is written to minimise
+// FP64 instructions:
+//   * every level stores the Jacobi-scaled coefficients w = T/D of its four
+//     faces and the scaled right-hand side f/D, so a Gauss-Seidel update is
+//     dp_P = f_P/D_P + sum w dp_nb (4 FMAs instead of 6 operations);
+//   * after a black half-sweep the black residuals are zero up to rounding
+//     (each black value was just solved from its red neighbours), so the
+//     restriction after pre-smoothing and the stopping norm after
+//     post-smoothing evaluate red cells only (exactly the same quantities in
+//     exact arithmetic; full evaluation when nu = 0);
+//   * divisions by dt are multiplications by 1/dt.
+// TM = double is the FP64 path (the oracle's algorithm and stopping tests);
+// TM = float runs FP32 V-cycles (unscaled coefficients: FP32 operations are
+// cheap, bytes are not) inside an FP64 defect-correction loop that performs
+// MIXED_INNER V-cycles per FP64 defect (FP64 Picard residual, FP64 outer
+// residual, FP64 correction and stopping norm).
 #include "rich_internal.cuh"
 #include <math.h>
 #include <algorithm>
@@ -30,17 +42,21 @@ namespace {
 constexpr unsigned long long ABS_MASK = 0x7FFFFFFFFFFFFFFFull;
 constexpr unsigned long long INF_BITS = 0x7FF0000000000000ull;
 constexpr int MAXL = RICH_MAX_LEVELS;
+constexpr int MIXED_INNER = 2;   // FP32 V-cycles per FP64 defect evaluation
 
-enum { A_TX, A_TZ, A_CDT, A_D, A_INVD, A_F, A_DP, A_TBT, A_TBB, N64 };
-enum { B_TX, B_TZ, B_D, B_INVD, B_F, B_DP, N32 };
+// FP64 unscaled operator (all levels): faces, mass term, diagonal, Dirichlet faces
+enum { A_TX, A_TZ, A_CDT, A_D, A_TBT, A_TBB, N64 };
+// multigrid arrays in the cycle precision.  FP64: wE wW wN wS q=1/D fh dp
+// (D shared with the FP64 operator).  FP32: Tx Tz D 1/D f dp.
+enum { B_0, B_1, B_2, B_3, B_4, B_5, B_6, NMG };
 
 struct FParams {
     int S, nlev, mixed;
     int nx[MAXL], nz[MAXL];
     unsigned mnx[MAXL], mhx[MAXL];          // magic reciprocals of nx and nx/2
     long long o64[MAXL][N64];               // byte offsets in the slot (-1: absent)
-    long long o32[MAXL][N32];
-    long long o_p, o_thold, o_Ks, o_a, o_K, o_th;
+    long long omg[MAXL][NMG];
+    long long o_f64, o_dp64, o_p, o_thold, o_Ks, o_a, o_K, o_th;
     long long slot_bytes;
     char* scratch;
     const double* lnKs;
@@ -54,7 +70,7 @@ struct FParams {
     int32_t* maxpic;
     int* queue;
     int nsteps, picard_maxit, mg_maxit, nu1, nu2;
-    double dt, tr, ts, p_top, p_bot, p_init, picard_tol, mg_tol, h, two_over_h2;
+    double inv_dt, tr, ts, p_top, p_bot, p_init, picard_tol, mg_tol, h, two_over_h2;
 };
 
 // c / d for c * d < 2^32 (m = floor(2^32 / d) + 1), d = 1 handled apart
@@ -92,28 +108,57 @@ __device__ __forceinline__ unsigned long long block_max(unsigned long long v, un
     return r;
 }
 
+struct Lv64 {
+    int nx, nz, nc;
+    unsigned mnx;
+    double *Tx, *Tz, *Cdt, *D, *Tbt, *Tbb;
+};
+
+// multigrid level in cycle precision T.  FP64 (scaled): c = {wE, wW, wN, wS},
+// q = 1/D, f = f/D (the coarsest level keeps f unscaled for the direct solve).
+// FP32 (unscaled): c = {Tx, Tz, -, -}, q = 1/D, f = f.
 template <typename T>
 struct Lv {
     int nx, nz, hx, nc;
     unsigned mnx, mhx;
-    T *Tx, *Tz, *D, *invD, *f, *dp;
+    T *c0, *c1, *c2, *c3, *D, *q, *f, *dp;
 };
 
-struct Lv64 {
-    int nx, nz, nc;
-    unsigned mnx;
-    double *Tx, *Tz, *Cdt, *D, *invD, *f, *dp, *Tbt, *Tbb;
-};
+template <typename T> struct Scaled { static constexpr bool value = sizeof(T) == 8; };
 
+// Gauss-Seidel value of cell P from its current neighbours
 template <typename T>
-__device__ __forceinline__ T offdiag(const T* Tx, const T* Tz, const T* x, int P, int i, int j,
-                                     int nx, int nz) {
-    T s = T(0);
-    if (i < nx - 1) s += Tx[P] * x[P + 1];
-    if (i > 0)      s += Tx[P - 1] * x[P - 1];
-    if (j < nz - 1) s += Tz[P] * x[P + nx];
-    if (j > 0)      s += Tz[P - nx] * x[P - nx];
-    return s;
+__device__ __forceinline__ T gs_value(const Lv<T>& L, int P, int i, int j) {
+    if constexpr (Scaled<T>::value) {
+        T v = L.f[P];
+        if (i < L.nx - 1) v += L.c0[P] * L.dp[P + 1];
+        if (i > 0)        v += L.c1[P] * L.dp[P - 1];
+        if (j < L.nz - 1) v += L.c2[P] * L.dp[P + L.nx];
+        if (j > 0)        v += L.c3[P] * L.dp[P - L.nx];
+        return v;
+    } else {
+        T s = T(0);
+        if (i < L.nx - 1) s += L.c0[P] * L.dp[P + 1];
+        if (i > 0)        s += L.c0[P - 1] * L.dp[P - 1];
+        if (j < L.nz - 1) s += L.c1[P] * L.dp[P + L.nx];
+        if (j > 0)        s += L.c1[P - L.nx] * L.dp[P - L.nx];
+        return (L.f[P] + s) * L.q[P];
+    }
+}
+
+// residual f - A dp at cell P (unscaled)
+template <typename T>
+__device__ __forceinline__ T residual(const Lv<T>& L, int P, int i, int j) {
+    if constexpr (Scaled<T>::value) {
+        return L.D[P] * (gs_value(L, P, i, j) - L.dp[P]);
+    } else {
+        T s = T(0);
+        if (i < L.nx - 1) s += L.c0[P] * L.dp[P + 1];
+        if (i > 0)        s += L.c0[P - 1] * L.dp[P - 1];
+        if (j < L.nz - 1) s += L.c1[P] * L.dp[P + L.nx];
+        if (j > 0)        s += L.c1[P - L.nx] * L.dp[P - L.nx];
+        return L.f[P] - (L.D[P] * L.dp[P] - s);
+    }
 }
 
 // one colour of red-black Gauss-Seidel over the level (red: i + j even)
@@ -123,24 +168,32 @@ __device__ __forceinline__ void rbgs(const Lv<T>& L, int colour) {
     for (int c = threadIdx.x; c < n; c += blockDim.x) {
         int j = fdiv(c, L.hx, L.mhx);
         int i = 2 * (c - j * L.hx) + ((j + colour) & 1);
-        int P = j * L.nx + i;
-        L.dp[P] = (L.f[P] + offdiag(L.Tx, L.Tz, L.dp, P, i, j, L.nx, L.nz)) * L.invD[P];
+        L.dp[j * L.nx + i] = gs_value(L, j * L.nx + i, i, j);
     }
     __syncthreads();
 }
 
+// restricted residual (Eq. transfer, R = 1/4 sum of the children); after a
+// black half-sweep only the two red children carry a residual
 template <typename T>
-__device__ __forceinline__ void resid_restrict(const Lv<T>& F, const Lv<T>& C) {
+__device__ __forceinline__ void resid_restrict(const Lv<T>& F, const Lv<T>& C, bool red_only,
+                                               bool coarsest) {
     for (int c = threadIdx.x; c < C.nc; c += blockDim.x) {
         int J = fdiv(c, C.nx, C.mnx), I = c - J * C.nx;
-        T r[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            int i = 2 * I + (k & 1), j = 2 * J + (k >> 1);
-            int P = j * F.nx + i;
-            r[k] = F.f[P] - (F.D[P] * F.dp[P] - offdiag(F.Tx, F.Tz, F.dp, P, i, j, F.nx, F.nz));
+        int i = 2 * I, j = 2 * J, P = j * F.nx + i;
+        T r00 = residual(F, P, i, j);
+        T r11 = residual(F, P + F.nx + 1, i + 1, j + 1);
+        T sum;
+        if (red_only) {
+            sum = r00 + r11;
+        } else {
+            T r10 = residual(F, P + 1, i + 1, j);
+            T r01 = residual(F, P + F.nx, i, j + 1);
+            sum = r00 + r10 + r01 + r11;
         }
-        C.f[c] = T(0.25) * (r[0] + r[1] + r[2] + r[3]);
+        T fc = T(0.25) * sum;
+        if constexpr (Scaled<T>::value) { if (!coarsest) fc *= C.q[c]; }
+        C.f[c] = fc;
         C.dp[c] = T(0);
     }
     __syncthreads();
@@ -160,18 +213,19 @@ __device__ __forceinline__ void prolong(const Lv<T>& F, const Lv<T>& C) {
 // exact coarsest solve: Gaussian elimination of the assembled five-point
 // matrix by warp 0 in shared memory (symmetric, diagonally dominant)
 template <typename T>
-__device__ __forceinline__ void coarse_solve(const Lv<T>& L, T* A) {
+__device__ __forceinline__ void coarse_solve(int nx, int nz, const T* Tx, const T* Tz, const T* D,
+                                             const T* f, T* dp, T* A) {
     if (threadIdx.x < 32) {
-        const int nn = L.nc, ld = nn + 1, lane = threadIdx.x;
+        const int nn = nx * nz, ld = nn + 1, lane = threadIdx.x;
         for (int r = lane; r < nn; r += 32) {
             for (int c = 0; c < nn; ++c) A[r * ld + c] = T(0);
-            int j = r / L.nx, i = r - j * L.nx;
-            A[r * ld + r] = L.D[r];
-            if (i < L.nx - 1) A[r * ld + r + 1] = -L.Tx[r];
-            if (i > 0)        A[r * ld + r - 1] = -L.Tx[r - 1];
-            if (j < L.nz - 1) A[r * ld + r + L.nx] = -L.Tz[r];
-            if (j > 0)        A[r * ld + r - L.nx] = -L.Tz[r - L.nx];
-            A[r * ld + nn] = L.f[r];
+            int j = r / nx, i = r - j * nx;
+            A[r * ld + r] = D[r];
+            if (i < nx - 1) A[r * ld + r + 1] = -Tx[r];
+            if (i > 0)      A[r * ld + r - 1] = -Tx[r - 1];
+            if (j < nz - 1) A[r * ld + r + nx] = -Tz[r];
+            if (j > 0)      A[r * ld + r - nx] = -Tz[r - nx];
+            A[r * ld + nn] = f[r];
         }
         __syncwarp();
         for (int k = 0; k < nn; ++k) {
@@ -189,33 +243,52 @@ __device__ __forceinline__ void coarse_solve(const Lv<T>& L, T* A) {
             }
         }
         __syncwarp();
-        for (int r = lane; r < nn; r += 32) L.dp[r] = A[r * ld + nn];
+        for (int r = lane; r < nn; r += 32) dp[r] = A[r * ld + nn];
     }
     __syncthreads();
 }
 
+// f0: unscaled finest right-hand side, used by the direct solve when the
+// finest grid is also the coarsest (FP64 levels keep f/D otherwise)
 template <typename T>
-__device__ void vcycle(const Lv<T>* L, int nlev, int nu1, int nu2, T* A) {
+__device__ void vcycle(const Lv<T>* L, const Lv64* L64, int nlev, int nu1, int nu2, T* A,
+                       const T* f0) {
     for (int l = 0; l < nlev - 1; ++l) {
         for (int it = 0; it < nu1; ++it) { rbgs(L[l], 0); rbgs(L[l], 1); }
-        resid_restrict(L[l], L[l + 1]);
+        resid_restrict(L[l], L[l + 1], nu1 > 0, l + 1 == nlev - 1);
     }
-    coarse_solve(L[nlev - 1], A);
+    const int c = nlev - 1;
+    if constexpr (Scaled<T>::value)
+        coarse_solve<T>(L64[c].nx, L64[c].nz, L64[c].Tx, L64[c].Tz, L64[c].D, c == 0 ? f0 : L[c].f,
+                        L[c].dp, A);
+    else
+        coarse_solve<T>(L[c].nx, L[c].nz, L[c].c0, L[c].c1, L[c].D, L[c].f, L[c].dp, A);
     for (int l = nlev - 2; l >= 0; --l) {
         prolong(L[l], L[l + 1]);
         for (int it = 0; it < nu2; ++it) { rbgs(L[l], 0); rbgs(L[l], 1); }
     }
 }
 
-// ||f - A dp||_inf on a level (as an IEEE bit pattern)
+// ||f - A dp||_inf on a level after a cycle ending with a black half-sweep
+// (red cells only) or, with red_only false, over every cell
 template <typename T>
-__device__ __forceinline__ unsigned long long resid_norm(const Lv<T>& L, unsigned long long* red) {
+__device__ __forceinline__ unsigned long long resid_norm(const Lv<T>& L, bool red_only,
+                                                         unsigned long long* red) {
     unsigned long long m = 0;
-    for (int q = threadIdx.x; q < L.nc; q += blockDim.x) {
-        int j = fdiv(q, L.nx, L.mnx), i = q - j * L.nx;
-        double r = L.f[q] - (L.D[q] * L.dp[q] - offdiag(L.Tx, L.Tz, L.dp, q, i, j, L.nx, L.nz));
-        unsigned long long b = abs_bits(r);
-        m = b > m ? b : m;
+    if (red_only) {
+        const int n = L.hx * L.nz;
+        for (int c = threadIdx.x; c < n; c += blockDim.x) {
+            int j = fdiv(c, L.hx, L.mhx);
+            int i = 2 * (c - j * L.hx) + (j & 1);
+            unsigned long long b = abs_bits((double)residual(L, j * L.nx + i, i, j));
+            m = b > m ? b : m;
+        }
+    } else {
+        for (int q = threadIdx.x; q < L.nc; q += blockDim.x) {
+            int j = fdiv(q, L.nx, L.mnx), i = q - j * L.nx;
+            unsigned long long b = abs_bits((double)residual(L, q, i, j));
+            m = b > m ? b : m;
+        }
     }
     return block_max(m, red);
 }
@@ -223,35 +296,34 @@ __device__ __forceinline__ unsigned long long resid_norm(const Lv<T>& L, unsigne
 template <typename TM>
 __global__ void __launch_bounds__(512)
 k_fused(const FParams P) {
+    constexpr bool SC = Scaled<TM>::value;
     extern __shared__ unsigned char smraw[];
     TM* Amat = reinterpret_cast<TM*>(smraw);
     __shared__ unsigned long long red[33];
     __shared__ int s_sample;
+    __shared__ Lv64 L64[MAXL];
+    __shared__ Lv<TM> LM[MAXL];
     const int tid = threadIdx.x, nt = blockDim.x;
     char* slot = P.scratch + (size_t)blockIdx.x * P.slot_bytes;
     const int nlev = P.nlev;
     const bool mixed = P.mixed;
-
-    // level descriptors live in shared memory (one copy per CTA, broadcast reads)
-    __shared__ Lv64 L64[MAXL];
-    __shared__ Lv<TM> LM[MAXL];
     if (tid < nlev) {
         const int l = tid;
         Lv64& a = L64[l];
         a.nx = P.nx[l]; a.nz = P.nz[l]; a.nc = a.nx * a.nz; a.mnx = P.mnx[l];
-        double** pp[N64] = {&a.Tx, &a.Tz, &a.Cdt, &a.D, &a.invD, &a.f, &a.dp, &a.Tbt, &a.Tbb};
-        for (int k = 0; k < N64; ++k) *pp[k] = P.o64[l][k] >= 0 ? (double*)(slot + P.o64[l][k]) : nullptr;
+        double** pp[N64] = {&a.Tx, &a.Tz, &a.Cdt, &a.D, &a.Tbt, &a.Tbb};
+        for (int k = 0; k < N64; ++k) *pp[k] = (double*)(slot + P.o64[l][k]);
         Lv<TM>& b = LM[l];
         b.nx = a.nx; b.nz = a.nz; b.hx = a.nx >> 1; b.nc = a.nc; b.mnx = P.mnx[l]; b.mhx = P.mhx[l];
-        if (mixed) {
-            TM** qq[N32] = {&b.Tx, &b.Tz, &b.D, &b.invD, &b.f, &b.dp};
-            for (int k = 0; k < N32; ++k) *qq[k] = (TM*)(slot + P.o32[l][k]);
-        } else {
-            b.Tx = (TM*)a.Tx; b.Tz = (TM*)a.Tz; b.D = (TM*)a.D; b.invD = (TM*)a.invD;
-            b.f = (TM*)a.f; b.dp = (TM*)a.dp;
-        }
+        TM** qq[NMG] = {&b.c0, &b.c1, &b.c2, &b.c3, &b.q, &b.f, &b.dp};
+        for (int k = 0; k < NMG; ++k) *qq[k] = P.omg[l][k] >= 0 ? (TM*)(slot + P.omg[l][k]) : nullptr;
+        if constexpr (SC) b.D = (TM*)a.D;                 // FP64: shares the operator diagonal
+        else b.D = b.c3;                                  // FP32: its own copy
+        if constexpr (!SC) b.c3 = nullptr;
     }
     __syncthreads();
+    double* f64 = (double*)(slot + P.o_f64);
+    double* dp64 = SC ? (double*)LM[0].dp : (double*)(slot + P.o_dp64);
     double* p = (double*)(slot + P.o_p);
     double* thold = (double*)(slot + P.o_thold);
     double* Ks = (double*)(slot + P.o_Ks);
@@ -259,8 +331,9 @@ k_fused(const FParams P) {
     double* K = (double*)(slot + P.o_K);
     double* th = (double*)(slot + P.o_th);
     const Lv64& F = L64[0];
+    const Lv<TM>& M0 = LM[0];
     const int nx = F.nx, nz = F.nz, nc = F.nc;
-    const double h = P.h, t2h = P.two_over_h2, dt = P.dt, tr = P.tr, ts = P.ts;
+    const double h = P.h, t2h = P.two_over_h2, idt = P.inv_dt, tr = P.tr, ts = P.ts;
 
     for (;;) {
         if (tid == 0) s_sample = atomicAdd(P.queue, 1);
@@ -314,7 +387,7 @@ k_fused(const FParams P) {
                         double E = exp(a * pp);
                         K[q] = ks * E;
                         th[q] = tr + (ts - tr) * E;
-                        F.Cdt[q] = ((ts - tr) * a * E) / dt;
+                        F.Cdt[q] = ((ts - tr) * a * E) * idt;
                     } else {
                         K[q] = ks; th[q] = ts; F.Cdt[q] = 0.0;
                     }
@@ -333,23 +406,27 @@ k_fused(const FParams P) {
                 for (int q = tid; q < nc; q += nt) {
                     int j = fdiv(q, nx, F.mnx), i = q - j * nx;
                     double pp = p[q];
-                    double R = (th[q] - thold[q]) / dt;
+                    double R = (th[q] - thold[q]) * idt;
                     double d = F.Cdt[q];
-                    if (i < nx - 1) { double t = F.Tx[q];     R += -t * (p[q + 1] - pp); d += t; }
-                    if (i > 0)      { double t = F.Tx[q - 1]; R += -t * (p[q - 1] - pp); d += t; }
-                    if (j < nz - 1) { double t = F.Tz[q];     R += -t * (p[q + nx] - pp) - t * h; d += t; }
+                    double te = 0.0, tw = 0.0, tn = 0.0, tsf = 0.0;
+                    if (i < nx - 1) { te = F.Tx[q];     R += -te * (p[q + 1] - pp); d += te; }
+                    if (i > 0)      { tw = F.Tx[q - 1]; R += -tw * (p[q - 1] - pp); d += tw; }
+                    if (j < nz - 1) { tn = F.Tz[q];     R += -tn * (p[q + nx] - pp) - tn * h; d += tn; }
                     else { double t = F.Tbt[i]; R += -t * (P.p_top - pp) - t * h / 2.0; d += t; }
-                    if (j > 0)      { double t = F.Tz[q - nx]; R += -t * (p[q - nx] - pp) + t * h; d += t; }
+                    if (j > 0)      { tsf = F.Tz[q - nx]; R += -tsf * (p[q - nx] - pp) + tsf * h; d += tsf; }
                     else { double t = F.Tbb[i]; R += t * (pp - P.p_bot) + t * h / 2.0; d += t; }
-                    F.f[q] = -R;
                     F.D[q] = d;
-                    double inv = 1.0 / d;
-                    F.invD[q] = inv;
-                    F.dp[q] = 0.0;
-                    if (mixed) {
-                        LM[0].Tx[q] = (TM)F.Tx[q]; LM[0].Tz[q] = (TM)F.Tz[q];
-                        LM[0].D[q] = (TM)d; LM[0].invD[q] = (TM)(1.0f / (float)d);
-                        LM[0].f[q] = (TM)(-R); LM[0].dp[q] = TM(0);
+                    f64[q] = -R;
+                    dp64[q] = 0.0;
+                    if constexpr (SC) {
+                        double inv = 1.0 / d;
+                        M0.q[q] = inv;
+                        M0.c0[q] = te * inv; M0.c1[q] = tw * inv; M0.c2[q] = tn * inv; M0.c3[q] = tsf * inv;
+                        M0.f[q] = -R * inv;
+                    } else {
+                        M0.c0[q] = (TM)te; M0.c1[q] = (TM)tn; M0.D[q] = (TM)d;
+                        M0.q[q] = (TM)(1.0f / (float)d);
+                        M0.f[q] = (TM)(-R); M0.dp[q] = TM(0);
                     }
                     unsigned long long b = abs_bits(R);
                     m = b > m ? b : m;
@@ -359,24 +436,27 @@ k_fused(const FParams P) {
                 for (int l = 1; l < nlev; ++l) {
                     const Lv64& Fl = L64[l - 1];
                     const Lv64& Cl = L64[l];
+                    const Lv<TM>& Ml = LM[l];
                     const int fx = Fl.nx;
                     for (int c = tid; c < Cl.nc; c += nt) {
                         int J = fdiv(c, Cl.nx, Cl.mnx), I = c - J * Cl.nx;
                         int f00 = (2 * J) * fx + 2 * I, f01 = f00 + fx;
                         double cd = 0.25 * (Fl.Cdt[f00] + Fl.Cdt[f00 + 1] + Fl.Cdt[f01] + Fl.Cdt[f01 + 1]);
-                        double d = cd, te = 0.0, tn = 0.0;
+                        double d = cd, te = 0.0, tw = 0.0, tn = 0.0, tsf = 0.0;
                         if (I < Cl.nx - 1) { te = 0.25 * (0.5 * (Fl.Tx[f00 + 1] + Fl.Tx[f01 + 1])); d += te; }
-                        if (I > 0)         { d += 0.25 * (0.5 * (Fl.Tx[f00 - 1] + Fl.Tx[f01 - 1])); }
+                        if (I > 0)         { tw = 0.25 * (0.5 * (Fl.Tx[f00 - 1] + Fl.Tx[f01 - 1])); d += tw; }
                         if (J < Cl.nz - 1) { tn = 0.25 * (0.5 * (Fl.Tz[f01] + Fl.Tz[f01 + 1])); d += tn; }
                         else d += Cl.Tbt[I];
-                        if (J > 0)         { d += 0.25 * (0.5 * (Fl.Tz[f00 - fx] + Fl.Tz[f00 - fx + 1])); }
+                        if (J > 0)         { tsf = 0.25 * (0.5 * (Fl.Tz[f00 - fx] + Fl.Tz[f00 - fx + 1])); d += tsf; }
                         else d += Cl.Tbb[I];
                         Cl.Tx[c] = te; Cl.Tz[c] = tn; Cl.Cdt[c] = cd; Cl.D[c] = d;
-                        if (mixed) {
-                            LM[l].Tx[c] = (TM)te; LM[l].Tz[c] = (TM)tn; LM[l].D[c] = (TM)d;
-                            LM[l].invD[c] = (TM)(1.0f / (float)d);
+                        if constexpr (SC) {
+                            double inv = 1.0 / d;
+                            Ml.q[c] = inv;
+                            Ml.c0[c] = te * inv; Ml.c1[c] = tw * inv; Ml.c2[c] = tn * inv; Ml.c3[c] = tsf * inv;
                         } else {
-                            Cl.invD[c] = 1.0 / d;
+                            Ml.c0[c] = (TM)te; Ml.c1[c] = (TM)tn; Ml.D[c] = (TM)d;
+                            Ml.q[c] = (TM)(1.0f / (float)d);
                         }
                     }
                     __syncthreads();
@@ -389,29 +469,36 @@ k_fused(const FParams P) {
                 int cyc = 0;
                 bool nonfinite = false;
                 while (rn >= target && cyc < P.mg_maxit) {
-                    vcycle<TM>(LM, nlev, P.nu1, P.nu2, Amat);
                     unsigned long long rb;
-                    if (!mixed) {
-                        rb = resid_norm<TM>(LM[0], red);
+                    if constexpr (SC) {
+                        vcycle<TM>(LM, L64, nlev, P.nu1, P.nu2, Amat, (const TM*)f64);
+                        ++cyc;
+                        rb = resid_norm<TM>(M0, P.nu2 > 0 && nlev > 1, red);
                     } else {
-                        // dp += e (FP64), then the FP64 defect: stopping norm and
-                        // the next FP32 right-hand side
-                        unsigned long long mm = 0;
-                        for (int q = tid; q < nc; q += nt) {
-                            F.dp[q] += (double)LM[0].dp[q];
+                        for (int in = 0; in < MIXED_INNER && cyc < P.mg_maxit; ++in) {
+                            vcycle<TM>(LM, L64, nlev, P.nu1, P.nu2, Amat, nullptr);
+                            ++cyc;
                         }
+                        // dp += e in FP64, then the FP64 defect: stopping norm and the
+                        // next FP32 right-hand side
+                        unsigned long long mm = 0;
+                        for (int q = tid; q < nc; q += nt) dp64[q] += (double)M0.dp[q];
                         __syncthreads();
                         for (int q = tid; q < nc; q += nt) {
                             int j = fdiv(q, nx, F.mnx), i = q - j * nx;
-                            double r = F.f[q] - (F.D[q] * F.dp[q] - offdiag(F.Tx, F.Tz, F.dp, q, i, j, nx, nz));
-                            LM[0].f[q] = (TM)r;
-                            LM[0].dp[q] = TM(0);
+                            double sn = 0.0;
+                            if (i < nx - 1) sn += F.Tx[q] * dp64[q + 1];
+                            if (i > 0)      sn += F.Tx[q - 1] * dp64[q - 1];
+                            if (j < nz - 1) sn += F.Tz[q] * dp64[q + nx];
+                            if (j > 0)      sn += F.Tz[q - nx] * dp64[q - nx];
+                            double r = f64[q] - (F.D[q] * dp64[q] - sn);
+                            M0.f[q] = (TM)r;
+                            M0.dp[q] = TM(0);
                             unsigned long long b = abs_bits(r);
                             mm = b > mm ? b : mm;
                         }
                         rb = block_max(mm, red);
                     }
-                    ++cyc;
                     if (rb > INF_BITS - 1) { nonfinite = true; break; }
                     rn = __longlong_as_double((long long)rb);
                 }
@@ -421,7 +508,7 @@ k_fused(const FParams P) {
                 // ---- p^{k+1} = p^k + dp, ||dp||_inf
                 unsigned long long dm = 0;
                 for (int q = tid; q < nc; q += nt) {
-                    double d = F.dp[q];
+                    double d = dp64[q];
                     p[q] += d;
                     unsigned long long b = abs_bits(d);
                     dm = b > dm ? b : dm;
@@ -474,23 +561,24 @@ static int fused_setup(const rich_problem_t* pb, int S, FParams& P) {
     P.S = S; P.nlev = nlev; P.mixed = mixed;
     size_t off = 0;
     int lx = pb->nx, lz = pb->nz;
+    const size_t w = mixed ? 4 : 8;
     for (int l = 0; l < nlev; ++l) {
         P.nx[l] = lx; P.nz[l] = lz; P.mnx[l] = magic(lx); P.mhx[l] = magic(lx / 2);
-        const size_t nc8 = (size_t)lx * lz * 8;
+        const size_t nc = (size_t)lx * lz;
         for (int k = 0; k < N64; ++k) {
-            size_t bytes = (k == A_TBT || k == A_TBB) ? (size_t)lx * 8 : nc8;
-            bool need = true;
-            if (mixed && (k == A_F || k == A_DP || k == A_INVD) && l > 0) need = false;
-            if (need) { P.o64[l][k] = (long long)off; off = al256(off + bytes); }
-            else P.o64[l][k] = -1;
+            size_t bytes = (k == A_TBT || k == A_TBB) ? (size_t)lx * 8 : nc * 8;
+            P.o64[l][k] = (long long)off; off = al256(off + bytes);
         }
-        for (int k = 0; k < N32; ++k) {
-            if (mixed) { P.o32[l][k] = (long long)off; off = al256(off + (size_t)lx * lz * 4); }
-            else P.o32[l][k] = -1;
+        for (int k = 0; k < NMG; ++k) {
+            // FP64: wE wW wN wS q f dp ; FP32: Tx Tz - D q f dp (slot B_2 unused)
+            if (mixed && k == B_2) { P.omg[l][k] = -1; continue; }
+            P.omg[l][k] = (long long)off; off = al256(off + nc * w);
         }
         lx /= 2; lz /= 2;
     }
     const size_t nc8 = (size_t)pb->nx * pb->nz * 8;
+    P.o_f64 = off; off = al256(off + nc8);
+    if (mixed) { P.o_dp64 = off; off = al256(off + nc8); } else P.o_dp64 = -1;
     P.o_p = off; off = al256(off + nc8);
     P.o_thold = off; off = al256(off + nc8);
     P.o_Ks = off; off = al256(off + nc8);
@@ -500,8 +588,8 @@ static int fused_setup(const rich_problem_t* pb, int S, FParams& P) {
     P.slot_bytes = (long long)off;
     P.nsteps = pb->nsteps; P.picard_maxit = pb->picard_maxit; P.mg_maxit = pb->mg_maxit;
     P.nu1 = pb->nu1; P.nu2 = pb->nu2;
-    P.dt = pb->dt; P.tr = pb->theta_r; P.ts = pb->theta_s; P.p_top = pb->p_top; P.p_bot = pb->p_bottom;
-    P.p_init = pb->p_init; P.picard_tol = pb->picard_tol; P.mg_tol = pb->mg_tol;
+    P.inv_dt = 1.0 / pb->dt; P.tr = pb->theta_r; P.ts = pb->theta_s; P.p_top = pb->p_top;
+    P.p_bot = pb->p_bottom; P.p_init = pb->p_init; P.picard_tol = pb->picard_tol; P.mg_tol = pb->mg_tol;
     P.h = 1.0 / pb->nz; P.two_over_h2 = 2.0 / (P.h * P.h);
     return 0;
 }
