@@ -148,6 +148,55 @@ def run_reference(args):
     }))
 
 
+MLMC_LEVELS = dict(nsamples=(20000, 5000, 1200, 300, 80), n0=16, steps0=5, t_final=0.1)
+
+
+def run_mlmc(args):
+    """Parametric-continuation MLMC over 16^2..256^2 (5 levels, N_l = 20000, 5000,
+    1200, 300, 80; 5 2^l steps to T = 0.1): reports V_l, C_l and the cost W(eps)
+    to RMSE 1e-3 from the measured V_l and C_l (Eq. MLMCSAMP_ch6)."""
+    import torch
+    import paper_1903_08741_gb300 as R
+    from paper_1903_08741_gb300 import build as B
+    B.build()
+    torch.cuda.set_device(0)
+    prec = R.MIXED if args.precision == "mixed" else R.FP64
+    cfg = R.MlmcConfig(**MLMC_LEVELS, coupling=args.coupling, eps=1e-3,
+                       problem=R.Problem(precision=prec, **PHYS))
+    for k in range(args.warmup):
+        small = R.MlmcConfig(nsamples=(64, 32, 16, 8, 4), n0=16, steps0=5, t_final=0.1,
+                             coupling=args.coupling, key_offset=100 + k,
+                             problem=R.Problem(precision=prec, **PHYS))
+        R.mlmc_estimate(small)
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = R.launch_count()
+    res = []
+    for k in range(args.steps):
+        cfg.key_offset = 10 * k
+        res.append(R.mlmc_estimate(cfg))
+    launches = R.launch_count() - l0
+    clk = clocks.stop()
+    r = res[-1]
+    secs = sum(x["seconds"] for x in res) / len(res)
+    out = {
+        "metric": "MLMC cost to RMSE 1e-3 (s)", "value": r["w_eps"], "unit": "s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == R.FP64 else "f32-in-f64", "data": "synthetic",
+        "config": {"workload": "mlmc5: 16^2..256^2, N_l = 20000/5000/1200/300/80, 5*2^l steps to T=0.1, "
+                               "alpha_l = alpha (l+1)/5, exp. cov. 0.3, seed 0",
+                   "coupling": "finest-grid draw, 2x2 averages" if args.coupling == 0 else "level-grid draw"},
+        "clocks": clk, "gpu_launches": launches,
+        "levels": {k: r[k] for k in ("n", "failed", "mean", "var", "cost", "cost_fine", "n_opt",
+                                     "mean_f", "var_f")},
+        "estimate": r["estimate"], "rmse": r["rmse"], "ml_variance": r["ml_variance"],
+        "w_mc_eps_s": r["w_mc_eps"], "mc_over_mlmc": r["w_mc_eps"] / r["w_eps"],
+        "bias_estimate": r["bias_estimate"], "run_seconds": secs,
+    }
+    print(json.dumps(out))
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -298,7 +347,8 @@ def main():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="mc128")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["mlmc5"], default="mc128")
+    ap.add_argument("--coupling", type=int, default=0, help="MLMC field coupling (0 exact, 1 level grid)")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
@@ -311,6 +361,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "mlmc5":
+        run_mlmc(args)
     else:
         run_ours(args)
 

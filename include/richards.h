@@ -116,6 +116,55 @@ int rich_solve_batch_host(rich_ctx_t ctx, const rich_problem_t* pb, int32_t nsam
                           double* qoi, double* p_final, int32_t* status, rich_stats_t* stats,
                           void* stream);
 
+/* Multilevel Monte Carlo with parametric continuation (Sec. 5, Eqs.
+ * telescope_ch6, MLMCestimator_ch6, SMC_ch6, MC_var_ch6, ML_var_ch6,
+ * eq:MLMCVar, MLMCSAMP_ch6).  Level l (0..L) pairs a fine solve on an
+ * (n0 2^l)^2 grid with steps0 2^l time steps of dt_l = t_final/(steps0 2^l)
+ * and nonlinearity alpha_l with a coarse solve on the level-(l-1) grid, time
+ * step and nonlinearity, both from ONE seeded random draw (the coarse member
+ * uses its 2x2 block means).  With continuation, alpha_l = alpha (l+1)/(L+1):
+ * only the finest level carries the full alpha field. */
+#define RICH_MLMC_MAX_LEVELS 8
+typedef struct {
+    rich_problem_t base;      /* physics and solver settings; nx, nz, nsteps, dt are set per level */
+    rich_field_t field;
+    int32_t nlevels;          /* L + 1, at most RICH_MLMC_MAX_LEVELS                      */
+    int32_t n0;               /* cells per side on level 0                                */
+    int32_t steps0;           /* time steps on level 0                                    */
+    double t_final;
+    int32_t nsamples[RICH_MLMC_MAX_LEVELS];  /* N_l                                       */
+    int32_t coupling;         /* 0: draw on the finest grid and average down (every level's
+                                 fine member has the law of the next level's coarse member,
+                                 so the telescoping sum is exact, Eq. fine_coarse);
+                                 1: draw on the pair's fine grid (cheaper, not exact)      */
+    int32_t continuation;     /* 1: alpha_l = alpha (l+1)/(L+1); 0: alpha on every level   */
+    int32_t batch;            /* samples per batch, 0 = automatic                          */
+    double eps;               /* RMSE target of the optimal-allocation report              */
+    uint32_t key_offset;      /* added to the level in the noise key (independent reruns)  */
+} rich_mlmc_cfg_t;
+
+typedef struct {
+    int32_t nlevels;
+    int64_t n[RICH_MLMC_MAX_LEVELS], failed[RICH_MLMC_MAX_LEVELS];
+    double mean[RICH_MLMC_MAX_LEVELS], var[RICH_MLMC_MAX_LEVELS];      /* Y_l = Q_l - Q_{l-1} */
+    double mean_f[RICH_MLMC_MAX_LEVELS], var_f[RICH_MLMC_MAX_LEVELS];  /* Q_l (fine member)   */
+    double mean_c[RICH_MLMC_MAX_LEVELS], var_c[RICH_MLMC_MAX_LEVELS];  /* Q_{l-1} (coarse)    */
+    double cost[RICH_MLMC_MAX_LEVELS];        /* GPU seconds per pair (fields + both solves) */
+    double cost_fine[RICH_MLMC_MAX_LEVELS];   /* seconds per single fine solve (fields + solve) */
+    double n_opt[RICH_MLMC_MAX_LEVELS];       /* Eq. MLMCSAMP_ch6 for eps                 */
+    double estimate;          /* sum of level means (Eq. MLMCestimator_ch6)              */
+    double rmse;              /* sqrt(sum V_l / N_l) (Eq. eq:MLMCVar)                    */
+    double ml_variance;       /* sum V[Q_l] - V[Q_{l-1}] (Eq. ML_var_ch6)                */
+    double w_eps;             /* eps^-2 (sum sqrt(V_l C_l))^2: seconds to RMSE eps        */
+    double w_mc_eps;          /* plain MC at the finest level: V[Q_L] C_L,fine / eps^2   */
+    double bias_estimate;     /* |E Y_L| / (2^1 - 1): first-order bias bound (Eq. discErr) */
+    double seconds;           /* wall time of the call                                   */
+} rich_mlmc_result_t;
+
+/* Run the estimator with the configured N_l and fill *out (HOST).  Synchronous;
+ * device memory is allocated and freed inside the call. */
+int rich_mlmc_estimate(rich_ctx_t ctx, const rich_mlmc_cfg_t* cfg, rich_mlmc_result_t* out);
+
 /* MC / MLMC level accumulation in FP64 on the device (Sec. 5, Eqs. SMC_ch6,
  * MC_var_ch6, ML_var_ch6): for i < n with Y_i = qoi_fine[i] - qoi_coarse[i]
  * (qoi_coarse NULL: Y_i = qoi_fine[i], the plain MC or level-0 term), adds to

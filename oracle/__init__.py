@@ -239,3 +239,42 @@ def optimal_samples(levels, eps):
     n_opt = [eps ** -2 * s * np.sqrt(L.var / L.cost) for L in levels]
     w = eps ** -2 * s * s
     return n_opt, w
+
+
+def mlmc_estimate(nsamples, n0, steps0, t_final, seed=0, coupling=0, continuation=1, key_offset=0,
+                  sigma2=1.0, corr_len=0.3, alpha_lo=0.5, alpha_span=1.5, nthreads=None, **phys):
+    """Parametric-continuation MLMC (Sec. 5) restated plainly: for level l draw
+    N_l field pairs (coupling 0: on the finest grid, averaged down L-l times;
+    coupling 1: on the level grid), solve the fine member on grid n0 2^l with
+    steps0 2^l steps and alpha_l, the coarse member on the 2x2-averaged fields
+    with the level-(l-1) grid, steps and alpha_{l-1}; Y_l = Q_l - Q_{l-1}.
+    Returns per-level Y, Qf, Qc, statuses and the level statistics."""
+    NL = len(nsamples)
+    L = NL - 1
+    nL = n0 << L
+    out = []
+    for l in range(NL):
+        M = n0 << l
+        scale = lambda k: (k + 1) / NL if continuation else 1.0
+        if coupling == 0:
+            lk, al = sample_fields(nL, nL, nsamples[l], seed=seed, level=l + key_offset, coarsen_times=L - l,
+                                   sigma2=sigma2, corr_len=corr_len, alpha_lo=alpha_lo,
+                                   alpha_span=alpha_span, nthreads=nthreads)
+        else:
+            lk, al = sample_fields(M, M, nsamples[l], seed=seed, level=l + key_offset, sigma2=sigma2,
+                                   corr_len=corr_len, alpha_lo=alpha_lo, alpha_span=alpha_span,
+                                   nthreads=nthreads)
+        pf = make_problem(nsteps=steps0 << l, dt=t_final / (steps0 << l), **phys)
+        _, qf, sf, _ = solve_batch(pf, lk, al, scale(l), want_p=False, nthreads=nthreads)
+        if l > 0:
+            blk = lambda x: x.reshape(x.shape[0], M // 2, 2, M // 2, 2).mean(axis=(2, 4))
+            lkc, alc = blk(lk), blk(al)
+            pc = make_problem(nsteps=steps0 << (l - 1), dt=t_final / (steps0 << (l - 1)), **phys)
+            _, qc, sc, _ = solve_batch(pc, lkc, alc, scale(l - 1), want_p=False, nthreads=nthreads)
+        else:
+            qc, sc = np.zeros_like(qf), np.zeros_like(sf)
+        bad = np.isin(sf, (PICARD_MAXIT, NONFINITE)) | np.isin(sc, (PICARD_MAXIT, NONFINITE)) \
+            | ~np.isfinite(qf) | ~np.isfinite(qc)
+        y = (qf - qc)[~bad]
+        out.append(dict(y=y, qf=qf[~bad], qc=qc[~bad], failed=int(bad.sum()), status_f=sf, status_c=sc))
+    return out

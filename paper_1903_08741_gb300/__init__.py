@@ -83,6 +83,58 @@ class FieldModel:
         return _Field(self.sigma2, self.corr_len, self.alpha_lo, self.alpha_span, self.seed)
 
 
+MLMC_MAX_LEVELS = 8
+
+
+class _MlmcCfg(C.Structure):
+    _fields_ = [("base", _Problem), ("field", _Field), ("nlevels", C.c_int32), ("n0", C.c_int32),
+                ("steps0", C.c_int32), ("t_final", C.c_double),
+                ("nsamples", C.c_int32 * MLMC_MAX_LEVELS), ("coupling", C.c_int32),
+                ("continuation", C.c_int32), ("batch", C.c_int32), ("eps", C.c_double),
+                ("key_offset", C.c_uint32)]
+
+
+_LV = C.c_double * MLMC_MAX_LEVELS
+_LI = C.c_int64 * MLMC_MAX_LEVELS
+
+
+class _MlmcResult(C.Structure):
+    _fields_ = [("nlevels", C.c_int32), ("n", _LI), ("failed", _LI), ("mean", _LV), ("var", _LV),
+                ("mean_f", _LV), ("var_f", _LV), ("mean_c", _LV), ("var_c", _LV), ("cost", _LV),
+                ("cost_fine", _LV), ("n_opt", _LV), ("estimate", C.c_double), ("rmse", C.c_double),
+                ("ml_variance", C.c_double), ("w_eps", C.c_double), ("w_mc_eps", C.c_double),
+                ("bias_estimate", C.c_double), ("seconds", C.c_double)]
+
+
+@dataclass
+class MlmcConfig:
+    """Levels l = 0..L: grid n0 2^l, steps0 2^l steps of t_final/(steps0 2^l),
+    alpha_l = alpha (l+1)/(L+1) with continuation (Sec. 5)."""
+    nsamples: tuple = (20000, 5000, 1200, 300, 80)
+    n0: int = 16
+    steps0: int = 5
+    t_final: float = 0.1
+    coupling: int = 0
+    continuation: int = 1
+    batch: int = 0
+    eps: float = 1e-3
+    key_offset: int = 0
+    problem: Problem = field(default_factory=Problem)
+    model: FieldModel = field(default_factory=FieldModel)
+
+    def _c(self):
+        c = _MlmcCfg()
+        c.base = self.problem._c()
+        c.field = self.model._c()
+        c.nlevels = len(self.nsamples)
+        c.n0, c.steps0, c.t_final = self.n0, self.steps0, self.t_final
+        for l, n in enumerate(self.nsamples):
+            c.nsamples[l] = n
+        c.coupling, c.continuation, c.batch, c.eps = self.coupling, self.continuation, self.batch, self.eps
+        c.key_offset = self.key_offset
+        return c
+
+
 @dataclass
 class Stats:
     picard_iters: int = 0
@@ -118,6 +170,7 @@ def lib():
         L.rich_profile_read.argtypes = [vp, C.POINTER(dbl), C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl)]
         L.rich_launch_count.restype = i64
         L.rich_solve_batch_noalloc.argtypes = [C.POINTER(_Problem), i32, vp, vp, dbl, vp, vp, vp]
+        L.rich_mlmc_estimate.argtypes = [vp, C.POINTER(_MlmcCfg), C.POINTER(_MlmcResult)]
         _lib = L
     return _lib
 
@@ -126,7 +179,7 @@ def exported_symbols():
     return ["rich_create", "rich_destroy", "rich_status_str", "rich_last_error",
             "rich_sample_fields", "rich_solve_batch", "rich_solve_batch_host",
             "rich_mlmc_accumulate", "rich_profile", "rich_profile_read", "rich_launch_count",
-            "rich_solve_batch_noalloc"]
+            "rich_solve_batch_noalloc", "rich_mlmc_estimate"]
 
 
 def _check(rc):
@@ -270,3 +323,17 @@ def solve_batch_noalloc(problem: Problem, lnKs, alpha, alpha_scale=1.0, qoi=None
                                           _dev_ptr(status, torch.int32, "status"),
                                           _stream(torch, lnKs.device.index)))
     return qoi, status
+
+
+def mlmc_estimate(cfg: MlmcConfig, device=0):
+    """Multilevel Monte Carlo with parametric continuation on one GPU (host result)."""
+    _torch()
+    r = _MlmcResult()
+    rc = _check(lib().rich_mlmc_estimate(context(device), C.byref(cfg._c()), C.byref(r)))
+    NL = r.nlevels
+    out = {k: list(getattr(r, k))[:NL] for k in ("n", "failed", "mean", "var", "mean_f", "var_f", "mean_c",
+                                                  "var_c", "cost", "cost_fine", "n_opt")}
+    out.update({k: getattr(r, k) for k in ("estimate", "rmse", "ml_variance", "w_eps", "w_mc_eps",
+                                            "bias_estimate", "seconds")})
+    out["nlevels"], out["rc"] = NL, rc
+    return out

@@ -119,8 +119,8 @@ extern "C" int rich_create(rich_ctx_t* out, int device) {
 extern "C" void rich_destroy(rich_ctx_t ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
-    if (ctx->ws.base) cudaFree(ctx->ws.base);
-    if (ctx->ws.h_counters) cudaFreeHost(ctx->ws.h_counters);
+    if (ctx->sb.base) cudaFree(ctx->sb.base);
+    if (ctx->stage) cudaFree(ctx->stage);
     if (ctx->fws.sqrt_lambda) cudaFree(ctx->fws.sqrt_lambda);
     if (ctx->fws.work) cudaFree(ctx->fws.work);
     if (ctx->fws.tw) cudaFree(ctx->fws.tw);
@@ -171,10 +171,10 @@ extern "C" int rich_solve_batch_host(rich_ctx_t ctx, const rich_problem_t* pb, i
     if (!lnKs || !alpha || !qoi) return RICH_ERR_INVALID;
     RICH_CUDA(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
-    int e = rich_ws_reserve(ctx, nsamples, pb->nx, pb->nz, pb->precision == RICH_MIXED);
-    if (e) return e;
     const size_t nc = (size_t)nsamples * pb->nx * pb->nz;
-    double* d_lk = ctx->ws.h_in;
+    int e = rich_stage_reserve(ctx, 3 * nc * 8 + (size_t)nsamples * 12 + 256);
+    if (e) return e;
+    double* d_lk = (double*)ctx->stage;
     double* d_al = d_lk + nc;
     double* d_p = d_al + nc;
     double* d_q = d_p + nc;

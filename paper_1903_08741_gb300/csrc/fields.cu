@@ -302,3 +302,16 @@ int rich_fields_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int nz, ui
     RICH_CUDA(cudaGetLastError());
     return 0;
 }
+
+// 2x2 block means of both fields (the coarse member of an MLMC pair)
+int rich_fields_average(rich_ctx* ctx, int S, int nx, int nz, const double* lk, const double* al,
+                        double* lkc, double* alc, cudaStream_t st) {
+    (void)ctx;
+    if (nx % 2 || nz % 2) return RICH_ERR_INVALID;
+    if (S == 0) return 0;
+    const int ncx = nx / 2, ncz = nz / 2;
+    rich_count_launch();
+    k_avg2<<<nb((long long)S * ncx * ncz), 256, 0, st>>>(S, ncx, ncz, lk, al, lkc, alc);
+    RICH_CUDA(cudaGetLastError());
+    return 0;
+}

@@ -623,7 +623,7 @@ static int fused_launch(const FParams& P, int grid, size_t smem, cudaStream_t st
 int rich_solve_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const double* lnKs,
                      const double* alpha, double alpha_scale, double* qoi, double* p_final,
                      int32_t* status, cudaStream_t st) {
-    rich_ws& w = ctx->ws;
+    rich_samplebuf& w = ctx->sb;
     FParams P;
     if (int e = fused_setup(pb, S, P)) return e;
     const size_t off = (size_t)P.slot_bytes;

@@ -53,3 +53,136 @@ extern "C" int rich_mlmc_accumulate(rich_ctx_t ctx, const double* qoi_fine, cons
     RICH_CUDA(cudaGetLastError());
     return 0;
 }
+
+// ------------------------------------------------------------------ estimator
+#include <chrono>
+#include <math.h>
+#include <vector>
+#include <algorithm>
+
+namespace {
+struct DevBuf {
+    void* p = nullptr;
+    ~DevBuf() { if (p) cudaFree(p); }
+};
+}
+
+extern "C" int rich_mlmc_estimate(rich_ctx_t ctx, const rich_mlmc_cfg_t* cfg, rich_mlmc_result_t* out) {
+    if (!ctx || !cfg || !out) return RICH_ERR_INVALID;
+    const int NL = cfg->nlevels, L = NL - 1;
+    if (NL < 1 || NL > RICH_MLMC_MAX_LEVELS || cfg->n0 < 2 || cfg->steps0 < 1 || !(cfg->t_final > 0) ||
+        (cfg->coupling != 0 && cfg->coupling != 1))
+        return RICH_ERR_INVALID;
+    for (int l = 0; l < NL; ++l)
+        if (cfg->nsamples[l] < 2) return RICH_ERR_INVALID;
+    RICH_CUDA(cudaSetDevice(ctx->device));
+    auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t st = nullptr;
+    RICH_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    struct StreamGuard { cudaStream_t s; ~StreamGuard() { cudaStreamDestroy(s); } } sg{st};
+    const int nL = cfg->n0 << L;
+    auto grid = [&](int l) { return cfg->n0 << l; };
+    auto steps = [&](int l) { return cfg->steps0 << l; };
+    auto ascale = [&](int l) { return cfg->continuation ? (double)(l + 1) / (double)NL : 1.0; };
+    int maxB = 0;
+    for (int l = 0; l < NL; ++l) maxB = std::max(maxB, cfg->nsamples[l]);
+    int B = cfg->batch > 0 ? cfg->batch : (int)std::max<long long>(1, (1ll << 31) / (16ll * nL * nL));
+    B = std::min(B, maxB);
+    const size_t fine_cells = (size_t)B * nL * nL;          // worst case: level L fine member
+    DevBuf lkf, alf, lkc, alc, qf, qc, sf, sc, acc;
+    auto dalloc = [&](DevBuf& b, size_t bytes) -> int {
+        cudaError_t e = cudaMalloc(&b.p, std::max<size_t>(bytes, 256));
+        if (e != cudaSuccess) { cudaGetLastError(); return RICH_ERR_OOM; }
+        return 0;
+    };
+    if (dalloc(lkf, fine_cells * 8) || dalloc(alf, fine_cells * 8) || dalloc(lkc, fine_cells * 2) ||
+        dalloc(alc, fine_cells * 2) || dalloc(qf, B * 8) || dalloc(qc, B * 8) || dalloc(sf, B * 4) ||
+        dalloc(sc, B * 4) || dalloc(acc, 8 * 8 * NL))
+        return RICH_ERR_OOM;
+    RICH_CUDA(cudaMemsetAsync(acc.p, 0, 8 * 8 * NL, st));
+    cudaEvent_t ev[4];
+    for (auto& e : ev) RICH_CUDA(cudaEventCreate(&e));
+    struct EvGuard { cudaEvent_t* e; ~EvGuard() { for (int k = 0; k < 4; ++k) cudaEventDestroy(e[k]); } } eg{ev};
+    std::vector<double> t_pair(NL, 0.0), t_fine(NL, 0.0);
+    int worst = 0;
+    for (int l = 0; l < NL; ++l) {
+        const int M = grid(l), nsl = cfg->nsamples[l];
+        rich_problem_t pf = cfg->base;
+        pf.nx = pf.nz = M; pf.nsteps = steps(l); pf.dt = cfg->t_final / steps(l);
+        rich_problem_t pc = cfg->base;
+        if (l > 0) { pc.nx = pc.nz = grid(l - 1); pc.nsteps = steps(l - 1); pc.dt = cfg->t_final / steps(l - 1); }
+        const int ndraw = cfg->coupling == 0 ? nL : M;
+        const int coarsen = cfg->coupling == 0 ? L - l : 0;
+        for (int b0 = 0; b0 < nsl; b0 += B) {
+            const int nb = std::min(B, nsl - b0);
+            RICH_CUDA(cudaEventRecord(ev[0], st));
+            int e = rich_fields_device(ctx, &cfg->field, ndraw, ndraw, (uint32_t)l + cfg->key_offset, b0, nb,
+                                       coarsen, (double*)lkf.p, (double*)alf.p, st);
+            if (e) return e;
+            if (l > 0) {
+                e = rich_fields_average(ctx, nb, M, M, (double*)lkf.p, (double*)alf.p, (double*)lkc.p,
+                                        (double*)alc.p, st);
+                if (e) return e;
+            }
+            RICH_CUDA(cudaEventRecord(ev[1], st));
+            int rc = rich_solve_device(ctx, &pf, nb, (double*)lkf.p, (double*)alf.p, ascale(l), (double*)qf.p,
+                                       nullptr, (int32_t*)sf.p, nullptr, st);
+            if (rc < 0) return rc;
+            worst = std::max(worst, rc);
+            RICH_CUDA(cudaEventRecord(ev[2], st));
+            if (l > 0) {
+                rc = rich_solve_device(ctx, &pc, nb, (double*)lkc.p, (double*)alc.p, ascale(l - 1), (double*)qc.p,
+                                       nullptr, (int32_t*)sc.p, nullptr, st);
+                if (rc < 0) return rc;
+                worst = std::max(worst, rc);
+            }
+            e = rich_mlmc_accumulate(ctx, (double*)qf.p, l > 0 ? (double*)qc.p : nullptr, (int32_t*)sf.p,
+                                     l > 0 ? (int32_t*)sc.p : nullptr, nb, (double*)acc.p + 8 * l, st);
+            if (e) return e;
+            RICH_CUDA(cudaEventRecord(ev[3], st));
+            RICH_CUDA(cudaEventSynchronize(ev[3]));
+            float a = 0, b = 0, c = 0;
+            RICH_CUDA(cudaEventElapsedTime(&a, ev[0], ev[1]));
+            RICH_CUDA(cudaEventElapsedTime(&b, ev[1], ev[2]));
+            RICH_CUDA(cudaEventElapsedTime(&c, ev[2], ev[3]));
+            t_pair[l] += 1e-3 * (a + b + c);
+            t_fine[l] += 1e-3 * (a + b);   // one draw + one fine solve (plain MC sample)
+        }
+    }
+    std::vector<double> h(8 * NL);
+    RICH_CUDA(cudaMemcpyAsync(h.data(), acc.p, 8 * 8 * NL, cudaMemcpyDeviceToHost, st));
+    RICH_CUDA(cudaStreamSynchronize(st));
+    rich_mlmc_result_t r{};
+    r.nlevels = NL;
+    double rmse2 = 0, ssum = 0;
+    for (int l = 0; l < NL; ++l) {
+        const double* a = &h[8 * l];
+        const double n = a[2];
+        r.n[l] = (int64_t)n; r.failed[l] = (int64_t)a[3];
+        auto mv = [&](double s1, double s2, double* m, double* v) {
+            *m = n > 0 ? s1 / n : NAN;
+            *v = n > 1 ? (s2 - n * (*m) * (*m)) / (n - 1) : NAN;
+        };
+        mv(a[0], a[1], &r.mean[l], &r.var[l]);
+        mv(a[4], a[5], &r.mean_f[l], &r.var_f[l]);
+        if (l > 0) mv(a[6], a[7], &r.mean_c[l], &r.var_c[l]);
+        r.cost[l] = t_pair[l] / cfg->nsamples[l];
+        r.cost_fine[l] = t_fine[l] / cfg->nsamples[l];
+        r.estimate += r.mean[l];
+        rmse2 += r.var[l] / n;
+        r.ml_variance += r.var_f[l] - (l > 0 ? r.var_c[l] : 0.0);
+        ssum += sqrt(std::max(r.var[l], 0.0) * r.cost[l]);
+    }
+    r.rmse = sqrt(rmse2);
+    if (cfg->eps > 0) {
+        const double e2 = cfg->eps * cfg->eps;
+        for (int l = 0; l < NL; ++l)
+            r.n_opt[l] = ssum * sqrt(std::max(r.var[l], 0.0) / r.cost[l]) / e2;
+        r.w_eps = ssum * ssum / e2;
+        r.w_mc_eps = r.var_f[L] * r.cost_fine[L] / e2;
+    }
+    r.bias_estimate = L > 0 ? fabs(r.mean[L]) / (2.0 - 1.0) : NAN;
+    r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = r;
+    return worst;
+}

@@ -17,30 +17,12 @@
 
 void rich_set_error(const char* msg, const char* file, int line);
 
-struct rich_level {
-    int nx, nz;
-    double *Tx, *Tz, *Cdt, *D, *invD, *f, *dp;   // [S][nz][nx]
-    double *Tbt, *Tbb;                           // [S][nx]
-    float *Tx32, *Tz32, *D32, *invD32, *f32, *dp32; // mixed-precision copies
-};
-
-// Device workspace of one batched solve, sized for S_cap samples of a grid.
-struct rich_ws {
-    int S_cap = 0, nx = 0, nz = 0, nlev = 0, mixed = 0;
-    rich_level lev[RICH_MAX_LEVELS];
-    double *p = nullptr, *thold = nullptr, *Ks = nullptr, *a = nullptr, *K = nullptr, *th = nullptr;
-    double *r = nullptr;                        // FP64 defect (mixed path)
-    int32_t *status = nullptr, *kpic = nullptr, *cyc = nullptr, *alive = nullptr;
+// per-sample status and counters of the last fused solve
+struct rich_samplebuf {
+    void* base = nullptr;
+    int cap = 0;
+    int32_t *status = nullptr, *maxpic = nullptr;
     int64_t *pic_total = nullptr, *mg_total = nullptr;
-    int32_t *maxpic = nullptr;
-    unsigned long long *nrm_f = nullptr, *nrm_r = nullptr, *nrm_dp = nullptr;
-    double* target = nullptr;
-    int32_t *list_pic = nullptr, *list_mg = nullptr, *list_tmp = nullptr;
-    int32_t* counters = nullptr;                // device [4]
-    int32_t* h_counters = nullptr;              // pinned host mirror [4]
-    double *h_in = nullptr;                     // staging for the host-buffer entry point
-    void* base = nullptr;                       // single allocation
-    size_t bytes = 0;
 };
 
 struct rich_field_ws {
@@ -67,11 +49,13 @@ struct rich_prof {
 struct rich_ctx {
     int device = 0;
     int sm_count = 0;
-    rich_ws ws;
+    rich_samplebuf sb;
     rich_field_ws fws;
     rich_prof prof;
     void* fused_scratch = nullptr;              // per-CTA slots of the fused solver
     size_t fused_bytes = 0;
+    void* stage = nullptr;                      // device staging of the host-buffer entry point
+    size_t stage_bytes = 0;
 };
 
 void rich_count_launch();
@@ -80,7 +64,8 @@ int rich_prof_end(rich_ctx* ctx, cudaStream_t st, double bytes, double flops);
 int rich_prof_harvest(rich_ctx* ctx);
 
 // ---- solver (solver.cu)
-int rich_ws_reserve(rich_ctx* ctx, int S, int nx, int nz, int mixed);
+int rich_samples_reserve(rich_ctx* ctx, int S);
+int rich_stage_reserve(rich_ctx* ctx, size_t bytes);
 int rich_solve_device(rich_ctx* ctx, const rich_problem_t* pb, int S, const double* lnKs,
                       const double* alpha, double alpha_scale, double* qoi, double* p_final,
                       int32_t* status, rich_stats_t* stats, cudaStream_t st);
@@ -92,6 +77,8 @@ void rich_prof_amend(rich_ctx* ctx, double bytes, double flops);
 int rich_check_problem(const rich_problem_t* pb);
 
 // ---- fields (fields.cu)
+int rich_fields_average(rich_ctx* ctx, int S, int nx, int nz, const double* lk, const double* al,
+                        double* lkc, double* alc, cudaStream_t st);
 int rich_fields_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int nz, uint32_t level,
                        int64_t first, int S, int coarsen, double* lnKs, double* alpha,
                        cudaStream_t st);

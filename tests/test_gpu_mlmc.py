@@ -1,0 +1,61 @@
+"""MLMC with parametric continuation on the GPU vs the oracle's restatement of
+Sec. 5, and the telescoping consistency of the coupled estimator."""
+import numpy as np
+import pytest
+
+import oracle as O
+from tests.inputs import PHYSICS, SOLVER
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    import paper_1903_08741_gb300 as R
+    from paper_1903_08741_gb300 import build
+    build.build()
+    return R
+
+
+def rel(a, b):
+    return abs(a - b) / max(abs(b), 1e-300)
+
+
+@pytest.mark.parametrize("coupling", [0, 1])
+def test_mlmc_matches_oracle(R, coupling):
+    ns, n0, s0, T = (24, 12, 6), 8, 2, 0.04
+    cfg = R.MlmcConfig(nsamples=ns, n0=n0, steps0=s0, t_final=T, coupling=coupling, eps=1e-3,
+                       problem=R.Problem(**PHYSICS, **SOLVER))
+    g = R.mlmc_estimate(cfg)
+    o = O.mlmc_estimate(ns, n0, s0, T, coupling=coupling, **PHYSICS, **SOLVER)
+    for l, lev in enumerate(o):
+        y, qf, qc = lev["y"], lev["qf"], lev["qc"]
+        assert g["n"][l] == y.size and g["failed"][l] == lev["failed"]
+        assert rel(g["mean"][l], y.mean()) < 1e-9
+        assert rel(g["var"][l], y.var(ddof=1)) < 1e-8
+        assert rel(g["mean_f"][l], qf.mean()) < 1e-9
+        assert rel(g["var_f"][l], qf.var(ddof=1)) < 1e-8
+        if l > 0:
+            assert rel(g["mean_c"][l], qc.mean()) < 1e-9
+            assert rel(g["var_c"][l], qc.var(ddof=1)) < 1e-8
+    est = sum(lev["y"].mean() for lev in o)
+    rmse = np.sqrt(sum(lev["y"].var(ddof=1) / lev["y"].size for lev in o))
+    assert rel(g["estimate"], est) < 1e-9 and rel(g["rmse"], rmse) < 1e-8
+    # optimal allocation and cost from the GPU's own V_l and C_l (Eq. MLMCSAMP_ch6)
+    s = sum(np.sqrt(v * c) for v, c in zip(g["var"], g["cost"]))
+    assert rel(g["w_eps"], s * s / 1e-6) < 1e-12
+    assert all(c > 0 for c in g["cost"])
+
+
+def test_mlmc_telescoping_consistency(R):
+    """Exact coupling: the level-l fine member (pair l) and the level-l coarse
+    member (pair l+1) have the same law, so their means agree within 4 sigma."""
+    ns = (1200, 600, 300)
+    cfg = R.MlmcConfig(nsamples=ns, n0=8, steps0=2, t_final=0.04, coupling=0,
+                       problem=R.Problem(**PHYSICS, **SOLVER))
+    g = R.mlmc_estimate(cfg)
+    for l in range(len(ns) - 1):
+        d = g["mean_f"][l] - g["mean_c"][l + 1]
+        se = np.sqrt(g["var_f"][l] / g["n"][l] + g["var_c"][l + 1] / g["n"][l + 1])
+        assert abs(d) < 4 * se, (l, d, se)

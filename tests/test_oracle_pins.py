@@ -355,3 +355,12 @@ def test_mlmc_combine_telescopes():
     est, rmse = O.mlmc_combine(levels)
     assert abs(est - (ys[0].mean() + ys[1].mean())) < 1e-14
     assert abs(rmse ** 2 - (ys[0].var(ddof=1) / 400 + ys[1].var(ddof=1) / 100)) < 1e-14
+
+
+def test_oracle_mlmc_telescoping():
+    """Coupled MLMC (Sec. 5, Eq. fine_coarse): with draws on the finest grid the
+    level-0 fine member and the level-1 coarse member estimate the same mean."""
+    o = O.mlmc_estimate((160, 160), 8, 2, 0.04, coupling=0, **PHYSICS, **SOLVER)
+    a, b = o[0]["qf"], o[1]["qc"]
+    se = np.sqrt(a.var(ddof=1) / a.size + b.var(ddof=1) / b.size)
+    assert abs(a.mean() - b.mean()) < 4 * se
