@@ -186,7 +186,9 @@ def run_mlmc(args):
         "dtype": "f64" if prec == R.FP64 else "f32-in-f64", "data": "synthetic",
         "config": {"workload": "mlmc5: 16^2..256^2, N_l = 20000/5000/1200/300/80, 5*2^l steps to T=0.1, "
                                "alpha_l = alpha (l+1)/5, exp. cov. 0.3, seed 0",
-                   "coupling": "finest-grid draw, 2x2 averages" if args.coupling == 0 else "level-grid draw"},
+                   "coupling": {0: "finest-grid draw, 2x2 averages of ln Ks and alpha",
+                                1: "level-grid draw, 2x2 averages of ln Ks and alpha",
+                                2: "covariance upscaling (2x2-averaged white noise)"}[args.coupling]},
         "clocks": clk, "gpu_launches": launches,
         "levels": {k: r[k] for k in ("n", "failed", "mean", "var", "cost", "cost_fine", "n_opt",
                                      "mean_f", "var_f")},

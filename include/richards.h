@@ -95,6 +95,19 @@ int rich_sample_fields(rich_ctx_t ctx, const rich_field_t* field, int32_t nx, in
                        uint32_t level, int64_t first_sample, int32_t nsamples,
                        int32_t coarsen_times, double* lnKs, double* alpha, void* stream);
 
+/* Coupled pair of fields by covariance upscaling (Appendix A, Eqs. averaging,
+ * cov_upscale): the fine fields on nx x nz as rich_sample_fields draws them,
+ * and the coarse fields on (nx/2) x (nz/2) from the SAME white noise averaged
+ * over 2x2 torus blocks (scaled by 1/2, so it stays standard normal) and
+ * filtered with the coarse grid's spectrum on the half-size torus.  Each member
+ * is an exact sample of its own grid's field, so MLMC telescoping is exact.
+ * Outputs (device): lnKs_f, alpha_f [S][nz][nx]; lnKs_c, alpha_c
+ * [S][nz/2][nx/2].  Asynchronous on `stream`. */
+int rich_sample_fields_pair(rich_ctx_t ctx, const rich_field_t* field, int32_t nx, int32_t nz,
+                            uint32_t level, int64_t first_sample, int32_t nsamples,
+                            double* lnKs_f, double* alpha_f, double* lnKs_c, double* alpha_c,
+                            void* stream);
+
 /* Solve nsamples independent problems (Sec. 4: backward Euler, modified
  * Picard, CCMG V(nu1,nu2) with red-black GS, harmonic-mean faces, piecewise-
  * constant transfers, rediscretised coarse operators).  Inputs lnKs, alpha
@@ -133,10 +146,13 @@ typedef struct {
     int32_t steps0;           /* time steps on level 0                                    */
     double t_final;
     int32_t nsamples[RICH_MLMC_MAX_LEVELS];  /* N_l                                       */
-    int32_t coupling;         /* 0: draw on the finest grid and average down (every level's
-                                 fine member has the law of the next level's coarse member,
-                                 so the telescoping sum is exact, Eq. fine_coarse);
-                                 1: draw on the pair's fine grid (cheaper, not exact)      */
+    int32_t coupling;         /* 0: draw on the finest grid and average ln Ks, alpha down
+                                 (every level's fine member has the law of the next level's
+                                 coarse member: exact telescoping, Eq. fine_coarse);
+                                 1: draw on the pair's fine grid, coarse member = 2x2 means
+                                 of ln Ks, alpha (cheap, not exact);
+                                 2: covariance upscaling, rich_sample_fields_pair (exact,
+                                 cheap; Appendix A)                                         */
     int32_t continuation;     /* 1: alpha_l = alpha (l+1)/(L+1); 0: alpha on every level   */
     int32_t batch;            /* samples per batch, 0 = automatic                          */
     double eps;               /* RMSE target of the optimal-allocation report              */

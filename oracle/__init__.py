@@ -79,6 +79,9 @@ def lib():
         L.orc_sample_fields.argtypes = [C.c_uint64, C.c_double, C.c_double, C.c_double, C.c_double,
                                         C.c_int32, C.c_int32, C.c_uint32, C.c_int64, C.c_int32,
                                         C.c_int32, _dp, _dp, C.c_int32]
+        L.orc_sample_fields_pair.argtypes = [C.c_uint64, C.c_double, C.c_double, C.c_double, C.c_double,
+                                             C.c_int32, C.c_int32, C.c_uint32, C.c_int64, C.c_int32,
+                                             _dp, _dp, _dp, _dp]
         L.orc_solve_one.argtypes = [C.POINTER(Problem), C.c_int32, C.c_int32, _dp, _dp, C.c_double,
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
                                     C.POINTER(Stats)]
@@ -151,6 +154,19 @@ def sample_fields(nx, nz, nsamples, seed=0, level=0, first_sample=0, coarsen_tim
     if rc:
         raise ValueError("invalid field arguments")
     return lnKs, alpha
+
+
+def sample_fields_pair(nx, nz, nsamples, seed=0, level=0, first_sample=0, sigma2=1.0, corr_len=0.3,
+                       alpha_lo=0.5, alpha_span=1.5):
+    """Fine [S, nz, nx] and coarse [S, nz/2, nx/2] fields by covariance upscaling."""
+    f = [np.empty((nsamples, nz, nx)) for _ in range(2)]
+    c = [np.empty((nsamples, nz // 2, nx // 2)) for _ in range(2)]
+    rc = lib().orc_sample_fields_pair(seed, sigma2, corr_len, alpha_lo, alpha_span, nx, nz, level,
+                                      first_sample, nsamples, f[0].reshape(-1), f[1].reshape(-1),
+                                      c[0].reshape(-1), c[1].reshape(-1))
+    if rc:
+        raise ValueError("invalid field arguments")
+    return f[0], f[1], c[0], c[1]
 
 
 # ---------------------------------------------------------------------- solver
@@ -256,7 +272,11 @@ def mlmc_estimate(nsamples, n0, steps0, t_final, seed=0, coupling=0, continuatio
     for l in range(NL):
         M = n0 << l
         scale = lambda k: (k + 1) / NL if continuation else 1.0
-        if coupling == 0:
+        if coupling == 2 and l > 0:
+            lk, al, lkc_up, alc_up = sample_fields_pair(M, M, nsamples[l], seed=seed, level=l + key_offset,
+                                                        sigma2=sigma2, corr_len=corr_len, alpha_lo=alpha_lo,
+                                                        alpha_span=alpha_span)
+        elif coupling == 0:
             lk, al = sample_fields(nL, nL, nsamples[l], seed=seed, level=l + key_offset, coarsen_times=L - l,
                                    sigma2=sigma2, corr_len=corr_len, alpha_lo=alpha_lo,
                                    alpha_span=alpha_span, nthreads=nthreads)
@@ -267,8 +287,11 @@ def mlmc_estimate(nsamples, n0, steps0, t_final, seed=0, coupling=0, continuatio
         pf = make_problem(nsteps=steps0 << l, dt=t_final / (steps0 << l), **phys)
         _, qf, sf, _ = solve_batch(pf, lk, al, scale(l), want_p=False, nthreads=nthreads)
         if l > 0:
-            blk = lambda x: x.reshape(x.shape[0], M // 2, 2, M // 2, 2).mean(axis=(2, 4))
-            lkc, alc = blk(lk), blk(al)
+            if coupling == 2:
+                lkc, alc = lkc_up, alc_up
+            else:
+                blk = lambda x: x.reshape(x.shape[0], M // 2, 2, M // 2, 2).mean(axis=(2, 4))
+                lkc, alc = blk(lk), blk(al)
             pc = make_problem(nsteps=steps0 << (l - 1), dt=t_final / (steps0 << (l - 1)), **phys)
             _, qc, sc, _ = solve_batch(pc, lkc, alc, scale(l - 1), want_p=False, nthreads=nthreads)
         else:

@@ -269,6 +269,72 @@ int orc_sample_fields(uint64_t seed, double sigma2, double corr_len, double alph
 }
 
 /* ------------------------------------------------------------------------- */
+/* Covariance upscaling (Appendix A, Eqs. averaging, cov_upscale): white noise */
+/* y on the fine torus gives the fine field; the coarse noise                  */
+/* y_c(I,J) = (1/2) * (sum of the 2x2 block of y) on the half-size torus gives  */
+/* the coarse field through the coarse grid's own spectrum (spacing 2h).       */
+/* ------------------------------------------------------------------------- */
+int orc_sample_fields_pair(uint64_t seed, double sigma2, double corr_len, double alpha_lo,
+                           double alpha_span, int32_t nx, int32_t nz, uint32_t level,
+                           int64_t first_sample, int32_t nsamples, double* lnKs_f, double* alpha_f,
+                           double* lnKs_c, double* alpha_c)
+{
+    if (nx < 2 || nz < 2 || nx % 2 || nz % 2 || nsamples < 0) return -1;
+    double h = 1.0 / nz;
+    int32_t px, pz;
+    orc_torus_size(nx, nz, h, sigma2, corr_len, &px, &pz);
+    int pxc = px / 2, pzc = pz / 2, ncx = nx / 2, ncz = nz / 2;
+    size_t nf = (size_t)px * pz, nc = (size_t)pxc * pzc;
+    double* sqf = (double*)malloc(sizeof(double) * nf);
+    double* sqc = (double*)malloc(sizeof(double) * nc);
+    double ratio;
+    orc_fftma_spectrum(px, pz, h, sigma2, corr_len, sqf, &ratio);
+    orc_fftma_spectrum(pxc, pzc, 2.0 * h, sigma2, corr_len, sqc, &ratio);
+    double* y = (double*)malloc(sizeof(double) * nf);
+    double* re = (double*)malloc(sizeof(double) * nf);
+    double* im = (double*)malloc(sizeof(double) * nf);
+    double sig = sqrt(sigma2);
+    for (int k = 0; k < nsamples; ++k) {
+        uint64_t sample = (uint64_t)(first_sample + k);
+        for (uint32_t fld = 0; fld < 2; ++fld) {
+            orc_white_noise(seed, level, sample, fld, (int64_t)nf, y);
+            /* fine member */
+            memcpy(re, y, sizeof(double) * nf);
+            memset(im, 0, sizeof(double) * nf);
+            orc_fft2(re, im, px, pz, 0);
+            for (size_t q = 0; q < nf; ++q) { re[q] *= sqf[q]; im[q] *= sqf[q]; }
+            orc_fft2(re, im, px, pz, 1);
+            for (int j = 0; j < nz; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    double z = re[(size_t)j * px + i];
+                    size_t o = (size_t)k * nx * nz + (size_t)j * nx + i;
+                    if (fld == 0) lnKs_f[o] = z;
+                    else alpha_f[o] = alpha_lo + alpha_span * 0.5 * erfc(-(z / sig) / sqrt(2.0));
+                }
+            /* coarse member from the averaged noise */
+            for (int J = 0; J < pzc; ++J)
+                for (int I = 0; I < pxc; ++I) {
+                    size_t a = (size_t)(2 * J) * px + 2 * I, b = a + px;
+                    re[(size_t)J * pxc + I] = 0.5 * (y[a] + y[a + 1] + y[b] + y[b + 1]);
+                }
+            memset(im, 0, sizeof(double) * nc);
+            orc_fft2(re, im, pxc, pzc, 0);
+            for (size_t q = 0; q < nc; ++q) { re[q] *= sqc[q]; im[q] *= sqc[q]; }
+            orc_fft2(re, im, pxc, pzc, 1);
+            for (int j = 0; j < ncz; ++j)
+                for (int i = 0; i < ncx; ++i) {
+                    double z = re[(size_t)j * pxc + i];
+                    size_t o = (size_t)k * ncx * ncz + (size_t)j * ncx + i;
+                    if (fld == 0) lnKs_c[o] = z;
+                    else alpha_c[o] = alpha_lo + alpha_span * 0.5 * erfc(-(z / sig) / sqrt(2.0));
+                }
+        }
+    }
+    free(sqf); free(sqc); free(y); free(re); free(im);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Closure: Gardner exponential model.                                        */
 /*   p < 0 : E = exp(a p), K = Ks E, theta = theta_r + (theta_s - theta_r) E, */
 /*           C = d theta / d p = (theta_s - theta_r) a E                      */

@@ -57,6 +57,10 @@ int  orc_sample_fields(uint64_t seed, double sigma2, double corr_len, double alp
                        double alpha_span, int32_t nx, int32_t nz, uint32_t level,
                        int64_t first_sample, int32_t nsamples, int32_t coarsen_times,
                        double* lnKs, double* alpha, int32_t nthreads);
+int  orc_sample_fields_pair(uint64_t seed, double sigma2, double corr_len, double alpha_lo,
+                            double alpha_span, int32_t nx, int32_t nz, uint32_t level,
+                            int64_t first_sample, int32_t nsamples, double* lnKs_f, double* alpha_f,
+                            double* lnKs_c, double* alpha_c);
 int  orc_solve_one(const orc_problem* pb, int32_t nx, int32_t nz, const double* lnKs,
                    const double* alpha, double alpha_scale, const double* src,
                    const double* p_init, double* p_final, double* qoi, orc_stats* st);

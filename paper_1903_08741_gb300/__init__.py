@@ -170,6 +170,7 @@ def lib():
         L.rich_profile_read.argtypes = [vp, C.POINTER(dbl), C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl)]
         L.rich_launch_count.restype = i64
         L.rich_solve_batch_noalloc.argtypes = [C.POINTER(_Problem), i32, vp, vp, dbl, vp, vp, vp]
+        L.rich_sample_fields_pair.argtypes = [vp, C.POINTER(_Field), i32, i32, u32, i64, i32, vp, vp, vp, vp, vp]
         L.rich_mlmc_estimate.argtypes = [vp, C.POINTER(_MlmcCfg), C.POINTER(_MlmcResult)]
         _lib = L
     return _lib
@@ -179,7 +180,7 @@ def exported_symbols():
     return ["rich_create", "rich_destroy", "rich_status_str", "rich_last_error",
             "rich_sample_fields", "rich_solve_batch", "rich_solve_batch_host",
             "rich_mlmc_accumulate", "rich_profile", "rich_profile_read", "rich_launch_count",
-            "rich_solve_batch_noalloc", "rich_mlmc_estimate"]
+            "rich_solve_batch_noalloc", "rich_mlmc_estimate", "rich_sample_fields_pair"]
 
 
 def _check(rc):
@@ -231,6 +232,21 @@ def sample_fields(nx, nz, nsamples, model: FieldModel | None = None, level=0, fi
                                     nsamples, coarsen_times, _dev_ptr(lk, torch.float64, "lnKs"),
                                     _dev_ptr(al, torch.float64, "alpha"), _stream(torch, device)))
     return lk, al
+
+
+def sample_fields_pair(nx, nz, nsamples, model: FieldModel | None = None, level=0, first_sample=0,
+                       device=0):
+    """Covariance-upscaled pair (Appendix A): fine [S, nz, nx] and coarse
+    [S, nz/2, nx/2] ln Ks and alpha from one white-noise draw."""
+    torch = _torch()
+    model = model or FieldModel()
+    d = f"cuda:{device}"
+    f = [torch.empty((nsamples, nz, nx), dtype=torch.float64, device=d) for _ in range(2)]
+    c = [torch.empty((nsamples, nz // 2, nx // 2), dtype=torch.float64, device=d) for _ in range(2)]
+    _check(lib().rich_sample_fields_pair(context(device), C.byref(model._c()), nx, nz, level, first_sample,
+                                         nsamples, *[_dev_ptr(t, torch.float64, "field") for t in (*f, *c)],
+                                         _stream(torch, device)))
+    return f[0], f[1], c[0], c[1]
 
 
 def solve_batch(problem: Problem, lnKs, alpha, alpha_scale=1.0, want_p=False, device=None):

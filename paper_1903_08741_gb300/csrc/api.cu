@@ -121,9 +121,8 @@ extern "C" void rich_destroy(rich_ctx_t ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->sb.base) cudaFree(ctx->sb.base);
     if (ctx->stage) cudaFree(ctx->stage);
-    if (ctx->fws.sqrt_lambda) cudaFree(ctx->fws.sqrt_lambda);
-    if (ctx->fws.work) cudaFree(ctx->fws.work);
-    if (ctx->fws.tw) cudaFree(ctx->fws.tw);
+    for (auto& e : ctx->spectra) { cudaFree(e.sq); cudaFree(e.tw); }
+    if (ctx->field_work) cudaFree(ctx->field_work);
     for (auto e : ctx->prof.ev) cudaEventDestroy(e);
     if (ctx->fused_scratch) cudaFree(ctx->fused_scratch);
     delete ctx;
@@ -148,6 +147,17 @@ extern "C" int rich_sample_fields(rich_ctx_t ctx, const rich_field_t* field, int
     RICH_CUDA(cudaSetDevice(ctx->device));
     return rich_fields_device(ctx, field, nx, nz, level, first_sample, nsamples, coarsen_times,
                               lnKs, alpha, (cudaStream_t)stream);
+}
+
+extern "C" int rich_sample_fields_pair(rich_ctx_t ctx, const rich_field_t* field, int32_t nx,
+                                       int32_t nz, uint32_t level, int64_t first_sample,
+                                       int32_t nsamples, double* lnKs_f, double* alpha_f,
+                                       double* lnKs_c, double* alpha_c, void* stream) {
+    if (!ctx || !field || nsamples < 0 || first_sample < 0) return RICH_ERR_INVALID;
+    if (nsamples > 0 && (!lnKs_f || !alpha_f || !lnKs_c || !alpha_c)) return RICH_ERR_INVALID;
+    RICH_CUDA(cudaSetDevice(ctx->device));
+    return rich_fields_pair_device(ctx, field, nx, nz, level, first_sample, nsamples, lnKs_f, alpha_f,
+                                   lnKs_c, alpha_c, (cudaStream_t)stream);
 }
 
 extern "C" int rich_solve_batch(rich_ctx_t ctx, const rich_problem_t* pb, int32_t nsamples,

@@ -212,51 +212,88 @@ int fft2(cplx* d, int S, int px, int pz, const cplx* twx, const cplx* twz, int i
 
 }  // namespace
 
-// spectrum sqrt(F c) on the smallest valid torus, cached in the context
-static int ensure_spectrum(rich_ctx* ctx, int nx, int nz, double sigma2, double corr_len,
-                           cudaStream_t st) {
-    rich_field_ws& f = ctx->fws;
-    if (f.sqrt_lambda && f.nx == nx && f.nz == nz && f.sigma2 == sigma2 && f.corr_len == corr_len)
-        return 0;
-    if (f.sqrt_lambda) { cudaFree(f.sqrt_lambda); f.sqrt_lambda = nullptr; }
-    if (f.tw) { cudaFree(f.tw); f.tw = nullptr; }
-    if (f.work) { cudaFree(f.work); f.work = nullptr; }
-    const double h = 1.0 / nz;
-    int px = 1, pz = 1;
-    while (px < 2 * nx) px <<= 1;
-    while (pz < 2 * nz) pz <<= 1;
-    for (int tries = 0; tries < 4; ++tries) {
-        const int npts = px * pz;
-        cplx *c = nullptr, *tw = nullptr;
-        RICH_CUDA(cudaMalloc(&c, sizeof(cplx) * npts));
-        RICH_CUDA(cudaMalloc(&tw, sizeof(cplx) * (px / 2 + pz / 2 + 2)));
-        rich_count_launch(); k_twiddles<<<nb(px / 2), 256, 0, st>>>(px, tw);
-        rich_count_launch(); k_twiddles<<<nb(pz / 2), 256, 0, st>>>(pz, tw + px / 2 + 1);
-        rich_count_launch(); k_cov<<<nb(npts), 256, 0, st>>>(px, pz, h, sigma2, corr_len, c);
-        if (int e = fft2(c, 1, px, pz, tw, tw + px / 2 + 1, 0, st)) return e;
-        std::vector<cplx> hl(npts);
-        RICH_CUDA(cudaMemcpyAsync(hl.data(), c, sizeof(cplx) * npts, cudaMemcpyDeviceToHost, st));
-        RICH_CUDA(cudaStreamSynchronize(st));
-        double lmin = hl[0].re, lmax = hl[0].re;
-        for (auto& v : hl) { lmin = std::min(lmin, v.re); lmax = std::max(lmax, v.re); }
-        bool ok = lmin / lmax >= -1e-12;
-        if (ok || tries == 3) {
-            RICH_CUDA(cudaMalloc(&f.sqrt_lambda, sizeof(double) * npts));
-            rich_count_launch(); k_sqrt_spec<<<nb(npts), 256, 0, st>>>(npts, c, f.sqrt_lambda);
-            RICH_CUDA(cudaStreamSynchronize(st));
-            cudaFree(c);
-            f.tw = (double*)tw;
-            f.px = px; f.pz = pz; f.nx = nx; f.nz = nz; f.sigma2 = sigma2; f.corr_len = corr_len;
-            // work buffer: enough samples per chunk for ~512 MB
-            f.chunk = (int)std::max<long long>(1, (512ll << 20) / ((long long)npts * sizeof(cplx) + 32ll * nx * nz));
-            RICH_CUDA(cudaMalloc(&f.work, (sizeof(cplx) * npts + 32 * (size_t)nx * nz) * f.chunk));
+// ---------------------------------------------------------------- host side
+// sqrt(F c) on a px x pz torus of spacing h, cached in the context
+static int spectrum_on(rich_ctx* ctx, int px, int pz, double h, double sigma2, double corr_len,
+                       cudaStream_t st, const rich_spectrum** out, double* min_ratio) {
+    for (const rich_spectrum& e : ctx->spectra)
+        if (e.px == px && e.pz == pz && e.h == h && e.sigma2 == sigma2 && e.corr_len == corr_len) {
+            *out = &e;
+            if (min_ratio) *min_ratio = e.min_ratio;
             return 0;
         }
-        cudaFree(c); cudaFree(tw);
-        px *= 2; pz *= 2;
+    const int npts = px * pz;
+    rich_spectrum e{};
+    e.px = px; e.pz = pz; e.h = h; e.sigma2 = sigma2; e.corr_len = corr_len;
+    cplx* c = nullptr;
+    RICH_CUDA(cudaMalloc(&c, sizeof(cplx) * npts));
+    RICH_CUDA(cudaMalloc(&e.tw, sizeof(cplx) * (px / 2 + pz / 2 + 2)));
+    cplx* tw = (cplx*)e.tw;
+    rich_count_launch(); k_twiddles<<<nb(px / 2), 256, 0, st>>>(px, tw);
+    rich_count_launch(); k_twiddles<<<nb(pz / 2), 256, 0, st>>>(pz, tw + px / 2 + 1);
+    rich_count_launch(); k_cov<<<nb(npts), 256, 0, st>>>(px, pz, h, sigma2, corr_len, c);
+    if (int r = fft2(c, 1, px, pz, tw, tw + px / 2 + 1, 0, st)) { cudaFree(c); return r; }
+    std::vector<cplx> hl(npts);
+    RICH_CUDA(cudaMemcpyAsync(hl.data(), c, sizeof(cplx) * npts, cudaMemcpyDeviceToHost, st));
+    RICH_CUDA(cudaStreamSynchronize(st));
+    double lmin = hl[0].re, lmax = hl[0].re;
+    for (auto& v : hl) { lmin = std::min(lmin, v.re); lmax = std::max(lmax, v.re); }
+    e.min_ratio = lmin / lmax;
+    RICH_CUDA(cudaMalloc(&e.sq, sizeof(double) * npts));
+    rich_count_launch(); k_sqrt_spec<<<nb(npts), 256, 0, st>>>(npts, c, e.sq);
+    RICH_CUDA(cudaStreamSynchronize(st));
+    cudaFree(c);
+    if (ctx->spectra.size() >= 16) {               // bounded cache: drop the oldest
+        cudaFree(ctx->spectra.front().sq); cudaFree(ctx->spectra.front().tw);
+        ctx->spectra.erase(ctx->spectra.begin());
+    }
+    ctx->spectra.push_back(e);
+    *out = &ctx->spectra.back();
+    if (min_ratio) *min_ratio = e.min_ratio;
+    return 0;
+}
+
+// smallest power-of-two torus of at least twice the grid per side whose
+// circulant spectrum has no eigenvalue below -1e-12 max (doubled up to 3 times)
+static int choose_torus(rich_ctx* ctx, int nx, int nz, double sigma2, double corr_len, cudaStream_t st,
+                        int* px, int* pz) {
+    const double h = 1.0 / nz;
+    int a = 1, b = 1;
+    while (a < 2 * nx) a <<= 1;
+    while (b < 2 * nz) b <<= 1;
+    for (int tries = 0; tries < 4; ++tries) {
+        const rich_spectrum* e = nullptr;
+        double ratio = 0;
+        if (int r = spectrum_on(ctx, a, b, h, sigma2, corr_len, st, &e, &ratio)) return r;
+        if (ratio >= -1e-12 || tries == 3) { *px = a; *pz = b; return 0; }
+        a *= 2; b *= 2;
     }
     return RICH_ERR_INVALID;
 }
+
+static int ensure_work(rich_ctx* ctx, size_t bytes) {
+    if (ctx->field_work && ctx->field_work_bytes >= bytes) return 0;
+    if (ctx->field_work) cudaFree(ctx->field_work);
+    ctx->field_work = nullptr; ctx->field_work_bytes = 0;
+    cudaError_t e = cudaMalloc(&ctx->field_work, bytes);
+    if (e != cudaSuccess) { cudaGetLastError(); return RICH_ERR_OOM; }
+    ctx->field_work_bytes = bytes;
+    return 0;
+}
+
+// FFT-MA of the packed noise in `work` ([cs][pz][px] complex) in place
+static int fftma_inplace(cplx* work, int cs, const rich_spectrum* sp, cudaStream_t st) {
+    const int px = sp->px, pz = sp->pz, npts = px * pz;
+    const cplx* twx = (const cplx*)sp->tw;
+    const cplx* twz = twx + px / 2 + 1;
+    if (int e = fft2(work, cs, px, pz, twx, twz, 0, st)) return e;
+    rich_count_launch();
+    k_filter<<<nb((long long)cs * npts), 256, 0, st>>>(cs, npts, sp->sq, work);
+    if (int e = fft2(work, cs, px, pz, twx, twz, 1, st)) return e;
+    return 0;
+}
+
+constexpr size_t CHUNK_BYTES = 512ull << 20;
 
 int rich_fields_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int nz, uint32_t level,
                        int64_t first, int S, int coarsen, double* lnKs, double* alpha,
@@ -265,28 +302,32 @@ int rich_fields_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int nz, ui
         fd->sigma2 <= 0 || fd->corr_len <= 0)
         return RICH_ERR_INVALID;
     if (S == 0) return 0;
-    if (int e = ensure_spectrum(ctx, nx, nz, fd->sigma2, fd->corr_len, st)) return e;
-    rich_field_ws& f = ctx->fws;
-    const int px = f.px, pz = f.pz, npts = px * pz;
-    const cplx* twx = (const cplx*)f.tw;
-    const cplx* twz = twx + px / 2 + 1;
-    cplx* work = (cplx*)f.work;
-    double* tmp = (double*)(work + (size_t)npts * f.chunk);   // [chunk][4][nz][nx] real scratch
+    int px = 0, pz = 0;
+    if (int e = choose_torus(ctx, nx, nz, fd->sigma2, fd->corr_len, st, &px, &pz)) return e;
+    const rich_spectrum* sp = nullptr;
+    if (int e = spectrum_on(ctx, px, pz, 1.0 / nz, fd->sigma2, fd->corr_len, st, &sp, nullptr)) return e;
+    const int npts = px * pz;
+    const size_t per = (size_t)npts * sizeof(cplx) + 32 * (size_t)nx * nz;
+    const int chunk = (int)std::max<size_t>(1, CHUNK_BYTES / per);
+    if (int e = ensure_work(ctx, per * std::min(chunk, S))) return e;
+    cplx* work = (cplx*)ctx->field_work;
+    const int cap = std::min(chunk, S);
+    double* tmp = (double*)(work + (size_t)npts * cap);   // [cap][4][nz][nx] real scratch
     const int nxo = nx >> coarsen, nzo = nz >> coarsen;
     const double inv_sigma = 1.0 / sqrt(fd->sigma2);
-    for (int s0 = 0; s0 < S; s0 += f.chunk) {
-        int cs = std::min(f.chunk, S - s0);
-        rich_count_launch(); k_noise<<<nb((long long)cs * (npts / 2)), 256, 0, st>>>(cs, npts, fd->seed, level, first + s0, work);
-        if (int e = fft2(work, cs, px, pz, twx, twz, 0, st)) return e;
-        rich_count_launch(); k_filter<<<nb((long long)cs * npts), 256, 0, st>>>(cs, npts, f.sqrt_lambda, work);
-        if (int e = fft2(work, cs, px, pz, twx, twz, 1, st)) return e;
+    for (int s0 = 0; s0 < S; s0 += cap) {
+        int cs = std::min(cap, S - s0);
+        rich_count_launch();
+        k_noise<<<nb((long long)cs * (npts / 2)), 256, 0, st>>>(cs, npts, fd->seed, level, first + s0, work);
+        if (int e = fftma_inplace(work, cs, sp, st)) return e;
         // real scratch: two ping-pong pairs of [cs][nz][nx] arrays
         const size_t blk = (size_t)cs * nx * nz;
         double* bl[2] = {tmp, tmp + 2 * blk};
         double* ba[2] = {tmp + blk, tmp + 3 * blk};
         double* wl = coarsen ? bl[0] : lnKs + (size_t)s0 * nx * nz;
         double* wa = coarsen ? ba[0] : alpha + (size_t)s0 * nx * nz;
-        rich_count_launch(); k_window<<<nb((long long)cs * nx * nz), 256, 0, st>>>(cs, nx, nz, px, pz, work, inv_sigma,
+        rich_count_launch();
+        k_window<<<nb((long long)cs * nx * nz), 256, 0, st>>>(cs, nx, nz, px, pz, work, inv_sigma,
                                                             fd->alpha_lo, fd->alpha_span, wl, wa);
         int cx = nx, cz = nz, cur = 0;
         for (int c = 0; c < coarsen; ++c) {
@@ -294,10 +335,74 @@ int rich_fields_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int nz, ui
             bool last = c == coarsen - 1;
             double* ol = last ? lnKs + (size_t)s0 * nxo * nzo : bl[1 - cur];
             double* oa = last ? alpha + (size_t)s0 * nxo * nzo : ba[1 - cur];
-            rich_count_launch(); k_avg2<<<nb((long long)cs * ncx * ncz), 256, 0, st>>>(cs, ncx, ncz, bl[cur], ba[cur], ol, oa);
+            rich_count_launch();
+            k_avg2<<<nb((long long)cs * ncx * ncz), 256, 0, st>>>(cs, ncx, ncz, bl[cur], ba[cur], ol, oa);
             cur = 1 - cur;
             cx = ncx; cz = ncz;
         }
+    }
+    RICH_CUDA(cudaGetLastError());
+    return 0;
+}
+
+namespace {
+// coarse white noise by 2x2 averaging on the torus, scaled by 1/2 so that it
+// stays standard normal (Appendix A, Eq. averaging); both packed fields at once
+__global__ void k_noise_upscale(int S, int pxc, int pzc, const cplx* __restrict__ y, cplx* yc) {
+    long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nc = pxc * pzc, fx = 2 * pxc;
+    if (g >= (long long)S * nc) return;
+    int s = (int)(g / nc), q = (int)(g - (long long)s * nc);
+    int J = q / pxc, I = q - J * pxc;
+    const cplx* b = y + (size_t)s * 4 * nc + (size_t)(2 * J) * fx + 2 * I;
+    cplx a = b[0], c = b[1], d = b[fx], e = b[fx + 1];
+    yc[g] = cplx{0.5 * (a.re + c.re + d.re + e.re), 0.5 * (a.im + c.im + d.im + e.im)};
+}
+}
+
+// Fine fields on nx x nz and coarse fields on (nx/2) x (nz/2) from one draw by
+// covariance upscaling (Appendix A, Eqs. averaging, cov_upscale): the coarse
+// white noise is half the 2x2 sums of the fine noise on the torus, filtered
+// with the coarse grid's own spectrum on the half-size torus.
+int rich_fields_pair_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int nz, uint32_t level,
+                            int64_t first, int S, double* lk_f, double* al_f, double* lk_c,
+                            double* al_c, cudaStream_t st) {
+    if (!pow2(nx) || !pow2(nz) || nx < 2 || nz < 2 || fd->sigma2 <= 0 || fd->corr_len <= 0)
+        return RICH_ERR_INVALID;
+    if (S == 0) return 0;
+    int px = 0, pz = 0;
+    if (int e = choose_torus(ctx, nx, nz, fd->sigma2, fd->corr_len, st, &px, &pz)) return e;
+    const rich_spectrum *spf = nullptr, *spc = nullptr;
+    if (int e = spectrum_on(ctx, px, pz, 1.0 / nz, fd->sigma2, fd->corr_len, st, &spf, nullptr)) return e;
+    if (int e = spectrum_on(ctx, px / 2, pz / 2, 2.0 / nz, fd->sigma2, fd->corr_len, st, &spc, nullptr)) return e;
+    // spectrum_on may reallocate the cache vector: look both up again
+    spectrum_on(ctx, px, pz, 1.0 / nz, fd->sigma2, fd->corr_len, st, &spf, nullptr);
+    spectrum_on(ctx, px / 2, pz / 2, 2.0 / nz, fd->sigma2, fd->corr_len, st, &spc, nullptr);
+    const int npf = px * pz, npc = npf / 4;
+    const size_t per = (size_t)(npf + npc) * sizeof(cplx);
+    const int cap = (int)std::min<size_t>((size_t)S, std::max<size_t>(1, CHUNK_BYTES / per));
+    if (int e = ensure_work(ctx, per * cap)) return e;
+    cplx* wf = (cplx*)ctx->field_work;
+    cplx* wc = wf + (size_t)npf * cap;
+    const double inv_sigma = 1.0 / sqrt(fd->sigma2);
+    for (int s0 = 0; s0 < S; s0 += cap) {
+        int cs = std::min(cap, S - s0);
+        rich_count_launch();
+        k_noise<<<nb((long long)cs * (npf / 2)), 256, 0, st>>>(cs, npf, fd->seed, level, first + s0, wf);
+        rich_count_launch();
+        k_noise_upscale<<<nb((long long)cs * npc), 256, 0, st>>>(cs, px / 2, pz / 2, wf, wc);
+        if (int e = fftma_inplace(wf, cs, spf, st)) return e;
+        if (int e = fftma_inplace(wc, cs, spc, st)) return e;
+        rich_count_launch();
+        k_window<<<nb((long long)cs * nx * nz), 256, 0, st>>>(cs, nx, nz, px, pz, wf, inv_sigma, fd->alpha_lo,
+                                                            fd->alpha_span, lk_f + (size_t)s0 * nx * nz,
+                                                            al_f + (size_t)s0 * nx * nz);
+        const int ncx = nx / 2, ncz = nz / 2;
+        rich_count_launch();
+        k_window<<<nb((long long)cs * ncx * ncz), 256, 0, st>>>(cs, ncx, ncz, px / 2, pz / 2, wc, inv_sigma,
+                                                              fd->alpha_lo, fd->alpha_span,
+                                                              lk_c + (size_t)s0 * ncx * ncz,
+                                                              al_c + (size_t)s0 * ncx * ncz);
     }
     RICH_CUDA(cudaGetLastError());
     return 0;

@@ -71,7 +71,7 @@ extern "C" int rich_mlmc_estimate(rich_ctx_t ctx, const rich_mlmc_cfg_t* cfg, ri
     if (!ctx || !cfg || !out) return RICH_ERR_INVALID;
     const int NL = cfg->nlevels, L = NL - 1;
     if (NL < 1 || NL > RICH_MLMC_MAX_LEVELS || cfg->n0 < 2 || cfg->steps0 < 1 || !(cfg->t_final > 0) ||
-        (cfg->coupling != 0 && cfg->coupling != 1))
+        (cfg->coupling < 0 || cfg->coupling > 2))
         return RICH_ERR_INVALID;
     for (int l = 0; l < NL; ++l)
         if (cfg->nsamples[l] < 2) return RICH_ERR_INVALID;
@@ -116,10 +116,15 @@ extern "C" int rich_mlmc_estimate(rich_ctx_t ctx, const rich_mlmc_cfg_t* cfg, ri
         for (int b0 = 0; b0 < nsl; b0 += B) {
             const int nb = std::min(B, nsl - b0);
             RICH_CUDA(cudaEventRecord(ev[0], st));
-            int e = rich_fields_device(ctx, &cfg->field, ndraw, ndraw, (uint32_t)l + cfg->key_offset, b0, nb,
+            int e;
+            if (cfg->coupling == 2 && l > 0)
+                e = rich_fields_pair_device(ctx, &cfg->field, M, M, (uint32_t)l + cfg->key_offset, b0, nb,
+                                            (double*)lkf.p, (double*)alf.p, (double*)lkc.p, (double*)alc.p, st);
+            else
+                e = rich_fields_device(ctx, &cfg->field, ndraw, ndraw, (uint32_t)l + cfg->key_offset, b0, nb,
                                        coarsen, (double*)lkf.p, (double*)alf.p, st);
             if (e) return e;
-            if (l > 0) {
+            if (l > 0 && cfg->coupling != 2) {
                 e = rich_fields_average(ctx, nb, M, M, (double*)lkf.p, (double*)alf.p, (double*)lkc.p,
                                         (double*)alc.p, st);
                 if (e) return e;

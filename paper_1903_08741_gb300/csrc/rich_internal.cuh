@@ -25,13 +25,12 @@ struct rich_samplebuf {
     int64_t *pic_total = nullptr, *mg_total = nullptr;
 };
 
-struct rich_field_ws {
-    int px = 0, pz = 0, nx = 0, nz = 0;
-    double sigma2 = -1, corr_len = -1;
-    double* sqrt_lambda = nullptr;              // [pz][px]
-    double* work = nullptr;                     // complex [chunk][pz][px][2]
-    double* tw = nullptr;                       // twiddles
-    int chunk = 0;
+// sqrt of the circulant covariance spectrum on one torus (+ FFT twiddles)
+struct rich_spectrum {
+    int px = 0, pz = 0;
+    double h = 0, sigma2 = 0, corr_len = 0, min_ratio = 0;
+    double* sq = nullptr;                       // [pz][px]
+    void* tw = nullptr;                         // twiddles of both line lengths
 };
 
 // Live timing of the finest-level smoothing launches (the dominant kernel):
@@ -50,7 +49,9 @@ struct rich_ctx {
     int device = 0;
     int sm_count = 0;
     rich_samplebuf sb;
-    rich_field_ws fws;
+    std::vector<rich_spectrum> spectra;         // cached FFT-MA filters
+    void* field_work = nullptr;                 // complex work buffer of the field sampler
+    size_t field_work_bytes = 0;
     rich_prof prof;
     void* fused_scratch = nullptr;              // per-CTA slots of the fused solver
     size_t fused_bytes = 0;
@@ -77,6 +78,9 @@ void rich_prof_amend(rich_ctx* ctx, double bytes, double flops);
 int rich_check_problem(const rich_problem_t* pb);
 
 // ---- fields (fields.cu)
+int rich_fields_pair_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int nz, uint32_t level,
+                            int64_t first, int S, double* lk_f, double* al_f, double* lk_c,
+                            double* al_c, cudaStream_t st);
 int rich_fields_average(rich_ctx* ctx, int S, int nx, int nz, const double* lk, const double* al,
                         double* lkc, double* alc, cudaStream_t st);
 int rich_fields_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int nz, uint32_t level,

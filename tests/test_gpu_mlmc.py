@@ -22,7 +22,7 @@ def rel(a, b):
     return abs(a - b) / max(abs(b), 1e-300)
 
 
-@pytest.mark.parametrize("coupling", [0, 1])
+@pytest.mark.parametrize("coupling", [0, 1, 2])
 def test_mlmc_matches_oracle(R, coupling):
     ns, n0, s0, T = (24, 12, 6), 8, 2, 0.04
     cfg = R.MlmcConfig(nsamples=ns, n0=n0, steps0=s0, t_final=T, coupling=coupling, eps=1e-3,

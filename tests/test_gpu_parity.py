@@ -97,6 +97,14 @@ def test_fields_match_oracle(R, nx, nz, c):
     assert np.abs(al.cpu().numpy() - al_o).max() < 1e-12
 
 
+@pytest.mark.parametrize("n", [8, 32, 64])
+def test_fields_pair_match_oracle(R, n):
+    o = O.sample_fields_pair(n, n, 5, seed=7, level=3, first_sample=11)
+    g = R.sample_fields_pair(n, n, 5, R.FieldModel(seed=7), level=3, first_sample=11)
+    for a, b in zip(g, o):
+        assert np.abs(a.cpu().numpy() - b).max() < 1e-12
+
+
 def test_fields_large_batch_chunks(R):
     """A batch larger than one FFT work chunk (128^2 grid, 256^2 torus)."""
     S = 40

@@ -364,3 +364,24 @@ def test_oracle_mlmc_telescoping():
     a, b = o[0]["qf"], o[1]["qc"]
     se = np.sqrt(a.var(ddof=1) / a.size + b.var(ddof=1) / b.size)
     assert abs(a.mean() - b.mean()) < 4 * se
+
+
+def test_covariance_upscaling_pair_is_exact_on_both_grids():
+    """Appendix A, Eqs. averaging / cov_upscale: the coarse member is an exact
+    exp(-r/0.3) field on the 8x8 grid (empirical covariance within 5 s.e.),
+    strongly correlated with the 2x2 means of the fine member."""
+    S, n, lam = 4096, 16, 0.3
+    lkf, alf, lkc, alc = O.sample_fields_pair(n, n, S, seed=3)
+    h = 2.0 / n
+    for axis in (1, 2):
+        for lag in range(0, 5):
+            a = np.take(lkc, np.arange(0, n // 2 - lag), axis=axis)
+            b = np.take(lkc, np.arange(lag, n // 2), axis=axis)
+            ps = (a * b).mean(axis=(1, 2))
+            assert abs(ps.mean() - np.exp(-lag * h / lam)) < 5 * ps.std(ddof=1) / np.sqrt(S) + 1e-3
+    blk = lkf.reshape(S, n // 2, 2, n // 2, 2).mean(axis=(2, 4))
+    assert np.corrcoef(blk.reshape(-1), lkc.reshape(-1))[0, 1] > 0.8
+    assert alc.min() > 0.5 and alc.max() < 2.0
+    # the fine member is the plain draw of the same (seed, level, sample)
+    lk1, al1 = O.sample_fields(n, n, 3, seed=3)
+    assert np.abs(lk1 - lkf[:3]).max() < 1e-13 and np.abs(al1 - alf[:3]).max() < 1e-13
