@@ -194,6 +194,33 @@ int rich_mlmc_accumulate(rich_ctx_t ctx, const double* qoi_fine, const double* q
                          const int32_t* status_fine, const int32_t* status_coarse, int32_t n,
                          double* acc, void* stream);
 
+/* ln Ks fields of a Karhunen-Loeve expansion (Sec. 3, Eq. KLexp_ch6):
+ * lnKs[s][c] = sum_j xi[s][j] kl_basis[j][c], with sqrt(lambda_j) folded into the
+ * basis.  kl_basis [n_kl][ncell], xi [S][n_kl], lnKs [S][ncell]: device arrays.
+ * S <= 65535.  Asynchronous on `stream`. */
+int rich_kl_fields(rich_ctx_t ctx, const double* kl_basis, int32_t n_kl, int32_t ncell,
+                   const double* xi, int32_t nsamples, double* lnKs, void* stream);
+
+/* Discrete adjoint: the QoI of rich_solve_batch for ln Ks = KL(xi) and its
+ * gradient with respect to the KL coefficients, dq_dxi [S][n_kl], by the
+ * adjoint of the converged time-stepped Picard/CCMG solve (configured
+ * instance; the paper has no adjoint): with R_n(p^n, p^{n-1}, m) = 0 the states
+ * of backward Euler and m = ln Ks,
+ *   J_N^T lam_N = dQ/dp^N,  J_n^T lam_n = diag(C(p^n)/dt) lam_{n+1},
+ *   dQ/dm = dQ/dm|explicit - sum_n (dR_n/dm)^T lam_n,  dQ/dxi_j = <basis_j, dQ/dm>,
+ * J_n the full Newton Jacobian (K'(p) inside the harmonic means included).
+ * J^T systems are solved by defect correction preconditioned with CCMG V-cycles
+ * of the Picard operator (FP32 V-cycles when pb->precision is RICH_MIXED) to a
+ * relative residual of 1e-11.  Memory: the states are checkpointed every
+ * ckpt_every steps and each segment is recomputed during the reverse sweep.
+ * dq_dlnKs [S][nz][nx] (device) may be NULL.  A J^T solve that stops at its
+ * iteration limit sets RICH_MG_MAXIT.  Synchronous (returns when done). */
+int rich_solve_batch_adjoint(rich_ctx_t ctx, const rich_problem_t* pb, int32_t nsamples,
+                             const double* kl_basis, int32_t n_kl, const double* xi,
+                             const double* alpha, double alpha_scale, int32_t ckpt_every,
+                             double* qoi, double* dq_dxi, double* dq_dlnKs, int32_t* status,
+                             rich_stats_t* stats, void* stream);
+
 /* Allocation-free solve.  The paper has no counterpart: this entry point exists
  * for callers that cannot call cudaMalloc -- code embedded in a host framework
  * that owns all device memory through its own pool allocator and forbids other

@@ -171,6 +171,9 @@ def lib():
         L.rich_launch_count.restype = i64
         L.rich_solve_batch_noalloc.argtypes = [C.POINTER(_Problem), i32, vp, vp, dbl, vp, vp, vp]
         L.rich_sample_fields_pair.argtypes = [vp, C.POINTER(_Field), i32, i32, u32, i64, i32, vp, vp, vp, vp, vp]
+        L.rich_kl_fields.argtypes = [vp, vp, i32, i32, vp, i32, vp, vp]
+        L.rich_solve_batch_adjoint.argtypes = [vp, C.POINTER(_Problem), i32, vp, i32, vp, vp, dbl, i32, vp, vp,
+                                               vp, vp, C.POINTER(_Stats), vp]
         L.rich_mlmc_estimate.argtypes = [vp, C.POINTER(_MlmcCfg), C.POINTER(_MlmcResult)]
         _lib = L
     return _lib
@@ -180,7 +183,8 @@ def exported_symbols():
     return ["rich_create", "rich_destroy", "rich_status_str", "rich_last_error",
             "rich_sample_fields", "rich_solve_batch", "rich_solve_batch_host",
             "rich_mlmc_accumulate", "rich_profile", "rich_profile_read", "rich_launch_count",
-            "rich_solve_batch_noalloc", "rich_mlmc_estimate", "rich_sample_fields_pair"]
+            "rich_solve_batch_noalloc", "rich_mlmc_estimate", "rich_sample_fields_pair",
+            "rich_kl_fields", "rich_solve_batch_adjoint"]
 
 
 def _check(rc):
@@ -353,3 +357,68 @@ def mlmc_estimate(cfg: MlmcConfig, device=0):
                                             "bias_estimate", "seconds")})
     out["nlevels"], out["rc"] = NL, rc
     return out
+
+
+def kl_fields(basis, xi):
+    """ln Ks [S, nz, nx] = sum_j xi[:, j] basis[j] (device tensors, float64)."""
+    torch = _torch()
+    nkl, nz, nx = basis.shape
+    S = xi.shape[0]
+    out = torch.empty((S, nz, nx), dtype=torch.float64, device=basis.device)
+    dev = basis.device.index
+    _check(lib().rich_kl_fields(context(dev), _dev_ptr(basis, torch.float64, "basis"), nkl, nz * nx,
+                                _dev_ptr(xi, torch.float64, "xi"), S, _dev_ptr(out, torch.float64, "lnKs"),
+                                _stream(torch, dev)))
+    return out
+
+
+def solve_batch_adjoint(problem: Problem, basis, xi, alpha, alpha_scale=1.0, ckpt_every=10, want_dlnks=False):
+    """QoI [S] and dQ/dxi [S, n_kl] by the discrete adjoint (device tensors).
+    Returns (qoi, dq_dxi, dq_dlnKs or None, status, Stats, rc)."""
+    torch = _torch()
+    nkl = basis.shape[0]
+    S = xi.shape[0]
+    dev = basis.device.index
+    qoi = torch.empty(S, dtype=torch.float64, device=basis.device)
+    dq = torch.empty((S, nkl), dtype=torch.float64, device=basis.device)
+    status = torch.empty(S, dtype=torch.int32, device=basis.device)
+    g = torch.empty((S, problem.nz, problem.nx), dtype=torch.float64, device=basis.device) if want_dlnks else None
+    st = _Stats()
+    rc = _check(lib().rich_solve_batch_adjoint(context(dev), C.byref(problem._c()), S,
+                                               _dev_ptr(basis, torch.float64, "basis"), nkl,
+                                               _dev_ptr(xi, torch.float64, "xi"),
+                                               _dev_ptr(alpha, torch.float64, "alpha"), alpha_scale, ckpt_every,
+                                               _dev_ptr(qoi, torch.float64, "qoi"), _dev_ptr(dq, torch.float64, "dq"),
+                                               None if g is None else _dev_ptr(g, torch.float64, "g"),
+                                               _dev_ptr(status, torch.int32, "status"), C.byref(st),
+                                               _stream(torch, dev)))
+    return qoi, dq, g, status, Stats(*[getattr(st, f) for f, _ in _Stats._fields_]), rc
+
+
+def _autograd():
+    import torch
+
+    class RichardsQoI(torch.autograd.Function):
+        """qoi = RichardsQoI.apply(xi, alpha, basis, problem[, alpha_scale, ckpt_every]):
+        bottom-flux QoI of each sample with ln Ks = basis^T xi; backward returns
+        grad_qoi[:, None] * dQ/dxi from the discrete adjoint."""
+
+        @staticmethod
+        def forward(ctx, xi, alpha, basis, problem, alpha_scale=1.0, ckpt_every=10):
+            qoi, dq, _, status, _, _ = solve_batch_adjoint(problem, basis, xi.detach().contiguous(),
+                                                           alpha, alpha_scale, ckpt_every)
+            ctx.save_for_backward(dq)
+            return qoi
+
+        @staticmethod
+        def backward(ctx, grad_qoi):
+            (dq,) = ctx.saved_tensors
+            return grad_qoi[:, None] * dq, None, None, None, None, None
+
+    return RichardsQoI
+
+
+def __getattr__(name):
+    if name == "RichardsQoI":
+        return _autograd()
+    raise AttributeError(name)

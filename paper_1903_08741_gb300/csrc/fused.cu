@@ -71,6 +71,11 @@ struct FParams {
     int* queue;
     int nsteps, picard_maxit, mg_maxit, nu1, nu2;
     double inv_dt, tr, ts, p_top, p_bot, p_init, picard_tol, mg_tol, h, two_over_h2;
+    // adjoint (k_adjoint only)
+    int ckpt_every, adj_maxit, adj_inner;
+    double adj_tol;
+    long long o_ckpt, o_seg, o_lam, o_rhs, o_r, o_dE, o_dW, o_dN, o_dS, o_dg, o_g;
+    double* g_out;
 };
 
 // c / d for c * d < 2^32 (m = floor(2^32 / d) + 1), d = 1 handled apart
@@ -293,58 +298,38 @@ __device__ __forceinline__ unsigned long long resid_norm(const Lv<T>& L, bool re
     return block_max(m, red);
 }
 
+// CTA-cooperative building blocks of one sample's solve.  Every method is
+// called by all threads of the CTA and ends with the CTA synchronised.
 template <typename TM>
-__global__ void __launch_bounds__(512)
-k_fused(const FParams P) {
-    constexpr bool SC = Scaled<TM>::value;
-    extern __shared__ unsigned char smraw[];
-    TM* Amat = reinterpret_cast<TM*>(smraw);
-    __shared__ unsigned long long red[33];
-    __shared__ int s_sample;
-    __shared__ Lv64 L64[MAXL];
-    __shared__ Lv<TM> LM[MAXL];
-    const int tid = threadIdx.x, nt = blockDim.x;
-    char* slot = P.scratch + (size_t)blockIdx.x * P.slot_bytes;
-    const int nlev = P.nlev;
-    const bool mixed = P.mixed;
-    if (tid < nlev) {
-        const int l = tid;
-        Lv64& a = L64[l];
-        a.nx = P.nx[l]; a.nz = P.nz[l]; a.nc = a.nx * a.nz; a.mnx = P.mnx[l];
-        double** pp[N64] = {&a.Tx, &a.Tz, &a.Cdt, &a.D, &a.Tbt, &a.Tbb};
-        for (int k = 0; k < N64; ++k) *pp[k] = (double*)(slot + P.o64[l][k]);
-        Lv<TM>& b = LM[l];
-        b.nx = a.nx; b.nz = a.nz; b.hx = a.nx >> 1; b.nc = a.nc; b.mnx = P.mnx[l]; b.mhx = P.mhx[l];
-        TM** qq[NMG] = {&b.c0, &b.c1, &b.c2, &b.c3, &b.q, &b.f, &b.dp};
-        for (int k = 0; k < NMG; ++k) *qq[k] = P.omg[l][k] >= 0 ? (TM*)(slot + P.omg[l][k]) : nullptr;
-        if constexpr (SC) b.D = (TM*)a.D;                 // FP64: shares the operator diagonal
-        else b.D = b.c3;                                  // FP32: its own copy
-        if constexpr (!SC) b.c3 = nullptr;
+struct Cta {
+    static constexpr bool SC = Scaled<TM>::value;
+    const FParams& P;
+    Lv64* L64;
+    Lv<TM>* LM;
+    TM* Amat;
+    unsigned long long* red;
+    double *f64, *dp64, *p, *thold, *Ks, *aa, *K, *th;
+    int nx, nz, nc, nlev, tid, nt;
+    double h, t2h, idt, tr, ts;
+
+    __device__ Cta(const FParams& P_, char* slot, Lv64* l64, Lv<TM>* lm, TM* A, unsigned long long* r)
+        : P(P_), L64(l64), LM(lm), Amat(A), red(r) {
+        f64 = (double*)(slot + P.o_f64);
+        dp64 = SC ? (double*)LM[0].dp : (double*)(slot + P.o_dp64);
+        p = (double*)(slot + P.o_p);
+        thold = (double*)(slot + P.o_thold);
+        Ks = (double*)(slot + P.o_Ks);
+        aa = (double*)(slot + P.o_a);
+        K = (double*)(slot + P.o_K);
+        th = (double*)(slot + P.o_th);
+        nx = L64[0].nx; nz = L64[0].nz; nc = L64[0].nc; nlev = P.nlev;
+        tid = threadIdx.x; nt = blockDim.x;
+        h = P.h; t2h = P.two_over_h2; idt = P.inv_dt; tr = P.tr; ts = P.ts;
     }
-    __syncthreads();
-    double* f64 = (double*)(slot + P.o_f64);
-    double* dp64 = SC ? (double*)LM[0].dp : (double*)(slot + P.o_dp64);
-    double* p = (double*)(slot + P.o_p);
-    double* thold = (double*)(slot + P.o_thold);
-    double* Ks = (double*)(slot + P.o_Ks);
-    double* aa = (double*)(slot + P.o_a);
-    double* K = (double*)(slot + P.o_K);
-    double* th = (double*)(slot + P.o_th);
-    const Lv64& F = L64[0];
-    const Lv<TM>& M0 = LM[0];
-    const int nx = F.nx, nz = F.nz, nc = F.nc;
-    const double h = P.h, t2h = P.two_over_h2, idt = P.inv_dt, tr = P.tr, ts = P.ts;
 
-    for (;;) {
-        if (tid == 0) s_sample = atomicAdd(P.queue, 1);
-        __syncthreads();
-        const int s = s_sample;
-        __syncthreads();
-        if (s >= P.S) break;
-        const double* lk = P.lnKs + (size_t)s * nc;
-        const double* al = P.alpha + (size_t)s * nc;
-
-        // ---- set-up: Ks, alpha * scale, initial head, Dirichlet faces (fixed)
+    // Ks, alpha * scale, initial head, Dirichlet faces (fixed for the solve)
+    __device__ void setup(const double* lk, const double* al) {
+        const Lv64& F = L64[0];
         for (int q = tid; q < nc; q += nt) {
             Ks[q] = exp(lk[q]);
             aa[q] = al[q] * P.alpha_scale;
@@ -366,173 +351,363 @@ k_fused(const FParams P) {
             }
             __syncthreads();
         }
+    }
 
-        int status = RICH_OK;
-        bool alive = true;
-        long long pic_tot = 0, mg_tot = 0;
-        int maxpic = 0;
-        for (int step = 0; step < P.nsteps && alive; ++step) {
-            for (int q = tid; q < nc; q += nt) {
-                double pp = p[q];
-                thold[q] = pp < 0.0 ? tr + (ts - tr) * exp(aa[q] * pp) : ts;
+    // theta^n of the step's old head
+    __device__ void theta_old() {
+        for (int q = tid; q < nc; q += nt) {
+            double pp = p[q];
+            thold[q] = pp < 0.0 ? tr + (ts - tr) * exp(aa[q] * pp) : ts;
+        }
+        __syncthreads();
+    }
+
+    // Picard system at p (Gardner closure, harmonic faces, f = -R), all levels;
+    // returns ||f||_inf as a bit pattern
+    __device__ unsigned long long assemble() {
+        const Lv64& F = L64[0];
+        const Lv<TM>& M0 = LM[0];
+        for (int q = tid; q < nc; q += nt) {
+            double pp = p[q], ks = Ks[q];
+            if (pp < 0.0) {
+                double a = aa[q];
+                double E = exp(a * pp);
+                K[q] = ks * E;
+                th[q] = tr + (ts - tr) * E;
+                F.Cdt[q] = ((ts - tr) * a * E) * idt;
+            } else {
+                K[q] = ks; th[q] = ts; F.Cdt[q] = 0.0;
+            }
+        }
+        __syncthreads();
+        for (int q = tid; q < nc; q += nt) {
+            int j = fdiv(q, nx, F.mnx), i = q - j * nx;
+            double kp = K[q];
+            if (i < nx - 1) { double ke = K[q + 1]; F.Tx[q] = t2h * kp * ke / (kp + ke); }
+            else F.Tx[q] = 0.0;
+            if (j < nz - 1) { double kn = K[q + nx]; F.Tz[q] = t2h * kp * kn / (kp + kn); }
+            else F.Tz[q] = 0.0;
+        }
+        __syncthreads();
+        unsigned long long m = 0;
+        for (int q = tid; q < nc; q += nt) {
+            int j = fdiv(q, nx, F.mnx), i = q - j * nx;
+            double pp = p[q];
+            double R = (th[q] - thold[q]) * idt;
+            double d = F.Cdt[q];
+            double te = 0.0, tw = 0.0, tn = 0.0, tsf = 0.0;
+            if (i < nx - 1) { te = F.Tx[q];     R += -te * (p[q + 1] - pp); d += te; }
+            if (i > 0)      { tw = F.Tx[q - 1]; R += -tw * (p[q - 1] - pp); d += tw; }
+            if (j < nz - 1) { tn = F.Tz[q];     R += -tn * (p[q + nx] - pp) - tn * h; d += tn; }
+            else { double t = F.Tbt[i]; R += -t * (P.p_top - pp) - t * h / 2.0; d += t; }
+            if (j > 0)      { tsf = F.Tz[q - nx]; R += -tsf * (p[q - nx] - pp) + tsf * h; d += tsf; }
+            else { double t = F.Tbb[i]; R += t * (pp - P.p_bot) + t * h / 2.0; d += t; }
+            F.D[q] = d;
+            f64[q] = -R;
+            dp64[q] = 0.0;
+            if constexpr (SC) {
+                double inv = 1.0 / d;
+                M0.q[q] = inv;
+                M0.c0[q] = te * inv; M0.c1[q] = tw * inv; M0.c2[q] = tn * inv; M0.c3[q] = tsf * inv;
+                M0.f[q] = -R * inv;
+            } else {
+                M0.c0[q] = (TM)te; M0.c1[q] = (TM)tn; M0.D[q] = (TM)d;
+                M0.q[q] = (TM)(1.0f / (float)d);
+                M0.f[q] = (TM)(-R); M0.dp[q] = TM(0);
+            }
+            unsigned long long b = abs_bits(R);
+            m = b > m ? b : m;
+        }
+        const unsigned long long fb = block_max(m, red);
+        // coarse operators (Fig. diffUpscale)
+        for (int l = 1; l < nlev; ++l) {
+            const Lv64& Fl = L64[l - 1];
+            const Lv64& Cl = L64[l];
+            const Lv<TM>& Ml = LM[l];
+            const int fx = Fl.nx;
+            for (int c = tid; c < Cl.nc; c += nt) {
+                int J = fdiv(c, Cl.nx, Cl.mnx), I = c - J * Cl.nx;
+                int f00 = (2 * J) * fx + 2 * I, f01 = f00 + fx;
+                double cd = 0.25 * (Fl.Cdt[f00] + Fl.Cdt[f00 + 1] + Fl.Cdt[f01] + Fl.Cdt[f01 + 1]);
+                double d = cd, te = 0.0, tw = 0.0, tn = 0.0, tsf = 0.0;
+                if (I < Cl.nx - 1) { te = 0.25 * (0.5 * (Fl.Tx[f00 + 1] + Fl.Tx[f01 + 1])); d += te; }
+                if (I > 0)         { tw = 0.25 * (0.5 * (Fl.Tx[f00 - 1] + Fl.Tx[f01 - 1])); d += tw; }
+                if (J < Cl.nz - 1) { tn = 0.25 * (0.5 * (Fl.Tz[f01] + Fl.Tz[f01 + 1])); d += tn; }
+                else d += Cl.Tbt[I];
+                if (J > 0)         { tsf = 0.25 * (0.5 * (Fl.Tz[f00 - fx] + Fl.Tz[f00 - fx + 1])); d += tsf; }
+                else d += Cl.Tbb[I];
+                Cl.Tx[c] = te; Cl.Tz[c] = tn; Cl.Cdt[c] = cd; Cl.D[c] = d;
+                if constexpr (SC) {
+                    double inv = 1.0 / d;
+                    Ml.q[c] = inv;
+                    Ml.c0[c] = te * inv; Ml.c1[c] = tw * inv; Ml.c2[c] = tn * inv; Ml.c3[c] = tsf * inv;
+                } else {
+                    Ml.c0[c] = (TM)te; Ml.c1[c] = (TM)tn; Ml.D[c] = (TM)d;
+                    Ml.q[c] = (TM)(1.0f / (float)d);
+                }
             }
             __syncthreads();
-            int k = 0;
-            for (;;) {
-                // ---- Picard system at p^k (Gardner closure, harmonic faces, f = -R)
-                for (int q = tid; q < nc; q += nt) {
-                    double pp = p[q], ks = Ks[q];
-                    if (pp < 0.0) {
-                        double a = aa[q];
-                        double E = exp(a * pp);
-                        K[q] = ks * E;
-                        th[q] = tr + (ts - tr) * E;
-                        F.Cdt[q] = ((ts - tr) * a * E) * idt;
-                    } else {
-                        K[q] = ks; th[q] = ts; F.Cdt[q] = 0.0;
-                    }
-                }
-                __syncthreads();
-                for (int q = tid; q < nc; q += nt) {
-                    int j = fdiv(q, nx, F.mnx), i = q - j * nx;
-                    double kp = K[q];
-                    if (i < nx - 1) { double ke = K[q + 1]; F.Tx[q] = t2h * kp * ke / (kp + ke); }
-                    else F.Tx[q] = 0.0;
-                    if (j < nz - 1) { double kn = K[q + nx]; F.Tz[q] = t2h * kp * kn / (kp + kn); }
-                    else F.Tz[q] = 0.0;
-                }
-                __syncthreads();
-                unsigned long long m = 0;
-                for (int q = tid; q < nc; q += nt) {
-                    int j = fdiv(q, nx, F.mnx), i = q - j * nx;
-                    double pp = p[q];
-                    double R = (th[q] - thold[q]) * idt;
-                    double d = F.Cdt[q];
-                    double te = 0.0, tw = 0.0, tn = 0.0, tsf = 0.0;
-                    if (i < nx - 1) { te = F.Tx[q];     R += -te * (p[q + 1] - pp); d += te; }
-                    if (i > 0)      { tw = F.Tx[q - 1]; R += -tw * (p[q - 1] - pp); d += tw; }
-                    if (j < nz - 1) { tn = F.Tz[q];     R += -tn * (p[q + nx] - pp) - tn * h; d += tn; }
-                    else { double t = F.Tbt[i]; R += -t * (P.p_top - pp) - t * h / 2.0; d += t; }
-                    if (j > 0)      { tsf = F.Tz[q - nx]; R += -tsf * (p[q - nx] - pp) + tsf * h; d += tsf; }
-                    else { double t = F.Tbb[i]; R += t * (pp - P.p_bot) + t * h / 2.0; d += t; }
-                    F.D[q] = d;
-                    f64[q] = -R;
-                    dp64[q] = 0.0;
-                    if constexpr (SC) {
-                        double inv = 1.0 / d;
-                        M0.q[q] = inv;
-                        M0.c0[q] = te * inv; M0.c1[q] = tw * inv; M0.c2[q] = tn * inv; M0.c3[q] = tsf * inv;
-                        M0.f[q] = -R * inv;
-                    } else {
-                        M0.c0[q] = (TM)te; M0.c1[q] = (TM)tn; M0.D[q] = (TM)d;
-                        M0.q[q] = (TM)(1.0f / (float)d);
-                        M0.f[q] = (TM)(-R); M0.dp[q] = TM(0);
-                    }
-                    unsigned long long b = abs_bits(R);
-                    m = b > m ? b : m;
-                }
-                const unsigned long long fb = block_max(m, red);   // includes the sync
-                // ---- coarse operators (Fig. diffUpscale)
-                for (int l = 1; l < nlev; ++l) {
-                    const Lv64& Fl = L64[l - 1];
-                    const Lv64& Cl = L64[l];
-                    const Lv<TM>& Ml = LM[l];
-                    const int fx = Fl.nx;
-                    for (int c = tid; c < Cl.nc; c += nt) {
-                        int J = fdiv(c, Cl.nx, Cl.mnx), I = c - J * Cl.nx;
-                        int f00 = (2 * J) * fx + 2 * I, f01 = f00 + fx;
-                        double cd = 0.25 * (Fl.Cdt[f00] + Fl.Cdt[f00 + 1] + Fl.Cdt[f01] + Fl.Cdt[f01 + 1]);
-                        double d = cd, te = 0.0, tw = 0.0, tn = 0.0, tsf = 0.0;
-                        if (I < Cl.nx - 1) { te = 0.25 * (0.5 * (Fl.Tx[f00 + 1] + Fl.Tx[f01 + 1])); d += te; }
-                        if (I > 0)         { tw = 0.25 * (0.5 * (Fl.Tx[f00 - 1] + Fl.Tx[f01 - 1])); d += tw; }
-                        if (J < Cl.nz - 1) { tn = 0.25 * (0.5 * (Fl.Tz[f01] + Fl.Tz[f01 + 1])); d += tn; }
-                        else d += Cl.Tbt[I];
-                        if (J > 0)         { tsf = 0.25 * (0.5 * (Fl.Tz[f00 - fx] + Fl.Tz[f00 - fx + 1])); d += tsf; }
-                        else d += Cl.Tbb[I];
-                        Cl.Tx[c] = te; Cl.Tz[c] = tn; Cl.Cdt[c] = cd; Cl.D[c] = d;
-                        if constexpr (SC) {
-                            double inv = 1.0 / d;
-                            Ml.q[c] = inv;
-                            Ml.c0[c] = te * inv; Ml.c1[c] = tw * inv; Ml.c2[c] = tn * inv; Ml.c3[c] = tsf * inv;
-                        } else {
-                            Ml.c0[c] = (TM)te; Ml.c1[c] = (TM)tn; Ml.D[c] = (TM)d;
-                            Ml.q[c] = (TM)(1.0f / (float)d);
-                        }
-                    }
-                    __syncthreads();
-                }
-                if (fb > INF_BITS - 1) { status = max(status, (int)RICH_NONFINITE); alive = false; break; }
-                // ---- multigrid solve of A dp = f
-                const double fn = __longlong_as_double((long long)fb);
-                const double target = P.mg_tol * (fn > 1.0 ? fn : 1.0);
-                double rn = fn;
-                int cyc = 0;
-                bool nonfinite = false;
-                while (rn >= target && cyc < P.mg_maxit) {
-                    unsigned long long rb;
-                    if constexpr (SC) {
-                        vcycle<TM>(LM, L64, nlev, P.nu1, P.nu2, Amat, (const TM*)f64);
-                        ++cyc;
-                        rb = resid_norm<TM>(M0, P.nu2 > 0 && nlev > 1, red);
-                    } else {
-                        for (int in = 0; in < MIXED_INNER && cyc < P.mg_maxit; ++in) {
-                            vcycle<TM>(LM, L64, nlev, P.nu1, P.nu2, Amat, nullptr);
-                            ++cyc;
-                        }
-                        // dp += e in FP64, then the FP64 defect: stopping norm and the
-                        // next FP32 right-hand side
-                        unsigned long long mm = 0;
-                        for (int q = tid; q < nc; q += nt) dp64[q] += (double)M0.dp[q];
-                        __syncthreads();
-                        for (int q = tid; q < nc; q += nt) {
-                            int j = fdiv(q, nx, F.mnx), i = q - j * nx;
-                            double sn = 0.0;
-                            if (i < nx - 1) sn += F.Tx[q] * dp64[q + 1];
-                            if (i > 0)      sn += F.Tx[q - 1] * dp64[q - 1];
-                            if (j < nz - 1) sn += F.Tz[q] * dp64[q + nx];
-                            if (j > 0)      sn += F.Tz[q - nx] * dp64[q - nx];
-                            double r = f64[q] - (F.D[q] * dp64[q] - sn);
-                            M0.f[q] = (TM)r;
-                            M0.dp[q] = TM(0);
-                            unsigned long long b = abs_bits(r);
-                            mm = b > mm ? b : mm;
-                        }
-                        rb = block_max(mm, red);
-                    }
-                    if (rb > INF_BITS - 1) { nonfinite = true; break; }
-                    rn = __longlong_as_double((long long)rb);
-                }
-                mg_tot += cyc;
-                if (nonfinite) { status = max(status, (int)RICH_NONFINITE); alive = false; break; }
-                if (!(rn < target)) status = max(status, (int)RICH_MG_MAXIT);
-                // ---- p^{k+1} = p^k + dp, ||dp||_inf
-                unsigned long long dm = 0;
-                for (int q = tid; q < nc; q += nt) {
-                    double d = dp64[q];
-                    p[q] += d;
-                    unsigned long long b = abs_bits(d);
-                    dm = b > dm ? b : dm;
-                }
-                const unsigned long long db = block_max(dm, red);
-                ++k;
-                ++pic_tot;
-                if (db > INF_BITS - 1) { status = max(status, (int)RICH_NONFINITE); alive = false; break; }
-                if (__longlong_as_double((long long)db) < P.picard_tol) break;
-                if (k >= P.picard_maxit) { status = max(status, (int)RICH_PICARD_MAXIT); alive = false; break; }
-            }
-            maxpic = max(maxpic, k);
         }
-        // ---- QoI: mean outward Darcy flux through the bottom faces
-        if (tid < 32) {
-            double acc = 0.0;
-            for (int i = tid; i < nx; i += 32) {
-                double kb = P.p_bot < 0.0 ? Ks[i] * exp(aa[i] * P.p_bot) : Ks[i];
-                acc += kb * (2.0 * (p[i] - P.p_bot) / h + 1.0);
+        return fb;
+    }
+
+    // FP64 residual f - A x of the finest operator at cell q
+    __device__ __forceinline__ double resid64(const double* f, const double* x, int q) const {
+        const Lv64& F = L64[0];
+        int j = fdiv(q, nx, F.mnx), i = q - j * nx;
+        double sn = 0.0;
+        if (i < nx - 1) sn += F.Tx[q] * x[q + 1];
+        if (i > 0)      sn += F.Tx[q - 1] * x[q - 1];
+        if (j < nz - 1) sn += F.Tz[q] * x[q + nx];
+        if (j > 0)      sn += F.Tz[q - nx] * x[q - nx];
+        return f[q] - (F.D[q] * x[q] - sn);
+    }
+
+    // multigrid solve of A dp = f from dp = 0 (set up by assemble()); stops
+    // when ||f - A dp||_inf < mg_tol max(1, ||f||_inf).  Returns false when a
+    // norm is not finite.
+    __device__ bool mg_solve(unsigned long long fb, long long& mg_tot, int& status) {
+        const Lv<TM>& M0 = LM[0];
+        const double fn = __longlong_as_double((long long)fb);
+        const double target = P.mg_tol * (fn > 1.0 ? fn : 1.0);
+        double rn = fn;
+        int cyc = 0;
+        while (rn >= target && cyc < P.mg_maxit) {
+            unsigned long long rb;
+            if constexpr (SC) {
+                vcycle<TM>(LM, L64, nlev, P.nu1, P.nu2, Amat, (const TM*)f64);
+                ++cyc;
+                rb = resid_norm<TM>(M0, P.nu2 > 0 && nlev > 1, red);
+            } else {
+                for (int in = 0; in < MIXED_INNER && cyc < P.mg_maxit; ++in) {
+                    vcycle<TM>(LM, L64, nlev, P.nu1, P.nu2, Amat, nullptr);
+                    ++cyc;
+                }
+                // dp += e in FP64, then the FP64 defect: stopping norm and the
+                // next FP32 right-hand side
+                unsigned long long mm = 0;
+                for (int q = tid; q < nc; q += nt) dp64[q] += (double)M0.dp[q];
+                __syncthreads();
+                for (int q = tid; q < nc; q += nt) {
+                    double r = resid64(f64, dp64, q);
+                    M0.f[q] = (TM)r;
+                    M0.dp[q] = TM(0);
+                    unsigned long long b = abs_bits(r);
+                    mm = b > mm ? b : mm;
+                }
+                rb = block_max(mm, red);
             }
+            if (rb > INF_BITS - 1) { mg_tot += cyc; return false; }
+            rn = __longlong_as_double((long long)rb);
+        }
+        mg_tot += cyc;
+        if (!(rn < target)) status = max(status, (int)RICH_MG_MAXIT);
+        return true;
+    }
+
+    // one implicit-Euler step by modified Picard (Sec. 4.1); returns false if
+    // the sample failed (status set)
+    __device__ bool time_step(long long& pic_tot, long long& mg_tot, int& maxpic, int& status) {
+        theta_old();
+        int k = 0;
+        bool alive = true;
+        for (;;) {
+            const unsigned long long fb = assemble();
+            if (fb > INF_BITS - 1) { status = max(status, (int)RICH_NONFINITE); alive = false; break; }
+            if (!mg_solve(fb, mg_tot, status)) { status = max(status, (int)RICH_NONFINITE); alive = false; break; }
+            unsigned long long dm = 0;
+            for (int q = tid; q < nc; q += nt) {
+                double d = dp64[q];
+                p[q] += d;
+                unsigned long long b = abs_bits(d);
+                dm = b > dm ? b : dm;
+            }
+            const unsigned long long db = block_max(dm, red);
+            ++k;
+            ++pic_tot;
+            if (db > INF_BITS - 1) { status = max(status, (int)RICH_NONFINITE); alive = false; break; }
+            if (__longlong_as_double((long long)db) < P.picard_tol) break;
+            if (k >= P.picard_maxit) { status = max(status, (int)RICH_PICARD_MAXIT); alive = false; break; }
+        }
+        maxpic = max(maxpic, k);
+        return alive;
+    }
+
+    // mean outward Darcy flux through the bottom faces (valid in warp 0)
+    __device__ double qoi_warp0() const {
+        double acc = 0.0;
+        for (int i = tid; i < nx; i += 32) {
+            double kb = P.p_bot < 0.0 ? Ks[i] * exp(aa[i] * P.p_bot) : Ks[i];
+            acc += kb * (2.0 * (p[i] - P.p_bot) / h + 1.0);
+        }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        return acc / nx;
+    }
+
+    // ------------------------------------------------------------ adjoint
+    // Jacobian pieces at the assembled state p = p^n: for every cell c and each
+    // interior face f (E, W, N, S) D_fc = T_f - g_cf dT_f/dp_c with
+    // g_cf = p_nb - p_c + s h (s = +1 north, -1 south), and the diagonal
+    // C_c/dt + Dirichlet T_b; so (J^T lam)_c = dg_c lam_c + sum_f D_fc (lam_c - lam_nb).
+    __device__ void adj_prepare(double* dE, double* dW, double* dN, double* dS, double* dg) {
+        const Lv64& F = L64[0];
+        for (int q = tid; q < nc; q += nt) {
+            int j = fdiv(q, nx, F.mnx), i = q - j * nx;
+            const double pc = p[q], kc = K[q];
+            const double dk = pc < 0.0 ? aa[q] * kc : 0.0;      // dK_c/dp_c
+            double e = 0.0, w = 0.0, n = 0.0, s = 0.0, d = F.Cdt[q];
+            if (i < nx - 1) { double kn = K[q + 1], den = kc + kn;
+                e = F.Tx[q] - (p[q + 1] - pc) * (t2h * kn * kn / (den * den)) * dk; }
+            if (i > 0)      { double kn = K[q - 1], den = kc + kn;
+                w = F.Tx[q - 1] - (p[q - 1] - pc) * (t2h * kn * kn / (den * den)) * dk; }
+            if (j < nz - 1) { double kn = K[q + nx], den = kc + kn;
+                n = F.Tz[q] - (p[q + nx] - pc + h) * (t2h * kn * kn / (den * den)) * dk; }
+            else d += F.Tbt[i];
+            if (j > 0)      { double kn = K[q - nx], den = kc + kn;
+                s = F.Tz[q - nx] - (p[q - nx] - pc - h) * (t2h * kn * kn / (den * den)) * dk; }
+            else d += F.Tbb[i];
+            dE[q] = e; dW[q] = w; dN[q] = n; dS[q] = s; dg[q] = d;
+        }
+        __syncthreads();
+    }
+
+    __device__ __forceinline__ double jt_apply(const double* dE, const double* dW, const double* dN,
+                                               const double* dS, const double* dg, const double* lam,
+                                               int q) const {
+        int j = fdiv(q, nx, L64[0].mnx), i = q - j * nx;
+        const double l = lam[q];
+        double v = dg[q] * l;
+        if (i < nx - 1) v += dE[q] * (l - lam[q + 1]);
+        if (i > 0)      v += dW[q] * (l - lam[q - 1]);
+        if (j < nz - 1) v += dN[q] * (l - lam[q + nx]);
+        if (j > 0)      v += dS[q] * (l - lam[q - nx]);
+        return v;
+    }
+
+    // approximate e = A^{-1} r by ninner V-cycles from e = 0 (A: the Picard
+    // operator assembled at the same state); e is returned in dp64 / M0.dp
+    __device__ void mg_apply(const double* r, int ninner) {
+        const Lv<TM>& M0 = LM[0];
+        for (int q = tid; q < nc; q += nt) {
+            if constexpr (SC) M0.f[q] = r[q] * M0.q[q];
+            else M0.f[q] = (TM)r[q];
+            M0.dp[q] = TM(0);
+        }
+        __syncthreads();
+        for (int k = 0; k < ninner; ++k) {
+            if constexpr (SC) vcycle<TM>(LM, L64, nlev, P.nu1, P.nu2, Amat, r);
+            else vcycle<TM>(LM, L64, nlev, P.nu1, P.nu2, Amat, nullptr);
+        }
+    }
+
+    // J^T lam = rhs by defect correction preconditioned with CCMG on A:
+    // lam += A^{-1}(rhs - J^T lam) until ||rhs - J^T lam|| <= adj_tol ||rhs||.
+    // Returns the number of outer iterations (adj_maxit + 1 when not converged).
+    __device__ int adj_solve(const double* dE, const double* dW, const double* dN, const double* dS,
+                             const double* dg, const double* rhs, double* lam, double* r) {
+        const Lv<TM>& M0 = LM[0];
+        unsigned long long m = 0;
+        for (int q = tid; q < nc; q += nt) {
+            lam[q] = 0.0;
+            r[q] = rhs[q];
+            unsigned long long b = abs_bits(rhs[q]);
+            m = b > m ? b : m;
+        }
+        const unsigned long long b0 = block_max(m, red);
+        const double target = P.adj_tol * __longlong_as_double((long long)b0);
+        if (b0 == 0) return 0;
+        for (int it = 1; it <= P.adj_maxit; ++it) {
+            mg_apply(r, P.adj_inner);
+            for (int q = tid; q < nc; q += nt) lam[q] += (double)M0.dp[q];
+            __syncthreads();
+            unsigned long long mm = 0;
+            for (int q = tid; q < nc; q += nt) {
+                double v = rhs[q] - jt_apply(dE, dW, dN, dS, dg, lam, q);
+                r[q] = v;
+                unsigned long long b = abs_bits(v);
+                mm = b > mm ? b : mm;
+            }
+            const unsigned long long rb = block_max(mm, red);
+            if (rb > INF_BITS - 1) return P.adj_maxit + 1;
+            if (__longlong_as_double((long long)rb) <= target) return it;
+        }
+        return P.adj_maxit + 1;
+    }
+
+    // g -= (dR/dm)^T lam at the assembled state (m = ln Ks): interior faces
+    // contribute -g_cf (lam_c - lam_nb) dT_f/dm_c with dT_f/dm_c =
+    // (2/h^2) K_nb^2 K_c / (K_c + K_nb)^2; Dirichlet faces -g_b T_b lam_c
+    __device__ void adj_grad_update(const double* lam, double* g) {
+        const Lv64& F = L64[0];
+        for (int q = tid; q < nc; q += nt) {
+            int j = fdiv(q, nx, F.mnx), i = q - j * nx;
+            const double pc = p[q], kc = K[q], lc = lam[q];
+            double v = 0.0;
+            if (i < nx - 1) { double kn = K[q + 1], den = kc + kn;
+                v -= (p[q + 1] - pc) * (lc - lam[q + 1]) * (t2h * kn * kn * kc / (den * den)); }
+            if (i > 0)      { double kn = K[q - 1], den = kc + kn;
+                v -= (p[q - 1] - pc) * (lc - lam[q - 1]) * (t2h * kn * kn * kc / (den * den)); }
+            if (j < nz - 1) { double kn = K[q + nx], den = kc + kn;
+                v -= (p[q + nx] - pc + h) * (lc - lam[q + nx]) * (t2h * kn * kn * kc / (den * den)); }
+            else v -= (P.p_top - pc + h / 2.0) * F.Tbt[i] * lc;
+            if (j > 0)      { double kn = K[q - nx], den = kc + kn;
+                v -= (p[q - nx] - pc - h) * (lc - lam[q - nx]) * (t2h * kn * kn * kc / (den * den)); }
+            else v -= (P.p_bot - pc - h / 2.0) * F.Tbb[i] * lc;
+            g[q] -= v;
+        }
+        __syncthreads();
+    }
+};
+
+template <typename TM>
+__device__ __forceinline__ void init_levels(const FParams& P, char* slot, Lv64* L64, Lv<TM>* LM) {
+    constexpr bool SC = Scaled<TM>::value;
+    const int nlev = P.nlev;
+    if ((int)threadIdx.x < nlev) {
+        const int l = threadIdx.x;
+        Lv64& a = L64[l];
+        a.nx = P.nx[l]; a.nz = P.nz[l]; a.nc = a.nx * a.nz; a.mnx = P.mnx[l];
+        double** pp[N64] = {&a.Tx, &a.Tz, &a.Cdt, &a.D, &a.Tbt, &a.Tbb};
+        for (int k = 0; k < N64; ++k) *pp[k] = (double*)(slot + P.o64[l][k]);
+        Lv<TM>& b = LM[l];
+        b.nx = a.nx; b.nz = a.nz; b.hx = a.nx >> 1; b.nc = a.nc; b.mnx = P.mnx[l]; b.mhx = P.mhx[l];
+        TM** qq[NMG] = {&b.c0, &b.c1, &b.c2, &b.c3, &b.q, &b.f, &b.dp};
+        for (int k = 0; k < NMG; ++k) *qq[k] = P.omg[l][k] >= 0 ? (TM*)(slot + P.omg[l][k]) : nullptr;
+        if constexpr (SC) b.D = (TM*)a.D;                 // FP64: shares the operator diagonal
+        else { b.D = b.c3; b.c3 = nullptr; }              // FP32: its own copy
+    }
+    __syncthreads();
+}
+
+template <typename TM>
+__global__ void __launch_bounds__(512)
+k_fused(const FParams P) {
+    extern __shared__ unsigned char smraw[];
+    __shared__ unsigned long long red[33];
+    __shared__ int s_sample;
+    __shared__ Lv64 L64[MAXL];
+    __shared__ Lv<TM> LM[MAXL];
+    char* slot = P.scratch + (size_t)blockIdx.x * P.slot_bytes;
+    init_levels<TM>(P, slot, L64, LM);
+    Cta<TM> C(P, slot, L64, LM, reinterpret_cast<TM*>(smraw), red);
+    const int nc = C.nc, tid = C.tid, nt = C.nt;
+    for (;;) {
+        if (tid == 0) s_sample = atomicAdd(P.queue, 1);
+        __syncthreads();
+        const int s = s_sample;
+        __syncthreads();
+        if (s >= P.S) break;
+        C.setup(P.lnKs + (size_t)s * nc, P.alpha + (size_t)s * nc);
+        int status = RICH_OK, maxpic = 0;
+        bool alive = true;
+        long long pic_tot = 0, mg_tot = 0;
+        for (int step = 0; step < P.nsteps && alive; ++step)
+            alive = C.time_step(pic_tot, mg_tot, maxpic, status);
+        if (tid < 32) {
+            const double q = C.qoi_warp0();
             if (tid == 0) {
-                P.qoi[s] = alive ? acc / nx : __longlong_as_double(0x7FF8000000000000ll);
+                P.qoi[s] = alive ? q : __longlong_as_double(0x7FF8000000000000ll);
                 if (P.status) P.status[s] = status;
                 if (P.pic_total) P.pic_total[s] = pic_tot;
                 if (P.mg_total) P.mg_total[s] = mg_tot;
@@ -540,7 +715,116 @@ k_fused(const FParams P) {
             }
         }
         if (P.p_final)
-            for (int q = tid; q < nc; q += nt) P.p_final[(size_t)s * nc + q] = p[q];
+            for (int q = tid; q < nc; q += nt) P.p_final[(size_t)s * nc + q] = C.p[q];
+        __syncthreads();
+    }
+}
+
+// Discrete adjoint of the converged time-stepped solve (one sample per CTA):
+// forward with a checkpoint of p every ckpt_every steps, then per segment
+// (last first) recompute its states from the checkpoint and step backwards:
+//   J_N^T lam_N = dQ/dp^N,  J_n^T lam_n = diag(C(p^n)/dt) lam_{n+1},
+//   dQ/dm = dQ/dm|explicit - sum_n (dR_n/dm)^T lam_n     (m = ln Ks).
+template <typename TM>
+__global__ void __launch_bounds__(512)
+k_adjoint(const FParams P) {
+    extern __shared__ unsigned char smraw[];
+    __shared__ unsigned long long red[33];
+    __shared__ int s_sample;
+    __shared__ Lv64 L64[MAXL];
+    __shared__ Lv<TM> LM[MAXL];
+    char* slot = P.scratch + (size_t)blockIdx.x * P.slot_bytes;
+    init_levels<TM>(P, slot, L64, LM);
+    Cta<TM> C(P, slot, L64, LM, reinterpret_cast<TM*>(smraw), red);
+    const int nc = C.nc, nx = C.nx, tid = C.tid, nt = C.nt;
+    const int CK = P.ckpt_every;
+    double* ckpt = (double*)(slot + P.o_ckpt);      // [nck][nc]
+    double* seg = (double*)(slot + P.o_seg);        // [CK][nc]
+    double* lam = (double*)(slot + P.o_lam);
+    double* rhs = (double*)(slot + P.o_rhs);
+    double* r = (double*)(slot + P.o_r);
+    double* dE = (double*)(slot + P.o_dE);
+    double* dW = (double*)(slot + P.o_dW);
+    double* dN = (double*)(slot + P.o_dN);
+    double* dS = (double*)(slot + P.o_dS);
+    double* dg = (double*)(slot + P.o_dg);
+    double* g = (double*)(slot + P.o_g);
+    const double NaN = __longlong_as_double(0x7FF8000000000000ll);
+    for (;;) {
+        if (tid == 0) s_sample = atomicAdd(P.queue, 1);
+        __syncthreads();
+        const int s = s_sample;
+        __syncthreads();
+        if (s >= P.S) break;
+        C.setup(P.lnKs + (size_t)s * nc, P.alpha + (size_t)s * nc);
+        int status = RICH_OK, maxpic = 0;
+        bool alive = true;
+        long long pic_tot = 0, mg_tot = 0, adj_its = 0;
+        // ---- forward with checkpoints p^0, p^CK, p^2CK, ...
+        for (int n = 1; n <= P.nsteps && alive; ++n) {
+            if ((n - 1) % CK == 0) {
+                double* dst = ckpt + (size_t)((n - 1) / CK) * nc;
+                for (int q = tid; q < nc; q += nt) dst[q] = C.p[q];
+                __syncthreads();
+            }
+            alive = C.time_step(pic_tot, mg_tot, maxpic, status);
+        }
+        double qv = 0.0;
+        if (tid < 32) qv = C.qoi_warp0();
+        if (alive) {
+            // ---- dQ/dp^N (rhs) and the explicit dQ/dm (g), bottom cells
+            for (int q = tid; q < nc; q += nt) {
+                double gv = 0.0, rv = 0.0;
+                if (q < nx) {
+                    double kb = P.p_bot < 0.0 ? C.Ks[q] * exp(C.aa[q] * P.p_bot) : C.Ks[q];
+                    rv = kb * (2.0 / C.h) / nx;
+                    gv = kb * (2.0 * (C.p[q] - P.p_bot) / C.h + 1.0) / nx;
+                }
+                rhs[q] = rv;
+                g[q] = gv;
+            }
+            __syncthreads();
+            const int nck = (P.nsteps + CK - 1) / CK;
+            for (int sg = nck - 1; sg >= 0 && alive; --sg) {
+                const int n0 = sg * CK, n1 = min(n0 + CK, P.nsteps);
+                // recompute p^{n0+1..n1} from the checkpoint
+                for (int q = tid; q < nc; q += nt) C.p[q] = ckpt[(size_t)sg * nc + q];
+                __syncthreads();
+                long long dpic = 0, dmg = 0;
+                int dmax = 0, dst = RICH_OK;
+                for (int n = n0 + 1; n <= n1 && alive; ++n) {
+                    alive = C.time_step(dpic, dmg, dmax, dst);
+                    double* dstp = seg + (size_t)(n - n0 - 1) * nc;
+                    for (int q = tid; q < nc; q += nt) dstp[q] = C.p[q];
+                    __syncthreads();
+                }
+                if (!alive) { status = max(status, dst); break; }
+                for (int n = n1; n > n0; --n) {
+                    // state p^n, operator and Jacobian at p^n
+                    const double* pn = seg + (size_t)(n - n0 - 1) * nc;
+                    for (int q = tid; q < nc; q += nt) C.p[q] = pn[q];
+                    __syncthreads();
+                    C.assemble();
+                    if (n < P.nsteps) {       // rhs = diag(C(p^n)/dt) lam_{n+1}
+                        for (int q = tid; q < nc; q += nt) rhs[q] = L64[0].Cdt[q] * lam[q];
+                        __syncthreads();
+                    }
+                    C.adj_prepare(dE, dW, dN, dS, dg);
+                    const int its = C.adj_solve(dE, dW, dN, dS, dg, rhs, lam, r);
+                    adj_its += its;
+                    if (its > P.adj_maxit) status = max(status, (int)RICH_MG_MAXIT);
+                    C.adj_grad_update(lam, g);
+                }
+            }
+        }
+        if (tid == 0) {
+            P.qoi[s] = alive ? qv : NaN;
+            if (P.status) P.status[s] = status;
+            if (P.pic_total) P.pic_total[s] = pic_tot;
+            if (P.mg_total) P.mg_total[s] = adj_its;
+            if (P.maxpic) P.maxpic[s] = maxpic;
+        }
+        for (int q = tid; q < nc; q += nt) P.g_out[(size_t)s * nc + q] = alive ? g[q] : NaN;
         __syncthreads();
     }
 }
@@ -551,7 +835,7 @@ size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 }  // namespace
 
 // Slot layout and problem constants of the fused kernel (no device work).
-static int fused_setup(const rich_problem_t* pb, int S, FParams& P) {
+static int fused_setup(const rich_problem_t* pb, int S, FParams& P, int ckpt_every = 0) {
     P = FParams{};
     const int nlev = rich_count_levels(pb->nx, pb->nz);
     if (nlev < 1) return RICH_ERR_INVALID;
@@ -585,6 +869,14 @@ static int fused_setup(const rich_problem_t* pb, int S, FParams& P) {
     P.o_a = off; off = al256(off + nc8);
     P.o_K = off; off = al256(off + nc8);
     P.o_th = off; off = al256(off + nc8);
+    if (ckpt_every > 0) {
+        const int nck = (pb->nsteps + ckpt_every - 1) / ckpt_every;
+        P.ckpt_every = ckpt_every;
+        P.o_ckpt = off; off = al256(off + nc8 * std::max(nck, 1));
+        P.o_seg = off; off = al256(off + nc8 * ckpt_every);
+        long long* adj[] = {&P.o_lam, &P.o_rhs, &P.o_r, &P.o_dE, &P.o_dW, &P.o_dN, &P.o_dS, &P.o_dg, &P.o_g};
+        for (long long* o : adj) { *o = (long long)off; off = al256(off + nc8); }
+    }
     P.slot_bytes = (long long)off;
     P.nsteps = pb->nsteps; P.picard_maxit = pb->picard_maxit; P.mg_maxit = pb->mg_maxit;
     P.nu1 = pb->nu1; P.nu2 = pb->nu2;
@@ -649,6 +941,47 @@ int rich_solve_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const doubl
     rich_prof_end(ctx, st, 0.0, 0.0);
     if (status)
         RICH_CUDA(cudaMemcpyAsync(status, w.status, sizeof(int32_t) * S, cudaMemcpyDeviceToDevice, st));
+    return 0;
+}
+
+// Discrete adjoint of S samples: QoI and dQ/d ln Ks [S][nz][nx] (g_out).
+int rich_adjoint_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const double* lnKs,
+                       const double* alpha, double alpha_scale, int ckpt_every, double adj_tol,
+                       int adj_maxit, double* qoi, double* g_out, cudaStream_t st) {
+    rich_samplebuf& w = ctx->sb;
+    FParams P;
+    if (ckpt_every < 1) return RICH_ERR_INVALID;
+    if (int e = fused_setup(pb, S, P, ckpt_every)) return e;
+    P.adj_tol = adj_tol; P.adj_maxit = adj_maxit; P.adj_inner = pb->precision == RICH_MIXED ? 2 : 1;
+    const size_t smem = fused_smem(P);
+    int occ = 0;
+    if (P.mixed) {
+        RICH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adjoint<float>, 512, smem));
+    } else {
+        RICH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adjoint<double>, 512, smem));
+    }
+    occ = std::max(occ, 1);
+    const int grid = std::max(1, std::min(S, ctx->sm_count * occ));
+    const size_t need = (size_t)grid * (size_t)P.slot_bytes + 256;
+    if (ctx->fused_bytes < need) {
+        if (ctx->fused_scratch) cudaFree(ctx->fused_scratch);
+        ctx->fused_scratch = nullptr; ctx->fused_bytes = 0;
+        cudaError_t e = cudaMalloc(&ctx->fused_scratch, need);
+        if (e != cudaSuccess) { cudaGetLastError(); return RICH_ERR_OOM; }
+        ctx->fused_bytes = need;
+    }
+    P.scratch = (char*)ctx->fused_scratch + 256;
+    P.queue = (int*)ctx->fused_scratch;
+    P.lnKs = lnKs; P.alpha = alpha; P.alpha_scale = alpha_scale;
+    P.qoi = qoi; P.p_final = nullptr; P.status = w.status; P.g_out = g_out;
+    P.pic_total = w.pic_total; P.mg_total = w.mg_total; P.maxpic = w.maxpic;
+    RICH_CUDA(cudaMemsetAsync(P.queue, 0, sizeof(int), st));
+    rich_count_launch();
+    rich_prof_begin(ctx, st);
+    if (P.mixed) k_adjoint<float><<<grid, 512, smem, st>>>(P);
+    else k_adjoint<double><<<grid, 512, smem, st>>>(P);
+    rich_prof_end(ctx, st, 0.0, 0.0);
+    RICH_CUDA(cudaGetLastError());
     return 0;
 }
 

@@ -75,6 +75,9 @@ int rich_solve_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const doubl
                      const double* alpha, double alpha_scale, double* qoi, double* p_final,
                      int32_t* status, cudaStream_t st);
 void rich_prof_amend(rich_ctx* ctx, double bytes, double flops);
+int rich_adjoint_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const double* lnKs,
+                       const double* alpha, double alpha_scale, int ckpt_every, double adj_tol,
+                       int adj_maxit, double* qoi, double* g_out, cudaStream_t st);
 int rich_check_problem(const rich_problem_t* pb);
 
 // ---- fields (fields.cu)
