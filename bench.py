@@ -199,6 +199,130 @@ def run_mlmc(args):
     print(json.dumps(out))
 
 
+def run_adjoint(args):
+    """Discrete adjoint (256^2 grid, 256 samples, 50 steps of dt = 0.002, ln Ks
+    from a 128-mode KL expansion of exp(-r/0.2), xi ~ N(0,1) seed 0, alpha as
+    in the 32^2 workload): gradients of the bottom-flux QoI w.r.t. the KL
+    coefficients per second.  --check adds central finite differences (step
+    1e-6, tight tolerances) on 2 samples x 2 coefficients."""
+    import numpy as np
+    import torch
+    import paper_1903_08741_gb300 as R
+    from paper_1903_08741_gb300 import build as B
+    from paper_1903_08741_gb300.kl import kl_basis
+    B.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda:0")
+    n, S, steps, dt, nkl = 256, args.samples or 256, args.time_steps or 50, 0.002, 128
+    prec = R.MIXED if args.precision == "mixed" else R.FP64
+    basis, lam = kl_basis(n, n, nkl, 1.0, 0.2)
+    Bd = torch.from_numpy(basis).to(dev)
+    xi = torch.from_numpy(np.random.default_rng(0).normal(size=(S, nkl))).to(dev)
+    _, al = R.sample_fields(n, n, S, R.FieldModel(seed=0))
+    pb = R.Problem(nx=n, nz=n, nsteps=steps, dt=dt, precision=prec, **PHYS)
+    for k in range(args.warmup):
+        small = R.Problem(nx=n, nz=n, nsteps=2, dt=dt, precision=prec, **PHYS)
+        R.solve_batch_adjoint(small, Bd, xi[:8].contiguous(), al[:8].contiguous(), ckpt_every=10)
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = R.launch_count()
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        q, dq, _, st, stats, rc = R.solve_batch_adjoint(pb, Bd, xi, al, ckpt_every=10)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    launches = R.launch_count() - l0
+    clk = clocks.stop()
+    stv = st.cpu().numpy()
+    out = {
+        "metric": "adjoint gradients/s", "value": S * args.steps / (ms / 1e3), "unit": "gradients/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == R.FP64 else "f32-in-f64", "data": "synthetic",
+        "config": {"workload": f"adjoint{n}: {n}x{n} grid, {S} samples, {steps} steps dt={dt}, "
+                               f"ln Ks = 128-mode KL (exp. cov. 0.2), checkpoint every 10 steps",
+                   "kl_variance_captured": float(lam.sum() / (n * n))},
+        "clocks": clk, "gpu_launches": launches,
+        "failed_samples": int(((stv == 1) | (stv == 3)).sum()),
+        "adjoint_linear_solve_limit_hit": int((stv == 2).sum()),
+        "picard_iters_per_sample": stats.picard_iters / S,
+        "adjoint_outer_iters_per_sample": stats.mg_cycles / S,
+        "mean_qoi": float(np.nanmean(q.cpu().numpy())),
+        "mean_abs_grad": float(np.nanmean(np.abs(dq.cpu().numpy()))),
+    }
+    if args.check:
+        tight = dict(PHYS)
+        tight.update(picard_tol=1e-13, mg_tol=1e-14, picard_maxit=200, mg_maxit=400)
+        pt = R.Problem(nx=n, nz=n, nsteps=steps, dt=dt, **tight)
+        sel = [0, 1]
+        qa, dqa, _, sta, _, _ = R.solve_batch_adjoint(pt, Bd, xi[sel].contiguous(), al[sel].contiguous())
+        errs = []
+        for j in (0, 7):
+            xp, xm = xi[sel].clone(), xi[sel].clone()
+            xp[:, j] += 1e-6
+            xm[:, j] -= 1e-6
+            qp = R.solve_batch(pt, R.kl_fields(Bd, xp), al[sel].contiguous())[0]
+            qm = R.solve_batch(pt, R.kl_fields(Bd, xm), al[sel].contiguous())[0]
+            fd = ((qp - qm) / 2e-6).cpu().numpy()
+            a = dqa[:, j].cpu().numpy()
+            errs += list(np.abs(a - fd) / np.maximum(np.abs(fd), 1e-300))
+        out["fd_check"] = {"samples": sel, "coefficients": [0, 7], "max_rel_err": float(max(errs)),
+                           "tolerances": "Picard 1e-13, MG 1e-14, step 1e-6"}
+    print(json.dumps(out))
+
+
+def run_mc512(args):
+    """512^2 grid, 160 steps of dt = 0.1/160 (h = dt scaling of the level
+    hierarchy), the 32^2 workload's field model: FP32 V-cycles in FP64 defect
+    correction vs the FP64 batched path on the same samples; QoI error of the
+    mixed path relative to FP64."""
+    import numpy as np
+    import torch
+    import paper_1903_08741_gb300 as R
+    from paper_1903_08741_gb300 import build as B
+    B.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda:0")
+    n, S, steps = 512, args.samples or 1024, args.time_steps or 160
+    dt = 0.1 / 160
+    lk, al = R.sample_fields(n, n, S, R.FieldModel(seed=0))
+    res = {}
+    stream = torch.cuda.current_stream(dev)
+    clocks = ClockSampler(0)
+    clocks.start()
+    for name, prec in (("mixed", R.MIXED), ("fp64", R.FP64)):
+        pb = R.Problem(nx=n, nz=n, nsteps=steps, dt=dt, precision=prec, **PHYS)
+        R.solve_batch(pb, lk[:4].contiguous(), al[:4].contiguous())       # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        q, _, st, stats, rc = R.solve_batch(pb, lk, al)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        res[name] = (q.cpu().numpy(), st.cpu().numpy(), e0.elapsed_time(e1), stats)
+    clk = clocks.stop()
+    qm, sm_, tm, stm = res["mixed"]
+    qd, sd, td, std_ = res["fp64"]
+    ok = (sm_ == 0) & (sd == 0)
+    rel = np.abs(qm[ok] - qd[ok]) / np.abs(qd[ok])
+    out = {
+        "metric": "Picard-MG solves/s", "value": S / (tm / 1e3), "unit": "solves/s", "n_gpus": 1,
+        "steps": 1, "warmup": 1, "ms_per_step": tm, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32-in-f64", "data": "synthetic",
+        "config": {"workload": f"mc512: {n}x{n} grid, {S} samples, {steps} steps dt={dt:.6g}"},
+        "clocks": clk,
+        "fp64": {"value": S / (td / 1e3), "ms": td, "vcycles_per_sample": std_.mg_cycles / S},
+        "mixed_vcycles_per_sample": stm.mg_cycles / S,
+        "speedup_mixed_vs_fp64": td / tm,
+        "qoi_rel_err_mixed_vs_fp64": {"max": float(rel.max()), "median": float(np.median(rel)), "n": int(ok.sum())},
+        "failed": {"mixed": int(((sm_ == 1) | (sm_ == 3)).sum()), "fp64": int(((sd == 1) | (sd == 3)).sum())},
+    }
+    print(json.dumps(out))
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -349,7 +473,8 @@ def main():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["mlmc5"], default="mc128")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["mlmc5", "adjoint256", "mc512"], default="mc128")
+    ap.add_argument("--check", action="store_true", help="adjoint workload: finite-difference check")
     ap.add_argument("--coupling", type=int, default=0, help="MLMC field coupling (0 exact, 1 level grid)")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--no-e2e", action="store_true")
@@ -365,6 +490,10 @@ def main():
         run_reference(args)
     elif args.workload == "mlmc5":
         run_mlmc(args)
+    elif args.workload == "adjoint256":
+        run_adjoint(args)
+    elif args.workload == "mc512":
+        run_mc512(args)
     else:
         run_ours(args)
 
