@@ -341,6 +341,8 @@ def run_ours(args):
     steps = args.time_steps or steps
     prec = R.MIXED if args.precision == "mixed" else R.FP64
     pb = R.Problem(nx=n, nz=n, nsteps=steps, dt=dt, precision=prec, **PHYS)
+    from paper_1903_08741_gb300 import autotune
+    block_threads, mixed_inner = autotune.tune(pb, S, device=local)
     model = R.FieldModel(seed=0)
     lk = torch.empty((S, n, n), dtype=torch.float64, device=dev)
     al = torch.empty_like(lk)
@@ -445,6 +447,7 @@ def run_ours(args):
         "config": {"workload": f"mc{n}: {n}x{n} grid, {S} samples/GPU, {steps} steps dt={dt}, "
                                f"{'FP64' if prec == R.FP64 else 'FP32 V-cycles in FP64 defect correction'}",
                    "global_batch": S * ws, "grid": [n, n], "time_steps": steps,
+                   "launch": {"block_threads": block_threads, "mixed_inner": mixed_inner, "from": "autotuner"},
                    "l2": "inputs larger than L2 (2 x %.0f MB fields per step, fresh samples each step)"
                          % (S * n * n * 8 / 1e6)},
         "clocks": clk, "gpu_launches": launches, "roofline": roof,

@@ -84,6 +84,15 @@ const char* rich_status_str(int code);
 /* Text of the last fatal error seen by the calling thread (never NULL). */
 const char* rich_last_error(void);
 
+/* Launch tuning of this context's solves (set by the autotuner of the Python
+ * package, which times the candidates and caches the choice per grid,
+ * precision and batch): block_threads 512 (two resident CTAs per SM) or 1024
+ * (one), 0 = default 512; mixed_inner = FP32 V-cycles per FP64 defect in
+ * RICH_MIXED solves, 0 = default 2 (1..16).  The computed solution does not
+ * depend on block_threads; mixed_inner changes how often the FP64 stopping
+ * test is evaluated (the FP64 tolerance holds either way). */
+int rich_set_tuning(rich_ctx_t ctx, int32_t block_threads, int32_t mixed_inner);
+
 /* Draw ln Ks and alpha for samples first_sample .. first_sample+nsamples-1 of
  * MLMC level `level` on an nx x nz grid, then average them over 2x2 blocks
  * coarsen_times times.  Outputs lnKs, alpha: device [nsamples][nz>>c][nx>>c].

@@ -171,6 +171,7 @@ def lib():
         L.rich_launch_count.restype = i64
         L.rich_solve_batch_noalloc.argtypes = [C.POINTER(_Problem), i32, vp, vp, dbl, vp, vp, vp]
         L.rich_sample_fields_pair.argtypes = [vp, C.POINTER(_Field), i32, i32, u32, i64, i32, vp, vp, vp, vp, vp]
+        L.rich_set_tuning.argtypes = [vp, i32, i32]
         L.rich_kl_fields.argtypes = [vp, vp, i32, i32, vp, i32, vp, vp]
         L.rich_solve_batch_adjoint.argtypes = [vp, C.POINTER(_Problem), i32, vp, i32, vp, vp, dbl, i32, vp, vp,
                                                vp, vp, C.POINTER(_Stats), vp]
@@ -184,7 +185,7 @@ def exported_symbols():
             "rich_sample_fields", "rich_solve_batch", "rich_solve_batch_host",
             "rich_mlmc_accumulate", "rich_profile", "rich_profile_read", "rich_launch_count",
             "rich_solve_batch_noalloc", "rich_mlmc_estimate", "rich_sample_fields_pair",
-            "rich_kl_fields", "rich_solve_batch_adjoint"]
+            "rich_kl_fields", "rich_solve_batch_adjoint", "rich_set_tuning"]
 
 
 def _check(rc):
@@ -203,6 +204,11 @@ def context(device: int = 0):
         _check(lib().rich_create(C.byref(h), device))
         _ctx[device] = h
     return _ctx[device]
+
+
+def set_tuning(block_threads=0, mixed_inner=0, device=0):
+    """Launch shape of the device's solves (see autotune.tune)."""
+    _check(lib().rich_set_tuning(context(device), block_threads, mixed_inner))
 
 
 def _torch():

@@ -1,0 +1,96 @@
+"""Autotuner of the fused solver's launch shape.
+
+Candidates: 512-thread CTAs (two resident per SM: more samples in flight) or
+1024-thread CTAs (one per SM: half the resident scratch slots, so more of the
+hierarchy stays in L2, and twice the threads per sample); for the mixed path
+also the number of FP32 V-cycles per FP64 defect (1..4).  Each candidate solves
+a probe batch of the same grid and precision (fresh seeded fields, two time
+steps) timed with CUDA events; the fastest is cached in a JSON file keyed by
+grid, precision and batch size (rounded up to a power of two) and applied to
+the context with rich_set_tuning.  The choice never changes an FP64 result
+(block shape) or the FP64 tolerance (inner cycles).
+"""
+from __future__ import annotations
+
+import json
+import os
+import time
+
+
+def cache_path():
+    base = os.environ.get("RICH_TUNE_CACHE")
+    if base:
+        return base
+    root = os.environ.get("XDG_CACHE_HOME", os.path.join(os.path.expanduser("~"), ".cache"))
+    return os.path.join(root, "librichards", "tune.json")
+
+
+def _bucket(n):
+    b = 1
+    while b < n:
+        b *= 2
+    return b
+
+
+def _key(problem, nsamples, device_name):
+    prec = "mixed" if problem.precision else "fp64"
+    return f"{device_name}|{problem.nx}x{problem.nz}|{prec}|S{_bucket(nsamples)}"
+
+
+def _load(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _save(path, data):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def tune(problem, nsamples, device=0, force=False, probe_steps=2, verbose=False):
+    """Return (block_threads, mixed_inner) for this grid/precision/batch and
+    apply it to the device's context; measures and caches when needed."""
+    import torch
+    import paper_1903_08741_gb300 as R
+    dev = torch.device(f"cuda:{device}")
+    name = torch.cuda.get_device_name(dev)
+    path = cache_path()
+    data = _load(path)
+    key = _key(problem, nsamples, name)
+    if key in data and not force:
+        bt, mi = data[key]["block_threads"], data[key]["mixed_inner"]
+        R.set_tuning(bt, mi, device)
+        return bt, mi
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    S = max(1, min(nsamples, 4 * sms))
+    lk, al = R.sample_fields(problem.nx, problem.nz, S, R.FieldModel(seed=987654321), device=device)
+    probe = R.Problem(**{**problem.__dict__, "nsteps": max(1, min(problem.nsteps, probe_steps))})
+    inners = [1, 2, 3, 4] if problem.precision else [0]
+    timings = {}
+    stream = torch.cuda.current_stream(dev)
+    for bt in (512, 1024):
+        for mi in inners:
+            R.set_tuning(bt, mi, device)
+            R.solve_batch(probe, lk[: min(S, 8)].contiguous(), al[: min(S, 8)].contiguous())
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            R.solve_batch(probe, lk, al)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            timings[f"{bt}/{mi}"] = e0.elapsed_time(e1)
+            if verbose:
+                print(f"tune {key}: block {bt} inner {mi}: {timings[f'{bt}/{mi}']:.1f} ms")
+    best = min(timings, key=timings.get)
+    bt, mi = (int(x) for x in best.split("/"))
+    data = _load(path)
+    data[key] = {"block_threads": bt, "mixed_inner": mi, "probe_ms": timings, "probe_samples": S,
+                 "probe_steps": probe.nsteps, "when": time.strftime("%Y-%m-%dT%H:%M:%S")}
+    _save(path, data)
+    R.set_tuning(bt, mi, device)
+    return bt, mi

@@ -138,6 +138,15 @@ int rich_check_problem(const rich_problem_t* pb) {
     return 0;
 }
 
+extern "C" int rich_set_tuning(rich_ctx_t ctx, int32_t block_threads, int32_t mixed_inner) {
+    if (!ctx || (block_threads != 0 && block_threads != 512 && block_threads != 1024) || mixed_inner < 0 ||
+        mixed_inner > 16)
+        return RICH_ERR_INVALID;
+    ctx->tune_threads = block_threads;
+    ctx->tune_mixed_inner = mixed_inner;
+    return 0;
+}
+
 extern "C" int rich_sample_fields(rich_ctx_t ctx, const rich_field_t* field, int32_t nx,
                                   int32_t nz, uint32_t level, int64_t first_sample,
                                   int32_t nsamples, int32_t coarsen_times, double* lnKs,

@@ -31,8 +31,8 @@
 // TM = double is the FP64 path (the oracle's algorithm and stopping tests);
 // TM = float runs FP32 V-cycles (unscaled coefficients: FP32 operations are
 // cheap, bytes are not) inside an FP64 defect-correction loop that performs
-// MIXED_INNER V-cycles per FP64 defect (FP64 Picard residual, FP64 outer
-// residual, FP64 correction and stopping norm).
+// a tunable number of V-cycles per FP64 defect (FP64 Picard residual, FP64
+// outer residual, FP64 correction and stopping norm).
 #include "rich_internal.cuh"
 #include <math.h>
 #include <algorithm>
@@ -42,7 +42,7 @@ namespace {
 constexpr unsigned long long ABS_MASK = 0x7FFFFFFFFFFFFFFFull;
 constexpr unsigned long long INF_BITS = 0x7FF0000000000000ull;
 constexpr int MAXL = RICH_MAX_LEVELS;
-constexpr int MIXED_INNER = 2;   // FP32 V-cycles per FP64 defect evaluation
+constexpr int MIXED_INNER_DEFAULT = 2;   // FP32 V-cycles per FP64 defect evaluation
 
 // FP64 unscaled operator (all levels): faces, mass term, diagonal, Dirichlet faces
 enum { A_TX, A_TZ, A_CDT, A_D, A_TBT, A_TBB, N64 };
@@ -72,6 +72,7 @@ struct FParams {
     int nsteps, picard_maxit, mg_maxit, nu1, nu2;
     double inv_dt, tr, ts, p_top, p_bot, p_init, picard_tol, mg_tol, h, two_over_h2;
     // adjoint (k_adjoint only)
+    int mixed_inner;            // FP32 V-cycles per FP64 defect (mixed path)
     int ckpt_every, adj_maxit, adj_inner;
     double adj_tol;
     long long o_ckpt, o_seg, o_lam, o_rhs, o_r, o_dE, o_dW, o_dN, o_dS, o_dg, o_g;
@@ -479,7 +480,7 @@ struct Cta {
                 ++cyc;
                 rb = resid_norm<TM>(M0, P.nu2 > 0 && nlev > 1, red);
             } else {
-                for (int in = 0; in < MIXED_INNER && cyc < P.mg_maxit; ++in) {
+                for (int in = 0; in < P.mixed_inner && cyc < P.mg_maxit; ++in) {
                     vcycle<TM>(LM, L64, nlev, P.nu1, P.nu2, Amat, nullptr);
                     ++cyc;
                 }
@@ -680,8 +681,8 @@ __device__ __forceinline__ void init_levels(const FParams& P, char* slot, Lv64* 
     __syncthreads();
 }
 
-template <typename TM>
-__global__ void __launch_bounds__(512)
+template <typename TM, int NT>
+__global__ void __launch_bounds__(NT)
 k_fused(const FParams P) {
     extern __shared__ unsigned char smraw[];
     __shared__ unsigned long long red[33];
@@ -891,21 +892,34 @@ static size_t fused_smem(const FParams& P) {
     return (size_t)nnc * (nnc + 1) * (P.mixed ? 4 : 8);
 }
 
-static int fused_occupancy(const FParams& P, size_t smem, int* occ) {
+// block shapes the fused kernel is built for: 512 threads (two resident CTAs
+// per SM at 64 registers) or 1024 (one; half the resident scratch slots)
+template <int NT>
+static int occ_nt(const FParams& P, size_t smem, int* occ) {
     if (P.mixed) {
-        RICH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_fused<float>, 512, smem));
+        RICH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_fused<float, NT>, NT, smem));
     } else {
-        RICH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_fused<double>, 512, smem));
+        RICH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_fused<double, NT>, NT, smem));
     }
     if (*occ < 1) *occ = 1;
     return 0;
 }
 
-static int fused_launch(const FParams& P, int grid, size_t smem, cudaStream_t st) {
+static int fused_occupancy(const FParams& P, size_t smem, int nt, int* occ) {
+    return nt == 1024 ? occ_nt<1024>(P, smem, occ) : occ_nt<512>(P, smem, occ);
+}
+
+template <int NT>
+static void launch_nt(const FParams& P, int grid, size_t smem, cudaStream_t st) {
+    if (P.mixed) k_fused<float, NT><<<grid, NT, smem, st>>>(P);
+    else k_fused<double, NT><<<grid, NT, smem, st>>>(P);
+}
+
+static int fused_launch(const FParams& P, int grid, size_t smem, int nt, cudaStream_t st) {
     RICH_CUDA(cudaMemsetAsync(P.queue, 0, sizeof(int), st));
     rich_count_launch();
-    if (P.mixed) k_fused<float><<<grid, 512, smem, st>>>(P);
-    else k_fused<double><<<grid, 512, smem, st>>>(P);
+    if (nt == 1024) launch_nt<1024>(P, grid, smem, st);
+    else launch_nt<512>(P, grid, smem, st);
     RICH_CUDA(cudaGetLastError());
     return 0;
 }
@@ -920,8 +934,10 @@ int rich_solve_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const doubl
     if (int e = fused_setup(pb, S, P)) return e;
     const size_t off = (size_t)P.slot_bytes;
     const size_t smem = fused_smem(P);
+    const int nt = ctx->tune_threads == 1024 ? 1024 : 512;
+    P.mixed_inner = ctx->tune_mixed_inner > 0 ? ctx->tune_mixed_inner : MIXED_INNER_DEFAULT;
     int occ = 0;
-    if (int e = fused_occupancy(P, smem, &occ)) return e;
+    if (int e = fused_occupancy(P, smem, nt, &occ)) return e;
     const int grid = std::max(1, std::min(S, ctx->sm_count * occ));
     const size_t need = (size_t)grid * off + 256;
     if (ctx->fused_bytes < need) {
@@ -937,7 +953,7 @@ int rich_solve_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const doubl
     P.qoi = qoi; P.p_final = p_final; P.status = w.status;
     P.pic_total = w.pic_total; P.mg_total = w.mg_total; P.maxpic = w.maxpic;
     rich_prof_begin(ctx, st);
-    if (int e = fused_launch(P, grid, smem, st)) return e;
+    if (int e = fused_launch(P, grid, smem, nt, st)) return e;
     rich_prof_end(ctx, st, 0.0, 0.0);
     if (status)
         RICH_CUDA(cudaMemcpyAsync(status, w.status, sizeof(int32_t) * S, cudaMemcpyDeviceToDevice, st));
@@ -953,6 +969,7 @@ int rich_adjoint_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const dou
     if (ckpt_every < 1) return RICH_ERR_INVALID;
     if (int e = fused_setup(pb, S, P, ckpt_every)) return e;
     P.adj_tol = adj_tol; P.adj_maxit = adj_maxit; P.adj_inner = pb->precision == RICH_MIXED ? 2 : 1;
+    P.mixed_inner = ctx->tune_mixed_inner > 0 ? ctx->tune_mixed_inner : MIXED_INNER_DEFAULT;
     const size_t smem = fused_smem(P);
     int occ = 0;
     if (P.mixed) {
@@ -1045,8 +1062,9 @@ extern "C" int rich_solve_batch_noalloc(const rich_problem_t* pb, int32_t nsampl
         return RICH_ERR_INVALID;
     }
     const size_t smem = fused_smem(P);
+    P.mixed_inner = MIXED_INNER_DEFAULT;
     int occ = 0;
-    if (int e = fused_occupancy(P, smem, &occ)) return e;
+    if (int e = fused_occupancy(P, smem, 512, &occ)) return e;
     const int grid = (int)std::min<long long>({(long long)nsamples, (long long)g_noalloc_sms[dev] * occ,
                                               (long long)slots});
     char* base = (char*)g_noalloc_addr[dev];
@@ -1055,5 +1073,5 @@ extern "C" int rich_solve_batch_noalloc(const rich_problem_t* pb, int32_t nsampl
     P.lnKs = lnKs; P.alpha = alpha; P.alpha_scale = alpha_scale;
     P.qoi = qoi; P.p_final = nullptr; P.status = status;
     P.pic_total = nullptr; P.mg_total = nullptr; P.maxpic = nullptr;
-    return fused_launch(P, grid, smem, (cudaStream_t)stream);
+    return fused_launch(P, grid, smem, 512, (cudaStream_t)stream);
 }

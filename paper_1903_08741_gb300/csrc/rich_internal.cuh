@@ -57,6 +57,8 @@ struct rich_ctx {
     size_t fused_bytes = 0;
     void* stage = nullptr;                      // device staging of the host-buffer entry point
     size_t stage_bytes = 0;
+    int tune_threads = 0;                       // fused-kernel block size (0: default 512)
+    int tune_mixed_inner = 0;                   // FP32 V-cycles per FP64 defect (0: default 2)
 };
 
 void rich_count_launch();

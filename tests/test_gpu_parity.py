@@ -211,3 +211,28 @@ def test_mc128_full_batch_sampled(R):
     ok = s_o == 0
     rel = np.abs(q[picks][ok] - q_o[ok]) / np.abs(q_o[ok])
     assert rel.max(initial=0) <= 1e-10
+
+
+def test_block_shape_does_not_change_fp64_results(R):
+    """The 1024-thread launch shape gives bit-identical FP64 results; the mixed
+    path with other inner-cycle counts stays within its 1e-6 QoI bound."""
+    lk, al = O.sample_fields(32, 32, 10, seed=6)
+    dev = torch.device("cuda:0")
+    a = (torch.from_numpy(lk).to(dev), torch.from_numpy(al).to(dev))
+    pb = gpu_problem(R, 32, 32, 3, 0.01)
+    try:
+        R.set_tuning(512, 0)
+        q1, p1, s1, _, _ = R.solve_batch(pb, *a, want_p=True)
+        R.set_tuning(1024, 0)
+        q2, p2, s2, _, _ = R.solve_batch(pb, *a, want_p=True)
+        assert torch.equal(s1, s2) and torch.equal(p1, p2)
+        ok = s1 == 0
+        assert torch.equal(q1[ok], q2[ok])
+        pm = gpu_problem(R, 32, 32, 3, 0.01, precision=R.MIXED)
+        for bt, mi in ((512, 1), (1024, 4)):
+            R.set_tuning(bt, mi)
+            qm, _, sm, _, _ = R.solve_batch(pm, *a)
+            okm = ok & (sm == 0)
+            assert (torch.abs(qm[okm] - q1[okm]) / torch.abs(q1[okm])).max() <= 1e-6
+    finally:
+        R.set_tuning(0, 0)
