@@ -104,6 +104,15 @@ int rich_sample_fields(rich_ctx_t ctx, const rich_field_t* field, int32_t nx, in
                        uint32_t level, int64_t first_sample, int32_t nsamples,
                        int32_t coarsen_times, double* lnKs, double* alpha, void* stream);
 
+/* As rich_sample_fields, with the index of the first sample read from DEVICE
+ * memory (*first_sample_dev) when the kernels run, so that a captured CUDA
+ * graph can draw a new sample range on every replay.  The spectrum and the
+ * work buffer of a grid are set up (with a host synchronisation) on its first
+ * use; make one call outside the capture first. */
+int rich_sample_fields_at(rich_ctx_t ctx, const rich_field_t* field, int32_t nx, int32_t nz,
+                          uint32_t level, const int64_t* first_sample_dev, int32_t nsamples,
+                          int32_t coarsen_times, double* lnKs, double* alpha, void* stream);
+
 /* Coupled pair of fields by covariance upscaling (Appendix A, Eqs. averaging,
  * cov_upscale): the fine fields on nx x nz as rich_sample_fields draws them,
  * and the coarse fields on (nx/2) x (nz/2) from the SAME white noise averaged
@@ -129,6 +138,15 @@ int rich_solve_batch(rich_ctx_t ctx, const rich_problem_t* pb, int32_t nsamples,
                      const double* lnKs, const double* alpha, double alpha_scale,
                      double* qoi, double* p_final, int32_t* status, rich_stats_t* stats,
                      void* stream);
+
+/* Enqueue-only form of rich_solve_batch: launches the fused solve on `stream`
+ * and returns without waiting, reading back nothing (no stats, return value 0
+ * or a negative error; per-sample results in status[]).  Stream-capturable
+ * once a first call with the same grid, precision and a batch at least as
+ * large has set up the device buffers. */
+int rich_solve_batch_async(rich_ctx_t ctx, const rich_problem_t* pb, int32_t nsamples,
+                           const double* lnKs, const double* alpha, double alpha_scale,
+                           double* qoi, double* p_final, int32_t* status, void* stream);
 
 /* As rich_solve_batch, but lnKs, alpha, qoi, p_final and status are HOST
  * arrays: the library copies inputs to its workspace and results back (the

@@ -172,6 +172,8 @@ def lib():
         L.rich_solve_batch_noalloc.argtypes = [C.POINTER(_Problem), i32, vp, vp, dbl, vp, vp, vp]
         L.rich_sample_fields_pair.argtypes = [vp, C.POINTER(_Field), i32, i32, u32, i64, i32, vp, vp, vp, vp, vp]
         L.rich_set_tuning.argtypes = [vp, i32, i32]
+        L.rich_sample_fields_at.argtypes = [vp, C.POINTER(_Field), i32, i32, u32, vp, i32, i32, vp, vp, vp]
+        L.rich_solve_batch_async.argtypes = [vp, C.POINTER(_Problem), i32, vp, vp, dbl, vp, vp, vp, vp]
         L.rich_kl_fields.argtypes = [vp, vp, i32, i32, vp, i32, vp, vp]
         L.rich_solve_batch_adjoint.argtypes = [vp, C.POINTER(_Problem), i32, vp, i32, vp, vp, dbl, i32, vp, vp,
                                                vp, vp, C.POINTER(_Stats), vp]
@@ -185,7 +187,8 @@ def exported_symbols():
             "rich_sample_fields", "rich_solve_batch", "rich_solve_batch_host",
             "rich_mlmc_accumulate", "rich_profile", "rich_profile_read", "rich_launch_count",
             "rich_solve_batch_noalloc", "rich_mlmc_estimate", "rich_sample_fields_pair",
-            "rich_kl_fields", "rich_solve_batch_adjoint", "rich_set_tuning"]
+            "rich_kl_fields", "rich_solve_batch_adjoint", "rich_set_tuning", "rich_sample_fields_at",
+            "rich_solve_batch_async"]
 
 
 def _check(rc):
@@ -428,3 +431,32 @@ def __getattr__(name):
     if name == "RichardsQoI":
         return _autograd()
     raise AttributeError(name)
+
+
+def sample_fields_at(nx, nz, nsamples, first_sample_dev, out, model: FieldModel | None = None, level=0,
+                     coarsen_times=0):
+    """sample_fields with the first sample index read from a device int64 tensor
+    (graph-capturable once the grid has been used outside the capture)."""
+    torch = _torch()
+    model = model or FieldModel()
+    lk, al = out
+    dev = lk.device.index
+    if first_sample_dev.dtype != torch.int64 or not first_sample_dev.is_cuda:
+        raise RichError("first_sample_dev must be a CUDA int64 tensor")
+    _check(lib().rich_sample_fields_at(context(dev), C.byref(model._c()), nx, nz, level,
+                                       C.c_void_p(first_sample_dev.data_ptr()), nsamples, coarsen_times,
+                                       _dev_ptr(lk, torch.float64, "lnKs"), _dev_ptr(al, torch.float64, "alpha"),
+                                       _stream(torch, dev)))
+    return lk, al
+
+
+def solve_batch_async(problem: Problem, lnKs, alpha, qoi, status, alpha_scale=1.0, p_final=None):
+    """Enqueue the fused solve on the current stream (no host synchronisation;
+    capturable in a CUDA graph after a first uncaptured call)."""
+    torch = _torch()
+    dev = lnKs.device.index
+    _check(lib().rich_solve_batch_async(context(dev), C.byref(problem._c()), lnKs.shape[0],
+                                        _dev_ptr(lnKs, torch.float64, "lnKs"), _dev_ptr(alpha, torch.float64, "alpha"),
+                                        alpha_scale, _dev_ptr(qoi, torch.float64, "qoi"),
+                                        None if p_final is None else _dev_ptr(p_final, torch.float64, "p_final"),
+                                        _dev_ptr(status, torch.int32, "status"), _stream(torch, dev)))

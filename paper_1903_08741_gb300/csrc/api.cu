@@ -158,6 +158,29 @@ extern "C" int rich_sample_fields(rich_ctx_t ctx, const rich_field_t* field, int
                               lnKs, alpha, (cudaStream_t)stream);
 }
 
+extern "C" int rich_sample_fields_at(rich_ctx_t ctx, const rich_field_t* field, int32_t nx,
+                                     int32_t nz, uint32_t level, const int64_t* first_sample_dev,
+                                     int32_t nsamples, int32_t coarsen_times, double* lnKs,
+                                     double* alpha, void* stream) {
+    if (!ctx || !field || nsamples < 0 || !first_sample_dev) return RICH_ERR_INVALID;
+    if (nsamples > 0 && (!lnKs || !alpha)) return RICH_ERR_INVALID;
+    RICH_CUDA(cudaSetDevice(ctx->device));
+    return rich_fields_device(ctx, field, nx, nz, level, 0, nsamples, coarsen_times, lnKs, alpha,
+                              (cudaStream_t)stream, first_sample_dev);
+}
+
+extern "C" int rich_solve_batch_async(rich_ctx_t ctx, const rich_problem_t* pb, int32_t nsamples,
+                                      const double* lnKs, const double* alpha, double alpha_scale,
+                                      double* qoi, double* p_final, int32_t* status, void* stream) {
+    if (!ctx || rich_check_problem(pb) || nsamples < 0) return RICH_ERR_INVALID;
+    if (nsamples == 0) return 0;
+    if (!lnKs || !alpha || !qoi) return RICH_ERR_INVALID;
+    RICH_CUDA(cudaSetDevice(ctx->device));
+    if (int e = rich_samples_reserve(ctx, nsamples)) return e;
+    return rich_solve_fused(ctx, pb, nsamples, lnKs, alpha, alpha_scale, qoi, p_final, status,
+                            (cudaStream_t)stream);
+}
+
 extern "C" int rich_sample_fields_pair(rich_ctx_t ctx, const rich_field_t* field, int32_t nx,
                                        int32_t nz, uint32_t level, int64_t first_sample,
                                        int32_t nsamples, double* lnKs_f, double* alpha_f,

@@ -37,12 +37,15 @@ __device__ __forceinline__ double u01(uint32_t hi, uint32_t lo) {
 
 // packed complex white noise: re = field 0, im = field 1, for samples
 // first..first+S-1 on the torus (npts = px*pz, even)
-__global__ void k_noise(int S, int npts, uint64_t seed, uint32_t level, int64_t first, cplx* out) {
+// (first sample = *first_dev + first when first_dev is given: a captured CUDA
+// graph can advance the sample range between replays)
+__global__ void k_noise(int S, int npts, uint64_t seed, uint32_t level, int64_t first,
+                        const int64_t* __restrict__ first_dev, cplx* out) {
     long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;   // (sample, pair)
     const int pairs = npts >> 1;
     if (g >= (long long)S * pairs) return;
     int s = (int)(g / pairs), q = (int)(g - (long long)s * pairs);
-    uint64_t sample = (uint64_t)(first + s);
+    uint64_t sample = (uint64_t)((first_dev ? *first_dev : 0) + first + s);
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32) ^ level;
     double y[2][2];
 #pragma unroll
@@ -297,7 +300,7 @@ constexpr size_t CHUNK_BYTES = 512ull << 20;
 
 int rich_fields_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int nz, uint32_t level,
                        int64_t first, int S, int coarsen, double* lnKs, double* alpha,
-                       cudaStream_t st) {
+                       cudaStream_t st, const int64_t* first_dev) {
     if (!pow2(nx) || !pow2(nz) || coarsen < 0 || (nx >> coarsen) < 1 || (nz >> coarsen) < 1 ||
         fd->sigma2 <= 0 || fd->corr_len <= 0)
         return RICH_ERR_INVALID;
@@ -318,7 +321,8 @@ int rich_fields_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int nz, ui
     for (int s0 = 0; s0 < S; s0 += cap) {
         int cs = std::min(cap, S - s0);
         rich_count_launch();
-        k_noise<<<nb((long long)cs * (npts / 2)), 256, 0, st>>>(cs, npts, fd->seed, level, first + s0, work);
+        k_noise<<<nb((long long)cs * (npts / 2)), 256, 0, st>>>(cs, npts, fd->seed, level, first + s0,
+                                                                 first_dev, work);
         if (int e = fftma_inplace(work, cs, sp, st)) return e;
         // real scratch: two ping-pong pairs of [cs][nz][nx] arrays
         const size_t blk = (size_t)cs * nx * nz;
@@ -388,7 +392,7 @@ int rich_fields_pair_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int n
     for (int s0 = 0; s0 < S; s0 += cap) {
         int cs = std::min(cap, S - s0);
         rich_count_launch();
-        k_noise<<<nb((long long)cs * (npf / 2)), 256, 0, st>>>(cs, npf, fd->seed, level, first + s0, wf);
+        k_noise<<<nb((long long)cs * (npf / 2)), 256, 0, st>>>(cs, npf, fd->seed, level, first + s0, nullptr, wf);
         rich_count_launch();
         k_noise_upscale<<<nb((long long)cs * npc), 256, 0, st>>>(cs, px / 2, pz / 2, wf, wc);
         if (int e = fftma_inplace(wf, cs, spf, st)) return e;

@@ -90,4 +90,4 @@ int rich_fields_average(rich_ctx* ctx, int S, int nx, int nz, const double* lk, 
                         double* lkc, double* alc, cudaStream_t st);
 int rich_fields_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int nz, uint32_t level,
                        int64_t first, int S, int coarsen, double* lnKs, double* alpha,
-                       cudaStream_t st);
+                       cudaStream_t st, const int64_t* first_dev = nullptr);

@@ -236,3 +236,44 @@ def test_block_shape_does_not_change_fp64_results(R):
             assert (torch.abs(qm[okm] - q1[okm]) / torch.abs(q1[okm])).max() <= 1e-6
     finally:
         R.set_tuning(0, 0)
+
+
+def test_graph_captured_step_matches_direct_calls(R):
+    """Fields at a device-side sample offset + async solve + accumulation,
+    captured once in a CUDA graph and replayed twice (the offset advances by
+    the batch each replay), equal the same calls made directly."""
+    dev = torch.device("cuda:0")
+    n, S = 16, 24
+    pb = gpu_problem(R, n, n, 2, 0.01)
+    model = R.FieldModel(seed=3)
+    lk = torch.empty((S, n, n), dtype=torch.float64, device=dev)
+    al = torch.empty_like(lk)
+    q = torch.empty(S, dtype=torch.float64, device=dev)
+    st = torch.empty(S, dtype=torch.int32, device=dev)
+    acc = torch.zeros(8, dtype=torch.float64, device=dev)
+    first = torch.zeros(1, dtype=torch.int64, device=dev)
+    side = torch.cuda.Stream(dev)
+    with torch.cuda.stream(side):
+        R.sample_fields_at(n, n, S, first, (lk, al), model)         # set-up outside the capture
+        R.solve_batch_async(pb, lk, al, q, st)
+        R.mlmc_accumulate(acc, q, st)
+        torch.cuda.synchronize(dev)
+        acc.zero_()
+        first.zero_()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            R.sample_fields_at(n, n, S, first, (lk, al), model)
+            R.solve_batch_async(pb, lk, al, q, st)
+            R.mlmc_accumulate(acc, q, st)
+            first.add_(S)
+    for rep in range(2):
+        g.replay()
+        torch.cuda.synchronize(dev)
+        lk_ref, al_ref = R.sample_fields(n, n, S, model, first_sample=rep * S)
+        q_ref, _, st_ref, _, _ = R.solve_batch(pb, lk_ref, al_ref)
+        assert torch.equal(lk, lk_ref) and torch.equal(al, al_ref)
+        assert torch.equal(st, st_ref)
+        ok = st_ref == 0
+        assert torch.equal(q[ok], q_ref[ok])
+    assert int(first.item()) == 2 * S
+    assert int(acc[2].item() + acc[3].item()) == 2 * S
