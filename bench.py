@@ -127,6 +127,25 @@ def dist_setup(args):
     return ws, rank, local, pg
 
 
+def merge_step_sums(pg, step_acc, acc):
+    """The estimator's one exchange: all-reduce (sum) the 8 FP64 MC sums of
+    this step over the ranks and add them to the running total."""
+    if pg is not None:
+        pg.all_reduce(step_acc)
+    acc += step_acc
+    return acc
+
+
+def max_over_ranks(pg, value, device):
+    """Slowest rank's time (the bench reports whole-job throughput)."""
+    if pg is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
 def cpu_baseline(n, nsamples, steps, dt, seed=0):
     """The FP64 oracle as it stands, on every host core: fields + solves of a
     bounded sample of the workload.  Returns (solves/s, cores, seconds)."""
@@ -182,8 +201,18 @@ def run_mlmc(args):
     B.build()
     torch.cuda.set_device(0)
     prec = R.MIXED if args.precision == "mixed" else R.FP64
-    cfg = R.MlmcConfig(**MLMC_LEVELS, coupling=args.coupling, eps=1e-3,
-                       problem=R.Problem(precision=prec, **PHYS))
+    from paper_1903_08741_gb300 import autotune
+    tt, ti = [], []
+    for l, nl in enumerate(MLMC_LEVELS["nsamples"]):
+        m = MLMC_LEVELS["n0"] << l
+        st_l = MLMC_LEVELS["steps0"] << l
+        bt, mi = autotune.tune(R.Problem(nx=m, nz=m, nsteps=st_l, dt=MLMC_LEVELS["t_final"] / st_l,
+                                         precision=prec, **PHYS), nl)
+        tt.append(bt)
+        ti.append(mi)
+    R.set_tuning(0, 0)
+    cfg = R.MlmcConfig(**MLMC_LEVELS, coupling=args.coupling, eps=1e-3, tune_threads=tuple(tt),
+                       tune_inner=tuple(ti), problem=R.Problem(precision=prec, **PHYS))
     for k in range(args.warmup):
         small = R.MlmcConfig(nsamples=(64, 32, 16, 8, 4), n0=16, steps0=5, t_final=0.1,
                              coupling=args.coupling, key_offset=100 + k,
@@ -216,7 +245,16 @@ def run_mlmc(args):
         "estimate": r["estimate"], "rmse": r["rmse"], "ml_variance": r["ml_variance"],
         "w_mc_eps_s": r["w_mc_eps"], "mc_over_mlmc": r["w_mc_eps"] / r["w_eps"],
         "bias_estimate": r["bias_estimate"], "run_seconds": secs,
+        "launch": {"block_threads": tt, "mixed_inner": ti, "from": "autotuner, per level"},
     }
+    if args.adaptive_eps > 0:
+        acfg = R.MlmcConfig(**{**MLMC_LEVELS, "nsamples": (512, 128, 32, 16, 8)}, coupling=args.coupling,
+                            eps=args.adaptive_eps, key_offset=1000, tune_threads=tuple(tt), tune_inner=tuple(ti),
+                            problem=R.Problem(precision=prec, **PHYS))
+        a = R.mlmc_adaptive(acfg, max_rounds=10)
+        out["adaptive"] = {"eps": args.adaptive_eps, "rounds": a["rounds"], "n": a["n"], "failed": a["failed"],
+                           "rmse": a["rmse"], "estimate": a["estimate"], "seconds": a["seconds"],
+                           "var": a["var"], "cost": a["cost"], "w_eps_predicted": a["w_eps"]}
     print(json.dumps(out))
 
 
@@ -315,8 +353,11 @@ def run_mc512(args):
     stream = torch.cuda.current_stream(dev)
     clocks = ClockSampler(0)
     clocks.start()
+    from paper_1903_08741_gb300 import autotune
+    tuning = {}
     for name, prec in (("mixed", R.MIXED), ("fp64", R.FP64)):
         pb = R.Problem(nx=n, nz=n, nsteps=steps, dt=dt, precision=prec, **PHYS)
+        tuning[name] = autotune.tune(pb, S)
         R.solve_batch(pb, lk[:4].contiguous(), al[:4].contiguous())       # warm-up
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -333,7 +374,8 @@ def run_mc512(args):
         "metric": "Picard-MG solves/s", "value": S / (tm / 1e3), "unit": "solves/s", "n_gpus": 1,
         "steps": 1, "warmup": 1, "ms_per_step": tm, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32-in-f64", "data": "synthetic",
-        "config": {"workload": f"mc512: {n}x{n} grid, {S} samples, {steps} steps dt={dt:.6g}"},
+        "config": {"workload": f"mc512: {n}x{n} grid, {S} samples, {steps} steps dt={dt:.6g}",
+                   "launch": {k: {"block_threads": v[0], "mixed_inner": v[1]} for k, v in tuning.items()}},
         "clocks": clk,
         "fp64": {"value": S / (td / 1e3), "ms": td, "vcycles_per_sample": std_.mg_cycles / S},
         "mixed_vcycles_per_sample": stm.mg_cycles / S,
@@ -371,13 +413,15 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     sample_base = rank * 1_000_000
 
+    step_acc = torch.zeros(8, dtype=torch.float64, device=dev)
+
     def step(k):
         R.sample_fields(n, n, S, model, level=0, first_sample=sample_base + k * S, device=local,
                         out=(lk, al))
         q, _, st, stats, rc = R.solve_batch(pb, lk, al, device=local)
-        R.mlmc_accumulate(acc, q, st)
-        if pg is not None:
-            pg.all_reduce(acc)
+        step_acc.zero_()
+        R.mlmc_accumulate(step_acc, q, st)
+        merge_step_sums(pg, step_acc, acc)
         return stats
 
     for k in range(args.warmup):
@@ -409,10 +453,7 @@ def run_ours(args):
     kms, klaunch, kbytes, kflops = R.profile_read(device=local)
     R.profile(False, device=local)
     clk = clocks.stop()
-    if pg is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(pg, ms, dev)
     total = S * args.steps * ws
     value = total / (ms / 1e3)
     a = acc.cpu().numpy()
@@ -440,11 +481,7 @@ def run_ours(args):
             gr.replay()
             g1.record(side)
             torch.cuda.synchronize(dev)
-        gms = g0.elapsed_time(g1)
-        if pg is not None:
-            t = torch.tensor([gms], dtype=torch.float64, device=dev)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            gms = float(t.item())
+        gms = max_over_ranks(pg, g0.elapsed_time(g1), dev)
         graph = {"value": S * ws / (gms / 1e3), "unit": "solves/s", "ms_per_step": gms,
                  "what": "fields + fused solve + accumulation captured as one CUDA graph, one replay"}
 
@@ -462,11 +499,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             qh, _, sh, _, _ = R.solve_batch_host(pb, hl.numpy(), ha.numpy(), device=local)
-        t_e2e = time.perf_counter() - t0
-        if pg is not None:
-            t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            t_e2e = float(t.item())
+        t_e2e = max_over_ranks(pg, time.perf_counter() - t0, dev)
         e2e = {"value": S * ws * args.e2e_steps / t_e2e, "unit": "solves/s",
                "h2d_bytes_per_step": 2 * S * n * n * 8, "d2h_bytes_per_step": S * 8 + S * 4}
 
@@ -533,6 +566,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["mlmc5", "adjoint256", "mc512"], default="mc128")
     ap.add_argument("--check", action="store_true", help="adjoint workload: finite-difference check")
+    ap.add_argument("--adaptive-eps", type=float, default=0.0, help="mlmc5: also run Algorithm PC_MLMC to this RMSE")
     ap.add_argument("--coupling", type=int, default=0, help="MLMC field coupling (0 exact, 1 level grid)")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--no-e2e", action="store_true")

@@ -184,6 +184,8 @@ typedef struct {
     int32_t batch;            /* samples per batch, 0 = automatic                          */
     double eps;               /* RMSE target of the optimal-allocation report              */
     uint32_t key_offset;      /* added to the level in the noise key (independent reruns)  */
+    int32_t tune_threads[RICH_MLMC_MAX_LEVELS];  /* per-level launch shape (0: context's)    */
+    int32_t tune_inner[RICH_MLMC_MAX_LEVELS];    /* per-level FP32 cycles per defect (0: ctx) */
 } rich_mlmc_cfg_t;
 
 typedef struct {
@@ -202,11 +204,21 @@ typedef struct {
     double w_mc_eps;          /* plain MC at the finest level: V[Q_L] C_L,fine / eps^2   */
     double bias_estimate;     /* |E Y_L| / (2^1 - 1): first-order bias bound (Eq. discErr) */
     double seconds;           /* wall time of the call                                   */
+    int32_t rounds;           /* sampling rounds (1 for rich_mlmc_estimate)              */
 } rich_mlmc_result_t;
 
 /* Run the estimator with the configured N_l and fill *out (HOST).  Synchronous;
  * device memory is allocated and freed inside the call. */
 int rich_mlmc_estimate(rich_ctx_t ctx, const rich_mlmc_cfg_t* cfg, rich_mlmc_result_t* out);
+
+/* Algorithm PC_MLMC of Sec. 5.2: warm-up with N*_l = cfg->nsamples, then
+ * repeatedly set N_l to the optimal allocation (Eq. MLMCSAMP_ch6) for RMSE
+ * cfg->eps from the current level variances and the per-sample costs measured
+ * so far, and draw the missing samples (continuing each level's sample
+ * stream), until no level needs more, max_rounds rounds are done, or a level
+ * would exceed nmax[l] (HOST array, may be NULL).  cfg->eps must be > 0. */
+int rich_mlmc_adaptive(rich_ctx_t ctx, const rich_mlmc_cfg_t* cfg, int32_t max_rounds,
+                       const int64_t* nmax, rich_mlmc_result_t* out);
 
 /* MC / MLMC level accumulation in FP64 on the device (Sec. 5, Eqs. SMC_ch6,
  * MC_var_ch6, ML_var_ch6): for i < n with Y_i = qoi_fine[i] - qoi_coarse[i]

@@ -91,7 +91,8 @@ class _MlmcCfg(C.Structure):
                 ("steps0", C.c_int32), ("t_final", C.c_double),
                 ("nsamples", C.c_int32 * MLMC_MAX_LEVELS), ("coupling", C.c_int32),
                 ("continuation", C.c_int32), ("batch", C.c_int32), ("eps", C.c_double),
-                ("key_offset", C.c_uint32)]
+                ("key_offset", C.c_uint32), ("tune_threads", C.c_int32 * MLMC_MAX_LEVELS),
+                ("tune_inner", C.c_int32 * MLMC_MAX_LEVELS)]
 
 
 _LV = C.c_double * MLMC_MAX_LEVELS
@@ -103,7 +104,7 @@ class _MlmcResult(C.Structure):
                 ("mean_f", _LV), ("var_f", _LV), ("mean_c", _LV), ("var_c", _LV), ("cost", _LV),
                 ("cost_fine", _LV), ("n_opt", _LV), ("estimate", C.c_double), ("rmse", C.c_double),
                 ("ml_variance", C.c_double), ("w_eps", C.c_double), ("w_mc_eps", C.c_double),
-                ("bias_estimate", C.c_double), ("seconds", C.c_double)]
+                ("bias_estimate", C.c_double), ("seconds", C.c_double), ("rounds", C.c_int32)]
 
 
 @dataclass
@@ -119,6 +120,8 @@ class MlmcConfig:
     batch: int = 0
     eps: float = 1e-3
     key_offset: int = 0
+    tune_threads: tuple = ()        # per level, 0 = the context's launch shape
+    tune_inner: tuple = ()          # per level, 0 = the context's FP32 cycles per defect
     problem: Problem = field(default_factory=Problem)
     model: FieldModel = field(default_factory=FieldModel)
 
@@ -132,6 +135,10 @@ class MlmcConfig:
             c.nsamples[l] = n
         c.coupling, c.continuation, c.batch, c.eps = self.coupling, self.continuation, self.batch, self.eps
         c.key_offset = self.key_offset
+        for l, v in enumerate(self.tune_threads):
+            c.tune_threads[l] = v
+        for l, v in enumerate(self.tune_inner):
+            c.tune_inner[l] = v
         return c
 
 
@@ -178,6 +185,7 @@ def lib():
         L.rich_solve_batch_adjoint.argtypes = [vp, C.POINTER(_Problem), i32, vp, i32, vp, vp, dbl, i32, vp, vp,
                                                vp, vp, C.POINTER(_Stats), vp]
         L.rich_mlmc_estimate.argtypes = [vp, C.POINTER(_MlmcCfg), C.POINTER(_MlmcResult)]
+        L.rich_mlmc_adaptive.argtypes = [vp, C.POINTER(_MlmcCfg), i32, vp, C.POINTER(_MlmcResult)]
         _lib = L
     return _lib
 
@@ -188,7 +196,7 @@ def exported_symbols():
             "rich_mlmc_accumulate", "rich_profile", "rich_profile_read", "rich_launch_count",
             "rich_solve_batch_noalloc", "rich_mlmc_estimate", "rich_sample_fields_pair",
             "rich_kl_fields", "rich_solve_batch_adjoint", "rich_set_tuning", "rich_sample_fields_at",
-            "rich_solve_batch_async"]
+            "rich_solve_batch_async", "rich_mlmc_adaptive"]
 
 
 def _check(rc):
@@ -354,18 +362,35 @@ def solve_batch_noalloc(problem: Problem, lnKs, alpha, alpha_scale=1.0, qoi=None
     return qoi, status
 
 
+def _mlmc_result(r, rc):
+    NL = r.nlevels
+    out = {k: list(getattr(r, k))[:NL] for k in ("n", "failed", "mean", "var", "mean_f", "var_f", "mean_c",
+                                                  "var_c", "cost", "cost_fine", "n_opt")}
+    out.update({k: getattr(r, k) for k in ("estimate", "rmse", "ml_variance", "w_eps", "w_mc_eps",
+                                            "bias_estimate", "seconds", "rounds")})
+    out["nlevels"], out["rc"] = NL, rc
+    return out
+
+
+def mlmc_adaptive(cfg: MlmcConfig, max_rounds=10, nmax=None, device=0):
+    """Algorithm PC_MLMC (Sec. 5.2): warm-up with cfg.nsamples, then optimal N_l for
+    RMSE cfg.eps from measured V_l and C_l, repeated until no level needs more."""
+    _torch()
+    r = _MlmcResult()
+    cap = None
+    if nmax is not None:
+        cap = (C.c_int64 * MLMC_MAX_LEVELS)(*[int(v) for v in nmax])
+    rc = _check(lib().rich_mlmc_adaptive(context(device), C.byref(cfg._c()), max_rounds,
+                                         None if cap is None else C.cast(cap, C.c_void_p), C.byref(r)))
+    return _mlmc_result(r, rc)
+
+
 def mlmc_estimate(cfg: MlmcConfig, device=0):
     """Multilevel Monte Carlo with parametric continuation on one GPU (host result)."""
     _torch()
     r = _MlmcResult()
     rc = _check(lib().rich_mlmc_estimate(context(device), C.byref(cfg._c()), C.byref(r)))
-    NL = r.nlevels
-    out = {k: list(getattr(r, k))[:NL] for k in ("n", "failed", "mean", "var", "mean_f", "var_f", "mean_c",
-                                                  "var_c", "cost", "cost_fine", "n_opt")}
-    out.update({k: getattr(r, k) for k in ("estimate", "rmse", "ml_variance", "w_eps", "w_mc_eps",
-                                            "bias_estimate", "seconds")})
-    out["nlevels"], out["rc"] = NL, rc
-    return out
+    return _mlmc_result(r, rc)
 
 
 def kl_fields(basis, xi):

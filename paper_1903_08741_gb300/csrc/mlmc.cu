@@ -61,133 +61,230 @@ extern "C" int rich_mlmc_accumulate(rich_ctx_t ctx, const double* qoi_fine, cons
 #include <algorithm>
 
 namespace {
+
 struct DevBuf {
     void* p = nullptr;
     ~DevBuf() { if (p) cudaFree(p); }
 };
-}
 
-extern "C" int rich_mlmc_estimate(rich_ctx_t ctx, const rich_mlmc_cfg_t* cfg, rich_mlmc_result_t* out) {
-    if (!ctx || !cfg || !out) return RICH_ERR_INVALID;
-    const int NL = cfg->nlevels, L = NL - 1;
-    if (NL < 1 || NL > RICH_MLMC_MAX_LEVELS || cfg->n0 < 2 || cfg->steps0 < 1 || !(cfg->t_final > 0) ||
-        (cfg->coupling < 0 || cfg->coupling > 2))
-        return RICH_ERR_INVALID;
-    for (int l = 0; l < NL; ++l)
-        if (cfg->nsamples[l] < 2) return RICH_ERR_INVALID;
-    RICH_CUDA(cudaSetDevice(ctx->device));
-    auto t0 = std::chrono::steady_clock::now();
+// One estimator run: device buffers for a batch of B pairs, FP64 level sums on
+// the device, per-level CUDA-event times.  Level l's samples are the indices
+// 0, 1, 2, ... of its own noise stream (key level + key_offset), so adding
+// samples later continues the stream exactly where it stopped.
+struct MlmcRun {
+    rich_ctx* ctx;
+    const rich_mlmc_cfg_t* cfg;
+    int NL, L, nL, B = 0;
     cudaStream_t st = nullptr;
-    RICH_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-    struct StreamGuard { cudaStream_t s; ~StreamGuard() { cudaStreamDestroy(s); } } sg{st};
-    const int nL = cfg->n0 << L;
-    auto grid = [&](int l) { return cfg->n0 << l; };
-    auto steps = [&](int l) { return cfg->steps0 << l; };
-    auto ascale = [&](int l) { return cfg->continuation ? (double)(l + 1) / (double)NL : 1.0; };
-    int maxB = 0;
-    for (int l = 0; l < NL; ++l) maxB = std::max(maxB, cfg->nsamples[l]);
-    int B = cfg->batch > 0 ? cfg->batch : (int)std::max<long long>(1, (1ll << 31) / (16ll * nL * nL));
-    B = std::min(B, maxB);
-    const size_t fine_cells = (size_t)B * nL * nL;          // worst case: level L fine member
+    cudaEvent_t ev[4] = {};
     DevBuf lkf, alf, lkc, alc, qf, qc, sf, sc, acc;
-    auto dalloc = [&](DevBuf& b, size_t bytes) -> int {
-        cudaError_t e = cudaMalloc(&b.p, std::max<size_t>(bytes, 256));
-        if (e != cudaSuccess) { cudaGetLastError(); return RICH_ERR_OOM; }
-        return 0;
-    };
-    if (dalloc(lkf, fine_cells * 8) || dalloc(alf, fine_cells * 8) || dalloc(lkc, fine_cells * 2) ||
-        dalloc(alc, fine_cells * 2) || dalloc(qf, B * 8) || dalloc(qc, B * 8) || dalloc(sf, B * 4) ||
-        dalloc(sc, B * 4) || dalloc(acc, 8 * 8 * NL))
-        return RICH_ERR_OOM;
-    RICH_CUDA(cudaMemsetAsync(acc.p, 0, 8 * 8 * NL, st));
-    cudaEvent_t ev[4];
-    for (auto& e : ev) RICH_CUDA(cudaEventCreate(&e));
-    struct EvGuard { cudaEvent_t* e; ~EvGuard() { for (int k = 0; k < 4; ++k) cudaEventDestroy(e[k]); } } eg{ev};
-    std::vector<double> t_pair(NL, 0.0), t_fine(NL, 0.0);
+    std::vector<double> t_pair, t_fine;
+    std::vector<long long> n_done;
     int worst = 0;
-    for (int l = 0; l < NL; ++l) {
-        const int M = grid(l), nsl = cfg->nsamples[l];
+
+    MlmcRun(rich_ctx* c, const rich_mlmc_cfg_t* g) : ctx(c), cfg(g) {
+        NL = g->nlevels; L = NL - 1; nL = g->n0 << L;
+        t_pair.assign(NL, 0.0); t_fine.assign(NL, 0.0); n_done.assign(NL, 0);
+    }
+    ~MlmcRun() {
+        for (auto& e : ev) if (e) cudaEventDestroy(e);
+        if (st) cudaStreamDestroy(st);
+    }
+    int grid(int l) const { return cfg->n0 << l; }
+    int steps(int l) const { return cfg->steps0 << l; }
+    double ascale(int l) const { return cfg->continuation ? (double)(l + 1) / (double)NL : 1.0; }
+
+    int init(int batch_hint) {
+        RICH_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        for (auto& e : ev) RICH_CUDA(cudaEventCreate(&e));
+        B = cfg->batch > 0 ? cfg->batch : (int)std::max<long long>(1, (1ll << 31) / (16ll * nL * nL));
+        B = std::max(1, std::min(B, batch_hint));
+        const size_t fine_cells = (size_t)B * nL * nL;       // worst case: level L fine member
+        auto dalloc = [&](DevBuf& b, size_t bytes) -> int {
+            cudaError_t e = cudaMalloc(&b.p, std::max<size_t>(bytes, 256));
+            if (e != cudaSuccess) { cudaGetLastError(); return RICH_ERR_OOM; }
+            return 0;
+        };
+        if (dalloc(lkf, fine_cells * 8) || dalloc(alf, fine_cells * 8) || dalloc(lkc, fine_cells * 2) ||
+            dalloc(alc, fine_cells * 2) || dalloc(qf, B * 8) || dalloc(qc, B * 8) || dalloc(sf, B * 4) ||
+            dalloc(sc, B * 4) || dalloc(acc, 8 * 8 * NL))
+            return RICH_ERR_OOM;
+        RICH_CUDA(cudaMemsetAsync(acc.p, 0, 8 * 8 * NL, st));
+        return 0;
+    }
+
+    // pairs first .. first+count-1 of level l: fields, fine and coarse solves, sums
+    int run_level(int l, long long first, long long count) {
+        const int M = grid(l);
         rich_problem_t pf = cfg->base;
         pf.nx = pf.nz = M; pf.nsteps = steps(l); pf.dt = cfg->t_final / steps(l);
         rich_problem_t pc = cfg->base;
         if (l > 0) { pc.nx = pc.nz = grid(l - 1); pc.nsteps = steps(l - 1); pc.dt = cfg->t_final / steps(l - 1); }
         const int ndraw = cfg->coupling == 0 ? nL : M;
         const int coarsen = cfg->coupling == 0 ? L - l : 0;
-        for (int b0 = 0; b0 < nsl; b0 += B) {
-            const int nb = std::min(B, nsl - b0);
-            RICH_CUDA(cudaEventRecord(ev[0], st));
-            int e;
-            if (cfg->coupling == 2 && l > 0)
-                e = rich_fields_pair_device(ctx, &cfg->field, M, M, (uint32_t)l + cfg->key_offset, b0, nb,
-                                            (double*)lkf.p, (double*)alf.p, (double*)lkc.p, (double*)alc.p, st);
-            else
-                e = rich_fields_device(ctx, &cfg->field, ndraw, ndraw, (uint32_t)l + cfg->key_offset, b0, nb,
-                                       coarsen, (double*)lkf.p, (double*)alf.p, st);
+        const int save_t = ctx->tune_threads, save_i = ctx->tune_mixed_inner;
+        if (cfg->tune_threads[l]) ctx->tune_threads = cfg->tune_threads[l];
+        if (cfg->tune_inner[l]) ctx->tune_mixed_inner = cfg->tune_inner[l];
+        int rc_all = 0;
+        for (long long b0 = 0; b0 < count && rc_all >= 0; b0 += B) {
+            const int nb = (int)std::min<long long>(B, count - b0);
+            const long long s0 = first + b0;
+            rc_all = batch(l, s0, nb, M, ndraw, coarsen, pf, pc);
+        }
+        ctx->tune_threads = save_t; ctx->tune_mixed_inner = save_i;
+        if (rc_all < 0) return rc_all;
+        n_done[l] += count;
+        return 0;
+    }
+    int batch(int l, long long s0, int nb, int M, int ndraw, int coarsen, const rich_problem_t& pf,
+              const rich_problem_t& pc) {
+        RICH_CUDA(cudaEventRecord(ev[0], st));
+        int e;
+        const uint32_t key = (uint32_t)l + cfg->key_offset;
+        if (cfg->coupling == 2 && l > 0)
+            e = rich_fields_pair_device(ctx, &cfg->field, M, M, key, s0, nb, (double*)lkf.p, (double*)alf.p,
+                                        (double*)lkc.p, (double*)alc.p, st);
+        else
+            e = rich_fields_device(ctx, &cfg->field, ndraw, ndraw, key, s0, nb, coarsen, (double*)lkf.p,
+                                   (double*)alf.p, st);
+        if (e) return e;
+        if (l > 0 && cfg->coupling != 2) {
+            e = rich_fields_average(ctx, nb, M, M, (double*)lkf.p, (double*)alf.p, (double*)lkc.p,
+                                    (double*)alc.p, st);
             if (e) return e;
-            if (l > 0 && cfg->coupling != 2) {
-                e = rich_fields_average(ctx, nb, M, M, (double*)lkf.p, (double*)alf.p, (double*)lkc.p,
-                                        (double*)alc.p, st);
-                if (e) return e;
-            }
-            RICH_CUDA(cudaEventRecord(ev[1], st));
-            int rc = rich_solve_device(ctx, &pf, nb, (double*)lkf.p, (double*)alf.p, ascale(l), (double*)qf.p,
-                                       nullptr, (int32_t*)sf.p, nullptr, st);
+        }
+        RICH_CUDA(cudaEventRecord(ev[1], st));
+        int rc = rich_solve_device(ctx, &pf, nb, (double*)lkf.p, (double*)alf.p, ascale(l), (double*)qf.p,
+                                   nullptr, (int32_t*)sf.p, nullptr, st);
+        if (rc < 0) return rc;
+        worst = std::max(worst, rc);
+        RICH_CUDA(cudaEventRecord(ev[2], st));
+        if (l > 0) {
+            rc = rich_solve_device(ctx, &pc, nb, (double*)lkc.p, (double*)alc.p, ascale(l - 1), (double*)qc.p,
+                                   nullptr, (int32_t*)sc.p, nullptr, st);
             if (rc < 0) return rc;
             worst = std::max(worst, rc);
-            RICH_CUDA(cudaEventRecord(ev[2], st));
-            if (l > 0) {
-                rc = rich_solve_device(ctx, &pc, nb, (double*)lkc.p, (double*)alc.p, ascale(l - 1), (double*)qc.p,
-                                       nullptr, (int32_t*)sc.p, nullptr, st);
-                if (rc < 0) return rc;
-                worst = std::max(worst, rc);
-            }
-            e = rich_mlmc_accumulate(ctx, (double*)qf.p, l > 0 ? (double*)qc.p : nullptr, (int32_t*)sf.p,
-                                     l > 0 ? (int32_t*)sc.p : nullptr, nb, (double*)acc.p + 8 * l, st);
-            if (e) return e;
-            RICH_CUDA(cudaEventRecord(ev[3], st));
-            RICH_CUDA(cudaEventSynchronize(ev[3]));
-            float a = 0, b = 0, c = 0;
-            RICH_CUDA(cudaEventElapsedTime(&a, ev[0], ev[1]));
-            RICH_CUDA(cudaEventElapsedTime(&b, ev[1], ev[2]));
-            RICH_CUDA(cudaEventElapsedTime(&c, ev[2], ev[3]));
-            t_pair[l] += 1e-3 * (a + b + c);
-            t_fine[l] += 1e-3 * (a + b);   // one draw + one fine solve (plain MC sample)
         }
+        e = rich_mlmc_accumulate(ctx, (double*)qf.p, l > 0 ? (double*)qc.p : nullptr, (int32_t*)sf.p,
+                                 l > 0 ? (int32_t*)sc.p : nullptr, nb, (double*)acc.p + 8 * l, st);
+        if (e) return e;
+        RICH_CUDA(cudaEventRecord(ev[3], st));
+        RICH_CUDA(cudaEventSynchronize(ev[3]));
+        float a = 0, b = 0, c = 0;
+        RICH_CUDA(cudaEventElapsedTime(&a, ev[0], ev[1]));
+        RICH_CUDA(cudaEventElapsedTime(&b, ev[1], ev[2]));
+        RICH_CUDA(cudaEventElapsedTime(&c, ev[2], ev[3]));
+        t_pair[l] += 1e-3 * (a + b + c);
+        t_fine[l] += 1e-3 * (a + b);      // one draw + one fine solve (plain MC sample)
+        return 0;
     }
-    std::vector<double> h(8 * NL);
-    RICH_CUDA(cudaMemcpyAsync(h.data(), acc.p, 8 * 8 * NL, cudaMemcpyDeviceToHost, st));
-    RICH_CUDA(cudaStreamSynchronize(st));
-    rich_mlmc_result_t r{};
-    r.nlevels = NL;
-    double rmse2 = 0, ssum = 0;
+
+    // level statistics from the device sums (Eqs. SMC_ch6, MC_var_ch6,
+    // eq:MLMCVar, ML_var_ch6, MLMCSAMP_ch6)
+    int finalize(rich_mlmc_result_t* out) {
+        std::vector<double> h(8 * NL);
+        RICH_CUDA(cudaMemcpyAsync(h.data(), acc.p, 8 * 8 * NL, cudaMemcpyDeviceToHost, st));
+        RICH_CUDA(cudaStreamSynchronize(st));
+        rich_mlmc_result_t r{};
+        r.nlevels = NL;
+        double rmse2 = 0, ssum = 0;
+        for (int l = 0; l < NL; ++l) {
+            const double* a = &h[8 * l];
+            const double n = a[2];
+            r.n[l] = (int64_t)n; r.failed[l] = (int64_t)a[3];
+            auto mv = [&](double s1, double s2, double* m, double* v) {
+                *m = n > 0 ? s1 / n : NAN;
+                *v = n > 1 ? (s2 - n * (*m) * (*m)) / (n - 1) : NAN;
+            };
+            mv(a[0], a[1], &r.mean[l], &r.var[l]);
+            mv(a[4], a[5], &r.mean_f[l], &r.var_f[l]);
+            if (l > 0) mv(a[6], a[7], &r.mean_c[l], &r.var_c[l]);
+            r.cost[l] = n_done[l] > 0 ? t_pair[l] / n_done[l] : NAN;
+            r.cost_fine[l] = n_done[l] > 0 ? t_fine[l] / n_done[l] : NAN;
+            r.estimate += r.mean[l];
+            rmse2 += r.var[l] / n;
+            r.ml_variance += r.var_f[l] - (l > 0 ? r.var_c[l] : 0.0);
+            ssum += sqrt(std::max(r.var[l], 0.0) * r.cost[l]);
+        }
+        r.rmse = sqrt(rmse2);
+        if (cfg->eps > 0) {
+            const double e2 = cfg->eps * cfg->eps;
+            for (int l = 0; l < NL; ++l) r.n_opt[l] = ssum * sqrt(std::max(r.var[l], 0.0) / r.cost[l]) / e2;
+            r.w_eps = ssum * ssum / e2;
+            r.w_mc_eps = r.var_f[L] * r.cost_fine[L] / e2;
+        }
+        r.bias_estimate = L > 0 ? fabs(r.mean[L]) / (2.0 - 1.0) : NAN;
+        *out = r;
+        return 0;
+    }
+};
+
+int check_cfg(const rich_mlmc_cfg_t* cfg) {
+    const int NL = cfg->nlevels;
+    if (NL < 1 || NL > RICH_MLMC_MAX_LEVELS || cfg->n0 < 2 || cfg->steps0 < 1 || !(cfg->t_final > 0) ||
+        cfg->coupling < 0 || cfg->coupling > 2)
+        return RICH_ERR_INVALID;
     for (int l = 0; l < NL; ++l) {
-        const double* a = &h[8 * l];
-        const double n = a[2];
-        r.n[l] = (int64_t)n; r.failed[l] = (int64_t)a[3];
-        auto mv = [&](double s1, double s2, double* m, double* v) {
-            *m = n > 0 ? s1 / n : NAN;
-            *v = n > 1 ? (s2 - n * (*m) * (*m)) / (n - 1) : NAN;
-        };
-        mv(a[0], a[1], &r.mean[l], &r.var[l]);
-        mv(a[4], a[5], &r.mean_f[l], &r.var_f[l]);
-        if (l > 0) mv(a[6], a[7], &r.mean_c[l], &r.var_c[l]);
-        r.cost[l] = t_pair[l] / cfg->nsamples[l];
-        r.cost_fine[l] = t_fine[l] / cfg->nsamples[l];
-        r.estimate += r.mean[l];
-        rmse2 += r.var[l] / n;
-        r.ml_variance += r.var_f[l] - (l > 0 ? r.var_c[l] : 0.0);
-        ssum += sqrt(std::max(r.var[l], 0.0) * r.cost[l]);
+        if (cfg->nsamples[l] < 2) return RICH_ERR_INVALID;
+        if (cfg->tune_threads[l] != 0 && cfg->tune_threads[l] != 512 && cfg->tune_threads[l] != 1024)
+            return RICH_ERR_INVALID;
+        if (cfg->tune_inner[l] < 0 || cfg->tune_inner[l] > 16) return RICH_ERR_INVALID;
     }
-    r.rmse = sqrt(rmse2);
-    if (cfg->eps > 0) {
-        const double e2 = cfg->eps * cfg->eps;
-        for (int l = 0; l < NL; ++l)
-            r.n_opt[l] = ssum * sqrt(std::max(r.var[l], 0.0) / r.cost[l]) / e2;
-        r.w_eps = ssum * ssum / e2;
-        r.w_mc_eps = r.var_f[L] * r.cost_fine[L] / e2;
+    return 0;
+}
+
+}  // namespace
+
+extern "C" int rich_mlmc_estimate(rich_ctx_t ctx, const rich_mlmc_cfg_t* cfg, rich_mlmc_result_t* out) {
+    if (!ctx || !cfg || !out || check_cfg(cfg)) return RICH_ERR_INVALID;
+    RICH_CUDA(cudaSetDevice(ctx->device));
+    auto t0 = std::chrono::steady_clock::now();
+    MlmcRun run(ctx, cfg);
+    int maxN = 0;
+    for (int l = 0; l < cfg->nlevels; ++l) maxN = std::max(maxN, cfg->nsamples[l]);
+    if (int e = run.init(maxN)) return e;
+    for (int l = 0; l < cfg->nlevels; ++l)
+        if (int e = run.run_level(l, 0, cfg->nsamples[l])) return e;
+    if (int e = run.finalize(out)) return e;
+    out->rounds = 1;
+    out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return run.worst;
+}
+
+// Algorithm PC_MLMC (Sec. 5.2): warm-up with N*_l = cfg->nsamples, then repeat
+// {N_l <- optimal allocation (Eq. MLMCSAMP_ch6) from the current V_l and the
+// per-sample costs measured so far; run the missing samples of every level}
+// until no level needs more samples, at most max_rounds rounds or until a
+// level would exceed nmax[l] (NULL: no cap).
+extern "C" int rich_mlmc_adaptive(rich_ctx_t ctx, const rich_mlmc_cfg_t* cfg, int32_t max_rounds,
+                                  const int64_t* nmax, rich_mlmc_result_t* out) {
+    if (!ctx || !cfg || !out || check_cfg(cfg) || !(cfg->eps > 0) || max_rounds < 1) return RICH_ERR_INVALID;
+    RICH_CUDA(cudaSetDevice(ctx->device));
+    auto t0 = std::chrono::steady_clock::now();
+    MlmcRun run(ctx, cfg);
+    int maxN = 0;
+    for (int l = 0; l < cfg->nlevels; ++l) maxN = std::max(maxN, cfg->nsamples[l]);
+    if (int e = run.init(std::max(maxN, 4096))) return e;
+    for (int l = 0; l < cfg->nlevels; ++l)
+        if (int e = run.run_level(l, 0, cfg->nsamples[l])) return e;
+    int rounds = 1;
+    for (;;) {
+        if (int e = run.finalize(out)) return e;
+        if (rounds >= max_rounds) break;
+        bool more = false;
+        std::vector<long long> add(cfg->nlevels, 0);
+        for (int l = 0; l < cfg->nlevels; ++l) {
+            long long target = (long long)ceil(out->n_opt[l]);
+            if (nmax) target = std::min<long long>(target, nmax[l]);
+            if (target > run.n_done[l]) { add[l] = target - run.n_done[l]; more = true; }
+        }
+        if (!more) break;
+        for (int l = 0; l < cfg->nlevels; ++l)
+            if (add[l] > 0)
+                if (int e = run.run_level(l, run.n_done[l], add[l])) return e;
+        ++rounds;
     }
-    r.bias_estimate = L > 0 ? fabs(r.mean[L]) / (2.0 - 1.0) : NAN;
-    r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    *out = r;
-    return worst;
+    out->rounds = rounds;
+    out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return run.worst;
 }

@@ -59,3 +59,33 @@ def test_mlmc_telescoping_consistency(R):
         d = g["mean_f"][l] - g["mean_c"][l + 1]
         se = np.sqrt(g["var_f"][l] / g["n"][l] + g["var_c"][l + 1] / g["n"][l + 1])
         assert abs(d) < 4 * se, (l, d, se)
+
+
+def test_adaptive_pc_mlmc(R):
+    """Algorithm PC_MLMC: the final N_l cover the optimal allocation computed
+    from the final V_l and C_l (so the sampling RMSE is at most eps), and since
+    each level continues its own sample stream, the statistics equal a one-shot
+    estimate with the final N_l."""
+    eps = 0.02
+    cfg = R.MlmcConfig(nsamples=(16, 8, 4), n0=8, steps0=2, t_final=0.04, coupling=2, eps=eps,
+                       problem=R.Problem(**PHYSICS, **SOLVER))
+    a = R.mlmc_adaptive(cfg, max_rounds=8)
+    assert a["rounds"] >= 2
+    n_final = [n + f for n, f in zip(a["n"], a["failed"])]
+    assert all(n >= w for n, w in zip(n_final, (16, 8, 4)))
+    assert all(nf >= np.ceil(no) - 1e-9 for nf, no in zip(n_final, a["n_opt"])) or a["rounds"] == 8
+    assert a["rmse"] <= eps * (1 + 1e-9) or a["rounds"] == 8
+    one = R.mlmc_estimate(R.MlmcConfig(nsamples=tuple(n_final), n0=8, steps0=2, t_final=0.04, coupling=2,
+                                       eps=eps, problem=R.Problem(**PHYSICS, **SOLVER)))
+    for k in ("n", "failed"):
+        assert one[k] == a[k]
+    for l in range(3):
+        assert rel(one["mean"][l], a["mean"][l]) < 1e-9 and rel(one["var"][l], a["var"][l]) < 1e-8
+
+
+def test_per_level_tuning_keeps_fp64_statistics(R):
+    base = dict(nsamples=(24, 12, 6), n0=8, steps0=2, t_final=0.04, coupling=2, eps=1e-3,
+                problem=R.Problem(**PHYSICS, **SOLVER))
+    g0 = R.mlmc_estimate(R.MlmcConfig(**base))
+    g1 = R.mlmc_estimate(R.MlmcConfig(**base, tune_threads=(1024, 512, 1024)))
+    assert g0["mean"] == g1["mean"] and g0["var"] == g1["var"]
