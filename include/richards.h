@@ -54,6 +54,8 @@ typedef struct {
     int32_t nu1, nu2;        /* red-black Gauss-Seidel steps before / after       */
     int32_t precision;       /* RICH_FP64, or RICH_MIXED: FP32 V-cycles inside an
                                 FP64 defect-correction loop                       */
+    int32_t cycle;           /* multigrid cycle index: 1 (or 0) V-cycle, 2 W-cycle
+                                (the paper's W(2,2), Sec. 4.2), at most 4         */
 } rich_problem_t;
 
 /* Random-field model: ln Ks Gaussian, exponential covariance sigma2*exp(-r/corr_len),

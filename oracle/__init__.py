@@ -42,7 +42,7 @@ class Problem(C.Structure):
                 ("theta_s", C.c_double), ("p_top", C.c_double), ("p_bottom", C.c_double),
                 ("p_init", C.c_double), ("picard_tol", C.c_double), ("picard_maxit", C.c_int32),
                 ("mg_tol", C.c_double), ("mg_maxit", C.c_int32), ("nu1", C.c_int32),
-                ("nu2", C.c_int32)]
+                ("nu2", C.c_int32), ("gamma", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -52,10 +52,11 @@ class Stats(C.Structure):
 
 def make_problem(nsteps=10, dt=0.01, theta_r=0.1, theta_s=0.5, p_top=-0.5, p_bottom=-5.0,
                  p_init=-5.0, picard_tol=1e-8, picard_maxit=50, mg_tol=1e-10, mg_maxit=100,
-                 nu1=2, nu2=2) -> Problem:
-    """Physics and solver settings of the configured instance (Gardner closure)."""
+                 nu1=2, nu2=2, gamma=1) -> Problem:
+    """Physics and solver settings of the configured instance (Gardner closure);
+    gamma = 1: V-cycles (configured), 2: W-cycles (the paper's choice, Sec. 4.2)."""
     return Problem(nsteps, dt, theta_r, theta_s, p_top, p_bottom, p_init, picard_tol,
-                   picard_maxit, mg_tol, mg_maxit, nu1, nu2)
+                   picard_maxit, mg_tol, mg_maxit, nu1, nu2, gamma)
 
 
 _lib = None
@@ -90,7 +91,7 @@ def lib():
         L.orc_picard_system.argtypes = [C.POINTER(Problem), C.c_int32, C.c_int32, _dp, _dp, C.c_double,
                                         _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
         L.orc_mg_solve.argtypes = [C.c_int32, C.c_int32, C.c_double, _dp, _dp, _dp, _dp, _dp, _dp,
-                                   C.c_double, C.c_int32, C.c_int32, C.c_int32, _dp,
+                                   C.c_double, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _dp,
                                    C.POINTER(C.c_int32), C.c_void_p]
         _lib = L
     return _lib
@@ -213,7 +214,7 @@ def picard_system(pb, lnKs, alpha, p, p_old, alpha_scale=1.0):
     return Tx, Tz, Tbt, Tbb, Cdt, f
 
 
-def mg_solve(Tx, Tz, Tbt, Tbb, Cdt, f, tol=1e-10, maxit=100, nu1=2, nu2=2):
+def mg_solve(Tx, Tz, Tbt, Tbb, Cdt, f, tol=1e-10, maxit=100, nu1=2, nu2=2, gamma=1):
     """CCMG V(nu1,nu2) solve from dp = 0; returns (dp, cycles, rc, residual history)."""
     Tx, Tz, Cdt, f = _f64(Tx), _f64(Tz), _f64(Cdt), _f64(f)
     nz, nx = f.shape
@@ -221,7 +222,7 @@ def mg_solve(Tx, Tz, Tbt, Tbb, Cdt, f, tol=1e-10, maxit=100, nu1=2, nu2=2):
     cyc = C.c_int32()
     hist = np.zeros(maxit + 1)
     rc = lib().orc_mg_solve(nx, nz, 1.0 / nz, Tx.reshape(-1), Tz.reshape(-1), _f64(Tbt), _f64(Tbb),
-                            Cdt.reshape(-1), f.reshape(-1), tol, maxit, nu1, nu2, dp.reshape(-1),
+                            Cdt.reshape(-1), f.reshape(-1), tol, maxit, nu1, nu2, gamma, dp.reshape(-1),
                             C.byref(cyc), _ptr(hist))
     return dp, cyc.value, rc, hist[: cyc.value + 1]
 

@@ -106,7 +106,7 @@ def forward_states(pb, lnks, alpha, alpha_scale=1.0):
     one = make_problem(nsteps=1, dt=pb.dt, theta_r=pb.theta_r, theta_s=pb.theta_s, p_top=pb.p_top,
                        p_bottom=pb.p_bottom, p_init=pb.p_init, picard_tol=pb.picard_tol,
                        picard_maxit=pb.picard_maxit, mg_tol=pb.mg_tol, mg_maxit=pb.mg_maxit,
-                       nu1=pb.nu1, nu2=pb.nu2)
+                       nu1=pb.nu1, nu2=pb.nu2, gamma=pb.gamma)
     states = [np.full((nz, nx), pb.p_init)]
     for n in range(pb.nsteps):
         p, q, rc, _ = solve_one(one, lnks, alpha, alpha_scale, p_init=states[-1])

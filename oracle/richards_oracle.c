@@ -546,8 +546,10 @@ static void coarse_solve(mg_level* L)
     free(A); free(b);
 }
 
-/* V(nu1, nu2)-cycle on level l (recursive, Sec. 4.2) */
-static void vcycle(mg_level* Ls, int l, int nlev, int nu1, int nu2)
+/* multigrid cycle on level l (recursive, Sec. 4.2): gamma = 1 gives the
+ * V(nu1, nu2)-cycle, gamma = 2 the W(nu1, nu2)-cycle (gamma coarse-grid
+ * cycles per visit; the exact coarsest solve is done once) */
+static void mgcycle(mg_level* Ls, int l, int nlev, int nu1, int nu2, int gamma)
 {
     mg_level* L = &Ls[l];
     if (l == nlev - 1) { coarse_solve(L); return; }
@@ -561,7 +563,8 @@ static void vcycle(mg_level* Ls, int l, int nlev, int nu1, int nu2)
             C->f[(size_t)J * C->nx + I] = 0.25 * (L->r[f00] + L->r[f00 + 1] + L->r[f01] + L->r[f01 + 1]);
             C->dp[(size_t)J * C->nx + I] = 0.0;
         }
-    vcycle(Ls, l + 1, nlev, nu1, nu2);
+    int reps = (l + 1 == nlev - 1) ? 1 : gamma;
+    for (int g = 0; g < reps; ++g) mgcycle(Ls, l + 1, nlev, nu1, nu2, gamma);
     /* piecewise-constant prolongation, Eq. transfer */
     for (int j = 0; j < L->nz; ++j)
         for (int i = 0; i < L->nx; ++i)
@@ -614,7 +617,7 @@ static double inf_norm(const double* x, size_t n)
  * ||f - A dp||_inf < tol * max(1, ||f||_inf) (reading R10) or maxit cycles.
  * Returns 0 if converged, 1 if not, 3 if the residual is not finite. */
 static int mg_solve_levels(mg_level* Ls, int nlev, double tol, int maxit, int nu1, int nu2,
-                           int* cycles, double* res_hist)
+                           int gamma, int* cycles, double* res_hist)
 {
     mg_level* L = &Ls[0];
     size_t n = (size_t)L->nx * L->nz;
@@ -629,7 +632,7 @@ static int mg_solve_levels(mg_level* Ls, int nlev, double tol, int maxit, int nu
     int it = 0;
     if (res_hist) res_hist[0] = rn;
     while (rn >= target && it < maxit) {
-        vcycle(Ls, 0, nlev, nu1, nu2);
+        mgcycle(Ls, 0, nlev, nu1, nu2, gamma < 1 ? 1 : gamma);
         rn = residual(L);
         ++it;
         if (res_hist) res_hist[it] = rn;
@@ -642,7 +645,7 @@ static int mg_solve_levels(mg_level* Ls, int nlev, double tol, int maxit, int nu
 
 int orc_mg_solve(int32_t nx, int32_t nz, double h, const double* Tx, const double* Tz,
                  const double* Tbt, const double* Tbb, const double* Cdt, const double* f,
-                 double tol, int32_t maxit, int32_t nu1, int32_t nu2, double* dp,
+                 double tol, int32_t maxit, int32_t nu1, int32_t nu2, int32_t gamma, double* dp,
                  int32_t* cycles, double* res_hist)
 {
     (void)h;
@@ -653,7 +656,7 @@ int orc_mg_solve(int32_t nx, int32_t nz, double h, const double* Tx, const doubl
     memcpy(Ls[0].Tx, Tx, n * 8); memcpy(Ls[0].Tz, Tz, n * 8); memcpy(Ls[0].Cdt, Cdt, n * 8);
     memcpy(Ls[0].Tbt, Tbt, nx * 8); memcpy(Ls[0].Tbb, Tbb, nx * 8); memcpy(Ls[0].f, f, n * 8);
     int cyc = 0;
-    int rc = mg_solve_levels(Ls, nlev, tol, maxit, nu1, nu2, &cyc, res_hist);
+    int rc = mg_solve_levels(Ls, nlev, tol, maxit, nu1, nu2, gamma, &cyc, res_hist);
     memcpy(dp, Ls[0].dp, n * 8);
     *cycles = cyc;
     free_levels(Ls, nlev);
@@ -687,7 +690,8 @@ int orc_solve_one(const orc_problem* pb, int32_t nx, int32_t nz, const double* l
                               L->Tx, L->Tz, L->Tbt, L->Tbb, L->Cdt, L->f);
             if (src) for (size_t q = 0; q < n; ++q) L->f[q] += src[q];
             int cyc = 0;
-            int rc = mg_solve_levels(Ls, nlev, pb->mg_tol, pb->mg_maxit, pb->nu1, pb->nu2, &cyc, NULL);
+            int rc = mg_solve_levels(Ls, nlev, pb->mg_tol, pb->mg_maxit, pb->nu1, pb->nu2, pb->gamma, &cyc,
+                                     NULL);
             S.mg_cycles += cyc;
             if (cyc > S.max_mg) S.max_mg = cyc;
             if (rc == 3) { status = ORC_NONFINITE; break; }

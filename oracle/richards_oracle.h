@@ -34,6 +34,7 @@ typedef struct {
     double mg_tol;         /* eps_MG; applied as eps_MG * max(1, ||f||_inf)  */
     int32_t mg_maxit;
     int32_t nu1, nu2;      /* pre/post red-black GS steps                    */
+    int32_t gamma;         /* cycle index: 1 = V-cycle, 2 = W-cycle          */
 } orc_problem;
 
 typedef struct {
@@ -74,6 +75,6 @@ int  orc_picard_system(const orc_problem* pb, int32_t nx, int32_t nz, const doub
                        double* Tbb, double* Cdt, double* f);
 int  orc_mg_solve(int32_t nx, int32_t nz, double h, const double* Tx, const double* Tz,
                   const double* Tbt, const double* Tbb, const double* Cdt, const double* f,
-                  double tol, int32_t maxit, int32_t nu1, int32_t nu2, double* dp,
+                  double tol, int32_t maxit, int32_t nu1, int32_t nu2, int32_t gamma, double* dp,
                   int32_t* cycles, double* res_hist);
 #endif

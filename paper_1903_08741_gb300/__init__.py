@@ -33,7 +33,7 @@ class _Problem(C.Structure):
                 ("theta_r", C.c_double), ("theta_s", C.c_double), ("p_top", C.c_double),
                 ("p_bottom", C.c_double), ("p_init", C.c_double), ("picard_tol", C.c_double),
                 ("picard_maxit", C.c_int32), ("mg_tol", C.c_double), ("mg_maxit", C.c_int32),
-                ("nu1", C.c_int32), ("nu2", C.c_int32), ("precision", C.c_int32)]
+                ("nu1", C.c_int32), ("nu2", C.c_int32), ("precision", C.c_int32), ("cycle", C.c_int32)]
 
 
 class _Field(C.Structure):
@@ -65,6 +65,7 @@ class Problem:
     nu1: int = 2
     nu2: int = 2
     precision: int = FP64
+    cycle: int = 1           # 1: V-cycle (configured), 2: W-cycle (the paper's)
 
     def _c(self):
         return _Problem(*[getattr(self, f.name) for f in dc_fields(self)])

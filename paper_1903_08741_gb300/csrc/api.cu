@@ -132,6 +132,7 @@ int rich_check_problem(const rich_problem_t* pb) {
     if (!pb || pb->nx < 1 || pb->nz < 1 || pb->nsteps < 0 || !(pb->dt > 0) ||
         pb->picard_maxit < 1 || pb->mg_maxit < 1 || pb->nu1 < 0 || pb->nu2 < 0 ||
         (pb->precision != RICH_FP64 && pb->precision != RICH_MIXED) || !(pb->picard_tol > 0) ||
+        pb->cycle < 0 || pb->cycle > 4 ||
         !(pb->mg_tol > 0))
         return RICH_ERR_INVALID;
     if (rich_count_levels(pb->nx, pb->nz) < 1) return RICH_ERR_INVALID;

@@ -69,7 +69,7 @@ struct FParams {
     int64_t* mg_total;
     int32_t* maxpic;
     int* queue;
-    int nsteps, picard_maxit, mg_maxit, nu1, nu2;
+    int nsteps, picard_maxit, mg_maxit, nu1, nu2, gamma;
     double inv_dt, tr, ts, p_top, p_bot, p_init, picard_tol, mg_tol, h, two_over_h2;
     // adjoint (k_adjoint only)
     int mixed_inner;            // FP32 V-cycles per FP64 defect (mixed path)
@@ -256,6 +256,46 @@ __device__ __forceinline__ void coarse_solve(int nx, int nz, const T* Tx, const 
 
 // f0: unscaled finest right-hand side, used by the direct solve when the
 // finest grid is also the coarsest (FP64 levels keep f/D otherwise)
+// exact solve on the coarsest level c (FP64 levels: the unscaled FP64
+// operator; f0 is the unscaled right-hand side when c is the finest level)
+template <typename T>
+__device__ __forceinline__ void coarsest(const Lv<T>* L, const Lv64* L64, int c, T* A, const T* f0) {
+    if constexpr (Scaled<T>::value)
+        coarse_solve<T>(L64[c].nx, L64[c].nz, L64[c].Tx, L64[c].Tz, L64[c].D, c == 0 ? f0 : L[c].f,
+                        L[c].dp, A);
+    else
+        coarse_solve<T>(L[c].nx, L[c].nz, L[c].c0, L[c].c1, L[c].D, L[c].f, L[c].dp, A);
+}
+
+// one cycle of index gamma >= 2 (W-cycle for gamma = 2, the paper's cycle,
+// Sec. 4.2): every visit of level l < nlev-2 runs gamma cycles on level l+1,
+// the visit of nlev-2 one exact coarsest solve.  The recursion is unrolled
+// into a depth-first walk whose per-level visit counts sit in 4-bit fields of
+// one register (no device stack); called uniformly by the whole CTA.
+template <typename T>
+__device__ void gcycle(const Lv<T>* L, const Lv64* L64, int nlev, int nu1, int nu2, int gamma, T* A,
+                       const T* f0) {
+    static_assert(RICH_MAX_LEVELS * 4 <= 64, "visit counters must fit one 64-bit word");
+    unsigned long long cnt = 0;
+    int l = 0;
+    for (;;) {
+        for (; l < nlev - 1; ++l) {                       // enter l: pre-smooth, restrict
+            for (int it = 0; it < nu1; ++it) { rbgs(L[l], 0); rbgs(L[l], 1); }
+            resid_restrict(L[l], L[l + 1], nu1 > 0, l + 1 == nlev - 1);
+            cnt &= ~(15ull << (4 * l));
+        }
+        coarsest<T>(L, L64, nlev - 1, A, f0);
+        for (;;) {                                        // leave l+1, back on l
+            if (--l < 0) return;
+            cnt += 1ull << (4 * l);
+            const int reps = (l + 1 == nlev - 1) ? 1 : gamma;
+            if ((int)((cnt >> (4 * l)) & 15) < reps) { ++l; break; }   // cycle l+1 again
+            prolong(L[l], L[l + 1]);
+            for (int it = 0; it < nu2; ++it) { rbgs(L[l], 0); rbgs(L[l], 1); }
+        }
+    }
+}
+
 template <typename T>
 __device__ void vcycle(const Lv<T>* L, const Lv64* L64, int nlev, int nu1, int nu2, T* A,
                        const T* f0) {
@@ -263,12 +303,7 @@ __device__ void vcycle(const Lv<T>* L, const Lv64* L64, int nlev, int nu1, int n
         for (int it = 0; it < nu1; ++it) { rbgs(L[l], 0); rbgs(L[l], 1); }
         resid_restrict(L[l], L[l + 1], nu1 > 0, l + 1 == nlev - 1);
     }
-    const int c = nlev - 1;
-    if constexpr (Scaled<T>::value)
-        coarse_solve<T>(L64[c].nx, L64[c].nz, L64[c].Tx, L64[c].Tz, L64[c].D, c == 0 ? f0 : L[c].f,
-                        L[c].dp, A);
-    else
-        coarse_solve<T>(L[c].nx, L[c].nz, L[c].c0, L[c].c1, L[c].D, L[c].f, L[c].dp, A);
+    coarsest<T>(L, L64, nlev - 1, A, f0);
     for (int l = nlev - 2; l >= 0; --l) {
         prolong(L[l], L[l + 1]);
         for (int it = 0; it < nu2; ++it) { rbgs(L[l], 0); rbgs(L[l], 1); }
@@ -301,7 +336,7 @@ __device__ __forceinline__ unsigned long long resid_norm(const Lv<T>& L, bool re
 
 // CTA-cooperative building blocks of one sample's solve.  Every method is
 // called by all threads of the CTA and ends with the CTA synchronised.
-template <typename TM>
+template <typename TM, bool WC = false>
 struct Cta {
     static constexpr bool SC = Scaled<TM>::value;
     const FParams& P;
@@ -452,6 +487,14 @@ struct Cta {
         return fb;
     }
 
+    // one multigrid cycle: the V-cycle, or (WC, a separate kernel
+    // instantiation so the V kernels keep their register allocation) the
+    // cycle of index P.gamma
+    __device__ void mgcycle(const TM* f0) {
+        if constexpr (WC) gcycle<TM>(LM, L64, nlev, P.nu1, P.nu2, P.gamma, Amat, f0);
+        else vcycle<TM>(LM, L64, nlev, P.nu1, P.nu2, Amat, f0);
+    }
+
     // FP64 residual f - A x of the finest operator at cell q
     __device__ __forceinline__ double resid64(const double* f, const double* x, int q) const {
         const Lv64& F = L64[0];
@@ -476,12 +519,12 @@ struct Cta {
         while (rn >= target && cyc < P.mg_maxit) {
             unsigned long long rb;
             if constexpr (SC) {
-                vcycle<TM>(LM, L64, nlev, P.nu1, P.nu2, Amat, (const TM*)f64);
+                mgcycle((const TM*)f64);
                 ++cyc;
                 rb = resid_norm<TM>(M0, P.nu2 > 0 && nlev > 1, red);
             } else {
                 for (int in = 0; in < P.mixed_inner && cyc < P.mg_maxit; ++in) {
-                    vcycle<TM>(LM, L64, nlev, P.nu1, P.nu2, Amat, nullptr);
+                    mgcycle(nullptr);
                     ++cyc;
                 }
                 // dp += e in FP64, then the FP64 defect: stopping norm and the
@@ -597,8 +640,8 @@ struct Cta {
         }
         __syncthreads();
         for (int k = 0; k < ninner; ++k) {
-            if constexpr (SC) vcycle<TM>(LM, L64, nlev, P.nu1, P.nu2, Amat, r);
-            else vcycle<TM>(LM, L64, nlev, P.nu1, P.nu2, Amat, nullptr);
+            if constexpr (SC) mgcycle(r);
+            else mgcycle(nullptr);
         }
     }
 
@@ -681,7 +724,7 @@ __device__ __forceinline__ void init_levels(const FParams& P, char* slot, Lv64* 
     __syncthreads();
 }
 
-template <typename TM, int NT>
+template <typename TM, int NT, bool WC>
 __global__ void __launch_bounds__(NT)
 k_fused(const FParams P) {
     extern __shared__ unsigned char smraw[];
@@ -691,7 +734,7 @@ k_fused(const FParams P) {
     __shared__ Lv<TM> LM[MAXL];
     char* slot = P.scratch + (size_t)blockIdx.x * P.slot_bytes;
     init_levels<TM>(P, slot, L64, LM);
-    Cta<TM> C(P, slot, L64, LM, reinterpret_cast<TM*>(smraw), red);
+    Cta<TM, WC> C(P, slot, L64, LM, reinterpret_cast<TM*>(smraw), red);
     const int nc = C.nc, tid = C.tid, nt = C.nt;
     for (;;) {
         if (tid == 0) s_sample = atomicAdd(P.queue, 1);
@@ -726,7 +769,7 @@ k_fused(const FParams P) {
 // (last first) recompute its states from the checkpoint and step backwards:
 //   J_N^T lam_N = dQ/dp^N,  J_n^T lam_n = diag(C(p^n)/dt) lam_{n+1},
 //   dQ/dm = dQ/dm|explicit - sum_n (dR_n/dm)^T lam_n     (m = ln Ks).
-template <typename TM>
+template <typename TM, bool WC>
 __global__ void __launch_bounds__(512)
 k_adjoint(const FParams P) {
     extern __shared__ unsigned char smraw[];
@@ -736,7 +779,7 @@ k_adjoint(const FParams P) {
     __shared__ Lv<TM> LM[MAXL];
     char* slot = P.scratch + (size_t)blockIdx.x * P.slot_bytes;
     init_levels<TM>(P, slot, L64, LM);
-    Cta<TM> C(P, slot, L64, LM, reinterpret_cast<TM*>(smraw), red);
+    Cta<TM, WC> C(P, slot, L64, LM, reinterpret_cast<TM*>(smraw), red);
     const int nc = C.nc, nx = C.nx, tid = C.tid, nt = C.nt;
     const int CK = P.ckpt_every;
     double* ckpt = (double*)(slot + P.o_ckpt);      // [nck][nc]
@@ -880,7 +923,7 @@ static int fused_setup(const rich_problem_t* pb, int S, FParams& P, int ckpt_eve
     }
     P.slot_bytes = (long long)off;
     P.nsteps = pb->nsteps; P.picard_maxit = pb->picard_maxit; P.mg_maxit = pb->mg_maxit;
-    P.nu1 = pb->nu1; P.nu2 = pb->nu2;
+    P.nu1 = pb->nu1; P.nu2 = pb->nu2; P.gamma = pb->cycle < 1 ? 1 : pb->cycle;
     P.inv_dt = 1.0 / pb->dt; P.tr = pb->theta_r; P.ts = pb->theta_s; P.p_top = pb->p_top;
     P.p_bot = pb->p_bottom; P.p_init = pb->p_init; P.picard_tol = pb->picard_tol; P.mg_tol = pb->mg_tol;
     P.h = 1.0 / pb->nz; P.two_over_h2 = 2.0 / (P.h * P.h);
@@ -894,32 +937,37 @@ static size_t fused_smem(const FParams& P) {
 
 // block shapes the fused kernel is built for: 512 threads (two resident CTAs
 // per SM at 64 registers) or 1024 (one; half the resident scratch slots)
-template <int NT>
+// (and, per shape, the V-cycle and the gamma >= 2 cycle instantiations)
+template <int NT, bool WC>
 static int occ_nt(const FParams& P, size_t smem, int* occ) {
     if (P.mixed) {
-        RICH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_fused<float, NT>, NT, smem));
+        RICH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_fused<float, NT, WC>, NT, smem));
     } else {
-        RICH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_fused<double, NT>, NT, smem));
+        RICH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_fused<double, NT, WC>, NT, smem));
     }
     if (*occ < 1) *occ = 1;
     return 0;
 }
 
 static int fused_occupancy(const FParams& P, size_t smem, int nt, int* occ) {
-    return nt == 1024 ? occ_nt<1024>(P, smem, occ) : occ_nt<512>(P, smem, occ);
+    const bool wc = P.gamma > 1;
+    if (nt == 1024) return wc ? occ_nt<1024, true>(P, smem, occ) : occ_nt<1024, false>(P, smem, occ);
+    return wc ? occ_nt<512, true>(P, smem, occ) : occ_nt<512, false>(P, smem, occ);
 }
 
-template <int NT>
+template <int NT, bool WC>
 static void launch_nt(const FParams& P, int grid, size_t smem, cudaStream_t st) {
-    if (P.mixed) k_fused<float, NT><<<grid, NT, smem, st>>>(P);
-    else k_fused<double, NT><<<grid, NT, smem, st>>>(P);
+    if (P.mixed) k_fused<float, NT, WC><<<grid, NT, smem, st>>>(P);
+    else k_fused<double, NT, WC><<<grid, NT, smem, st>>>(P);
 }
 
 static int fused_launch(const FParams& P, int grid, size_t smem, int nt, cudaStream_t st) {
     RICH_CUDA(cudaMemsetAsync(P.queue, 0, sizeof(int), st));
     rich_count_launch();
-    if (nt == 1024) launch_nt<1024>(P, grid, smem, st);
-    else launch_nt<512>(P, grid, smem, st);
+    const bool wc = P.gamma > 1;
+    if (nt == 1024) { if (wc) launch_nt<1024, true>(P, grid, smem, st); else launch_nt<1024, false>(P, grid, smem, st); }
+    else if (wc) launch_nt<512, true>(P, grid, smem, st);
+    else launch_nt<512, false>(P, grid, smem, st);
     RICH_CUDA(cudaGetLastError());
     return 0;
 }
@@ -972,11 +1020,9 @@ int rich_adjoint_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const dou
     P.mixed_inner = ctx->tune_mixed_inner > 0 ? ctx->tune_mixed_inner : MIXED_INNER_DEFAULT;
     const size_t smem = fused_smem(P);
     int occ = 0;
-    if (P.mixed) {
-        RICH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adjoint<float>, 512, smem));
-    } else {
-        RICH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adjoint<double>, 512, smem));
-    }
+    const void* kern = P.mixed ? (P.gamma > 1 ? (const void*)k_adjoint<float, true> : (const void*)k_adjoint<float, false>)
+                               : (P.gamma > 1 ? (const void*)k_adjoint<double, true> : (const void*)k_adjoint<double, false>);
+    RICH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 512, smem));
     occ = std::max(occ, 1);
     const int grid = std::max(1, std::min(S, ctx->sm_count * occ));
     const size_t need = (size_t)grid * (size_t)P.slot_bytes + 256;
@@ -995,8 +1041,11 @@ int rich_adjoint_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const dou
     RICH_CUDA(cudaMemsetAsync(P.queue, 0, sizeof(int), st));
     rich_count_launch();
     rich_prof_begin(ctx, st);
-    if (P.mixed) k_adjoint<float><<<grid, 512, smem, st>>>(P);
-    else k_adjoint<double><<<grid, 512, smem, st>>>(P);
+    if (P.mixed) {
+        if (P.gamma > 1) k_adjoint<float, true><<<grid, 512, smem, st>>>(P);
+        else k_adjoint<float, false><<<grid, 512, smem, st>>>(P);
+    } else if (P.gamma > 1) k_adjoint<double, true><<<grid, 512, smem, st>>>(P);
+    else k_adjoint<double, false><<<grid, 512, smem, st>>>(P);
     rich_prof_end(ctx, st, 0.0, 0.0);
     RICH_CUDA(cudaGetLastError());
     return 0;

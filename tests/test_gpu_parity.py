@@ -41,6 +41,8 @@ def orc_problem(nsteps, dt, **kw):
     d.update(SOLVER)
     d.update(kw)
     d.pop("precision", None)
+    if "cycle" in d:
+        d["gamma"] = d.pop("cycle")
     return O.make_problem(nsteps=nsteps, dt=dt, **d)
 
 
@@ -277,3 +279,47 @@ def test_graph_captured_step_matches_direct_calls(R):
         assert torch.equal(q[ok], q_ref[ok])
     assert int(first.item()) == 2 * S
     assert int(acc[2].item() + acc[3].item()) == 2 * S
+
+
+# --------------------------------------------------------------- W-cycle
+@pytest.mark.parametrize("nx,nz,S,steps,cycle", [(32, 32, 16, 4, 2), (48, 32, 5, 3, 2), (64, 64, 6, 2, 3),
+                                                 (4, 4, 3, 2, 2)])
+def test_w_cycle_matches_oracle(R, nx, nz, S, steps, cycle):
+    """Cycle index 2 (the paper's W-cycle) and 3: pressure head and QoI within
+    1e-10 of the oracle's recursive cycle, statuses and counts as for V."""
+    compare(R, nx, nz, S, steps, 0.01, cycle=cycle)
+
+
+def test_w_cycle_needs_fewer_cycles_than_v(R):
+    """Same fields, same answers to 1e-9; the W-cycle needs fewer cycles."""
+    dev = torch.device("cuda:0")
+    lk, al = O.sample_fields(128, 128, 8, seed=3)
+    lk, al = torch.from_numpy(lk).to(dev), torch.from_numpy(al).to(dev)
+    out = {c: R.solve_batch(gpu_problem(R, 128, 128, 4, 0.01, cycle=c), lk, al, 1.0) for c in (1, 2)}
+    (qv, _, sv, stv, _), (qw, _, sw, stw, _) = out[1], out[2]
+    ok = (sv.cpu() == 0) & (sw.cpu() == 0)
+    assert ok.sum() >= 4
+    assert torch.allclose(qv.cpu()[ok], qw.cpu()[ok], rtol=1e-9, atol=0)
+    assert stw.mg_cycles < stv.mg_cycles
+
+
+def test_w_cycle_mixed_precision_within_1e6(R):
+    """FP32 W-cycles inside FP64 defect correction: QoI within 1e-6 of the
+    oracle's FP64 W-cycle solve."""
+    lk, al = O.sample_fields(64, 64, 8, seed=2)
+    _, q_o, s_o, _ = O.solve_batch(orc_problem(3, 0.01, cycle=2), lk, al, 1.0, nthreads=NTH)
+    dev = torch.device("cuda:0")
+    q, _, s, _, _ = R.solve_batch(gpu_problem(R, 64, 64, 3, 0.01, cycle=2, precision=R.MIXED),
+                                  torch.from_numpy(lk).to(dev), torch.from_numpy(al).to(dev), 1.0)
+    q, s = q.cpu().numpy(), s.cpu().numpy()
+    ok = (s == 0) & (s_o == 0)
+    assert ok.sum() >= 4
+    assert (np.abs(q[ok] - q_o[ok]) / np.abs(q_o[ok])).max() <= 1e-6
+
+
+def test_invalid_cycle_index_rejected(R):
+    dev = torch.device("cuda:0")
+    lk, al = O.sample_fields(8, 8, 1, seed=0)
+    with pytest.raises(R.RichError):
+        R.solve_batch(gpu_problem(R, 8, 8, 1, 0.01, cycle=5), torch.from_numpy(lk).to(dev),
+                      torch.from_numpy(al).to(dev), 1.0)

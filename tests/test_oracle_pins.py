@@ -224,9 +224,14 @@ def test_mg_poisson_matches_dense_and_contracts(n):
     assert np.all(np.diff(hist) < 0)
     rho = (hist[-1] / hist[0]) ** (1.0 / cyc)
     assert rho < 0.5, rho
-    # dense reference: same operator from the incidence-matrix construction,
-    # with Dirichlet data zero (phi_D = 0 means p_D = -z_D) -- use linearity:
-    # A dp = f for the head correction.
+    ref = np.linalg.solve(poisson_dense(n), f.reshape(-1)).reshape(n, n)
+    assert np.abs(dp - ref).max() < 1e-10 * np.abs(ref).max()
+
+
+def poisson_dense(n):
+    """Dense 5-point operator of the unit-conductivity grid: neighbours at
+    1/h^2, Dirichlet faces (top, bottom) at 2/h^2 through the half cell, no
+    flow through the sides."""
     h = 1.0 / n
     A = np.zeros((n * n, n * n))
     for j in range(n):
@@ -239,8 +244,33 @@ def test_mg_poisson_matches_dense_and_contracts(n):
                     A[P, b * n + a] -= t
                 elif 0 <= a < n:      # beyond top/bottom: Dirichlet at h/2
                     A[P, P] += 2 / h ** 2
-    ref = np.linalg.solve(A, f.reshape(-1)).reshape(n, n)
-    assert np.abs(dp - ref).max() < 1e-10 * np.abs(ref).max()
+    return A
+
+
+@pytest.mark.parametrize("n", [4, 16, 32, 64])
+def test_w_cycle_converges_to_dense_and_beats_v(n):
+    """Cycle index gamma = 2 (the W-cycle of Sec. 4.2): converges to the dense
+    solution; with two levels (4^2 -> 2^2, the coarsest grid) it is the
+    V-cycle exactly; with three or more levels it visits the coarse grids
+    more often and contracts strictly faster than the V-cycle (and needs more
+    coarse-grid work, so it is not the V-cycle under another name)."""
+    rng = np.random.default_rng(5)
+    z = np.zeros((n, n))
+    Tx, Tz, Tbt, Tbb, Cdt, f0 = O.picard_system(problem(), z, z, np.full((n, n), -1.0),
+                                                np.full((n, n), -1.0))
+    f = rng.normal(size=(n, n))
+    runs = {g: O.mg_solve(Tx, Tz, Tbt, Tbb, Cdt, f, tol=1e-13, maxit=200, gamma=g) for g in (1, 2, 3)}
+    ref = np.linalg.solve(poisson_dense(n), f.reshape(-1)).reshape(n, n)
+    rho = {}
+    for g, (dp, cyc, rc, hist) in runs.items():
+        assert rc == 0
+        assert np.abs(dp - ref).max() < 1e-10 * np.abs(ref).max()
+        rho[g] = (hist[min(4, cyc)] / hist[0]) ** (1.0 / min(4, cyc))
+    if n == 4:
+        assert np.array_equal(runs[1][0], runs[2][0]) and runs[1][1] == runs[2][1]
+    else:
+        assert rho[2] < 0.9 * rho[1], rho
+        assert rho[3] <= rho[2] * 1.05, rho
 
 
 # ------------------------------------------------------------ nonlinear pins
