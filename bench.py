@@ -146,18 +146,37 @@ def max_over_ranks(pg, value, device):
     return float(t.item())
 
 
-def cpu_baseline(n, nsamples, steps, dt, seed=0):
+# covariance of the Gaussian fields: the configured exponential exp(-r/0.3) and
+# the paper's Matern sets Phi_1, Phi_2 (Eq. nonIsotropic and its table)
+FIELDS = {"exp": {}, "phi1": dict(nu=1.0, corr_len=0.2, corr_len_z=0.2),
+          "phi2": dict(nu=0.5, corr_len=0.1, corr_len_z=0.01)}
+FIELD_TEXT = {"exp": "exp. cov. 0.3", "phi1": "Matern Phi_1 (nu 1, 0.2, 0.2)",
+              "phi2": "Matern Phi_2 (nu 0.5, 0.1, 0.01)"}
+
+
+def cpu_baseline(n, nsamples, steps, dt, seed=0, field="exp", cycle=1):
     """The FP64 oracle as it stands, on every host core: fields + solves of a
     bounded sample of the workload.  Returns (solves/s, cores, seconds)."""
     import oracle as O
     cores = os.cpu_count() or 1
     O.build()
     t0 = time.perf_counter()
-    lk, al = O.sample_fields(n, n, nsamples, seed=seed, first_sample=10_000_000, nthreads=cores)
-    pb = O.make_problem(nsteps=steps, dt=dt, **PHYS)
+    lk, al = O.sample_fields(n, n, nsamples, seed=seed, first_sample=10_000_000, nthreads=cores,
+                             **FIELDS[field])
+    pb = O.make_problem(nsteps=steps, dt=dt, gamma=cycle, **PHYS)
     O.solve_batch(pb, lk, al, nthreads=cores, want_p=False)
     dt_s = time.perf_counter() - t0
     return nsamples / dt_s, cores, dt_s
+
+
+def workload_suffix(args):
+    """Non-default field model / cycle, appended to the workload name."""
+    out = ""
+    if args.field != "exp":
+        out += ", " + FIELD_TEXT[args.field]
+    if args.cycle != 1:
+        out += f", cycle index {args.cycle}"
+    return out
 
 
 def run_reference(args):
@@ -168,10 +187,10 @@ def run_reference(args):
     cores = os.cpu_count() or 1
     per_step = max(cores, args.ref_samples or cores)
     for _ in range(args.warmup):
-        cpu_baseline(n, per_step, steps, dt)
+        cpu_baseline(n, per_step, steps, dt, field=args.field, cycle=args.cycle)
     t = 0.0
     for _ in range(args.steps):
-        _, _, s = cpu_baseline(n, per_step, steps, dt)
+        _, _, s = cpu_baseline(n, per_step, steps, dt, field=args.field, cycle=args.cycle)
         t += s
     value = per_step * args.steps / t
     sample = f"{per_step} samples per step of the {n}x{n}, {steps}-step workload"
@@ -180,8 +199,8 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"mc{n}: {n}x{n} grid, {S} samples, {steps} steps dt={dt}, FP64",
-                   "sample": sample},
+        "config": {"workload": f"mc{n}: {n}x{n} grid, {S} samples, {steps} steps dt={dt}, FP64"
+                               + workload_suffix(args), "sample": sample},
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -207,16 +226,17 @@ def run_mlmc(args):
         m = MLMC_LEVELS["n0"] << l
         st_l = MLMC_LEVELS["steps0"] << l
         bt, mi = autotune.tune(R.Problem(nx=m, nz=m, nsteps=st_l, dt=MLMC_LEVELS["t_final"] / st_l,
-                                         precision=prec, **PHYS), nl)
+                                         precision=prec, cycle=args.cycle, **PHYS), nl)
         tt.append(bt)
         ti.append(mi)
     R.set_tuning(0, 0)
+    model = R.FieldModel(seed=0, **FIELDS[args.field])
+    base = R.Problem(precision=prec, cycle=args.cycle, **PHYS)
     cfg = R.MlmcConfig(**MLMC_LEVELS, coupling=args.coupling, eps=1e-3, tune_threads=tuple(tt),
-                       tune_inner=tuple(ti), problem=R.Problem(precision=prec, **PHYS))
+                       tune_inner=tuple(ti), problem=base, model=model)
     for k in range(args.warmup):
         small = R.MlmcConfig(nsamples=(64, 32, 16, 8, 4), n0=16, steps0=5, t_final=0.1,
-                             coupling=args.coupling, key_offset=100 + k,
-                             problem=R.Problem(precision=prec, **PHYS))
+                             coupling=args.coupling, key_offset=100 + k, problem=base, model=model)
         R.mlmc_estimate(small)
     clocks = ClockSampler(0)
     clocks.start()
@@ -235,7 +255,8 @@ def run_mlmc(args):
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if prec == R.FP64 else "f32-in-f64", "data": "synthetic",
         "config": {"workload": "mlmc5: 16^2..256^2, N_l = 20000/5000/1200/300/80, 5*2^l steps to T=0.1, "
-                               "alpha_l = alpha (l+1)/5, exp. cov. 0.3, seed 0",
+                               f"alpha_l = alpha (l+1)/5, {FIELD_TEXT[args.field]}, seed 0"
+                               + (f", cycle index {args.cycle}" if args.cycle > 1 else ""),
                    "coupling": {0: "finest-grid draw, 2x2 averages of ln Ks and alpha",
                                 1: "level-grid draw, 2x2 averages of ln Ks and alpha",
                                 2: "covariance upscaling (2x2-averaged white noise)"}[args.coupling]},
@@ -250,7 +271,7 @@ def run_mlmc(args):
     if args.adaptive_eps > 0:
         acfg = R.MlmcConfig(**{**MLMC_LEVELS, "nsamples": (512, 128, 32, 16, 8)}, coupling=args.coupling,
                             eps=args.adaptive_eps, key_offset=1000, tune_threads=tuple(tt), tune_inner=tuple(ti),
-                            problem=R.Problem(precision=prec, **PHYS))
+                            problem=base, model=model)
         a = R.mlmc_adaptive(acfg, max_rounds=10)
         out["adaptive"] = {"eps": args.adaptive_eps, "rounds": a["rounds"], "n": a["n"], "failed": a["failed"],
                            "rmse": a["rmse"], "estimate": a["estimate"], "seconds": a["seconds"],
@@ -403,10 +424,10 @@ def run_ours(args):
     S = args.samples or S
     steps = args.time_steps or steps
     prec = R.MIXED if args.precision == "mixed" else R.FP64
-    pb = R.Problem(nx=n, nz=n, nsteps=steps, dt=dt, precision=prec, **PHYS)
+    pb = R.Problem(nx=n, nz=n, nsteps=steps, dt=dt, precision=prec, cycle=args.cycle, **PHYS)
     from paper_1903_08741_gb300 import autotune
     block_threads, mixed_inner = autotune.tune(pb, S, device=local)
-    model = R.FieldModel(seed=0)
+    model = R.FieldModel(seed=0, **FIELDS[args.field])
     lk = torch.empty((S, n, n), dtype=torch.float64, device=dev)
     al = torch.empty_like(lk)
     acc = torch.zeros(8, dtype=torch.float64, device=dev)
@@ -512,7 +533,8 @@ def run_ours(args):
     frac_alu = k_tflops / FP64_TFLOPS_NOMINAL if prec == R.FP64 else 0.0
     per_launch_bytes = kbytes / max(klaunch, 1)
     kname = f"k_fused<{'double' if prec == R.FP64 else 'float'},{block_threads}> (persistent fused solve)"
-    default_workload = args.workload == "mc128" and not args.samples and not args.time_steps
+    default_workload = (args.workload == "mc128" and not args.samples and not args.time_steps
+                        and args.field == "exp" and args.cycle == 1)
     traffic = captured_traffic("fp64" if prec == R.FP64 else "mixed", block_threads, default_workload)
     if prec == R.FP64 and frac_alu > frac_hbm:
         roof = {"bound": "alu", "achieved": k_tflops, "peak": FP64_TFLOPS_NOMINAL, "unit": "TFLOP/s",
@@ -531,7 +553,8 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if prec == R.FP64 else "f32-in-f64", "data": "synthetic",
         "config": {"workload": f"mc{n}: {n}x{n} grid, {S} samples/GPU, {steps} steps dt={dt}, "
-                               f"{'FP64' if prec == R.FP64 else 'FP32 V-cycles in FP64 defect correction'}",
+                               f"{'FP64' if prec == R.FP64 else 'FP32 V-cycles in FP64 defect correction'}"
+                               + workload_suffix(args),
                    "global_batch": S * ws, "grid": [n, n], "time_steps": steps,
                    "launch": {"block_threads": block_threads, "mixed_inner": mixed_inner, "from": "autotuner"},
                    "l2": "inputs larger than L2 (2 x %.0f MB fields per step, fresh samples each step)"
@@ -551,7 +574,7 @@ def run_ours(args):
     if not args.no_cpu and ws == 1:
         cores = os.cpu_count() or 1
         ns = args.cpu_samples or cores
-        v, c, secs = cpu_baseline(n, ns, steps, dt)
+        v, c, secs = cpu_baseline(n, ns, steps, dt, field=args.field, cycle=args.cycle)
         out["cpu_baseline"] = {"value": v, "unit": "solves/s", "cores": c, "kind": "oracle",
                                "sample": f"{ns} samples of the {n}x{n}, {steps}-step workload "
                                          f"(fields + solves), {secs:.1f} s"}
@@ -569,6 +592,10 @@ def main():
     ap.add_argument("--adaptive-eps", type=float, default=0.0, help="mlmc5: also run Algorithm PC_MLMC to this RMSE")
     ap.add_argument("--coupling", type=int, default=0, help="MLMC field coupling (0 exact, 1 level grid)")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--field", choices=sorted(FIELDS), default="exp",
+                    help="covariance of the fields: exponential 0.3 (configured) or Matern Phi_1 / Phi_2")
+    ap.add_argument("--cycle", type=int, default=1, choices=[1, 2, 3],
+                    help="multigrid cycle index: 1 V-cycle (configured), 2 W-cycle")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)

@@ -58,14 +58,23 @@ typedef struct {
                                 (the paper's W(2,2), Sec. 4.2), at most 4         */
 } rich_problem_t;
 
-/* Random-field model: ln Ks Gaussian, exponential covariance sigma2*exp(-r/corr_len),
- * drawn by FFT moving average (Appendix A, Eqs. convol1-product2); alpha =
- * alpha_lo + alpha_span * Phi(g) with g an independent unit-variance field of the
- * same correlation (the marginal transform Y = F_Y^-1(F_Z(Z)) of Sec. 3.1). */
+/* Random-field model: ln Ks Gaussian, drawn by FFT moving average (Appendix A,
+ * Eqs. convol1-product2); alpha = alpha_lo + alpha_span * Phi(g) with g an
+ * independent unit-variance field of the same correlation (the marginal
+ * transform Y = F_Y^-1(F_Z(Z)) of Sec. 3.1).  Covariance at offset (dx, dz),
+ * r = sqrt((dx/corr_len)^2 + (dz/corr_len_z)^2):
+ *   nu = 0       sigma2 exp(-r)  (exponential; the zero-initialised default)
+ *   0 < nu <= 16 the Matern function of Eq. nonIsotropic,
+ *                sigma2 2^(1-nu)/Gamma(nu) (2 sqrt(nu) r)^nu K_nu(2 sqrt(nu) r);
+ *                the paper's Phi_1 = (nu 1, 0.2, 0.2, 1), Phi_2 = (0.5, 0.1, 0.01, 1).
+ * Invalid (RICH_ERR_INVALID): sigma2 <= 0, corr_len <= 0, corr_len_z < 0, nu
+ * outside [0, 16]. */
 typedef struct {
     double sigma2, corr_len;
     double alpha_lo, alpha_span;
     uint64_t seed;
+    double nu;               /* Matern smoothness; 0 selects the exponential      */
+    double corr_len_z;       /* correlation length along z; 0: equal to corr_len  */
 } rich_field_t;
 
 /* Host-side counters of a solve (summed over samples). */

@@ -45,6 +45,12 @@ class Problem(C.Structure):
                 ("nu2", C.c_int32), ("gamma", C.c_int32)]
 
 
+class Cov(C.Structure):
+    """Covariance of the Gaussian fields (nu = 0: exponential; nu > 0: Matern)."""
+    _fields_ = [("sigma2", C.c_double), ("corr_len", C.c_double), ("corr_len_z", C.c_double),
+                ("nu", C.c_double)]
+
+
 class Stats(C.Structure):
     _fields_ = [("picard_iters", C.c_int64), ("mg_cycles", C.c_int64),
                 ("max_picard", C.c_int32), ("max_mg", C.c_int32)]
@@ -73,14 +79,18 @@ def lib():
         L.orc_white_noise.argtypes = [C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint32, C.c_int64, _dp]
         L.orc_fft2.argtypes = [_dp, _dp, C.c_int32, C.c_int32, C.c_int32]
         L.orc_fft2.restype = C.c_int
-        L.orc_fftma_spectrum.argtypes = [C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double,
+        L.orc_bessel_k.argtypes = [C.c_double, C.c_double]
+        L.orc_bessel_k.restype = C.c_double
+        L.orc_covariance.argtypes = [C.POINTER(Cov), C.c_double, C.c_double]
+        L.orc_covariance.restype = C.c_double
+        L.orc_fftma_spectrum.argtypes = [C.c_int32, C.c_int32, C.c_double, C.POINTER(Cov),
                                          _dp, C.POINTER(C.c_double)]
-        L.orc_torus_size.argtypes = [C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double,
+        L.orc_torus_size.argtypes = [C.c_int32, C.c_int32, C.c_double, C.POINTER(Cov),
                                      C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
-        L.orc_sample_fields.argtypes = [C.c_uint64, C.c_double, C.c_double, C.c_double, C.c_double,
+        L.orc_sample_fields.argtypes = [C.c_uint64, C.POINTER(Cov), C.c_double, C.c_double,
                                         C.c_int32, C.c_int32, C.c_uint32, C.c_int64, C.c_int32,
                                         C.c_int32, _dp, _dp, C.c_int32]
-        L.orc_sample_fields_pair.argtypes = [C.c_uint64, C.c_double, C.c_double, C.c_double, C.c_double,
+        L.orc_sample_fields_pair.argtypes = [C.c_uint64, C.POINTER(Cov), C.c_double, C.c_double,
                                              C.c_int32, C.c_int32, C.c_uint32, C.c_int64, C.c_int32,
                                              _dp, _dp, _dp, _dp]
         L.orc_solve_one.argtypes = [C.POINTER(Problem), C.c_int32, C.c_int32, _dp, _dp, C.c_double,
@@ -129,27 +139,41 @@ def fft2(x, inverse=False):
     return re + 1j * im
 
 
-def torus_size(nx, nz, sigma2=1.0, corr_len=0.3):
+def bessel_k(nu, x):
+    """K_nu(x), x > 0, by the oracle's trapezoidal rule on its integral representation."""
+    return lib().orc_bessel_k(nu, x)
+
+
+def covariance(dx, dz, sigma2=1.0, corr_len=0.3, corr_len_z=0.0, nu=0.0):
+    """Field covariance at offset (dx, dz): exponential (nu = 0) or Matern (Eq. nonIsotropic)."""
+    return lib().orc_covariance(C.byref(Cov(sigma2, corr_len, corr_len_z, nu)), dx, dz)
+
+
+def torus_size(nx, nz, sigma2=1.0, corr_len=0.3, corr_len_z=0.0, nu=0.0):
     px, pz = C.c_int32(), C.c_int32()
-    lib().orc_torus_size(nx, nz, 1.0 / nz, sigma2, corr_len, C.byref(px), C.byref(pz))
+    lib().orc_torus_size(nx, nz, 1.0 / nz, C.byref(Cov(sigma2, corr_len, corr_len_z, nu)),
+                         C.byref(px), C.byref(pz))
     return px.value, pz.value
 
 
-def fftma_sqrt_spectrum(px, pz, h, sigma2=1.0, corr_len=0.3):
+def fftma_sqrt_spectrum(px, pz, h, sigma2=1.0, corr_len=0.3, corr_len_z=0.0, nu=0.0):
     s = np.empty(px * pz, np.float64)
     ratio = C.c_double()
-    lib().orc_fftma_spectrum(px, pz, h, sigma2, corr_len, s, C.byref(ratio))
+    lib().orc_fftma_spectrum(px, pz, h, C.byref(Cov(sigma2, corr_len, corr_len_z, nu)), s,
+                             C.byref(ratio))
     return s.reshape(pz, px), ratio.value
 
 
 def sample_fields(nx, nz, nsamples, seed=0, level=0, first_sample=0, coarsen_times=0,
-                  sigma2=1.0, corr_len=0.3, alpha_lo=0.5, alpha_span=1.5, nthreads=None):
+                  sigma2=1.0, corr_len=0.3, alpha_lo=0.5, alpha_span=1.5, nthreads=None,
+                  corr_len_z=0.0, nu=0.0):
     """ln Ks and alpha fields [S, nz>>c, nx>>c] drawn by FFT-MA on the nx x nz grid."""
     nthreads = nthreads or os.cpu_count() or 1
     nxo, nzo = nx >> coarsen_times, nz >> coarsen_times
     lnKs = np.empty((nsamples, nzo, nxo), np.float64)
     alpha = np.empty((nsamples, nzo, nxo), np.float64)
-    rc = lib().orc_sample_fields(seed, sigma2, corr_len, alpha_lo, alpha_span, nx, nz, level,
+    cv = Cov(sigma2, corr_len, corr_len_z, nu)
+    rc = lib().orc_sample_fields(seed, C.byref(cv), alpha_lo, alpha_span, nx, nz, level,
                                  first_sample, nsamples, coarsen_times, lnKs.reshape(-1),
                                  alpha.reshape(-1), nthreads)
     if rc:
@@ -158,11 +182,12 @@ def sample_fields(nx, nz, nsamples, seed=0, level=0, first_sample=0, coarsen_tim
 
 
 def sample_fields_pair(nx, nz, nsamples, seed=0, level=0, first_sample=0, sigma2=1.0, corr_len=0.3,
-                       alpha_lo=0.5, alpha_span=1.5):
+                       alpha_lo=0.5, alpha_span=1.5, corr_len_z=0.0, nu=0.0):
     """Fine [S, nz, nx] and coarse [S, nz/2, nx/2] fields by covariance upscaling."""
     f = [np.empty((nsamples, nz, nx)) for _ in range(2)]
     c = [np.empty((nsamples, nz // 2, nx // 2)) for _ in range(2)]
-    rc = lib().orc_sample_fields_pair(seed, sigma2, corr_len, alpha_lo, alpha_span, nx, nz, level,
+    cv = Cov(sigma2, corr_len, corr_len_z, nu)
+    rc = lib().orc_sample_fields_pair(seed, C.byref(cv), alpha_lo, alpha_span, nx, nz, level,
                                       first_sample, nsamples, f[0].reshape(-1), f[1].reshape(-1),
                                       c[0].reshape(-1), c[1].reshape(-1))
     if rc:
@@ -259,7 +284,8 @@ def optimal_samples(levels, eps):
 
 
 def mlmc_estimate(nsamples, n0, steps0, t_final, seed=0, coupling=0, continuation=1, key_offset=0,
-                  sigma2=1.0, corr_len=0.3, alpha_lo=0.5, alpha_span=1.5, nthreads=None, **phys):
+                  sigma2=1.0, corr_len=0.3, alpha_lo=0.5, alpha_span=1.5, nthreads=None,
+                  corr_len_z=0.0, nu=0.0, **phys):
     """Parametric-continuation MLMC (Sec. 5) restated plainly: for level l draw
     N_l field pairs (coupling 0: on the finest grid, averaged down L-l times;
     coupling 1: on the level grid), solve the fine member on grid n0 2^l with
@@ -273,18 +299,14 @@ def mlmc_estimate(nsamples, n0, steps0, t_final, seed=0, coupling=0, continuatio
     for l in range(NL):
         M = n0 << l
         scale = lambda k: (k + 1) / NL if continuation else 1.0
+        fm = dict(seed=seed, level=l + key_offset, sigma2=sigma2, corr_len=corr_len, corr_len_z=corr_len_z,
+                  nu=nu, alpha_lo=alpha_lo, alpha_span=alpha_span)
         if coupling == 2 and l > 0:
-            lk, al, lkc_up, alc_up = sample_fields_pair(M, M, nsamples[l], seed=seed, level=l + key_offset,
-                                                        sigma2=sigma2, corr_len=corr_len, alpha_lo=alpha_lo,
-                                                        alpha_span=alpha_span)
+            lk, al, lkc_up, alc_up = sample_fields_pair(M, M, nsamples[l], **fm)
         elif coupling == 0:
-            lk, al = sample_fields(nL, nL, nsamples[l], seed=seed, level=l + key_offset, coarsen_times=L - l,
-                                   sigma2=sigma2, corr_len=corr_len, alpha_lo=alpha_lo,
-                                   alpha_span=alpha_span, nthreads=nthreads)
+            lk, al = sample_fields(nL, nL, nsamples[l], coarsen_times=L - l, nthreads=nthreads, **fm)
         else:
-            lk, al = sample_fields(M, M, nsamples[l], seed=seed, level=l + key_offset, sigma2=sigma2,
-                                   corr_len=corr_len, alpha_lo=alpha_lo, alpha_span=alpha_span,
-                                   nthreads=nthreads)
+            lk, al = sample_fields(M, M, nsamples[l], nthreads=nthreads, **fm)
         pf = make_problem(nsteps=steps0 << l, dt=t_final / (steps0 << l), **phys)
         _, qf, sf, _ = solve_batch(pf, lk, al, scale(l), want_p=False, nthreads=nthreads)
         if l > 0:

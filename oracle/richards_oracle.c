@@ -137,12 +137,53 @@ int orc_fft2(double* re, double* im, int32_t nx, int32_t nz, int32_t inverse)
 }
 
 /* ------------------------------------------------------------------------- */
-/* FFT-MA (Appendix A).  The covariance c(r) = sigma2 exp(-r / corr_len) is   */
-/* sampled on a px x pz torus with periodic distances; its DFT is the         */
-/* spectrum Lambda of the circulant covariance; F(s) = sqrt(Lambda)           */
-/* (Eq. product1) and z = F^-1(F(s) . F(y)) (Eq. product2 and the one after). */
+/* Modified Bessel function of the second kind, x > 0, nu >= 0, from its       */
+/* integral representation K_nu(x) = int_0^inf exp(-x cosh t) cosh(nu t) dt    */
+/* (DLMF 10.32.9) by the trapezoidal rule: the integrand is analytic and even  */
+/* with doubly exponential decay, so the rule converges geometrically          */
+/* (Trefethen and Weideman, SIAM Review 56, 2014).  Near t = 0 it behaves like */
+/* exp(-x t^2 / 2), so the step is min(1/16, 1/(2 sqrt x)), which keeps the     */
+/* aliasing error of that Gaussian below exp(-8 pi^2).  The sum stops once a   */
+/* term is below 1e-18 of the sum and past the integrand's maximum.            */
 /* ------------------------------------------------------------------------- */
-int orc_fftma_spectrum(int32_t px, int32_t pz, double h, double sigma2, double corr_len,
+double orc_bessel_k(double nu, double x)
+{
+    const double tau = x > 64.0 ? 0.5 / sqrt(x) : 1.0 / 16.0;
+    double sum = 0.5 * exp(-x);
+    for (int k = 1; k < 4096; ++k) {
+        double t = k * tau;
+        double term = exp(-x * cosh(t)) * cosh(nu * t);
+        sum += term;
+        if (term <= 1e-18 * sum && x * sinh(t) > nu) break;
+    }
+    return tau * sum;
+}
+
+/* Covariance of the Gaussian fields at offset (dx, dz).  nu > 0: the          */
+/* anisotropic Matern function of Eq. nonIsotropic,                            */
+/*   sigma2 2^(1-nu)/Gamma(nu) (2 sqrt(nu) r)^nu K_nu(2 sqrt(nu) r),           */
+/*   r = sqrt((dx/lx)^2 + (dz/lz)^2)  (value sigma2 at r = 0);                 */
+/* nu = 0: the exponential sigma2 exp(-r) (with lz = lx: exp(-|d|/lx)).        */
+/* Supported: 0 < nu <= 16 (Gamma(nu) and x^nu stay finite).                   */
+/* lz <= 0 means lz = lx (isotropic).                                          */
+/* ------------------------------------------------------------------------- */
+double orc_covariance(const orc_cov* cv, double dx, double dz)
+{
+    double lx = cv->corr_len, lz = cv->corr_len_z > 0.0 ? cv->corr_len_z : cv->corr_len;
+    double r = (lz == lx) ? sqrt(dx * dx + dz * dz) / lx : sqrt((dx / lx) * (dx / lx) + (dz / lz) * (dz / lz));
+    if (!(cv->nu > 0.0)) return cv->sigma2 * exp(-r);
+    if (r == 0.0) return cv->sigma2;
+    double x = 2.0 * sqrt(cv->nu) * r;
+    return cv->sigma2 * pow(2.0, 1.0 - cv->nu) / tgamma(cv->nu) * pow(x, cv->nu) * orc_bessel_k(cv->nu, x);
+}
+
+/* ------------------------------------------------------------------------- */
+/* FFT-MA (Appendix A).  The covariance is sampled on a px x pz torus with    */
+/* periodic distances; its DFT is the spectrum Lambda of the circulant        */
+/* covariance; F(s) = sqrt(Lambda) (Eq. product1) and z = F^-1(F(s) . F(y))   */
+/* (Eq. product2 and the one after).                                          */
+/* ------------------------------------------------------------------------- */
+int orc_fftma_spectrum(int32_t px, int32_t pz, double h, const orc_cov* cv,
                        double* sqrt_lambda, double* min_ratio)
 {
     size_t n = (size_t)px * pz;
@@ -152,8 +193,7 @@ int orc_fftma_spectrum(int32_t px, int32_t pz, double h, double sigma2, double c
         for (int a = 0; a < px; ++a) {
             int ia = a < px - a ? a : px - a;
             int ib = b < pz - b ? b : pz - b;
-            double dx = ia * h, dz = ib * h;
-            re[(size_t)b * px + a] = sigma2 * exp(-sqrt(dx * dx + dz * dz) / corr_len);
+            re[(size_t)b * px + a] = orc_covariance(cv, ia * h, ib * h);
         }
     int rc = orc_fft2(re, im, px, pz, 0);
     if (rc) { free(re); free(im); return rc; }
@@ -169,14 +209,13 @@ static int next_pow2(int n) { int p = 1; while (p < n) p <<= 1; return p; }
 
 /* Smallest torus (powers of two, at least twice the grid per side, grown by  */
 /* doubling) whose spectrum has no eigenvalue below -1e-12 * max.             */
-int orc_torus_size(int32_t nx, int32_t nz, double h, double sigma2, double corr_len,
-                   int32_t* px, int32_t* pz)
+int orc_torus_size(int32_t nx, int32_t nz, double h, const orc_cov* cv, int32_t* px, int32_t* pz)
 {
     int a = next_pow2(2 * nx), b = next_pow2(2 * nz);
     for (int tries = 0; tries < 4; ++tries) {
         double* s = (double*)malloc(sizeof(double) * (size_t)a * b);
         double ratio = 0.0;
-        orc_fftma_spectrum(a, b, h, sigma2, corr_len, s, &ratio);
+        orc_fftma_spectrum(a, b, h, cv, s, &ratio);
         free(s);
         if (ratio >= -1e-12) { *px = a; *pz = b; return 0; }
         a *= 2; b *= 2;
@@ -186,7 +225,7 @@ int orc_torus_size(int32_t nx, int32_t nz, double h, double sigma2, double corr_
 }
 
 typedef struct {
-    uint64_t seed; double sigma2, corr_len, alpha_lo, alpha_span;
+    uint64_t seed; double sigma2, alpha_lo, alpha_span;
     int32_t nx, nz, px, pz; uint32_t level; int64_t first; int32_t ns, coarsen;
     const double* sq; double* lnKs; double* alpha; int32_t nthreads, tid;
 } orc_field_job;
@@ -241,7 +280,7 @@ static void* field_worker(void* arg)
     return NULL;
 }
 
-int orc_sample_fields(uint64_t seed, double sigma2, double corr_len, double alpha_lo,
+int orc_sample_fields(uint64_t seed, const orc_cov* cv, double alpha_lo,
                       double alpha_span, int32_t nx, int32_t nz, uint32_t level,
                       int64_t first_sample, int32_t nsamples, int32_t coarsen_times,
                       double* lnKs, double* alpha, int32_t nthreads)
@@ -250,15 +289,15 @@ int orc_sample_fields(uint64_t seed, double sigma2, double corr_len, double alph
     if ((nx % (1 << coarsen_times)) || (nz % (1 << coarsen_times))) return -1;
     double h = 1.0 / nz;
     int32_t px, pz;
-    orc_torus_size(nx, nz, h, sigma2, corr_len, &px, &pz);
+    orc_torus_size(nx, nz, h, cv, &px, &pz);
     double* sq = (double*)malloc(sizeof(double) * (size_t)px * pz);
     double ratio;
-    orc_fftma_spectrum(px, pz, h, sigma2, corr_len, sq, &ratio);
+    orc_fftma_spectrum(px, pz, h, cv, sq, &ratio);
     if (nthreads < 1) nthreads = 1;
     orc_field_job* jobs = (orc_field_job*)malloc(sizeof(orc_field_job) * nthreads);
     pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * nthreads);
     for (int t = 0; t < nthreads; ++t) {
-        orc_field_job J = { seed, sigma2, corr_len, alpha_lo, alpha_span, nx, nz, px, pz, level,
+        orc_field_job J = { seed, cv->sigma2, alpha_lo, alpha_span, nx, nz, px, pz, level,
                             first_sample, nsamples, coarsen_times, sq, lnKs, alpha, nthreads, t };
         jobs[t] = J;
         pthread_create(&th[t], NULL, field_worker, &jobs[t]);
@@ -274,7 +313,7 @@ int orc_sample_fields(uint64_t seed, double sigma2, double corr_len, double alph
 /* y_c(I,J) = (1/2) * (sum of the 2x2 block of y) on the half-size torus gives  */
 /* the coarse field through the coarse grid's own spectrum (spacing 2h).       */
 /* ------------------------------------------------------------------------- */
-int orc_sample_fields_pair(uint64_t seed, double sigma2, double corr_len, double alpha_lo,
+int orc_sample_fields_pair(uint64_t seed, const orc_cov* cv, double alpha_lo,
                            double alpha_span, int32_t nx, int32_t nz, uint32_t level,
                            int64_t first_sample, int32_t nsamples, double* lnKs_f, double* alpha_f,
                            double* lnKs_c, double* alpha_c)
@@ -282,18 +321,18 @@ int orc_sample_fields_pair(uint64_t seed, double sigma2, double corr_len, double
     if (nx < 2 || nz < 2 || nx % 2 || nz % 2 || nsamples < 0) return -1;
     double h = 1.0 / nz;
     int32_t px, pz;
-    orc_torus_size(nx, nz, h, sigma2, corr_len, &px, &pz);
+    orc_torus_size(nx, nz, h, cv, &px, &pz);
     int pxc = px / 2, pzc = pz / 2, ncx = nx / 2, ncz = nz / 2;
     size_t nf = (size_t)px * pz, nc = (size_t)pxc * pzc;
     double* sqf = (double*)malloc(sizeof(double) * nf);
     double* sqc = (double*)malloc(sizeof(double) * nc);
     double ratio;
-    orc_fftma_spectrum(px, pz, h, sigma2, corr_len, sqf, &ratio);
-    orc_fftma_spectrum(pxc, pzc, 2.0 * h, sigma2, corr_len, sqc, &ratio);
+    orc_fftma_spectrum(px, pz, h, cv, sqf, &ratio);
+    orc_fftma_spectrum(pxc, pzc, 2.0 * h, cv, sqc, &ratio);
     double* y = (double*)malloc(sizeof(double) * nf);
     double* re = (double*)malloc(sizeof(double) * nf);
     double* im = (double*)malloc(sizeof(double) * nf);
-    double sig = sqrt(sigma2);
+    double sig = sqrt(cv->sigma2);
     for (int k = 0; k < nsamples; ++k) {
         uint64_t sample = (uint64_t)(first_sample + k);
         for (uint32_t fld = 0; fld < 2; ++fld) {

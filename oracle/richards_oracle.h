@@ -44,21 +44,27 @@ typedef struct {
     int32_t max_mg;        /* largest V-cycle count in one Picard iteration */
 } orc_stats;
 
+/* covariance of the Gaussian fields: nu = 0 exponential sigma2 exp(-r/corr_len);
+ * nu > 0 Matern (Eq. nonIsotropic) with correlation lengths corr_len (x) and
+ * corr_len_z (z; <= 0: same as x) */
+typedef struct { double sigma2, corr_len, corr_len_z, nu; } orc_cov;
+
 enum { ORC_OK = 0, ORC_PICARD_MAXIT = 1, ORC_MG_MAXIT = 2, ORC_NONFINITE = 3 };
 
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 void orc_white_noise(uint64_t seed, uint32_t level, uint64_t sample, uint32_t field,
                      int64_t npts, double* y);
 int  orc_fft2(double* re, double* im, int32_t nx, int32_t nz, int32_t inverse);
-int  orc_fftma_spectrum(int32_t px, int32_t pz, double h, double sigma2, double corr_len,
+double orc_bessel_k(double nu, double x);
+double orc_covariance(const orc_cov* cv, double dx, double dz);
+int  orc_fftma_spectrum(int32_t px, int32_t pz, double h, const orc_cov* cv,
                         double* sqrt_lambda, double* min_ratio);
-int  orc_torus_size(int32_t nx, int32_t nz, double h, double sigma2, double corr_len,
-                    int32_t* px, int32_t* pz);
-int  orc_sample_fields(uint64_t seed, double sigma2, double corr_len, double alpha_lo,
+int  orc_torus_size(int32_t nx, int32_t nz, double h, const orc_cov* cv, int32_t* px, int32_t* pz);
+int  orc_sample_fields(uint64_t seed, const orc_cov* cv, double alpha_lo,
                        double alpha_span, int32_t nx, int32_t nz, uint32_t level,
                        int64_t first_sample, int32_t nsamples, int32_t coarsen_times,
                        double* lnKs, double* alpha, int32_t nthreads);
-int  orc_sample_fields_pair(uint64_t seed, double sigma2, double corr_len, double alpha_lo,
+int  orc_sample_fields_pair(uint64_t seed, const orc_cov* cv, double alpha_lo,
                             double alpha_span, int32_t nx, int32_t nz, uint32_t level,
                             int64_t first_sample, int32_t nsamples, double* lnKs_f, double* alpha_f,
                             double* lnKs_c, double* alpha_c);

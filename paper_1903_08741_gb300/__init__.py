@@ -38,7 +38,8 @@ class _Problem(C.Structure):
 
 class _Field(C.Structure):
     _fields_ = [("sigma2", C.c_double), ("corr_len", C.c_double), ("alpha_lo", C.c_double),
-                ("alpha_span", C.c_double), ("seed", C.c_uint64)]
+                ("alpha_span", C.c_double), ("seed", C.c_uint64), ("nu", C.c_double),
+                ("corr_len_z", C.c_double)]
 
 
 class _Stats(C.Structure):
@@ -73,15 +74,31 @@ class Problem:
 
 @dataclass
 class FieldModel:
-    """ln Ks ~ GRF(0, sigma2 exp(-r/corr_len)); alpha = alpha_lo + alpha_span Phi(g)."""
+    """ln Ks ~ GRF(0, C); alpha = alpha_lo + alpha_span Phi(g).  C is the
+    exponential sigma2 exp(-r/corr_len) for nu = 0, else the anisotropic Matern
+    function (Eq. nonIsotropic) with lengths corr_len (x), corr_len_z (z; 0 =
+    corr_len).  FieldModel.phi1() / phi2() give the paper's two parameter sets."""
     sigma2: float = 1.0
     corr_len: float = 0.3
     alpha_lo: float = 0.5
     alpha_span: float = 1.5
     seed: int = 0
+    nu: float = 0.0
+    corr_len_z: float = 0.0
+
+    @classmethod
+    def phi1(cls, **kw):
+        """Isotropic Matern, (nu, lx, lz, sigma2) = (1, 0.2, 0.2, 1)."""
+        return cls(**{**dict(sigma2=1.0, corr_len=0.2, corr_len_z=0.2, nu=1.0), **kw})
+
+    @classmethod
+    def phi2(cls, **kw):
+        """Anisotropic Matern, (nu, lx, lz, sigma2) = (0.5, 0.1, 0.01, 1)."""
+        return cls(**{**dict(sigma2=1.0, corr_len=0.1, corr_len_z=0.01, nu=0.5), **kw})
 
     def _c(self):
-        return _Field(self.sigma2, self.corr_len, self.alpha_lo, self.alpha_span, self.seed)
+        return _Field(self.sigma2, self.corr_len, self.alpha_lo, self.alpha_span, self.seed, self.nu,
+                      self.corr_len_z)
 
 
 MLMC_MAX_LEVELS = 8

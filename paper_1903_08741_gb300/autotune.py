@@ -34,7 +34,8 @@ def _bucket(n):
 
 def _key(problem, nsamples, device_name):
     prec = "mixed" if problem.precision else "fp64"
-    return f"{device_name}|{problem.nx}x{problem.nz}|{prec}|S{_bucket(nsamples)}"
+    cyc = "" if problem.cycle <= 1 else f"|W{problem.cycle}"    # V-cycle keys stay as they were
+    return f"{device_name}|{problem.nx}x{problem.nz}|{prec}|S{_bucket(nsamples)}{cyc}"
 
 
 def _load(path):

@@ -128,14 +128,46 @@ __global__ void k_filter(int S, int npts, const double* __restrict__ sq, cplx* d
     d[g].re *= w; d[g].im *= w;
 }
 
-// covariance on the torus: c(a, b) = sigma2 exp(-r / corr_len), periodic distances
-__global__ void k_cov(int px, int pz, double h, double sigma2, double corr_len, cplx* c) {
+// covariance model of one spectrum: nu = 0 exponential sigma2 exp(-r);
+// nu > 0 the Matern function of Eq. nonIsotropic, norm = sigma2 2^(1-nu)/Gamma(nu)
+struct CovModel {
+    double sigma2, lx, lz, nu, norm;
+};
+
+// K_nu(x) for x > 0 from K_nu(x) = int_0^inf exp(-x cosh t) cosh(nu t) dt
+// (DLMF 10.32.9): trapezoidal sum, geometrically convergent for this
+// analytic, doubly exponentially decaying integrand; the step resolves the
+// exp(-x t^2/2) peak at large x (min(1/16, 1/(2 sqrt x))), the sum ends past
+// the integrand's maximum once a term adds less than 1e-18 (at most 4095 terms)
+__device__ double bessel_k(double nu, double x) {
+    const double dt = x > 64.0 ? 0.5 / sqrt(x) : 0.0625;
+    double acc = 0.5 * exp(-x);
+    for (int k = 1; k < 4096; ++k) {
+        const double t = k * dt;
+        const double f = exp(-x * cosh(t)) * cosh(nu * t);
+        acc += f;
+        if (f <= 1e-18 * acc && x * sinh(t) > nu) break;
+    }
+    return dt * acc;
+}
+
+// covariance on the torus at the periodic offset of point (a, b)
+__global__ void k_cov(int px, int pz, double h, CovModel cm, cplx* c) {
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= px * pz) return;
     int b = g / px, a = g - b * px;
     int ia = min(a, px - a), ib = min(b, pz - b);
     double dx = ia * h, dz = ib * h;
-    c[g] = cplx{sigma2 * exp(-sqrt(dx * dx + dz * dz) / corr_len), 0.0};
+    const double r = cm.lz == cm.lx ? sqrt(dx * dx + dz * dz) / cm.lx
+                                    : sqrt((dx / cm.lx) * (dx / cm.lx) + (dz / cm.lz) * (dz / cm.lz));
+    double v;
+    if (cm.nu == 0.0) v = cm.sigma2 * exp(-r);
+    else if (r == 0.0) v = cm.sigma2;
+    else {
+        const double x = 2.0 * sqrt(cm.nu) * r;
+        v = cm.norm * pow(x, cm.nu) * bessel_k(cm.nu, x);
+    }
+    c[g] = cplx{v, 0.0};
 }
 
 __global__ void k_sqrt_spec(int npts, const cplx* __restrict__ lam, double* sq) {
@@ -216,25 +248,36 @@ int fft2(cplx* d, int S, int px, int pz, const cplx* twx, const cplx* twz, int i
 }  // namespace
 
 // ---------------------------------------------------------------- host side
+// a field model outside the supported range: sigma2, corr_len > 0,
+// corr_len_z >= 0 (0: isotropic), 0 <= nu <= 16
+bool bad_field(const rich_field_t* fd) {
+    return !(fd->sigma2 > 0) || !(fd->corr_len > 0) || !(fd->corr_len_z >= 0) || !(fd->nu >= 0) ||
+           !(fd->nu <= 16);
+}
+
 // sqrt(F c) on a px x pz torus of spacing h, cached in the context
-static int spectrum_on(rich_ctx* ctx, int px, int pz, double h, double sigma2, double corr_len,
+static int spectrum_on(rich_ctx* ctx, int px, int pz, double h, const rich_field_t* fd,
                        cudaStream_t st, const rich_spectrum** out, double* min_ratio) {
+    const double sigma2 = fd->sigma2, corr_len = fd->corr_len, nu = fd->nu;
+    const double lz = fd->corr_len_z > 0 ? fd->corr_len_z : fd->corr_len;
     for (const rich_spectrum& e : ctx->spectra)
-        if (e.px == px && e.pz == pz && e.h == h && e.sigma2 == sigma2 && e.corr_len == corr_len) {
+        if (e.px == px && e.pz == pz && e.h == h && e.sigma2 == sigma2 && e.corr_len == corr_len &&
+            e.corr_len_z == lz && e.nu == nu) {
             *out = &e;
             if (min_ratio) *min_ratio = e.min_ratio;
             return 0;
         }
     const int npts = px * pz;
     rich_spectrum e{};
-    e.px = px; e.pz = pz; e.h = h; e.sigma2 = sigma2; e.corr_len = corr_len;
+    e.px = px; e.pz = pz; e.h = h; e.sigma2 = sigma2; e.corr_len = corr_len; e.corr_len_z = lz; e.nu = nu;
+    const CovModel cm{sigma2, corr_len, lz, nu, nu > 0 ? sigma2 * pow(2.0, 1.0 - nu) / tgamma(nu) : 0.0};
     cplx* c = nullptr;
     RICH_CUDA(cudaMalloc(&c, sizeof(cplx) * npts));
     RICH_CUDA(cudaMalloc(&e.tw, sizeof(cplx) * (px / 2 + pz / 2 + 2)));
     cplx* tw = (cplx*)e.tw;
     rich_count_launch(); k_twiddles<<<nb(px / 2), 256, 0, st>>>(px, tw);
     rich_count_launch(); k_twiddles<<<nb(pz / 2), 256, 0, st>>>(pz, tw + px / 2 + 1);
-    rich_count_launch(); k_cov<<<nb(npts), 256, 0, st>>>(px, pz, h, sigma2, corr_len, c);
+    rich_count_launch(); k_cov<<<nb(npts), 256, 0, st>>>(px, pz, h, cm, c);
     if (int r = fft2(c, 1, px, pz, tw, tw + px / 2 + 1, 0, st)) { cudaFree(c); return r; }
     std::vector<cplx> hl(npts);
     RICH_CUDA(cudaMemcpyAsync(hl.data(), c, sizeof(cplx) * npts, cudaMemcpyDeviceToHost, st));
@@ -258,7 +301,7 @@ static int spectrum_on(rich_ctx* ctx, int px, int pz, double h, double sigma2, d
 
 // smallest power-of-two torus of at least twice the grid per side whose
 // circulant spectrum has no eigenvalue below -1e-12 max (doubled up to 3 times)
-static int choose_torus(rich_ctx* ctx, int nx, int nz, double sigma2, double corr_len, cudaStream_t st,
+static int choose_torus(rich_ctx* ctx, int nx, int nz, const rich_field_t* fd, cudaStream_t st,
                         int* px, int* pz) {
     const double h = 1.0 / nz;
     int a = 1, b = 1;
@@ -267,7 +310,7 @@ static int choose_torus(rich_ctx* ctx, int nx, int nz, double sigma2, double cor
     for (int tries = 0; tries < 4; ++tries) {
         const rich_spectrum* e = nullptr;
         double ratio = 0;
-        if (int r = spectrum_on(ctx, a, b, h, sigma2, corr_len, st, &e, &ratio)) return r;
+        if (int r = spectrum_on(ctx, a, b, h, fd, st, &e, &ratio)) return r;
         if (ratio >= -1e-12 || tries == 3) { *px = a; *pz = b; return 0; }
         a *= 2; b *= 2;
     }
@@ -302,13 +345,13 @@ int rich_fields_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int nz, ui
                        int64_t first, int S, int coarsen, double* lnKs, double* alpha,
                        cudaStream_t st, const int64_t* first_dev) {
     if (!pow2(nx) || !pow2(nz) || coarsen < 0 || (nx >> coarsen) < 1 || (nz >> coarsen) < 1 ||
-        fd->sigma2 <= 0 || fd->corr_len <= 0)
+        bad_field(fd))
         return RICH_ERR_INVALID;
     if (S == 0) return 0;
     int px = 0, pz = 0;
-    if (int e = choose_torus(ctx, nx, nz, fd->sigma2, fd->corr_len, st, &px, &pz)) return e;
+    if (int e = choose_torus(ctx, nx, nz, fd, st, &px, &pz)) return e;
     const rich_spectrum* sp = nullptr;
-    if (int e = spectrum_on(ctx, px, pz, 1.0 / nz, fd->sigma2, fd->corr_len, st, &sp, nullptr)) return e;
+    if (int e = spectrum_on(ctx, px, pz, 1.0 / nz, fd, st, &sp, nullptr)) return e;
     const int npts = px * pz;
     const size_t per = (size_t)npts * sizeof(cplx) + 32 * (size_t)nx * nz;
     const int chunk = (int)std::max<size_t>(1, CHUNK_BYTES / per);
@@ -371,17 +414,17 @@ __global__ void k_noise_upscale(int S, int pxc, int pzc, const cplx* __restrict_
 int rich_fields_pair_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int nz, uint32_t level,
                             int64_t first, int S, double* lk_f, double* al_f, double* lk_c,
                             double* al_c, cudaStream_t st) {
-    if (!pow2(nx) || !pow2(nz) || nx < 2 || nz < 2 || fd->sigma2 <= 0 || fd->corr_len <= 0)
+    if (!pow2(nx) || !pow2(nz) || nx < 2 || nz < 2 || bad_field(fd))
         return RICH_ERR_INVALID;
     if (S == 0) return 0;
     int px = 0, pz = 0;
-    if (int e = choose_torus(ctx, nx, nz, fd->sigma2, fd->corr_len, st, &px, &pz)) return e;
+    if (int e = choose_torus(ctx, nx, nz, fd, st, &px, &pz)) return e;
     const rich_spectrum *spf = nullptr, *spc = nullptr;
-    if (int e = spectrum_on(ctx, px, pz, 1.0 / nz, fd->sigma2, fd->corr_len, st, &spf, nullptr)) return e;
-    if (int e = spectrum_on(ctx, px / 2, pz / 2, 2.0 / nz, fd->sigma2, fd->corr_len, st, &spc, nullptr)) return e;
+    if (int e = spectrum_on(ctx, px, pz, 1.0 / nz, fd, st, &spf, nullptr)) return e;
+    if (int e = spectrum_on(ctx, px / 2, pz / 2, 2.0 / nz, fd, st, &spc, nullptr)) return e;
     // spectrum_on may reallocate the cache vector: look both up again
-    spectrum_on(ctx, px, pz, 1.0 / nz, fd->sigma2, fd->corr_len, st, &spf, nullptr);
-    spectrum_on(ctx, px / 2, pz / 2, 2.0 / nz, fd->sigma2, fd->corr_len, st, &spc, nullptr);
+    spectrum_on(ctx, px, pz, 1.0 / nz, fd, st, &spf, nullptr);
+    spectrum_on(ctx, px / 2, pz / 2, 2.0 / nz, fd, st, &spc, nullptr);
     const int npf = px * pz, npc = npf / 4;
     const size_t per = (size_t)(npf + npc) * sizeof(cplx);
     const int cap = (int)std::min<size_t>((size_t)S, std::max<size_t>(1, CHUNK_BYTES / per));

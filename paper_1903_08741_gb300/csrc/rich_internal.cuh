@@ -28,7 +28,7 @@ struct rich_samplebuf {
 // sqrt of the circulant covariance spectrum on one torus (+ FFT twiddles)
 struct rich_spectrum {
     int px = 0, pz = 0;
-    double h = 0, sigma2 = 0, corr_len = 0, min_ratio = 0;
+    double h = 0, sigma2 = 0, corr_len = 0, corr_len_z = 0, nu = 0, min_ratio = 0;
     double* sq = nullptr;                       // [pz][px]
     void* tw = nullptr;                         // twiddles of both line lengths
 };
@@ -83,6 +83,7 @@ int rich_adjoint_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const dou
 int rich_check_problem(const rich_problem_t* pb);
 
 // ---- fields (fields.cu)
+bool bad_field(const rich_field_t* fd);
 int rich_fields_pair_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int nz, uint32_t level,
                             int64_t first, int S, double* lk_f, double* al_f, double* lk_c,
                             double* al_c, cudaStream_t st);

@@ -52,11 +52,16 @@ def test_status_strings_without_gpu(libpath):
 def test_struct_layouts_match_c(tmp_path):
     src = tmp_path / "sz.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "richards.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(rich_problem_t),'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(rich_problem_t),'
                    ' sizeof(rich_field_t), sizeof(rich_stats_t), offsetof(rich_problem_t, precision),'
-                   ' offsetof(rich_stats_t, seconds)); return 0;}\n')
+                   ' offsetof(rich_stats_t, seconds), offsetof(rich_problem_t, cycle),'
+                   ' offsetof(rich_field_t, nu), offsetof(rich_field_t, corr_len_z),'
+                   ' sizeof(rich_mlmc_cfg_t), offsetof(rich_mlmc_cfg_t, tune_inner),'
+                   ' sizeof(rich_mlmc_result_t)); return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     vals = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     assert vals == [C.sizeof(R._Problem), C.sizeof(R._Field), C.sizeof(R._Stats),
-                    R._Problem.precision.offset, R._Stats.seconds.offset]
+                    R._Problem.precision.offset, R._Stats.seconds.offset, R._Problem.cycle.offset,
+                    R._Field.nu.offset, R._Field.corr_len_z.offset, C.sizeof(R._MlmcCfg),
+                    R._MlmcCfg.tune_inner.offset, C.sizeof(R._MlmcResult)]

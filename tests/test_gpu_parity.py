@@ -107,6 +107,33 @@ def test_fields_pair_match_oracle(R, n):
         assert np.abs(a.cpu().numpy() - b).max() < 1e-12
 
 
+MATERN = {"phi1": dict(nu=1.0, corr_len=0.2, corr_len_z=0.2), "phi2": dict(nu=0.5, corr_len=0.1, corr_len_z=0.01),
+          "nu2.5": dict(nu=2.5, corr_len=0.15, corr_len_z=0.3)}
+
+
+@pytest.mark.parametrize("name", sorted(MATERN))
+@pytest.mark.parametrize("n", [32, 64])
+def test_matern_fields_match_oracle(R, name, n):
+    """Matern fields (Eq. nonIsotropic; the paper's Phi_1, Phi_2 and a smooth
+    anisotropic case): GPU spectrum + FFT-MA against the oracle, to 1e-12."""
+    kw = MATERN[name]
+    lk_o, al_o = O.sample_fields(n, n, 5, seed=13, level=1, first_sample=2, **kw)
+    lk, al = R.sample_fields(n, n, 5, R.FieldModel(seed=13, **kw), level=1, first_sample=2)
+    assert np.abs(lk.cpu().numpy() - lk_o).max() < 1e-12
+    assert np.abs(al.cpu().numpy() - al_o).max() < 1e-12
+    o = O.sample_fields_pair(n, n, 3, seed=13, level=2, **kw)
+    g = R.sample_fields_pair(n, n, 3, R.FieldModel(seed=13, **kw), level=2)
+    for a, b in zip(g, o):
+        assert np.abs(a.cpu().numpy() - b).max() < 1e-12
+
+
+def test_matern_presets_and_invalid(R):
+    assert R.FieldModel.phi1().nu == 1.0 and R.FieldModel.phi2().corr_len_z == 0.01
+    for bad in (dict(nu=-1.0), dict(nu=17.0), dict(corr_len_z=-0.1)):
+        with pytest.raises(R.RichError):
+            R.sample_fields(16, 16, 1, R.FieldModel(**bad))
+
+
 def test_fields_large_batch_chunks(R):
     """A batch larger than one FFT work chunk (128^2 grid, 256^2 torus)."""
     S = 40

@@ -101,6 +101,78 @@ def test_fields_empirical_covariance_and_marginals():
     assert stats.kstest(u, "uniform").pvalue > 1e-3
 
 
+# ------------------------------------------------- Matern covariance (Eq. nonIsotropic)
+def test_bessel_k_matches_library():
+    """The oracle's K_nu (trapezoidal rule on its integral representation)
+    against scipy's modified Bessel function of the second kind."""
+    from scipy import special
+    for nu in (0.5, 1.0, 1.5, 2.5, 0.3, 3.7):
+        for x in np.geomspace(1e-4, 100.0, 300):
+            assert abs(O.bessel_k(nu, x) / special.kv(nu, x) - 1.0) < 1e-13, (nu, x)
+
+
+def test_matern_special_cases():
+    """Eq. nonIsotropic at half-integer nu has closed forms in x = 2 sqrt(nu) r:
+    nu = 1/2 the exponential exp(-x) (= exp(-sqrt 2 r)), nu = 3/2 (1 + x) exp(-x),
+    nu = 5/2 (1 + x + x^2/3) exp(-x); nu = 1 is sigma2 x K_1(x); large nu tends
+    to the squared exponential exp(-r^2) (nu <= 16 is supported).  Anisotropy scales each axis by its
+    own length; r = 0 gives the variance; nu = 0 is the configured exp(-|d|/l)."""
+    from scipy import special
+    lx, lz, s2 = 0.1, 0.01, 1.7
+    rng = np.random.default_rng(1)
+    for dx, dz in rng.uniform(0, 0.2, size=(20, 2)) * np.array([1.0, 0.1]):
+        r = np.hypot(dx / lx, dz / lz)
+        forms = {0.5: lambda x: np.exp(-x), 1.5: lambda x: (1 + x) * np.exp(-x),
+                 2.5: lambda x: (1 + x + x * x / 3) * np.exp(-x), 1.0: lambda x: x * special.kv(1, x)}
+        for nu, f in forms.items():
+            x = 2 * np.sqrt(nu) * r
+            got = O.covariance(dx, dz, sigma2=s2, corr_len=lx, corr_len_z=lz, nu=nu)
+            assert abs(got - s2 * f(x)) < 1e-13 * s2, (nu, dx, dz)
+    # towards the squared exponential: the gap halves as nu doubles (O(1/nu))
+    gaps = [max(abs(O.covariance(r * lx, 0.0, corr_len=lx, nu=nu) - np.exp(-r * r)) for r in np.linspace(0, 3, 61))
+            for nu in (4.0, 8.0, 16.0)]
+    assert gaps[2] < 0.016 and 0.4 < gaps[1] / gaps[0] < 0.6 and 0.4 < gaps[2] / gaps[1] < 0.6, gaps
+    assert O.covariance(0.0, 0.0, sigma2=s2, corr_len=lx, corr_len_z=lz, nu=1.0) == s2
+    assert O.covariance(0.05, 0.0, corr_len=0.2, nu=1.0) == O.covariance(0.0, 0.05, corr_len=0.2, nu=1.0)
+    assert abs(O.covariance(0.3, 0.4, corr_len=0.3) - np.exp(-0.5 / 0.3)) < 1e-15
+
+
+@pytest.mark.parametrize("px,pz,h,lx,lz,nu", [(32, 32, 1 / 16, 0.2, 0.2, 1.0), (32, 64, 1 / 32, 0.1, 0.01, 0.5)])
+def test_fftma_exact_covariance_matern(px, pz, h, lx, lz, nu):
+    """Phi_1 = (1, 0.2, 0.2, 1) and Phi_2 = (0.5, 0.1, 0.01, 1) of the paper's
+    Matern table: the circular autocorrelation of s = F^-1 sqrt(F c) equals the
+    torus covariance, by brute force over all lags (Appendix A)."""
+    from scipy import special
+    sq, ratio = O.fftma_sqrt_spectrum(px, pz, h, 1.0, lx, corr_len_z=lz, nu=nu)
+    assert ratio >= -1e-12
+    s = np.real(np.fft.ifft2(sq))
+    F = np.fft.fft2(s)
+    acorr = np.real(np.fft.ifft2(F * np.conj(F)))       # all lags at once
+    for b in range(pz):
+        for a in range(px):
+            dx, dz = min(a, px - a) * h, min(b, pz - b) * h
+            r = np.hypot(dx / lx, dz / lz)
+            x = 2 * np.sqrt(nu) * r
+            c = 1.0 if r == 0 else 2 ** (1 - nu) / special.gamma(nu) * x ** nu * special.kv(nu, x)
+            assert abs(acorr[b, a] - c) < 1e-12, (a, b)
+
+
+def test_fields_anisotropic_empirical_covariance():
+    """4096 Phi_2 fields on 32x32 (h = 1/32, lz = 0.01 < h): the lag-1
+    correlation along x is exp(-sqrt2 h/0.1) and along z exp(-sqrt2 h/0.01),
+    within 5 standard errors."""
+    n, S = 32, 4096
+    lnks, _ = O.sample_fields(n, n, S, seed=4, corr_len=0.1, corr_len_z=0.01, nu=0.5)
+    h = 1.0 / n
+    for axis, lam in ((2, 0.1), (1, 0.01)):
+        for lag in (0, 1, 2):
+            a = np.take(lnks, np.arange(0, n - lag), axis=axis)
+            b = np.take(lnks, np.arange(lag, n), axis=axis)
+            per = (a * b).mean(axis=(1, 2))
+            se = per.std(ddof=1) / np.sqrt(S)
+            assert abs(per.mean() - np.exp(-np.sqrt(2) * lag * h / lam)) < 5 * se + 1e-3, (axis, lag)
+
+
 def test_fields_coarsening_is_2x2_mean():
     """coarsen_times = 1 returns the 2x2 block means of the fine draw."""
     lk, al = O.sample_fields(16, 16, 3, seed=5)
