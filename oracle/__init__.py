@@ -42,7 +42,34 @@ class Problem(C.Structure):
                 ("theta_s", C.c_double), ("p_top", C.c_double), ("p_bottom", C.c_double),
                 ("p_init", C.c_double), ("picard_tol", C.c_double), ("picard_maxit", C.c_int32),
                 ("mg_tol", C.c_double), ("mg_maxit", C.c_int32), ("nu1", C.c_int32),
-                ("nu2", C.c_int32), ("gamma", C.c_int32)]
+                ("nu2", C.c_int32), ("gamma", C.c_int32), ("closure", C.c_int32),
+                ("init_decay", C.c_double)]
+
+
+GARDNER, VAN_GENUCHTEN = 0, 1
+
+
+class Soil(C.Structure):
+    """Per-cell soil parameters of a batch (see orc_soil)."""
+    _fields_ = [("lnKs", C.c_void_p), ("alpha", C.c_void_p), ("n", C.c_void_p),
+                ("theta_s", C.c_void_p), ("theta_r", C.c_void_p), ("alpha_scale", C.c_double),
+                ("alpha_shift", C.c_double), ("n_shift", C.c_double)]
+
+
+class SoilModel(C.Structure):
+    """Marginals of the five soil fields (see orc_soil_model)."""
+    _fields_ = [("lnks_mean", C.c_double), ("alpha_lo", C.c_double), ("alpha_span", C.c_double),
+                ("n_lo", C.c_double), ("n_span", C.c_double), ("theta_s_lo", C.c_double),
+                ("theta_s_span", C.c_double), ("theta_r_lo", C.c_double), ("theta_r_span", C.c_double)]
+
+
+def soil_model(alpha_bl, n_bl, ks_bl=0.2, theta_s_bl=0.5, theta_r_bl=0.05, d_alpha=0.2, d_n=0.05,
+               d_theta_s=0.05, d_theta_r=0.005):
+    """Table soilparams: ln Ks = ln Ks_bl + Z; every other parameter baseline +
+    U(-d, d) (lo = baseline - d, span = 2 d)."""
+    import math
+    return SoilModel(math.log(ks_bl), alpha_bl - d_alpha, 2 * d_alpha, n_bl - d_n, 2 * d_n,
+                     theta_s_bl - d_theta_s, 2 * d_theta_s, theta_r_bl - d_theta_r, 2 * d_theta_r)
 
 
 class Cov(C.Structure):
@@ -58,11 +85,23 @@ class Stats(C.Structure):
 
 def make_problem(nsteps=10, dt=0.01, theta_r=0.1, theta_s=0.5, p_top=-0.5, p_bottom=-5.0,
                  p_init=-5.0, picard_tol=1e-8, picard_maxit=50, mg_tol=1e-10, mg_maxit=100,
-                 nu1=2, nu2=2, gamma=1) -> Problem:
+                 nu1=2, nu2=2, gamma=1, closure=0, init_decay=0.0) -> Problem:
     """Physics and solver settings of the configured instance (Gardner closure);
     gamma = 1: V-cycles (configured), 2: W-cycles (the paper's choice, Sec. 4.2)."""
     return Problem(nsteps, dt, theta_r, theta_s, p_top, p_bottom, p_init, picard_tol,
-                   picard_maxit, mg_tol, mg_maxit, nu1, nu2, gamma)
+                   picard_maxit, mg_tol, mg_maxit, nu1, nu2, gamma, closure, init_decay)
+
+
+def infiltration_problem(nsteps=10, dt=0.01, picard_tol=1e-5, mg_tol=1e-5, gamma=2, **kw) -> Problem:
+    """The infiltration problem of Sec. 4.3 (Eq. travellingwave) with the van
+    Genuchten-Mualem closure: p(x,z,0) = -0.4 (1 - exp(-80 z)), p = -0.4 on the
+    top, 0.1 on the bottom, theta_s = 0.5, theta_r = 0.05 (per-cell fields
+    override them), W(2,2) cycles and tolerances 1e-5 as in the paper."""
+    d = dict(nsteps=nsteps, dt=dt, theta_r=0.05, theta_s=0.5, p_top=-0.4, p_bottom=0.1, p_init=-0.4,
+             picard_tol=picard_tol, picard_maxit=50, mg_tol=mg_tol, mg_maxit=100, nu1=2, nu2=2,
+             gamma=gamma, closure=VAN_GENUCHTEN, init_decay=80.0)
+    d.update(kw)
+    return make_problem(**d)
 
 
 _lib = None
@@ -93,6 +132,16 @@ def lib():
         L.orc_sample_fields_pair.argtypes = [C.c_uint64, C.POINTER(Cov), C.c_double, C.c_double,
                                              C.c_int32, C.c_int32, C.c_uint32, C.c_int64, C.c_int32,
                                              _dp, _dp, _dp, _dp]
+        L.orc_solve_batch_soil.argtypes = [C.POINTER(Problem), C.c_int32, C.c_int32, C.c_int32,
+                                           C.POINTER(Soil), C.c_void_p, _dp, _i32p, C.POINTER(Stats),
+                                           C.c_int32]
+        L.orc_solve_one_soil.argtypes = [C.POINTER(Problem), C.c_int32, C.c_int32, C.POINTER(Soil),
+                                         C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
+                                         C.POINTER(Stats)]
+        L.orc_closure.argtypes = [C.c_int32] + [C.c_double] * 6 + [C.POINTER(C.c_double)] * 3
+        L.orc_sample_soil.argtypes = [C.c_uint64, C.POINTER(Cov), C.POINTER(SoilModel), C.c_int32,
+                                      C.c_int32, C.c_uint32, C.c_int64, C.c_int32, C.c_int32,
+                                      _dp, _dp, _dp, _dp, _dp, C.c_int32]
         L.orc_solve_one.argtypes = [C.POINTER(Problem), C.c_int32, C.c_int32, _dp, _dp, C.c_double,
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
                                     C.POINTER(Stats)]
@@ -225,6 +274,66 @@ def solve_batch(pb, lnKs, alpha, alpha_scale=1.0, want_p=True, nthreads=None):
     if rc < 0:
         raise ValueError("invalid grid")
     return p, qoi, status, st
+
+
+def solve_batch_soil(pb, lnKs, alpha, n=None, theta_s=None, theta_r=None, alpha_scale=1.0,
+                     alpha_shift=0.0, n_shift=0.0, want_p=True, nthreads=None):
+    """Solve every sample with per-cell soil fields [S, nz, nx] (van
+    Genuchten-Mualem needs n; theta fields optional); returns (p, qoi, status, stats)."""
+    nthreads = nthreads or os.cpu_count() or 1
+    arrs = [None if a is None else _f64(a) for a in (lnKs, alpha, n, theta_s, theta_r)]
+    S, nz, nx = arrs[0].shape
+    so = Soil(*[_ptr(a) for a in arrs], alpha_scale, alpha_shift, n_shift)
+    p = np.empty((S, nz, nx), np.float64) if want_p else None
+    qoi = np.empty(S, np.float64)
+    status = np.zeros(S, np.int32)
+    st = Stats()
+    rc = lib().orc_solve_batch_soil(C.byref(pb), nx, nz, S, C.byref(so), _ptr(p), qoi, status,
+                                    C.byref(st), nthreads)
+    if rc < 0:
+        raise ValueError("invalid grid or soil arrays")
+    return p, qoi, status, st
+
+
+def solve_one_soil(pb, lnKs, alpha, n=None, theta_s=None, theta_r=None, src=None, p_init=None,
+                   alpha_scale=1.0, alpha_shift=0.0, n_shift=0.0):
+    """One sample with per-cell soil fields [nz, nx], an optional source and
+    initial head; returns (p, qoi, status, stats)."""
+    arrs = [None if a is None else _f64(a) for a in (lnKs, alpha, n, theta_s, theta_r)]
+    nz, nx = arrs[0].shape
+    so = Soil(*[_ptr(a) for a in arrs], alpha_scale, alpha_shift, n_shift)
+    src = None if src is None else _f64(src)
+    p_init = None if p_init is None else _f64(p_init)
+    p = np.empty((nz, nx))
+    q = C.c_double()
+    st = Stats()
+    rc = lib().orc_solve_one_soil(C.byref(pb), nx, nz, C.byref(so), _ptr(src), _ptr(p_init), _ptr(p),
+                                  C.byref(q), C.byref(st))
+    if rc < 0:
+        raise ValueError("invalid grid or soil arrays")
+    return p, q.value, rc, st
+
+
+def closure(kind, Ks, a, n, theta_r, theta_s, p):
+    """(K, theta, C) of one cell at head p (kind 0 Gardner, 1 van Genuchten-Mualem)."""
+    K, th, Cc = C.c_double(), C.c_double(), C.c_double()
+    if lib().orc_closure(kind, Ks, a, n, theta_r, theta_s, p, C.byref(K), C.byref(th), C.byref(Cc)):
+        raise ValueError("unknown closure")
+    return K.value, th.value, Cc.value
+
+
+def sample_soil(nx, nz, nsamples, model, seed=0, level=0, first_sample=0, coarsen_times=0, sigma2=1.0,
+                corr_len=0.3, corr_len_z=0.0, nu=0.0, nthreads=None):
+    """The five soil fields (ln Ks, alpha, n, theta_s, theta_r), each [S, nz>>c, nx>>c]."""
+    nthreads = nthreads or os.cpu_count() or 1
+    nxo, nzo = nx >> coarsen_times, nz >> coarsen_times
+    out = [np.empty((nsamples, nzo, nxo)) for _ in range(5)]
+    cv = Cov(sigma2, corr_len, corr_len_z, nu)
+    rc = lib().orc_sample_soil(seed, C.byref(cv), C.byref(model), nx, nz, level, first_sample, nsamples,
+                               coarsen_times, *[o.reshape(-1) for o in out], nthreads)
+    if rc:
+        raise ValueError("invalid field arguments")
+    return tuple(out)
 
 
 def picard_system(pb, lnKs, alpha, p, p_old, alpha_scale=1.0):

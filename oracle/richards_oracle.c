@@ -224,10 +224,16 @@ int orc_torus_size(int32_t nx, int32_t nz, double h, const orc_cov* cv, int32_t*
     return 1;
 }
 
+/* Fields of one draw: field 0 is Gaussian (out = shift0 + z), fields f >= 1
+ * are lo[f] + span[f] * Phi(z / sigma) with Phi(x) = erfc(-x / sqrt 2) / 2
+ * (the relation Y = F_Y^-1(F_Z(Z)) of Sec. 3.1 for a uniform marginal); all
+ * are then 2x2-averaged `coarsen` times.  Field f uses noise stream f. */
+#define ORC_MAX_FIELDS 5
 typedef struct {
-    uint64_t seed; double sigma2, alpha_lo, alpha_span;
+    uint64_t seed; double sigma2; int32_t nf; double shift0;
+    double lo[ORC_MAX_FIELDS], span[ORC_MAX_FIELDS]; double* out[ORC_MAX_FIELDS];
     int32_t nx, nz, px, pz; uint32_t level; int64_t first; int32_t ns, coarsen;
-    const double* sq; double* lnKs; double* alpha; int32_t nthreads, tid;
+    const double* sq; int32_t nthreads, tid;
 } orc_field_job;
 
 static void* field_worker(void* arg)
@@ -237,53 +243,44 @@ static void* field_worker(void* arg)
     int nxo = J->nx >> J->coarsen, nzo = J->nz >> J->coarsen;
     double* re = (double*)malloc(sizeof(double) * n);
     double* im = (double*)malloc(sizeof(double) * n);
-    double* z[2];
-    z[0] = (double*)malloc(sizeof(double) * (size_t)J->nx * J->nz);
-    z[1] = (double*)malloc(sizeof(double) * (size_t)J->nx * J->nz);
+    double* z = (double*)malloc(sizeof(double) * (size_t)J->nx * J->nz);
+    double sig = sqrt(J->sigma2);
     for (int k = J->tid; k < J->ns; k += J->nthreads) {
         uint64_t sample = (uint64_t)(J->first + k);
-        for (uint32_t fld = 0; fld < 2; ++fld) {
-            orc_white_noise(J->seed, J->level, sample, fld, (int64_t)n, re);
+        for (int fld = 0; fld < J->nf; ++fld) {
+            orc_white_noise(J->seed, J->level, sample, (uint32_t)fld, (int64_t)n, re);
             memset(im, 0, sizeof(double) * n);
             orc_fft2(re, im, J->px, J->pz, 0);
             for (size_t q = 0; q < n; ++q) { re[q] *= J->sq[q]; im[q] *= J->sq[q]; }
             orc_fft2(re, im, J->px, J->pz, 1);
             for (int j = 0; j < J->nz; ++j)
-                for (int i = 0; i < J->nx; ++i)
-                    z[fld][(size_t)j * J->nx + i] = re[(size_t)j * J->px + i];
-        }
-        /* ln Ks = z0 (Eq. RandK with Ks^(bl) = 1); alpha = lo + span * Phi(g),
-         * g = z1 / sigma, Phi(x) = erfc(-x / sqrt 2) / 2 (the relation
-         * Y = F_Y^-1(F_Z(Z)) of Sec. 3.1 for a uniform marginal). */
-        int cx = J->nx, cz = J->nz;
-        double sig = sqrt(J->sigma2);
-        for (size_t q = 0; q < (size_t)cx * cz; ++q) {
-            double g = z[1][q] / sig;
-            z[1][q] = J->alpha_lo + J->alpha_span * 0.5 * erfc(-g / sqrt(2.0));
-        }
-        /* 2x2 averaging of ln Ks and alpha, coarsen times */
-        for (int c = 0; c < J->coarsen; ++c) {
-            int ncx = cx / 2, ncz = cz / 2;
-            for (int f = 0; f < 2; ++f)
+                for (int i = 0; i < J->nx; ++i) {
+                    double v = re[(size_t)j * J->px + i];
+                    z[(size_t)j * J->nx + i] = fld == 0 ? J->shift0 + v
+                        : J->lo[fld] + J->span[fld] * 0.5 * erfc(-(v / sig) / sqrt(2.0));
+                }
+            /* 2x2 averaging, coarsen times */
+            int cx = J->nx, cz = J->nz;
+            for (int c = 0; c < J->coarsen; ++c) {
+                int ncx = cx / 2, ncz = cz / 2;
                 for (int j = 0; j < ncz; ++j)
                     for (int i = 0; i < ncx; ++i) {
-                        double s = z[f][(size_t)(2 * j) * cx + 2 * i] + z[f][(size_t)(2 * j) * cx + 2 * i + 1]
-                                 + z[f][(size_t)(2 * j + 1) * cx + 2 * i] + z[f][(size_t)(2 * j + 1) * cx + 2 * i + 1];
-                        z[f][(size_t)j * ncx + i] = 0.25 * s;
+                        double t = z[(size_t)(2 * j) * cx + 2 * i] + z[(size_t)(2 * j) * cx + 2 * i + 1]
+                                 + z[(size_t)(2 * j + 1) * cx + 2 * i] + z[(size_t)(2 * j + 1) * cx + 2 * i + 1];
+                        z[(size_t)j * ncx + i] = 0.25 * t;
                     }
-            cx = ncx; cz = ncz;
+                cx = ncx; cz = ncz;
+            }
+            memcpy(J->out[fld] + (size_t)k * nxo * nzo, z, sizeof(double) * (size_t)nxo * nzo);
         }
-        memcpy(J->lnKs + (size_t)k * nxo * nzo, z[0], sizeof(double) * (size_t)nxo * nzo);
-        memcpy(J->alpha + (size_t)k * nxo * nzo, z[1], sizeof(double) * (size_t)nxo * nzo);
     }
-    free(re); free(im); free(z[0]); free(z[1]);
+    free(re); free(im); free(z);
     return NULL;
 }
 
-int orc_sample_fields(uint64_t seed, const orc_cov* cv, double alpha_lo,
-                      double alpha_span, int32_t nx, int32_t nz, uint32_t level,
-                      int64_t first_sample, int32_t nsamples, int32_t coarsen_times,
-                      double* lnKs, double* alpha, int32_t nthreads)
+static int sample_n(uint64_t seed, const orc_cov* cv, int nf, double shift0, const double* lo,
+                    const double* span, double** out, int32_t nx, int32_t nz, uint32_t level,
+                    int64_t first_sample, int32_t nsamples, int32_t coarsen_times, int32_t nthreads)
 {
     if (nx < 1 || nz < 1 || nsamples < 0 || coarsen_times < 0) return -1;
     if ((nx % (1 << coarsen_times)) || (nz % (1 << coarsen_times))) return -1;
@@ -297,14 +294,44 @@ int orc_sample_fields(uint64_t seed, const orc_cov* cv, double alpha_lo,
     orc_field_job* jobs = (orc_field_job*)malloc(sizeof(orc_field_job) * nthreads);
     pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * nthreads);
     for (int t = 0; t < nthreads; ++t) {
-        orc_field_job J = { seed, cv->sigma2, alpha_lo, alpha_span, nx, nz, px, pz, level,
-                            first_sample, nsamples, coarsen_times, sq, lnKs, alpha, nthreads, t };
+        orc_field_job J;
+        memset(&J, 0, sizeof J);
+        J.seed = seed; J.sigma2 = cv->sigma2; J.nf = nf; J.shift0 = shift0;
+        for (int f = 0; f < nf; ++f) { J.lo[f] = lo[f]; J.span[f] = span[f]; J.out[f] = out[f]; }
+        J.nx = nx; J.nz = nz; J.px = px; J.pz = pz; J.level = level; J.first = first_sample;
+        J.ns = nsamples; J.coarsen = coarsen_times; J.sq = sq; J.nthreads = nthreads; J.tid = t;
         jobs[t] = J;
         pthread_create(&th[t], NULL, field_worker, &jobs[t]);
     }
     for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
     free(jobs); free(th); free(sq);
     return 0;
+}
+
+/* ln Ks = z_0 (Eq. RandK with Ks^(bl) = 1) and alpha = lo + span Phi(z_1 / sigma) */
+int orc_sample_fields(uint64_t seed, const orc_cov* cv, double alpha_lo,
+                      double alpha_span, int32_t nx, int32_t nz, uint32_t level,
+                      int64_t first_sample, int32_t nsamples, int32_t coarsen_times,
+                      double* lnKs, double* alpha, int32_t nthreads)
+{
+    double lo[2] = { 0.0, alpha_lo }, span[2] = { 0.0, alpha_span };
+    double* out[2] = { lnKs, alpha };
+    return sample_n(seed, cv, 2, 0.0, lo, span, out, nx, nz, level, first_sample, nsamples,
+                    coarsen_times, nthreads);
+}
+
+/* The five soil fields of Table soilparams: ln Ks (noise stream 0), alpha (1),
+ * n (2), theta_s (3), theta_r (4). */
+int orc_sample_soil(uint64_t seed, const orc_cov* cv, const orc_soil_model* sm, int32_t nx, int32_t nz,
+                    uint32_t level, int64_t first_sample, int32_t nsamples, int32_t coarsen_times,
+                    double* lnKs, double* alpha, double* n, double* theta_s, double* theta_r,
+                    int32_t nthreads)
+{
+    double lo[5] = { 0.0, sm->alpha_lo, sm->n_lo, sm->theta_s_lo, sm->theta_r_lo };
+    double span[5] = { 0.0, sm->alpha_span, sm->n_span, sm->theta_s_span, sm->theta_r_span };
+    double* out[5] = { lnKs, alpha, n, theta_s, theta_r };
+    return sample_n(seed, cv, 5, sm->lnks_mean, lo, span, out, nx, nz, level, first_sample, nsamples,
+                    coarsen_times, nthreads);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -374,30 +401,71 @@ int orc_sample_fields_pair(uint64_t seed, const orc_cov* cv, double alpha_lo,
 }
 
 /* ------------------------------------------------------------------------- */
-/* Closure: Gardner exponential model.                                        */
+/* Closures.  K, theta and C = d theta / d p at head p for one cell.          */
+/* Gardner exponential model (kind 0):                                        */
 /*   p < 0 : E = exp(a p), K = Ks E, theta = theta_r + (theta_s - theta_r) E, */
-/*           C = d theta / d p = (theta_s - theta_r) a E                      */
-/*   p >= 0: K = Ks, theta = theta_s, C = 0   (saturated branch, Eqs. Sw, Krw)*/
+/*           C = (theta_s - theta_r) a E                                      */
+/* van Genuchten-Mualem (kind 1; Eqs. Sw, sc_van, Krw), m = 1 - 1/n:          */
+/*   p < 0 : an = (a |p|)^n, S = (1 + an)^-m, theta = theta_r + (theta_s -    */
+/*           theta_r) S, C = (theta_s - theta_r) a m n (1 + an)^-(m+1)        */
+/*           (a |p|)^(n-1), K = Ks S^(1/2) (1 - (1 - S^(1/m))^m)^2 with the   */
+/*           exact identity 1 - S^(1/m) = an / (1 + an) (no cancellation as   */
+/*           S -> 1)                                                          */
+/* Both: p >= 0 gives K = Ks, theta = theta_s, C = 0 (saturated branch).      */
 /* ------------------------------------------------------------------------- */
-static void closure(double Ks, double a, double p, double tr, double ts,
-                    double* K, double* theta, double* C)
+typedef struct { double Ks, a, n, tr, ts; } cellp;
+
+static void closure(int kind, const cellp* c, double p, double* K, double* theta, double* C)
 {
-    if (p < 0.0) {
-        double E = exp(a * p);
-        *K = Ks * E;
-        *theta = tr + (ts - tr) * E;
-        *C = (ts - tr) * a * E;
-    } else {
-        *K = Ks;
-        *theta = ts;
+    if (!(p < 0.0)) {
+        *K = c->Ks;
+        *theta = c->ts;
         *C = 0.0;
+    } else if (kind == 0) {
+        double E = exp(c->a * p);
+        *K = c->Ks * E;
+        *theta = c->tr + (c->ts - c->tr) * E;
+        *C = (c->ts - c->tr) * c->a * E;
+    } else {
+        double m = 1.0 - 1.0 / c->n;
+        double ap = c->a * fabs(p);
+        double an = pow(ap, c->n);
+        double S = pow(1.0 + an, -m);
+        double b = 1.0 - pow(an / (1.0 + an), m);
+        *K = c->Ks * sqrt(S) * b * b;
+        *theta = c->tr + (c->ts - c->tr) * S;
+        *C = (c->ts - c->tr) * c->a * m * c->n * pow(1.0 + an, -(m + 1.0)) * pow(ap, c->n - 1.0);
     }
 }
 
-/* Conductivity on a Dirichlet face (reading R2). */
-static double k_dirichlet(double Ks, double a, double pD)
+int orc_closure(int32_t kind, double Ks, double a, double n, double theta_r, double theta_s,
+                double p, double* K, double* theta, double* C)
 {
-    return pD < 0.0 ? Ks * exp(a * pD) : Ks;
+    if (kind != 0 && kind != 1) return -1;
+    cellp c = { Ks, a, n, theta_r, theta_s };
+    closure(kind, &c, p, K, theta, C);
+    return 0;
+}
+
+/* parameters of cell q of one sample (soil pointers already offset) */
+static cellp cell_at(const orc_problem* pb, const orc_soil* so, size_t q)
+{
+    cellp c;
+    c.Ks = exp(so->lnKs[q]);
+    c.a = so->alpha[q] * so->alpha_scale + so->alpha_shift;
+    c.n = so->n ? so->n[q] + so->n_shift : 0.0;
+    c.tr = (pb->closure == 1 && so->theta_r) ? so->theta_r[q] : pb->theta_r;
+    c.ts = (pb->closure == 1 && so->theta_s) ? so->theta_s[q] : pb->theta_s;
+    return c;
+}
+
+/* Conductivity on a Dirichlet face (reading R2): the closure's K at the
+ * boundary head with the adjacent cell's parameters. */
+static double k_dirichlet(int kind, const cellp* c, double pD)
+{
+    double K, th, C;
+    closure(kind, c, pD, &K, &th, &C);
+    return K;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -412,19 +480,19 @@ static double k_dirichlet(double Ks, double a, double pD)
 /* Residual R_P = (theta_P - theta_P^old)/dt + sum(out-fluxes) - src_P, and   */
 /* the Picard system is  (C/dt) dp + L(T) dp = f := -R.                       */
 /* ------------------------------------------------------------------------- */
-int orc_picard_system(const orc_problem* pb, int32_t nx, int32_t nz, const double* lnKs,
-                      const double* alpha, double alpha_scale, const double* p,
-                      const double* p_old, double* Tx, double* Tz, double* Tbt,
-                      double* Tbb, double* Cdt, double* f)
+static void picard_system(const orc_problem* pb, int32_t nx, int32_t nz, const orc_soil* so,
+                          const double* p, const double* p_old, double* Tx, double* Tz,
+                          double* Tbt, double* Tbb, double* Cdt, double* f)
 {
     const double h = 1.0 / nz, h2 = h * h;
     const size_t n = (size_t)nx * nz;
+    const int kind = pb->closure;
     double* K = (double*)malloc(sizeof(double) * n);
     double* th = (double*)malloc(sizeof(double) * n);
     double* C = (double*)malloc(sizeof(double) * n);
     for (size_t q = 0; q < n; ++q) {
-        double Ks = exp(lnKs[q]), a = alpha[q] * alpha_scale;
-        closure(Ks, a, p[q], pb->theta_r, pb->theta_s, &K[q], &th[q], &C[q]);
+        cellp c = cell_at(pb, so, q);
+        closure(kind, &c, p[q], &K[q], &th[q], &C[q]);
     }
     for (int j = 0; j < nz; ++j)
         for (int i = 0; i < nx; ++i) {
@@ -433,17 +501,16 @@ int orc_picard_system(const orc_problem* pb, int32_t nx, int32_t nz, const doubl
             Tz[P] = (j < nz - 1) ? (2.0 / h2) * K[P] * K[P + nx] / (K[P] + K[P + nx]) : 0.0;
         }
     for (int i = 0; i < nx; ++i) {
-        size_t T = (size_t)(nz - 1) * nx + i, B = (size_t)i;
-        Tbt[i] = (2.0 / h2) * k_dirichlet(exp(lnKs[T]), alpha[T] * alpha_scale, pb->p_top);
-        Tbb[i] = (2.0 / h2) * k_dirichlet(exp(lnKs[B]), alpha[B] * alpha_scale, pb->p_bottom);
+        cellp ct = cell_at(pb, so, (size_t)(nz - 1) * nx + i), cb = cell_at(pb, so, (size_t)i);
+        Tbt[i] = (2.0 / h2) * k_dirichlet(kind, &ct, pb->p_top);
+        Tbb[i] = (2.0 / h2) * k_dirichlet(kind, &cb, pb->p_bottom);
     }
-    double theta_old_scratch;
     for (int j = 0; j < nz; ++j)
         for (int i = 0; i < nx; ++i) {
             size_t P = (size_t)j * nx + i;
             double Kd, thold, Cd;
-            closure(exp(lnKs[P]), alpha[P] * alpha_scale, p_old[P], pb->theta_r, pb->theta_s,
-                    &Kd, &thold, &Cd);
+            cellp c = cell_at(pb, so, P);
+            closure(kind, &c, p_old[P], &Kd, &thold, &Cd);
             double R = (th[P] - thold) / pb->dt;
             if (i < nx - 1) R += -Tx[P] * (p[P + 1] - p[P]);
             if (i > 0)      R += -Tx[P - 1] * (p[P - 1] - p[P]);
@@ -454,8 +521,17 @@ int orc_picard_system(const orc_problem* pb, int32_t nx, int32_t nz, const doubl
             f[P] = -R;
             Cdt[P] = C[P] / pb->dt;
         }
-    (void)theta_old_scratch;
     free(K); free(th); free(C);
+}
+
+int orc_picard_system(const orc_problem* pb, int32_t nx, int32_t nz, const double* lnKs,
+                      const double* alpha, double alpha_scale, const double* p,
+                      const double* p_old, double* Tx, double* Tz, double* Tbt,
+                      double* Tbb, double* Cdt, double* f)
+{
+    if (pb->closure != 0) return -1;      /* the soil arrays of closure 1 are not given */
+    orc_soil so = { lnKs, alpha, NULL, NULL, NULL, alpha_scale, 0.0, 0.0 };
+    picard_system(pb, nx, nz, &so, p, p_old, Tx, Tz, Tbt, Tbb, Cdt, f);
     return 0;
 }
 
@@ -705,19 +781,28 @@ int orc_mg_solve(int32_t nx, int32_t nz, double h, const double* Tx, const doubl
 /* ------------------------------------------------------------------------- */
 /* Time loop with modified Picard (Sec. 4.1) and the bottom-flux QoI.         */
 /* ------------------------------------------------------------------------- */
-int orc_solve_one(const orc_problem* pb, int32_t nx, int32_t nz, const double* lnKs,
-                  const double* alpha, double alpha_scale, const double* src,
-                  const double* p_init, double* p_final, double* qoi, orc_stats* st)
+static int solve_soil(const orc_problem* pb, int32_t nx, int32_t nz, const orc_soil* so,
+                      const double* src, const double* p_init, double* p_final, double* qoi,
+                      orc_stats* st)
 {
     int nlev = count_levels(nx, nz);
     if (nlev < 1 || nx < 1 || nz < 1) return -1;
+    if (pb->closure != 0 && (pb->closure != 1 || !so->n)) return -1;
     const size_t n = (size_t)nx * nz;
     const double h = 1.0 / nz;
     mg_level* Ls = alloc_levels(nx, nz, nlev);
     mg_level* L = &Ls[0];
     double* p = (double*)malloc(n * 8);
     double* p_old = (double*)malloc(n * 8);
-    for (size_t q = 0; q < n; ++q) p[q] = p_init ? p_init[q] : pb->p_init;
+    /* initial head: given, uniform, or p_init (1 - exp(-init_decay z)) at the
+     * cell centres z_j = (j + 1/2) h (Eq. travellingwave) */
+    for (int j = 0; j < nz; ++j)
+        for (int i = 0; i < nx; ++i) {
+            size_t q = (size_t)j * nx + i;
+            if (p_init) p[q] = p_init[q];
+            else if (pb->init_decay > 0.0) p[q] = pb->p_init * (1.0 - exp(-pb->init_decay * (j + 0.5) * h));
+            else p[q] = pb->p_init;
+        }
     int status = ORC_OK;
     orc_stats S = { 0, 0, 0, 0 };
     for (int step = 0; step < pb->nsteps && status != ORC_PICARD_MAXIT && status != ORC_NONFINITE; ++step) {
@@ -725,8 +810,7 @@ int orc_solve_one(const orc_problem* pb, int32_t nx, int32_t nz, const double* l
         int k = 0, converged = 0;
         while (!converged) {
             if (k >= pb->picard_maxit) { status = ORC_PICARD_MAXIT; break; }
-            orc_picard_system(pb, nx, nz, lnKs, alpha, alpha_scale, p, p_old,
-                              L->Tx, L->Tz, L->Tbt, L->Tbb, L->Cdt, L->f);
+            picard_system(pb, nx, nz, so, p, p_old, L->Tx, L->Tz, L->Tbt, L->Tbb, L->Cdt, L->f);
             if (src) for (size_t q = 0; q < n; ++q) L->f[q] += src[q];
             int cyc = 0;
             int rc = mg_solve_levels(Ls, nlev, pb->mg_tol, pb->mg_maxit, pb->nu1, pb->nu2, pb->gamma, &cyc,
@@ -748,7 +832,8 @@ int orc_solve_one(const orc_problem* pb, int32_t nx, int32_t nz, const double* l
      * over the nx faces: q.n = K_b (2 (p_P - p_bot)/h + 1). */
     double Q = 0.0;
     for (int i = 0; i < nx; ++i) {
-        double Kb = k_dirichlet(exp(lnKs[i]), alpha[i] * alpha_scale, pb->p_bottom);
+        cellp c = cell_at(pb, so, (size_t)i);
+        double Kb = k_dirichlet(pb->closure, &c, pb->p_bottom);
         Q += Kb * (2.0 * (p[i] - pb->p_bottom) / h + 1.0);
     }
     Q /= nx;
@@ -761,8 +846,24 @@ int orc_solve_one(const orc_problem* pb, int32_t nx, int32_t nz, const double* l
     return status;
 }
 
+int orc_solve_one_soil(const orc_problem* pb, int32_t nx, int32_t nz, const orc_soil* so,
+                       const double* src, const double* p_init, double* p_final, double* qoi,
+                       orc_stats* st)
+{
+    return solve_soil(pb, nx, nz, so, src, p_init, p_final, qoi, st);
+}
+
+int orc_solve_one(const orc_problem* pb, int32_t nx, int32_t nz, const double* lnKs,
+                  const double* alpha, double alpha_scale, const double* src,
+                  const double* p_init, double* p_final, double* qoi, orc_stats* st)
+{
+    if (pb->closure != 0) return -1;
+    orc_soil so = { lnKs, alpha, NULL, NULL, NULL, alpha_scale, 0.0, 0.0 };
+    return solve_soil(pb, nx, nz, &so, src, p_init, p_final, qoi, st);
+}
+
 typedef struct {
-    const orc_problem* pb; int32_t nx, nz, ns; const double *lnKs, *alpha; double as;
+    const orc_problem* pb; int32_t nx, nz, ns; const orc_soil* so;
     double *p_final, *qoi; int32_t* status; orc_stats st; int32_t nthreads, tid;
 } orc_solve_job;
 
@@ -772,10 +873,14 @@ static void* solve_worker(void* arg)
     size_t n = (size_t)J->nx * J->nz;
     orc_stats acc = { 0, 0, 0, 0 };
     for (int s = J->tid; s < J->ns; s += J->nthreads) {
+        const orc_soil* B = J->so;
+        size_t o = (size_t)s * n;
+        orc_soil so = { B->lnKs + o, B->alpha + o, B->n ? B->n + o : NULL,
+                        B->theta_s ? B->theta_s + o : NULL, B->theta_r ? B->theta_r + o : NULL,
+                        B->alpha_scale, B->alpha_shift, B->n_shift };
         orc_stats st;
-        int rc = orc_solve_one(J->pb, J->nx, J->nz, J->lnKs + s * n, J->alpha + s * n, J->as,
-                               NULL, NULL, J->p_final ? J->p_final + s * n : NULL,
-                               &J->qoi[s], &st);
+        int rc = solve_soil(J->pb, J->nx, J->nz, &so, NULL, NULL, J->p_final ? J->p_final + o : NULL,
+                            &J->qoi[s], &st);
         J->status[s] = rc;
         acc.picard_iters += st.picard_iters; acc.mg_cycles += st.mg_cycles;
         if (st.max_picard > acc.max_picard) acc.max_picard = st.max_picard;
@@ -785,18 +890,17 @@ static void* solve_worker(void* arg)
     return NULL;
 }
 
-int orc_solve_batch(const orc_problem* pb, int32_t nx, int32_t nz, int32_t nsamples,
-                    const double* lnKs, const double* alpha, double alpha_scale,
-                    double* p_final, double* qoi, int32_t* status, orc_stats* st,
-                    int32_t nthreads)
+int orc_solve_batch_soil(const orc_problem* pb, int32_t nx, int32_t nz, int32_t nsamples,
+                         const orc_soil* soil, double* p_final, double* qoi, int32_t* status,
+                         orc_stats* st, int32_t nthreads)
 {
     if (count_levels(nx, nz) < 1 || nsamples < 0) return -1;
+    if (pb->closure != 0 && (pb->closure != 1 || !soil->n)) return -1;
     if (nthreads < 1) nthreads = 1;
     orc_solve_job* jobs = (orc_solve_job*)malloc(sizeof(orc_solve_job) * nthreads);
     pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * nthreads);
     for (int t = 0; t < nthreads; ++t) {
-        orc_solve_job J = { pb, nx, nz, nsamples, lnKs, alpha, alpha_scale, p_final, qoi, status,
-                            { 0, 0, 0, 0 }, nthreads, t };
+        orc_solve_job J = { pb, nx, nz, nsamples, soil, p_final, qoi, status, { 0, 0, 0, 0 }, nthreads, t };
         jobs[t] = J;
         pthread_create(&th[t], NULL, solve_worker, &jobs[t]);
     }
@@ -812,4 +916,14 @@ int orc_solve_batch(const orc_problem* pb, int32_t nx, int32_t nz, int32_t nsamp
     if (st) *st = acc;
     free(jobs); free(th);
     return worst;
+}
+
+int orc_solve_batch(const orc_problem* pb, int32_t nx, int32_t nz, int32_t nsamples,
+                    const double* lnKs, const double* alpha, double alpha_scale,
+                    double* p_final, double* qoi, int32_t* status, orc_stats* st,
+                    int32_t nthreads)
+{
+    if (pb->closure != 0) return -1;
+    orc_soil so = { lnKs, alpha, NULL, NULL, NULL, alpha_scale, 0.0, 0.0 };
+    return orc_solve_batch_soil(pb, nx, nz, nsamples, &so, p_final, qoi, status, st, nthreads);
 }

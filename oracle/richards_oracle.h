@@ -16,8 +16,10 @@
  *     arithmetic means of fine face coefficients (Fig. diffUpscale), stop on
  *     ||L dp - f||_inf < eps_MG (Sec. 4.2)
  *   - FFT moving-average Gaussian fields (Appendix A, Eqs. convol1-product2)
- *   - closure: Gardner exponential model (the configured instance), with the
- *     saturated branch for p >= 0 as in Eqs. Sw, Krw.
+ *   - closures: Gardner exponential model (the configured instance), with the
+ *     saturated branch for p >= 0 as in Eqs. Sw, Krw; van Genuchten-Mualem
+ *     (Sec. 2.1, Eqs. Sw, sc_van, Krw) with per-cell Ks, alpha, n, theta_s,
+ *     theta_r fields (Table soilparams).
  */
 #ifndef RICHARDS_ORACLE_H
 #define RICHARDS_ORACLE_H
@@ -35,7 +37,29 @@ typedef struct {
     int32_t mg_maxit;
     int32_t nu1, nu2;      /* pre/post red-black GS steps                    */
     int32_t gamma;         /* cycle index: 1 = V-cycle, 2 = W-cycle          */
+    int32_t closure;       /* 0 Gardner exponential, 1 van Genuchten-Mualem  */
+    double init_decay;     /* > 0: p(x,z,0) = p_init (1 - exp(-init_decay z))
+                              (the infiltration problem, Eq. travellingwave) */
 } orc_problem;
+
+/* Per-cell soil parameters of a batch, each [S][nz][nx].  n, theta_s and
+ * theta_r are read by the van Genuchten-Mualem closure only (theta arrays may
+ * be NULL: the problem's constants).  Effective parameters:
+ * Ks = exp(lnKs), alpha_eff = alpha * alpha_scale + alpha_shift,
+ * n_eff = n + n_shift (the parametric continuation of Sec. 5). */
+typedef struct {
+    const double *lnKs, *alpha, *n, *theta_s, *theta_r;
+    double alpha_scale, alpha_shift, n_shift;
+} orc_soil;
+
+/* Marginals of the five soil fields (Table soilparams): ln Ks = lnks_mean + Z,
+ * every other field lo + span * Phi(g) with g a unit-variance field of the
+ * same covariance (Y = F_Y^-1(F_Z(Z)) for a uniform marginal, Sec. 3.1). */
+typedef struct {
+    double lnks_mean;
+    double alpha_lo, alpha_span, n_lo, n_span;
+    double theta_s_lo, theta_s_span, theta_r_lo, theta_r_span;
+} orc_soil_model;
 
 typedef struct {
     int64_t picard_iters;  /* total Picard iterations over all steps        */
@@ -68,6 +92,18 @@ int  orc_sample_fields_pair(uint64_t seed, const orc_cov* cv, double alpha_lo,
                             double alpha_span, int32_t nx, int32_t nz, uint32_t level,
                             int64_t first_sample, int32_t nsamples, double* lnKs_f, double* alpha_f,
                             double* lnKs_c, double* alpha_c);
+int  orc_sample_soil(uint64_t seed, const orc_cov* cv, const orc_soil_model* sm, int32_t nx, int32_t nz,
+                     uint32_t level, int64_t first_sample, int32_t nsamples, int32_t coarsen_times,
+                     double* lnKs, double* alpha, double* n, double* theta_s, double* theta_r,
+                     int32_t nthreads);
+int  orc_closure(int32_t kind, double Ks, double a, double n, double theta_r, double theta_s,
+                 double p, double* K, double* theta, double* C);
+int  orc_solve_one_soil(const orc_problem* pb, int32_t nx, int32_t nz, const orc_soil* soil,
+                        const double* src, const double* p_init, double* p_final, double* qoi,
+                        orc_stats* st);
+int  orc_solve_batch_soil(const orc_problem* pb, int32_t nx, int32_t nz, int32_t nsamples,
+                          const orc_soil* soil, double* p_final, double* qoi, int32_t* status,
+                          orc_stats* st, int32_t nthreads);
 int  orc_solve_one(const orc_problem* pb, int32_t nx, int32_t nz, const double* lnKs,
                    const double* alpha, double alpha_scale, const double* src,
                    const double* p_init, double* p_final, double* qoi, orc_stats* st);

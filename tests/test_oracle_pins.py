@@ -231,7 +231,7 @@ def test_saturated_limit_columns_closed_form():
     assert rc == 0 and np.abs(p - exact[:, None]).max() < 1e-9
 
 
-def hydraulic_head_dense_solve(lnks):
+def hydraulic_head_dense_solve(lnks, p_top=PHYSICS["p_top"], p_bot=PHYSICS["p_bottom"]):
     """Steady saturated flow solved for the hydraulic head phi = p + z with a
     dense direct solve of G^T diag(c) G phi = b phi_D, where G is the
     face-cell incidence matrix, c the face conductances (inverse of the sum of
@@ -261,8 +261,8 @@ def hydraulic_head_dense_solve(lnks):
         bt, bb = 1.0 / rhalf[nz - 1, i], 1.0 / rhalf[0, i]
         A[idx(i, nz - 1), idx(i, nz - 1)] += bt
         A[idx(i, 0), idx(i, 0)] += bb
-        rhs[idx(i, nz - 1)] += bt * (PHYSICS["p_top"] + 1.0)
-        rhs[idx(i, 0)] += bb * (PHYSICS["p_bottom"] + 0.0)
+        rhs[idx(i, nz - 1)] += bt * (p_top + 1.0)
+        rhs[idx(i, 0)] += bb * (p_bot + 0.0)
     phi = np.linalg.solve(A, rhs).reshape(nz, nx)
     z = (np.arange(nz) + 0.5) * h
     return phi - z[:, None]
