@@ -43,15 +43,18 @@ FP64_TFLOPS_NOMINAL = 1.25      # GB300 FP64 (non-tensor) peak: 152 SMs x 2 FMA/
 # launch of the default workload's timed step, from an ncu capture (see
 # profiles/); valid only while the kernel source is the one captured.
 TRAFFIC = {
-    # (precision, block_threads): (sha256 of csrc/fused.cu, bytes per launch)
-    ("fp64", 1024): ("384931da7a0e5b1960d4ff392143d4b7387e9fe1e11465843e9fc3efc44c1c35", 38.95e12 + 11.16e12),
+    # (precision, block_threads): (fused_sha() of the captured sources, bytes per launch)
 }
 
 
 def fused_sha():
+    """sha256 over the fused solver's sources (kernel header, then host code)."""
     import hashlib
-    with open(os.path.join(ROOT, "paper_1903_08741_gb300", "csrc", "fused.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()
+    h = hashlib.sha256()
+    for name in ("fused_kernel.cuh", "fused.cu"):
+        with open(os.path.join(ROOT, "paper_1903_08741_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def captured_traffic(prec_name, block_threads, default_workload):

@@ -35,11 +35,13 @@ enum {
 };
 
 enum { RICH_FP64 = 0, RICH_MIXED = 1 };
+/* closures (rich_problem_t.closure) */
+enum { RICH_GARDNER = 0, RICH_VAN_GENUCHTEN = 1 };
 
 typedef struct rich_ctx* rich_ctx_t;
 
-/* Physics and solver settings of one batch (Gardner closure, Sec. 2 with the
- * configured closure; Picard, Sec. 4.1; CCMG, Sec. 4.2). */
+/* Physics and solver settings of one batch (Sec. 2: Gardner or van
+ * Genuchten-Mualem closure; Picard, Sec. 4.1; CCMG, Sec. 4.2). */
 typedef struct {
     int32_t nx, nz;          /* cells per side; must coarsen by 2 to <= 64 cells  */
     int32_t nsteps;          /* implicit-Euler steps (Eq. Mixed_based)            */
@@ -56,6 +58,13 @@ typedef struct {
                                 FP64 defect-correction loop                       */
     int32_t cycle;           /* multigrid cycle index: 1 (or 0) V-cycle, 2 W-cycle
                                 (the paper's W(2,2), Sec. 4.2), at most 4         */
+    int32_t closure;         /* RICH_GARDNER (zero-initialised default) or
+                                RICH_VAN_GENUCHTEN (Sec. 2.1, Eqs. Sw, sc_van,
+                                Krw; needs per-cell n: rich_solve_soil)           */
+    double init_decay;       /* 0: uniform p_init; > 0: initial head
+                                p_init (1 - exp(-init_decay z)) at the cell
+                                centres (the infiltration problem, Eq.
+                                travellingwave: p_init -0.4, init_decay 80)       */
 } rich_problem_t;
 
 /* Random-field model: ln Ks Gaussian, drawn by FFT moving average (Appendix A,
@@ -166,6 +175,51 @@ int rich_solve_batch_host(rich_ctx_t ctx, const rich_problem_t* pb, int32_t nsam
                           const double* lnKs, const double* alpha, double alpha_scale,
                           double* qoi, double* p_final, int32_t* status, rich_stats_t* stats,
                           void* stream);
+
+/* Per-cell soil fields of a batch, each [S][nz][nx] DEVICE memory owned by
+ * the caller: outputs of rich_sample_soil, inputs of rich_solve_soil.  The
+ * van Genuchten-Mualem closure reads ln Ks, alpha, n and (when non-NULL)
+ * theta_s, theta_r (NULL: the problem's constants); Gardner reads ln Ks and
+ * alpha only. */
+typedef struct {
+    double* lnKs;
+    double* alpha;
+    double* n;
+    double* theta_s;
+    double* theta_r;
+} rich_soil_t;
+
+/* Marginals of the five soil fields (Table soilparams): ln Ks = lnks_mean + Z
+ * (Eq. RandK with Ks^(bl) = exp(lnks_mean)); alpha, n, theta_s, theta_r are
+ * lo + span * Phi(g) with g a unit-variance field of the same covariance
+ * (uniform marginals, Sec. 3.1).  The paper's table: alpha_bl +- 0.2,
+ * n_bl +- 0.05, theta_s 0.5 +- 0.05, theta_r 0.05 +- 0.005, Ks_bl = 0.2. */
+typedef struct {
+    double lnks_mean;
+    double n_lo, n_span;
+    double theta_s_lo, theta_s_span;
+    double theta_r_lo, theta_r_span;
+} rich_soil_model_t;
+
+/* The five soil fields of samples first_sample .. +nsamples-1 by FFT-MA
+ * (Appendix A), with the covariance and the alpha marginal of `field` and
+ * the other marginals of `soil`.  Field k of a sample uses the white-noise
+ * stream k (0 ln Ks, 1 alpha, 2 n, 3 theta_s, 4 theta_r), so ln Ks and alpha
+ * are the draws rich_sample_fields makes (ln Ks shifted by lnks_mean).
+ * coarsen_times 2x2 averages as rich_sample_fields.  out->theta_s/theta_r may
+ * be NULL (not drawn).  Asynchronous on `stream`. */
+int rich_sample_soil(rich_ctx_t ctx, const rich_field_t* field, const rich_soil_model_t* soil,
+                     int32_t nx, int32_t nz, uint32_t level, int64_t first_sample,
+                     int32_t nsamples, int32_t coarsen_times, const rich_soil_t* out, void* stream);
+
+/* As rich_solve_batch with per-cell soil fields (either closure) and the
+ * additive continuation of Sec. 5: alpha_eff = alpha * alpha_scale +
+ * alpha_shift, n_eff = n + n_shift (the paper's (grad alpha, grad n)
+ * hierarchy uses negative alpha shifts and positive n shifts on coarse
+ * levels).  RICH_ERR_INVALID if the closure needs n and soil->n is NULL. */
+int rich_solve_soil(rich_ctx_t ctx, const rich_problem_t* pb, int32_t nsamples,
+                    const rich_soil_t* soil, double alpha_scale, double alpha_shift, double n_shift,
+                    double* qoi, double* p_final, int32_t* status, rich_stats_t* stats, void* stream);
 
 /* Multilevel Monte Carlo with parametric continuation (Sec. 5, Eqs.
  * telescope_ch6, MLMCestimator_ch6, SMC_ch6, MC_var_ch6, ML_var_ch6,

@@ -6,8 +6,9 @@ the computation runs in the library's CUDA kernels.  There is no CPU fallback:
 importing the binding without a built ``librichards.so`` raises, and so does
 calling it without a CUDA device.
 
-Entry points (same names as the C ABI): ``sample_fields``, ``solve_batch``,
-``solve_batch_host``, ``mlmc_estimate``.
+Entry points (same names as the C ABI): ``sample_fields``, ``sample_soil``,
+``solve_batch``, ``solve_soil``, ``solve_batch_host``, ``mlmc_estimate`` and
+the others listed by ``exported_symbols``.
 """
 from __future__ import annotations
 
@@ -22,6 +23,7 @@ LIB_PATH = os.path.join(_PKG, "librichards.so")
 
 OK, PICARD_MAXIT, MG_MAXIT, NONFINITE = 0, 1, 2, 3
 FP64, MIXED = 0, 1
+GARDNER, VAN_GENUCHTEN = 0, 1
 
 
 class RichError(RuntimeError):
@@ -33,7 +35,19 @@ class _Problem(C.Structure):
                 ("theta_r", C.c_double), ("theta_s", C.c_double), ("p_top", C.c_double),
                 ("p_bottom", C.c_double), ("p_init", C.c_double), ("picard_tol", C.c_double),
                 ("picard_maxit", C.c_int32), ("mg_tol", C.c_double), ("mg_maxit", C.c_int32),
-                ("nu1", C.c_int32), ("nu2", C.c_int32), ("precision", C.c_int32), ("cycle", C.c_int32)]
+                ("nu1", C.c_int32), ("nu2", C.c_int32), ("precision", C.c_int32), ("cycle", C.c_int32),
+                ("closure", C.c_int32), ("init_decay", C.c_double)]
+
+
+class _Soil(C.Structure):
+    _fields_ = [("lnKs", C.c_void_p), ("alpha", C.c_void_p), ("n", C.c_void_p), ("theta_s", C.c_void_p),
+                ("theta_r", C.c_void_p)]
+
+
+class _SoilModel(C.Structure):
+    _fields_ = [("lnks_mean", C.c_double), ("n_lo", C.c_double), ("n_span", C.c_double),
+                ("theta_s_lo", C.c_double), ("theta_s_span", C.c_double), ("theta_r_lo", C.c_double),
+                ("theta_r_span", C.c_double)]
 
 
 class _Field(C.Structure):
@@ -67,9 +81,42 @@ class Problem:
     nu2: int = 2
     precision: int = FP64
     cycle: int = 1           # 1: V-cycle (configured), 2: W-cycle (the paper's)
+    closure: int = GARDNER   # or VAN_GENUCHTEN (Sec. 2.1; solve_soil with per-cell n)
+    init_decay: float = 0.0  # > 0: p(x,z,0) = p_init (1 - exp(-init_decay z))
 
     def _c(self):
         return _Problem(*[getattr(self, f.name) for f in dc_fields(self)])
+
+    @classmethod
+    def infiltration(cls, **kw):
+        """The infiltration problem of Sec. 4.3 (Eq. travellingwave) with the van
+        Genuchten-Mualem closure: initial head -0.4 (1 - exp(-80 z)), top -0.4,
+        bottom 0.1, theta_s 0.5, theta_r 0.05 (per-cell fields override them),
+        W(2,2) cycles and Picard / MG tolerances 1e-5."""
+        d = dict(theta_r=0.05, theta_s=0.5, p_top=-0.4, p_bottom=0.1, p_init=-0.4, picard_tol=1e-5,
+                 mg_tol=1e-5, cycle=2, closure=VAN_GENUCHTEN, init_decay=80.0)
+        d.update(kw)
+        return cls(**d)
+
+
+@dataclass
+class SoilModel:
+    """Marginals of the soil fields (Table soilparams): ln Ks = ln ks_bl + Z and
+    baseline +- half-width uniform fields for n, theta_s, theta_r (alpha's range
+    is the FieldModel's alpha_lo / alpha_span; see soil_field_model)."""
+    ks_bl: float = 0.2
+    n_bl: float = 1.45
+    theta_s_bl: float = 0.5
+    theta_r_bl: float = 0.05
+    d_n: float = 0.05
+    d_theta_s: float = 0.05
+    d_theta_r: float = 0.005
+
+    def _c(self):
+        import math
+        return _SoilModel(math.log(self.ks_bl), self.n_bl - self.d_n, 2 * self.d_n,
+                          self.theta_s_bl - self.d_theta_s, 2 * self.d_theta_s,
+                          self.theta_r_bl - self.d_theta_r, 2 * self.d_theta_r)
 
 
 @dataclass
@@ -202,6 +249,10 @@ def lib():
         L.rich_kl_fields.argtypes = [vp, vp, i32, i32, vp, i32, vp, vp]
         L.rich_solve_batch_adjoint.argtypes = [vp, C.POINTER(_Problem), i32, vp, i32, vp, vp, dbl, i32, vp, vp,
                                                vp, vp, C.POINTER(_Stats), vp]
+        L.rich_sample_soil.argtypes = [vp, C.POINTER(_Field), C.POINTER(_SoilModel), i32, i32, u32, i64, i32,
+                                       i32, C.POINTER(_Soil), vp]
+        L.rich_solve_soil.argtypes = [vp, C.POINTER(_Problem), i32, C.POINTER(_Soil), dbl, dbl, dbl, vp, vp, vp,
+                                      C.POINTER(_Stats), vp]
         L.rich_mlmc_estimate.argtypes = [vp, C.POINTER(_MlmcCfg), C.POINTER(_MlmcResult)]
         L.rich_mlmc_adaptive.argtypes = [vp, C.POINTER(_MlmcCfg), i32, vp, C.POINTER(_MlmcResult)]
         _lib = L
@@ -214,7 +265,7 @@ def exported_symbols():
             "rich_mlmc_accumulate", "rich_profile", "rich_profile_read", "rich_launch_count",
             "rich_solve_batch_noalloc", "rich_mlmc_estimate", "rich_sample_fields_pair",
             "rich_kl_fields", "rich_solve_batch_adjoint", "rich_set_tuning", "rich_sample_fields_at",
-            "rich_solve_batch_async", "rich_mlmc_adaptive"]
+            "rich_solve_batch_async", "rich_mlmc_adaptive", "rich_sample_soil", "rich_solve_soil"]
 
 
 def _check(rc):
@@ -308,6 +359,54 @@ def solve_batch(problem: Problem, lnKs, alpha, alpha_scale=1.0, want_p=False, de
                                        None if p is None else _dev_ptr(p, torch.float64, "p"),
                                        _dev_ptr(status, torch.int32, "status"), C.byref(st),
                                        _stream(torch, device)))
+    return qoi, p, status, Stats(*[getattr(st, f) for f, _ in _Stats._fields_]), rc
+
+
+def soil_field_model(alpha_bl, model: FieldModel | None = None, d_alpha=0.2):
+    """A FieldModel whose alpha marginal is alpha_bl +- d_alpha (Table soilparams)."""
+    model = model or FieldModel.phi1()
+    return FieldModel(**{**{f.name: getattr(model, f.name) for f in dc_fields(model)},
+                         "alpha_lo": alpha_bl - d_alpha, "alpha_span": 2 * d_alpha})
+
+
+def sample_soil(nx, nz, nsamples, model: FieldModel, soil: SoilModel, level=0, first_sample=0,
+                coarsen_times=0, device=0, thetas=True):
+    """The five soil fields (ln Ks, alpha, n, theta_s, theta_r) on device, each
+    [nsamples, nz >> c, nx >> c] float64 (theta fields None when thetas=False)."""
+    torch = _torch()
+    shape = (nsamples, nz >> coarsen_times, nx >> coarsen_times)
+    k = 5 if thetas else 3
+    out = [torch.empty(shape, dtype=torch.float64, device=f"cuda:{device}") for _ in range(k)] + [None] * (5 - k)
+    ptrs = _Soil(*[None if t is None else _dev_ptr(t, torch.float64, "soil field").value for t in out])
+    _check(lib().rich_sample_soil(context(device), C.byref(model._c()), C.byref(soil._c()), nx, nz, level,
+                                  first_sample, nsamples, coarsen_times, C.byref(ptrs), _stream(torch, device)))
+    return tuple(out)
+
+
+def solve_soil(problem: Problem, lnKs, alpha, n=None, theta_s=None, theta_r=None, alpha_scale=1.0,
+               alpha_shift=0.0, n_shift=0.0, want_p=False, device=None):
+    """Solve with per-cell soil fields ([S, nz, nx] float64 CUDA tensors; the van
+    Genuchten-Mualem closure needs n) and the additive continuation shifts of
+    Sec. 5.  Returns (qoi, p_final or None, status, Stats, rc)."""
+    torch = _torch()
+    device = lnKs.device.index if device is None else device
+    S = lnKs.shape[0]
+    for t in (alpha, n, theta_s, theta_r):
+        if t is not None and tuple(t.shape) != tuple(lnKs.shape):
+            raise RichError("soil fields must share the shape [S, nz, nx]")
+    if tuple(lnKs.shape) != (S, problem.nz, problem.nx):
+        raise RichError("soil fields must be [S, nz, nx]")
+    qoi = torch.empty(S, dtype=torch.float64, device=lnKs.device)
+    status = torch.empty(S, dtype=torch.int32, device=lnKs.device)
+    p = torch.empty_like(lnKs) if want_p else None
+    ptrs = _Soil(*[None if t is None else _dev_ptr(t, torch.float64, "soil field").value
+                   for t in (lnKs, alpha, n, theta_s, theta_r)])
+    st = _Stats()
+    rc = _check(lib().rich_solve_soil(context(device), C.byref(problem._c()), S, C.byref(ptrs), alpha_scale,
+                                      alpha_shift, n_shift, _dev_ptr(qoi, torch.float64, "qoi"),
+                                      None if p is None else _dev_ptr(p, torch.float64, "p"),
+                                      _dev_ptr(status, torch.int32, "status"), C.byref(st),
+                                      _stream(torch, device)))
     return qoi, p, status, Stats(*[getattr(st, f) for f, _ in _Stats._fields_]), rc
 
 

@@ -13,8 +13,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "librichards.so")
-SOURCES = ["api.cu", "solver.cu", "fused.cu", "fields.cu", "mlmc.cu", "adjoint.cu"]
-HEADERS = [os.path.join(CSRC, "rich_internal.cuh"), os.path.join(ROOT, "include", "richards.h")]
+SOURCES = ["api.cu", "solver.cu", "fused.cu", "fused_vg.cu", "fields.cu", "mlmc.cu", "adjoint.cu"]
+HEADERS = [os.path.join(CSRC, "rich_internal.cuh"), os.path.join(CSRC, "fused_kernel.cuh"),
+           os.path.join(ROOT, "include", "richards.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-diag-suppress", "177"]
 

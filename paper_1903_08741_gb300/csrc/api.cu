@@ -1,5 +1,6 @@
 // C-ABI entry points of librichards (declared in include/richards.h).
 #include "rich_internal.cuh"
+#include <cmath>
 #include <stdio.h>
 #include <string.h>
 #include <new>
@@ -132,8 +133,8 @@ int rich_check_problem(const rich_problem_t* pb) {
     if (!pb || pb->nx < 1 || pb->nz < 1 || pb->nsteps < 0 || !(pb->dt > 0) ||
         pb->picard_maxit < 1 || pb->mg_maxit < 1 || pb->nu1 < 0 || pb->nu2 < 0 ||
         (pb->precision != RICH_FP64 && pb->precision != RICH_MIXED) || !(pb->picard_tol > 0) ||
-        pb->cycle < 0 || pb->cycle > 4 ||
-        !(pb->mg_tol > 0))
+        pb->cycle < 0 || pb->cycle > 4 || (pb->closure != RICH_GARDNER && pb->closure != RICH_VAN_GENUCHTEN) ||
+        !(pb->init_decay >= 0) || !(pb->init_decay < 1e300) || !(pb->mg_tol > 0))
         return RICH_ERR_INVALID;
     if (rich_count_levels(pb->nx, pb->nz) < 1) return RICH_ERR_INVALID;
     return 0;
@@ -203,6 +204,35 @@ extern "C" int rich_solve_batch(rich_ctx_t ctx, const rich_problem_t* pb, int32_
     RICH_CUDA(cudaSetDevice(ctx->device));
     return rich_solve_device(ctx, pb, nsamples, lnKs, alpha, alpha_scale, qoi, p_final, status,
                              stats, (cudaStream_t)stream);
+}
+
+extern "C" int rich_solve_soil(rich_ctx_t ctx, const rich_problem_t* pb, int32_t nsamples,
+                               const rich_soil_t* soil, double alpha_scale, double alpha_shift,
+                               double n_shift, double* qoi, double* p_final, int32_t* status,
+                               rich_stats_t* stats, void* stream) {
+    if (!ctx || rich_check_problem(pb) || nsamples < 0 || !soil) return RICH_ERR_INVALID;
+    if (!std::isfinite(alpha_scale) || !std::isfinite(alpha_shift) || !std::isfinite(n_shift))
+        return RICH_ERR_INVALID;
+    if (nsamples == 0) { if (stats) *stats = rich_stats_t{}; return 0; }
+    if (!soil->lnKs || !soil->alpha || !qoi) return RICH_ERR_INVALID;
+    if (pb->closure == RICH_VAN_GENUCHTEN && !soil->n) return RICH_ERR_INVALID;
+    RICH_CUDA(cudaSetDevice(ctx->device));
+    rich_soil_in in;
+    in.n = soil->n; in.theta_s = soil->theta_s; in.theta_r = soil->theta_r;
+    in.alpha_shift = alpha_shift; in.n_shift = n_shift;
+    return rich_solve_device(ctx, pb, nsamples, soil->lnKs, soil->alpha, alpha_scale, qoi, p_final, status,
+                             stats, (cudaStream_t)stream, &in);
+}
+
+extern "C" int rich_sample_soil(rich_ctx_t ctx, const rich_field_t* field, const rich_soil_model_t* soil,
+                                int32_t nx, int32_t nz, uint32_t level, int64_t first_sample,
+                                int32_t nsamples, int32_t coarsen_times, const rich_soil_t* out,
+                                void* stream) {
+    if (!ctx || !field || !soil || !out || nsamples < 0 || first_sample < 0) return RICH_ERR_INVALID;
+    if (nsamples > 0 && (!out->lnKs || !out->alpha || !out->n)) return RICH_ERR_INVALID;
+    RICH_CUDA(cudaSetDevice(ctx->device));
+    return rich_soil_device(ctx, field, soil, nx, nz, level, first_sample, nsamples, coarsen_times, out,
+                            (cudaStream_t)stream);
 }
 
 extern "C" int rich_solve_batch_host(rich_ctx_t ctx, const rich_problem_t* pb, int32_t nsamples,

@@ -35,12 +35,12 @@ __device__ __forceinline__ double u01(uint32_t hi, uint32_t lo) {
     return ((double)m + 0.5) * (1.0 / 9007199254740992.0);
 }
 
-// packed complex white noise: re = field 0, im = field 1, for samples
-// first..first+S-1 on the torus (npts = px*pz, even)
+// packed complex white noise: re = field fld0, im = field fld0 + 1, for
+// samples first..first+S-1 on the torus (npts = px*pz, even)
 // (first sample = *first_dev + first when first_dev is given: a captured CUDA
 // graph can advance the sample range between replays)
 __global__ void k_noise(int S, int npts, uint64_t seed, uint32_t level, int64_t first,
-                        const int64_t* __restrict__ first_dev, cplx* out) {
+                        const int64_t* __restrict__ first_dev, cplx* out, uint32_t fld0 = 0) {
     long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;   // (sample, pair)
     const int pairs = npts >> 1;
     if (g >= (long long)S * pairs) return;
@@ -50,7 +50,7 @@ __global__ void k_noise(int S, int npts, uint64_t seed, uint32_t level, int64_t 
     double y[2][2];
 #pragma unroll
     for (int fld = 0; fld < 2; ++fld) {
-        uint32_t c[4] = {(uint32_t)q, (uint32_t)fld, (uint32_t)sample, (uint32_t)(sample >> 32)};
+        uint32_t c[4] = {(uint32_t)q, fld0 + (uint32_t)fld, (uint32_t)sample, (uint32_t)(sample >> 32)};
         philox10(c, k0, k1);
         double a = u01(c[0], c[1]), b = u01(c[2], c[3]);
         double r = sqrt(-2.0 * log(a));
@@ -177,19 +177,32 @@ __global__ void k_sqrt_spec(int npts, const cplx* __restrict__ lam, double* sq) 
     sq[g] = v > 0.0 ? sqrt(v) : 0.0;
 }
 
-// window of the torus -> ln Ks and alpha (Phi(x) = erfc(-x/sqrt 2)/2), in place
-// into a compact [S][nz][nx] pair of real arrays
+// marginal transforms of a packed pair: the re lane is Gaussian (shift + z,
+// ln Ks) or uniform, the im lane uniform: lo + span Phi(z / sigma) with
+// Phi(x) = erfc(-x/sqrt 2)/2 (Y = F_Y^-1(F_Z(Z)), Sec. 3.1)
+struct PackTr {
+    int re_uniform;
+    double re_a, re_b;      // Gaussian: shift re_a; uniform: lo re_a, span re_b
+    double im_lo, im_span;
+};
+
+__device__ __forceinline__ double uniform_of(double z, double inv_sigma, double lo, double span) {
+    double gg = z * inv_sigma;
+    return lo + span * 0.5 * erfc(-gg / sqrt(2.0));
+}
+
+// window of the torus -> the pair's two fields, in place into a compact
+// [S][nz][nx] pair of real arrays (al may be null: the im lane is unused)
 __global__ void k_window(int S, int nx, int nz, int px, int pz, const cplx* __restrict__ d,
-                         double inv_sigma, double alo, double aspan, double* lk, double* al) {
+                         double inv_sigma, PackTr tr, double* lk, double* al) {
     long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int nc = nx * nz;
     if (g >= (long long)S * nc) return;
     int s = (int)(g / nc), q = (int)(g - (long long)s * nc);
     int j = q / nx, i = q - j * nx;
     cplx v = d[(size_t)s * px * pz + (size_t)j * px + i];
-    lk[g] = v.re;
-    double gg = v.im * inv_sigma;
-    al[g] = alo + aspan * 0.5 * erfc(-gg / sqrt(2.0));
+    lk[g] = tr.re_uniform ? uniform_of(v.re, inv_sigma, tr.re_a, tr.re_b) : v.re + tr.re_a;
+    if (al) al[g] = uniform_of(v.im, inv_sigma, tr.im_lo, tr.im_span);
 }
 
 // one 2x2 averaging step of both fields
@@ -202,7 +215,7 @@ __global__ void k_avg2(int S, int nxc, int nzc, const double* __restrict__ lf,
     int J = q / nxc, I = q - J * nxc;
     size_t f00 = (size_t)s * 4 * nc + (size_t)(2 * J) * fx + 2 * I, f01 = f00 + fx;
     lc[g] = 0.25 * (lf[f00] + lf[f00 + 1] + lf[f01] + lf[f01 + 1]);
-    ac[g] = 0.25 * (af[f00] + af[f00 + 1] + af[f01] + af[f01 + 1]);
+    if (ac) ac[g] = 0.25 * (af[f00] + af[f00 + 1] + af[f01] + af[f01 + 1]);
 }
 
 inline unsigned nb(long long w, int t = 256) { return (unsigned)((w + t - 1) / t); }
@@ -341,9 +354,20 @@ static int fftma_inplace(cplx* work, int cs, const rich_spectrum* sp, cudaStream
 
 constexpr size_t CHUNK_BYTES = 512ull << 20;
 
-int rich_fields_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int nz, uint32_t level,
-                       int64_t first, int S, int coarsen, double* lnKs, double* alpha,
-                       cudaStream_t st, const int64_t* first_dev) {
+// one packed pair of fields: noise streams fld0, fld0 + 1, their marginal
+// transforms and [S][nz>>c][nx>>c] outputs (out_im null: im lane unused)
+struct Pack {
+    uint32_t fld0;
+    PackTr tr;
+    double* out_re;
+    double* out_im;
+};
+
+// FFT-MA draws of npk packed pairs per sample, chunked over samples so the
+// complex work buffer stays within CHUNK_BYTES
+static int packs_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int nz, uint32_t level,
+                        int64_t first, int S, int coarsen, int npk, const Pack* pk, cudaStream_t st,
+                        const int64_t* first_dev) {
     if (!pow2(nx) || !pow2(nz) || coarsen < 0 || (nx >> coarsen) < 1 || (nz >> coarsen) < 1 ||
         bad_field(fd))
         return RICH_ERR_INVALID;
@@ -363,33 +387,66 @@ int rich_fields_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int nz, ui
     const double inv_sigma = 1.0 / sqrt(fd->sigma2);
     for (int s0 = 0; s0 < S; s0 += cap) {
         int cs = std::min(cap, S - s0);
-        rich_count_launch();
-        k_noise<<<nb((long long)cs * (npts / 2)), 256, 0, st>>>(cs, npts, fd->seed, level, first + s0,
-                                                                 first_dev, work);
-        if (int e = fftma_inplace(work, cs, sp, st)) return e;
-        // real scratch: two ping-pong pairs of [cs][nz][nx] arrays
-        const size_t blk = (size_t)cs * nx * nz;
-        double* bl[2] = {tmp, tmp + 2 * blk};
-        double* ba[2] = {tmp + blk, tmp + 3 * blk};
-        double* wl = coarsen ? bl[0] : lnKs + (size_t)s0 * nx * nz;
-        double* wa = coarsen ? ba[0] : alpha + (size_t)s0 * nx * nz;
-        rich_count_launch();
-        k_window<<<nb((long long)cs * nx * nz), 256, 0, st>>>(cs, nx, nz, px, pz, work, inv_sigma,
-                                                            fd->alpha_lo, fd->alpha_span, wl, wa);
-        int cx = nx, cz = nz, cur = 0;
-        for (int c = 0; c < coarsen; ++c) {
-            int ncx = cx / 2, ncz = cz / 2;
-            bool last = c == coarsen - 1;
-            double* ol = last ? lnKs + (size_t)s0 * nxo * nzo : bl[1 - cur];
-            double* oa = last ? alpha + (size_t)s0 * nxo * nzo : ba[1 - cur];
+        for (int k = 0; k < npk; ++k) {
+            const Pack& P = pk[k];
             rich_count_launch();
-            k_avg2<<<nb((long long)cs * ncx * ncz), 256, 0, st>>>(cs, ncx, ncz, bl[cur], ba[cur], ol, oa);
-            cur = 1 - cur;
-            cx = ncx; cz = ncz;
+            k_noise<<<nb((long long)cs * (npts / 2)), 256, 0, st>>>(cs, npts, fd->seed, level, first + s0,
+                                                                     first_dev, work, P.fld0);
+            if (int e = fftma_inplace(work, cs, sp, st)) return e;
+            // real scratch: two ping-pong pairs of [cs][nz][nx] arrays
+            const size_t blk = (size_t)cs * nx * nz;
+            double* bl[2] = {tmp, tmp + 2 * blk};
+            double* ba[2] = {tmp + blk, tmp + 3 * blk};
+            const bool im = P.out_im != nullptr;
+            double* wl = coarsen ? bl[0] : P.out_re + (size_t)s0 * nx * nz;
+            double* wa = !im ? nullptr : coarsen ? ba[0] : P.out_im + (size_t)s0 * nx * nz;
+            rich_count_launch();
+            k_window<<<nb((long long)cs * nx * nz), 256, 0, st>>>(cs, nx, nz, px, pz, work, inv_sigma, P.tr,
+                                                                wl, wa);
+            int cx = nx, cz = nz, cur = 0;
+            for (int c = 0; c < coarsen; ++c) {
+                int ncx = cx / 2, ncz = cz / 2;
+                bool last = c == coarsen - 1;
+                double* ol = last ? P.out_re + (size_t)s0 * nxo * nzo : bl[1 - cur];
+                double* oa = !im ? nullptr : last ? P.out_im + (size_t)s0 * nxo * nzo : ba[1 - cur];
+                rich_count_launch();
+                k_avg2<<<nb((long long)cs * ncx * ncz), 256, 0, st>>>(cs, ncx, ncz, bl[cur], im ? ba[cur] : nullptr,
+                                                                       ol, oa);
+                cur = 1 - cur;
+                cx = ncx; cz = ncz;
+            }
         }
     }
     RICH_CUDA(cudaGetLastError());
     return 0;
+}
+
+int rich_fields_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int nz, uint32_t level,
+                       int64_t first, int S, int coarsen, double* lnKs, double* alpha,
+                       cudaStream_t st, const int64_t* first_dev) {
+    const Pack pk{0u, PackTr{0, 0.0, 0.0, fd->alpha_lo, fd->alpha_span}, lnKs, alpha};
+    return packs_device(ctx, fd, nx, nz, level, first, S, coarsen, 1, &pk, st, first_dev);
+}
+
+// The five soil fields (Table soilparams): streams 0/1 ln Ks (lnks_mean + Z)
+// and alpha, 2/3 n and theta_s, 4 theta_r (the im lane of the last pack
+// unused); theta fields are skipped when their outputs are null
+int rich_soil_device(rich_ctx* ctx, const rich_field_t* fd, const rich_soil_model_t* sm, int nx, int nz,
+                     uint32_t level, int64_t first, int S, int coarsen, const rich_soil_t* out,
+                     cudaStream_t st) {
+    if (!(sm->n_span >= 0) || !(sm->theta_s_span >= 0) || !(sm->theta_r_span >= 0) ||
+        !(sm->lnks_mean > -700 && sm->lnks_mean < 700))
+        return RICH_ERR_INVALID;
+    Pack pk[3];
+    int npk = 0;
+    pk[npk++] = Pack{0u, PackTr{0, sm->lnks_mean, 0.0, fd->alpha_lo, fd->alpha_span}, out->lnKs, out->alpha};
+    if (out->theta_s)
+        pk[npk++] = Pack{2u, PackTr{1, sm->n_lo, sm->n_span, sm->theta_s_lo, sm->theta_s_span}, out->n, out->theta_s};
+    else
+        pk[npk++] = Pack{2u, PackTr{1, sm->n_lo, sm->n_span, 0.0, 0.0}, out->n, nullptr};
+    if (out->theta_r)
+        pk[npk++] = Pack{4u, PackTr{1, sm->theta_r_lo, sm->theta_r_span, 0.0, 0.0}, out->theta_r, nullptr};
+    return packs_device(ctx, fd, nx, nz, level, first, S, coarsen, npk, pk, st, nullptr);
 }
 
 namespace {
@@ -441,13 +498,13 @@ int rich_fields_pair_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int n
         if (int e = fftma_inplace(wf, cs, spf, st)) return e;
         if (int e = fftma_inplace(wc, cs, spc, st)) return e;
         rich_count_launch();
-        k_window<<<nb((long long)cs * nx * nz), 256, 0, st>>>(cs, nx, nz, px, pz, wf, inv_sigma, fd->alpha_lo,
-                                                            fd->alpha_span, lk_f + (size_t)s0 * nx * nz,
+        const PackTr tr{0, 0.0, 0.0, fd->alpha_lo, fd->alpha_span};
+        k_window<<<nb((long long)cs * nx * nz), 256, 0, st>>>(cs, nx, nz, px, pz, wf, inv_sigma, tr,
+                                                            lk_f + (size_t)s0 * nx * nz,
                                                             al_f + (size_t)s0 * nx * nz);
         const int ncx = nx / 2, ncz = nz / 2;
         rich_count_launch();
-        k_window<<<nb((long long)cs * ncx * ncz), 256, 0, st>>>(cs, ncx, ncz, px / 2, pz / 2, wc, inv_sigma,
-                                                              fd->alpha_lo, fd->alpha_span,
+        k_window<<<nb((long long)cs * ncx * ncz), 256, 0, st>>>(cs, ncx, ncz, px / 2, pz / 2, wc, inv_sigma, tr,
                                                               lk_c + (size_t)s0 * ncx * ncz,
                                                               al_c + (size_t)s0 * ncx * ncz);
     }

@@ -1,0 +1,970 @@
+// Device side of the persistent fused solver (kernel templates), shared by
+// the translation units that instantiate them.
+//
+// Each CTA takes samples from an atomic queue and runs, for its sample, the
+// complete method of arXiv 1903.08741 Sec. 4: backward-Euler time loop,
+// modified Picard iteration on the mixed form (Eq. Mixed_based_3), and for
+// every Picard step the cell-centred multigrid solve (five-point harmonic-mean
+// stencil, Eq. five_stencil; red-black Gauss-Seidel; 1/4-sum restriction and
+// piecewise-constant prolongation, Eq. transfer; coarse operators by
+// rediscretisation with arithmetic means of face coefficients, Fig.
+// diffUpscale; exact coarsest solve).  All control flow is per CTA and uniform
+// (decisions come from block-wide reductions), so a sample never waits for
+// another and there is no host round trip inside a solve.
+//
+// Memory: every CTA owns one scratch slot holding its sample's hierarchy; the
+// slots of the resident CTAs are largely L2 (small grids: L1) resident.
+// Scratch arrays are read with plain loads (they are rewritten inside the
+// kernel; __syncthreads orders the accesses).
+//
+// Precision and instruction budget.  GB300 issues 2 FP64 FMAs per SM and
+// clock (1/64 of its FP32 rate), so the FP64 V-cycle is written to minimise
+// FP64 instructions:
+//   * every level stores the Jacobi-scaled coefficients w = T/D of its four
+//     faces and the scaled right-hand side f/D, so a Gauss-Seidel update is
+//     dp_P = f_P/D_P + sum w dp_nb (4 FMAs instead of 6 operations);
+//   * after a black half-sweep the black residuals are zero up to rounding
+//     (each black value was just solved from its red neighbours), so the
+//     restriction after pre-smoothing and the stopping norm after
+//     post-smoothing evaluate red cells only (exactly the same quantities in
+//     exact arithmetic; full evaluation when nu = 0);
+//   * divisions by dt are multiplications by 1/dt.
+// TM = double is the FP64 path (the oracle's algorithm and stopping tests);
+// TM = float runs FP32 V-cycles (unscaled coefficients: FP32 operations are
+// cheap, bytes are not) inside an FP64 defect-correction loop that performs
+// a tunable number of V-cycles per FP64 defect (FP64 Picard residual, FP64
+// outer residual, FP64 correction and stopping norm).
+
+#pragma once
+#include "rich_internal.cuh"
+#include <math.h>
+
+// launch parameters and slot layout, shared across translation units
+namespace rich_fused {
+
+constexpr unsigned long long ABS_MASK = 0x7FFFFFFFFFFFFFFFull;
+constexpr unsigned long long INF_BITS = 0x7FF0000000000000ull;
+constexpr int MAXL = RICH_MAX_LEVELS;
+constexpr int MIXED_INNER_DEFAULT = 2;   // FP32 V-cycles per FP64 defect evaluation
+
+// FP64 unscaled operator (all levels): faces, mass term, diagonal, Dirichlet faces
+enum { A_TX, A_TZ, A_CDT, A_D, A_TBT, A_TBB, N64 };
+// multigrid arrays in the cycle precision.  FP64: wE wW wN wS q=1/D fh dp
+// (D shared with the FP64 operator).  FP32: Tx Tz D 1/D f dp.
+enum { B_0, B_1, B_2, B_3, B_4, B_5, B_6, NMG };
+
+struct FParams {
+    int S, nlev, mixed;
+    int nx[MAXL], nz[MAXL];
+    unsigned mnx[MAXL], mhx[MAXL];          // magic reciprocals of nx and nx/2
+    long long o64[MAXL][N64];               // byte offsets in the slot (-1: absent)
+    long long omg[MAXL][NMG];
+    long long o_f64, o_dp64, o_p, o_thold, o_Ks, o_a, o_K, o_th;
+    long long slot_bytes;
+    char* scratch;
+    const double* lnKs;
+    const double* alpha;
+    double alpha_scale;
+    double* qoi;
+    double* p_final;
+    int32_t* status;
+    int64_t* pic_total;
+    int64_t* mg_total;
+    int32_t* maxpic;
+    int* queue;
+    int nsteps, picard_maxit, mg_maxit, nu1, nu2, gamma;
+    double inv_dt, tr, ts, p_top, p_bot, p_init, picard_tol, mg_tol, h, two_over_h2;
+    // adjoint (k_adjoint only)
+    int mixed_inner;            // FP32 V-cycles per FP64 defect (mixed path)
+    int ckpt_every, adj_maxit, adj_inner;
+    double adj_tol;
+    long long o_ckpt, o_seg, o_lam, o_rhs, o_r, o_dE, o_dW, o_dN, o_dS, o_dg, o_g;
+    double* g_out;
+    // closure 1 (van Genuchten-Mualem): per-cell n, theta_s, theta_r inputs
+    // (theta arrays may be null: the problem's constants), continuation
+    // shifts, and the slot arrays n, m = 1 - 1/n, theta_r, theta_s
+    int closure;
+    double alpha_shift, n_shift, init_decay;
+    const double* n_in;
+    const double* ts_in;
+    const double* tr_in;
+    long long o_n, o_m, o_trc, o_tsc;
+};
+
+// launch shapes of the van Genuchten-Mualem instantiations (fused_vg.cu)
+int rich_vg_occupancy(const FParams& P, size_t smem, int nt, int* occ);
+void rich_vg_launch(const FParams& P, int grid, size_t smem, int nt, cudaStream_t st);
+
+}  // namespace rich_fused
+
+namespace {
+using namespace rich_fused;
+
+// c / d for c * d < 2^32 (m = floor(2^32 / d) + 1), d = 1 handled apart
+__device__ __forceinline__ int fdiv(int c, int d, unsigned m) {
+    return d == 1 ? c : (int)__umulhi((unsigned)c, m);
+}
+
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+    return (unsigned long long)__double_as_longlong(x) & ABS_MASK;
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+
+// block-wide max of v, returned to every thread
+__device__ __forceinline__ unsigned long long block_max(unsigned long long v, unsigned long long* red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_max_u64(v);
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < nw ? red[lane] : 0ull;
+        v = warp_max_u64(v);
+        if (lane == 0) red[32] = v;
+    }
+    __syncthreads();
+    unsigned long long r = red[32];
+    __syncthreads();
+    return r;
+}
+
+struct Lv64 {
+    int nx, nz, nc;
+    unsigned mnx;
+    double *Tx, *Tz, *Cdt, *D, *Tbt, *Tbb;
+};
+
+// multigrid level in cycle precision T.  FP64 (scaled): c = {wE, wW, wN, wS},
+// q = 1/D, f = f/D (the coarsest level keeps f unscaled for the direct solve).
+// FP32 (unscaled): c = {Tx, Tz, -, -}, q = 1/D, f = f.
+template <typename T>
+struct Lv {
+    int nx, nz, hx, nc;
+    unsigned mnx, mhx;
+    T *c0, *c1, *c2, *c3, *D, *q, *f, *dp;
+};
+
+template <typename T> struct Scaled { static constexpr bool value = sizeof(T) == 8; };
+
+// Gauss-Seidel value of cell P from its current neighbours
+template <typename T>
+__device__ __forceinline__ T gs_value(const Lv<T>& L, int P, int i, int j) {
+    if constexpr (Scaled<T>::value) {
+        T v = L.f[P];
+        if (i < L.nx - 1) v += L.c0[P] * L.dp[P + 1];
+        if (i > 0)        v += L.c1[P] * L.dp[P - 1];
+        if (j < L.nz - 1) v += L.c2[P] * L.dp[P + L.nx];
+        if (j > 0)        v += L.c3[P] * L.dp[P - L.nx];
+        return v;
+    } else {
+        T s = T(0);
+        if (i < L.nx - 1) s += L.c0[P] * L.dp[P + 1];
+        if (i > 0)        s += L.c0[P - 1] * L.dp[P - 1];
+        if (j < L.nz - 1) s += L.c1[P] * L.dp[P + L.nx];
+        if (j > 0)        s += L.c1[P - L.nx] * L.dp[P - L.nx];
+        return (L.f[P] + s) * L.q[P];
+    }
+}
+
+// residual f - A dp at cell P (unscaled)
+template <typename T>
+__device__ __forceinline__ T residual(const Lv<T>& L, int P, int i, int j) {
+    if constexpr (Scaled<T>::value) {
+        return L.D[P] * (gs_value(L, P, i, j) - L.dp[P]);
+    } else {
+        T s = T(0);
+        if (i < L.nx - 1) s += L.c0[P] * L.dp[P + 1];
+        if (i > 0)        s += L.c0[P - 1] * L.dp[P - 1];
+        if (j < L.nz - 1) s += L.c1[P] * L.dp[P + L.nx];
+        if (j > 0)        s += L.c1[P - L.nx] * L.dp[P - L.nx];
+        return L.f[P] - (L.D[P] * L.dp[P] - s);
+    }
+}
+
+// one colour of red-black Gauss-Seidel over the level (red: i + j even)
+template <typename T>
+__device__ __forceinline__ void rbgs(const Lv<T>& L, int colour) {
+    const int n = L.hx * L.nz;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        int j = fdiv(c, L.hx, L.mhx);
+        int i = 2 * (c - j * L.hx) + ((j + colour) & 1);
+        L.dp[j * L.nx + i] = gs_value(L, j * L.nx + i, i, j);
+    }
+    __syncthreads();
+}
+
+// restricted residual (Eq. transfer, R = 1/4 sum of the children); after a
+// black half-sweep only the two red children carry a residual
+template <typename T>
+__device__ __forceinline__ void resid_restrict(const Lv<T>& F, const Lv<T>& C, bool red_only,
+                                               bool coarsest) {
+    for (int c = threadIdx.x; c < C.nc; c += blockDim.x) {
+        int J = fdiv(c, C.nx, C.mnx), I = c - J * C.nx;
+        int i = 2 * I, j = 2 * J, P = j * F.nx + i;
+        T r00 = residual(F, P, i, j);
+        T r11 = residual(F, P + F.nx + 1, i + 1, j + 1);
+        T sum;
+        if (red_only) {
+            sum = r00 + r11;
+        } else {
+            T r10 = residual(F, P + 1, i + 1, j);
+            T r01 = residual(F, P + F.nx, i, j + 1);
+            sum = r00 + r10 + r01 + r11;
+        }
+        T fc = T(0.25) * sum;
+        if constexpr (Scaled<T>::value) { if (!coarsest) fc *= C.q[c]; }
+        C.f[c] = fc;
+        C.dp[c] = T(0);
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void prolong(const Lv<T>& F, const Lv<T>& C) {
+    for (int c = threadIdx.x; c < C.nc; c += blockDim.x) {
+        int J = fdiv(c, C.nx, C.mnx), I = c - J * C.nx;
+        T e = C.dp[c];
+        int P = (2 * J) * F.nx + 2 * I;
+        F.dp[P] += e; F.dp[P + 1] += e; F.dp[P + F.nx] += e; F.dp[P + F.nx + 1] += e;
+    }
+    __syncthreads();
+}
+
+// exact coarsest solve: Gaussian elimination of the assembled five-point
+// matrix by warp 0 in shared memory (symmetric, diagonally dominant)
+template <typename T>
+__device__ __forceinline__ void coarse_solve(int nx, int nz, const T* Tx, const T* Tz, const T* D,
+                                             const T* f, T* dp, T* A) {
+    if (threadIdx.x < 32) {
+        const int nn = nx * nz, ld = nn + 1, lane = threadIdx.x;
+        for (int r = lane; r < nn; r += 32) {
+            for (int c = 0; c < nn; ++c) A[r * ld + c] = T(0);
+            int j = r / nx, i = r - j * nx;
+            A[r * ld + r] = D[r];
+            if (i < nx - 1) A[r * ld + r + 1] = -Tx[r];
+            if (i > 0)      A[r * ld + r - 1] = -Tx[r - 1];
+            if (j < nz - 1) A[r * ld + r + nx] = -Tz[r];
+            if (j > 0)      A[r * ld + r - nx] = -Tz[r - nx];
+            A[r * ld + nn] = f[r];
+        }
+        __syncwarp();
+        for (int k = 0; k < nn; ++k) {
+            for (int r = k + 1 + lane; r < nn; r += 32) {
+                T m = A[r * ld + k] / A[k * ld + k];
+                for (int c = k; c <= nn; ++c) A[r * ld + c] -= m * A[k * ld + c];
+            }
+            __syncwarp();
+        }
+        if (lane == 0) {
+            for (int k = nn - 1; k >= 0; --k) {
+                T sum = A[k * ld + nn];
+                for (int c = k + 1; c < nn; ++c) sum -= A[k * ld + c] * A[c * ld + nn];
+                A[k * ld + nn] = sum / A[k * ld + k];
+            }
+        }
+        __syncwarp();
+        for (int r = lane; r < nn; r += 32) dp[r] = A[r * ld + nn];
+    }
+    __syncthreads();
+}
+
+// f0: unscaled finest right-hand side, used by the direct solve when the
+// finest grid is also the coarsest (FP64 levels keep f/D otherwise)
+// exact solve on the coarsest level c (FP64 levels: the unscaled FP64
+// operator; f0 is the unscaled right-hand side when c is the finest level)
+template <typename T>
+__device__ __forceinline__ void coarsest(const Lv<T>* L, const Lv64* L64, int c, T* A, const T* f0) {
+    if constexpr (Scaled<T>::value)
+        coarse_solve<T>(L64[c].nx, L64[c].nz, L64[c].Tx, L64[c].Tz, L64[c].D, c == 0 ? f0 : L[c].f,
+                        L[c].dp, A);
+    else
+        coarse_solve<T>(L[c].nx, L[c].nz, L[c].c0, L[c].c1, L[c].D, L[c].f, L[c].dp, A);
+}
+
+// one cycle of index gamma >= 2 (W-cycle for gamma = 2, the paper's cycle,
+// Sec. 4.2): every visit of level l < nlev-2 runs gamma cycles on level l+1,
+// the visit of nlev-2 one exact coarsest solve.  The recursion is unrolled
+// into a depth-first walk whose per-level visit counts sit in 4-bit fields of
+// one register (no device stack); called uniformly by the whole CTA.
+template <typename T>
+__device__ void gcycle(const Lv<T>* L, const Lv64* L64, int nlev, int nu1, int nu2, int gamma, T* A,
+                       const T* f0) {
+    static_assert(RICH_MAX_LEVELS * 4 <= 64, "visit counters must fit one 64-bit word");
+    unsigned long long cnt = 0;
+    int l = 0;
+    for (;;) {
+        for (; l < nlev - 1; ++l) {                       // enter l: pre-smooth, restrict
+            for (int it = 0; it < nu1; ++it) { rbgs(L[l], 0); rbgs(L[l], 1); }
+            resid_restrict(L[l], L[l + 1], nu1 > 0, l + 1 == nlev - 1);
+            cnt &= ~(15ull << (4 * l));
+        }
+        coarsest<T>(L, L64, nlev - 1, A, f0);
+        for (;;) {                                        // leave l+1, back on l
+            if (--l < 0) return;
+            cnt += 1ull << (4 * l);
+            const int reps = (l + 1 == nlev - 1) ? 1 : gamma;
+            if ((int)((cnt >> (4 * l)) & 15) < reps) { ++l; break; }   // cycle l+1 again
+            prolong(L[l], L[l + 1]);
+            for (int it = 0; it < nu2; ++it) { rbgs(L[l], 0); rbgs(L[l], 1); }
+        }
+    }
+}
+
+template <typename T>
+__device__ void vcycle(const Lv<T>* L, const Lv64* L64, int nlev, int nu1, int nu2, T* A,
+                       const T* f0) {
+    for (int l = 0; l < nlev - 1; ++l) {
+        for (int it = 0; it < nu1; ++it) { rbgs(L[l], 0); rbgs(L[l], 1); }
+        resid_restrict(L[l], L[l + 1], nu1 > 0, l + 1 == nlev - 1);
+    }
+    coarsest<T>(L, L64, nlev - 1, A, f0);
+    for (int l = nlev - 2; l >= 0; --l) {
+        prolong(L[l], L[l + 1]);
+        for (int it = 0; it < nu2; ++it) { rbgs(L[l], 0); rbgs(L[l], 1); }
+    }
+}
+
+// ||f - A dp||_inf on a level after a cycle ending with a black half-sweep
+// (red cells only) or, with red_only false, over every cell
+template <typename T>
+__device__ __forceinline__ unsigned long long resid_norm(const Lv<T>& L, bool red_only,
+                                                         unsigned long long* red) {
+    unsigned long long m = 0;
+    if (red_only) {
+        const int n = L.hx * L.nz;
+        for (int c = threadIdx.x; c < n; c += blockDim.x) {
+            int j = fdiv(c, L.hx, L.mhx);
+            int i = 2 * (c - j * L.hx) + (j & 1);
+            unsigned long long b = abs_bits((double)residual(L, j * L.nx + i, i, j));
+            m = b > m ? b : m;
+        }
+    } else {
+        for (int q = threadIdx.x; q < L.nc; q += blockDim.x) {
+            int j = fdiv(q, L.nx, L.mnx), i = q - j * L.nx;
+            unsigned long long b = abs_bits((double)residual(L, q, i, j));
+            m = b > m ? b : m;
+        }
+    }
+    return block_max(m, red);
+}
+
+// van Genuchten-Mualem closure at p < 0 (Eqs. Sw, sc_van, Krw) with
+// m = 1 - 1/n and an = (a|p|)^n: S = (1 + an)^-m, K_rw = S^(1/2) (1 - (an /
+// (1 + an))^m)^2 (1 - S^(1/m) = an/(1 + an) exactly) and dS/dp = m n S an /
+// ((1 + an) |p|), the Eq. sc_van capacity divided by theta_s - theta_r.  In
+// logarithms: l = log(a|p|), an = exp(n l), S = exp(-m log1p(an)) and
+// (an / (1 + an))^m = exp(m (n l - log1p(an))).
+__device__ __forceinline__ double vg_sat(double a, double n, double m, double p) {
+    return exp(-m * log1p(exp(n * log(-a * p))));
+}
+
+__device__ __forceinline__ void vg_eval(double a, double n, double m, double p, double& S, double& krw,
+                                        double& dS) {
+    const double nl = n * log(-a * p);
+    const double an = exp(nl);
+    const double l1 = log1p(an);
+    S = exp(-m * l1);
+    const double b = 1.0 - exp(m * (nl - l1));
+    krw = sqrt(S) * b * b;
+    dS = m * n * S * an / ((1.0 + an) * (-p));
+}
+
+// CTA-cooperative building blocks of one sample's solve.  Every method is
+// called by all threads of the CTA and ends with the CTA synchronised.
+template <typename TM, bool WC = false, int CL = 0>
+struct Cta {
+    static constexpr bool SC = Scaled<TM>::value;
+    const FParams& P;
+    Lv64* L64;
+    Lv<TM>* LM;
+    TM* Amat;
+    unsigned long long* red;
+    double *f64, *dp64, *p, *thold, *Ks, *aa, *K, *th;
+    double *nn, *mm, *trc, *tsc;          // closure 1: per-cell n, m, theta_r, theta_s
+    int nx, nz, nc, nlev, tid, nt;
+    double h, t2h, idt, tr, ts;
+
+    __device__ Cta(const FParams& P_, char* slot, Lv64* l64, Lv<TM>* lm, TM* A, unsigned long long* r)
+        : P(P_), L64(l64), LM(lm), Amat(A), red(r) {
+        f64 = (double*)(slot + P.o_f64);
+        dp64 = SC ? (double*)LM[0].dp : (double*)(slot + P.o_dp64);
+        p = (double*)(slot + P.o_p);
+        thold = (double*)(slot + P.o_thold);
+        Ks = (double*)(slot + P.o_Ks);
+        aa = (double*)(slot + P.o_a);
+        K = (double*)(slot + P.o_K);
+        th = (double*)(slot + P.o_th);
+        if constexpr (CL == 1) {
+            nn = (double*)(slot + P.o_n); mm = (double*)(slot + P.o_m);
+            trc = (double*)(slot + P.o_trc); tsc = (double*)(slot + P.o_tsc);
+        } else {
+            nn = mm = trc = tsc = nullptr;
+        }
+        nx = L64[0].nx; nz = L64[0].nz; nc = L64[0].nc; nlev = P.nlev;
+        tid = threadIdx.x; nt = blockDim.x;
+        h = P.h; t2h = P.two_over_h2; idt = P.inv_dt; tr = P.tr; ts = P.ts;
+    }
+
+    // conductivity of cell q's soil at head pp (Dirichlet faces, QoI)
+    __device__ __forceinline__ double k_at(int q, double pp) const {
+        if constexpr (CL == 0) {
+            return pp < 0.0 ? Ks[q] * exp(aa[q] * pp) : Ks[q];
+        } else {
+            if (!(pp < 0.0)) return Ks[q];
+            double S, krw, dS;
+            vg_eval(aa[q], nn[q], mm[q], pp, S, krw, dS);
+            return Ks[q] * krw;
+        }
+    }
+
+    // Ks, alpha * scale + shift, (closure 1: n + shift, m, theta_r, theta_s),
+    // initial head (uniform, or p_init (1 - exp(-init_decay z)) at the cell
+    // centres, Eq. travellingwave), Dirichlet faces (fixed for the solve)
+    __device__ void setup(int s) {
+        const Lv64& F = L64[0];
+        const size_t o = (size_t)s * nc;
+        const double* lk = P.lnKs + o;
+        const double* al = P.alpha + o;
+        for (int q = tid; q < nc; q += nt) {
+            Ks[q] = exp(lk[q]);
+            aa[q] = al[q] * P.alpha_scale + P.alpha_shift;
+            if (P.init_decay > 0.0) {
+                const int j = fdiv(q, nx, F.mnx);
+                p[q] = P.p_init * (1.0 - exp(-P.init_decay * (j + 0.5) * h));
+            } else {
+                p[q] = P.p_init;
+            }
+            if constexpr (CL == 1) {
+                const double n = P.n_in[o + q] + P.n_shift;
+                nn[q] = n;
+                mm[q] = 1.0 - 1.0 / n;
+                trc[q] = P.tr_in ? P.tr_in[o + q] : tr;
+                tsc[q] = P.ts_in ? P.ts_in[o + q] : ts;
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < nx; i += nt) {
+            int T = (nz - 1) * nx + i, B = i;
+            F.Tbt[i] = t2h * k_at(T, P.p_top);
+            F.Tbb[i] = t2h * k_at(B, P.p_bot);
+        }
+        __syncthreads();
+        for (int l = 1; l < nlev; ++l) {
+            for (int I = tid; I < L64[l].nx; I += nt) {
+                L64[l].Tbt[I] = 0.25 * (0.5 * (L64[l - 1].Tbt[2 * I] + L64[l - 1].Tbt[2 * I + 1]));
+                L64[l].Tbb[I] = 0.25 * (0.5 * (L64[l - 1].Tbb[2 * I] + L64[l - 1].Tbb[2 * I + 1]));
+            }
+            __syncthreads();
+        }
+    }
+
+    // theta^n of the step's old head
+    __device__ void theta_old() {
+        for (int q = tid; q < nc; q += nt) {
+            double pp = p[q];
+            if constexpr (CL == 0) {
+                thold[q] = pp < 0.0 ? tr + (ts - tr) * exp(aa[q] * pp) : ts;
+            } else {
+                const double r = trc[q], t = tsc[q];
+                thold[q] = pp < 0.0 ? r + (t - r) * vg_sat(aa[q], nn[q], mm[q], pp) : t;
+            }
+        }
+        __syncthreads();
+    }
+
+    // Picard system at p (Gardner closure, harmonic faces, f = -R), all levels;
+    // returns ||f||_inf as a bit pattern
+    __device__ unsigned long long assemble() {
+        const Lv64& F = L64[0];
+        const Lv<TM>& M0 = LM[0];
+        for (int q = tid; q < nc; q += nt) {
+            double pp = p[q], ks = Ks[q];
+            if constexpr (CL == 0) {
+                if (pp < 0.0) {
+                    double a = aa[q];
+                    double E = exp(a * pp);
+                    K[q] = ks * E;
+                    th[q] = tr + (ts - tr) * E;
+                    F.Cdt[q] = ((ts - tr) * a * E) * idt;
+                } else {
+                    K[q] = ks; th[q] = ts; F.Cdt[q] = 0.0;
+                }
+            } else {
+                const double r = trc[q], t = tsc[q];
+                if (pp < 0.0) {
+                    double S, krw, dS;
+                    vg_eval(aa[q], nn[q], mm[q], pp, S, krw, dS);
+                    K[q] = ks * krw;
+                    th[q] = r + (t - r) * S;
+                    F.Cdt[q] = ((t - r) * dS) * idt;
+                } else {
+                    K[q] = ks; th[q] = t; F.Cdt[q] = 0.0;
+                }
+            }
+        }
+        __syncthreads();
+        for (int q = tid; q < nc; q += nt) {
+            int j = fdiv(q, nx, F.mnx), i = q - j * nx;
+            double kp = K[q];
+            if (i < nx - 1) { double ke = K[q + 1]; F.Tx[q] = t2h * kp * ke / (kp + ke); }
+            else F.Tx[q] = 0.0;
+            if (j < nz - 1) { double kn = K[q + nx]; F.Tz[q] = t2h * kp * kn / (kp + kn); }
+            else F.Tz[q] = 0.0;
+        }
+        __syncthreads();
+        unsigned long long m = 0;
+        for (int q = tid; q < nc; q += nt) {
+            int j = fdiv(q, nx, F.mnx), i = q - j * nx;
+            double pp = p[q];
+            double R = (th[q] - thold[q]) * idt;
+            double d = F.Cdt[q];
+            double te = 0.0, tw = 0.0, tn = 0.0, tsf = 0.0;
+            if (i < nx - 1) { te = F.Tx[q];     R += -te * (p[q + 1] - pp); d += te; }
+            if (i > 0)      { tw = F.Tx[q - 1]; R += -tw * (p[q - 1] - pp); d += tw; }
+            if (j < nz - 1) { tn = F.Tz[q];     R += -tn * (p[q + nx] - pp) - tn * h; d += tn; }
+            else { double t = F.Tbt[i]; R += -t * (P.p_top - pp) - t * h / 2.0; d += t; }
+            if (j > 0)      { tsf = F.Tz[q - nx]; R += -tsf * (p[q - nx] - pp) + tsf * h; d += tsf; }
+            else { double t = F.Tbb[i]; R += t * (pp - P.p_bot) + t * h / 2.0; d += t; }
+            F.D[q] = d;
+            f64[q] = -R;
+            dp64[q] = 0.0;
+            if constexpr (SC) {
+                double inv = 1.0 / d;
+                M0.q[q] = inv;
+                M0.c0[q] = te * inv; M0.c1[q] = tw * inv; M0.c2[q] = tn * inv; M0.c3[q] = tsf * inv;
+                M0.f[q] = -R * inv;
+            } else {
+                M0.c0[q] = (TM)te; M0.c1[q] = (TM)tn; M0.D[q] = (TM)d;
+                M0.q[q] = (TM)(1.0f / (float)d);
+                M0.f[q] = (TM)(-R); M0.dp[q] = TM(0);
+            }
+            unsigned long long b = abs_bits(R);
+            m = b > m ? b : m;
+        }
+        const unsigned long long fb = block_max(m, red);
+        // coarse operators (Fig. diffUpscale)
+        for (int l = 1; l < nlev; ++l) {
+            const Lv64& Fl = L64[l - 1];
+            const Lv64& Cl = L64[l];
+            const Lv<TM>& Ml = LM[l];
+            const int fx = Fl.nx;
+            for (int c = tid; c < Cl.nc; c += nt) {
+                int J = fdiv(c, Cl.nx, Cl.mnx), I = c - J * Cl.nx;
+                int f00 = (2 * J) * fx + 2 * I, f01 = f00 + fx;
+                double cd = 0.25 * (Fl.Cdt[f00] + Fl.Cdt[f00 + 1] + Fl.Cdt[f01] + Fl.Cdt[f01 + 1]);
+                double d = cd, te = 0.0, tw = 0.0, tn = 0.0, tsf = 0.0;
+                if (I < Cl.nx - 1) { te = 0.25 * (0.5 * (Fl.Tx[f00 + 1] + Fl.Tx[f01 + 1])); d += te; }
+                if (I > 0)         { tw = 0.25 * (0.5 * (Fl.Tx[f00 - 1] + Fl.Tx[f01 - 1])); d += tw; }
+                if (J < Cl.nz - 1) { tn = 0.25 * (0.5 * (Fl.Tz[f01] + Fl.Tz[f01 + 1])); d += tn; }
+                else d += Cl.Tbt[I];
+                if (J > 0)         { tsf = 0.25 * (0.5 * (Fl.Tz[f00 - fx] + Fl.Tz[f00 - fx + 1])); d += tsf; }
+                else d += Cl.Tbb[I];
+                Cl.Tx[c] = te; Cl.Tz[c] = tn; Cl.Cdt[c] = cd; Cl.D[c] = d;
+                if constexpr (SC) {
+                    double inv = 1.0 / d;
+                    Ml.q[c] = inv;
+                    Ml.c0[c] = te * inv; Ml.c1[c] = tw * inv; Ml.c2[c] = tn * inv; Ml.c3[c] = tsf * inv;
+                } else {
+                    Ml.c0[c] = (TM)te; Ml.c1[c] = (TM)tn; Ml.D[c] = (TM)d;
+                    Ml.q[c] = (TM)(1.0f / (float)d);
+                }
+            }
+            __syncthreads();
+        }
+        return fb;
+    }
+
+    // one multigrid cycle: the V-cycle, or (WC, a separate kernel
+    // instantiation so the V kernels keep their register allocation) the
+    // cycle of index P.gamma
+    __device__ void mgcycle(const TM* f0) {
+        if constexpr (WC) gcycle<TM>(LM, L64, nlev, P.nu1, P.nu2, P.gamma, Amat, f0);
+        else vcycle<TM>(LM, L64, nlev, P.nu1, P.nu2, Amat, f0);
+    }
+
+    // FP64 residual f - A x of the finest operator at cell q
+    __device__ __forceinline__ double resid64(const double* f, const double* x, int q) const {
+        const Lv64& F = L64[0];
+        int j = fdiv(q, nx, F.mnx), i = q - j * nx;
+        double sn = 0.0;
+        if (i < nx - 1) sn += F.Tx[q] * x[q + 1];
+        if (i > 0)      sn += F.Tx[q - 1] * x[q - 1];
+        if (j < nz - 1) sn += F.Tz[q] * x[q + nx];
+        if (j > 0)      sn += F.Tz[q - nx] * x[q - nx];
+        return f[q] - (F.D[q] * x[q] - sn);
+    }
+
+    // multigrid solve of A dp = f from dp = 0 (set up by assemble()); stops
+    // when ||f - A dp||_inf < mg_tol max(1, ||f||_inf).  Returns false when a
+    // norm is not finite.
+    __device__ bool mg_solve(unsigned long long fb, long long& mg_tot, int& status) {
+        const Lv<TM>& M0 = LM[0];
+        const double fn = __longlong_as_double((long long)fb);
+        const double target = P.mg_tol * (fn > 1.0 ? fn : 1.0);
+        double rn = fn;
+        int cyc = 0;
+        while (rn >= target && cyc < P.mg_maxit) {
+            unsigned long long rb;
+            if constexpr (SC) {
+                mgcycle((const TM*)f64);
+                ++cyc;
+                rb = resid_norm<TM>(M0, P.nu2 > 0 && nlev > 1, red);
+            } else {
+                for (int in = 0; in < P.mixed_inner && cyc < P.mg_maxit; ++in) {
+                    mgcycle(nullptr);
+                    ++cyc;
+                }
+                // dp += e in FP64, then the FP64 defect: stopping norm and the
+                // next FP32 right-hand side
+                unsigned long long mm = 0;
+                for (int q = tid; q < nc; q += nt) dp64[q] += (double)M0.dp[q];
+                __syncthreads();
+                for (int q = tid; q < nc; q += nt) {
+                    double r = resid64(f64, dp64, q);
+                    M0.f[q] = (TM)r;
+                    M0.dp[q] = TM(0);
+                    unsigned long long b = abs_bits(r);
+                    mm = b > mm ? b : mm;
+                }
+                rb = block_max(mm, red);
+            }
+            if (rb > INF_BITS - 1) { mg_tot += cyc; return false; }
+            rn = __longlong_as_double((long long)rb);
+        }
+        mg_tot += cyc;
+        if (!(rn < target)) status = max(status, (int)RICH_MG_MAXIT);
+        return true;
+    }
+
+    // one implicit-Euler step by modified Picard (Sec. 4.1); returns false if
+    // the sample failed (status set)
+    __device__ bool time_step(long long& pic_tot, long long& mg_tot, int& maxpic, int& status) {
+        theta_old();
+        int k = 0;
+        bool alive = true;
+        for (;;) {
+            const unsigned long long fb = assemble();
+            if (fb > INF_BITS - 1) { status = max(status, (int)RICH_NONFINITE); alive = false; break; }
+            if (!mg_solve(fb, mg_tot, status)) { status = max(status, (int)RICH_NONFINITE); alive = false; break; }
+            unsigned long long dm = 0;
+            for (int q = tid; q < nc; q += nt) {
+                double d = dp64[q];
+                p[q] += d;
+                unsigned long long b = abs_bits(d);
+                dm = b > dm ? b : dm;
+            }
+            const unsigned long long db = block_max(dm, red);
+            ++k;
+            ++pic_tot;
+            if (db > INF_BITS - 1) { status = max(status, (int)RICH_NONFINITE); alive = false; break; }
+            if (__longlong_as_double((long long)db) < P.picard_tol) break;
+            if (k >= P.picard_maxit) { status = max(status, (int)RICH_PICARD_MAXIT); alive = false; break; }
+        }
+        maxpic = max(maxpic, k);
+        return alive;
+    }
+
+    // mean outward Darcy flux through the bottom faces (valid in warp 0)
+    __device__ double qoi_warp0() const {
+        double acc = 0.0;
+        for (int i = tid; i < nx; i += 32) {
+            double kb = k_at(i, P.p_bot);
+            acc += kb * (2.0 * (p[i] - P.p_bot) / h + 1.0);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        return acc / nx;
+    }
+
+    // ------------------------------------------------------------ adjoint
+    // Jacobian pieces at the assembled state p = p^n: for every cell c and each
+    // interior face f (E, W, N, S) D_fc = T_f - g_cf dT_f/dp_c with
+    // g_cf = p_nb - p_c + s h (s = +1 north, -1 south), and the diagonal
+    // C_c/dt + Dirichlet T_b; so (J^T lam)_c = dg_c lam_c + sum_f D_fc (lam_c - lam_nb).
+    __device__ void adj_prepare(double* dE, double* dW, double* dN, double* dS, double* dg) {
+        const Lv64& F = L64[0];
+        for (int q = tid; q < nc; q += nt) {
+            int j = fdiv(q, nx, F.mnx), i = q - j * nx;
+            const double pc = p[q], kc = K[q];
+            const double dk = pc < 0.0 ? aa[q] * kc : 0.0;      // dK_c/dp_c
+            double e = 0.0, w = 0.0, n = 0.0, s = 0.0, d = F.Cdt[q];
+            if (i < nx - 1) { double kn = K[q + 1], den = kc + kn;
+                e = F.Tx[q] - (p[q + 1] - pc) * (t2h * kn * kn / (den * den)) * dk; }
+            if (i > 0)      { double kn = K[q - 1], den = kc + kn;
+                w = F.Tx[q - 1] - (p[q - 1] - pc) * (t2h * kn * kn / (den * den)) * dk; }
+            if (j < nz - 1) { double kn = K[q + nx], den = kc + kn;
+                n = F.Tz[q] - (p[q + nx] - pc + h) * (t2h * kn * kn / (den * den)) * dk; }
+            else d += F.Tbt[i];
+            if (j > 0)      { double kn = K[q - nx], den = kc + kn;
+                s = F.Tz[q - nx] - (p[q - nx] - pc - h) * (t2h * kn * kn / (den * den)) * dk; }
+            else d += F.Tbb[i];
+            dE[q] = e; dW[q] = w; dN[q] = n; dS[q] = s; dg[q] = d;
+        }
+        __syncthreads();
+    }
+
+    __device__ __forceinline__ double jt_apply(const double* dE, const double* dW, const double* dN,
+                                               const double* dS, const double* dg, const double* lam,
+                                               int q) const {
+        int j = fdiv(q, nx, L64[0].mnx), i = q - j * nx;
+        const double l = lam[q];
+        double v = dg[q] * l;
+        if (i < nx - 1) v += dE[q] * (l - lam[q + 1]);
+        if (i > 0)      v += dW[q] * (l - lam[q - 1]);
+        if (j < nz - 1) v += dN[q] * (l - lam[q + nx]);
+        if (j > 0)      v += dS[q] * (l - lam[q - nx]);
+        return v;
+    }
+
+    // approximate e = A^{-1} r by ninner V-cycles from e = 0 (A: the Picard
+    // operator assembled at the same state); e is returned in dp64 / M0.dp
+    __device__ void mg_apply(const double* r, int ninner) {
+        const Lv<TM>& M0 = LM[0];
+        for (int q = tid; q < nc; q += nt) {
+            if constexpr (SC) M0.f[q] = r[q] * M0.q[q];
+            else M0.f[q] = (TM)r[q];
+            M0.dp[q] = TM(0);
+        }
+        __syncthreads();
+        for (int k = 0; k < ninner; ++k) {
+            if constexpr (SC) mgcycle(r);
+            else mgcycle(nullptr);
+        }
+    }
+
+    // J^T lam = rhs by defect correction preconditioned with CCMG on A:
+    // lam += A^{-1}(rhs - J^T lam) until ||rhs - J^T lam|| <= adj_tol ||rhs||.
+    // Returns the number of outer iterations (adj_maxit + 1 when not converged).
+    __device__ int adj_solve(const double* dE, const double* dW, const double* dN, const double* dS,
+                             const double* dg, const double* rhs, double* lam, double* r) {
+        const Lv<TM>& M0 = LM[0];
+        unsigned long long m = 0;
+        for (int q = tid; q < nc; q += nt) {
+            lam[q] = 0.0;
+            r[q] = rhs[q];
+            unsigned long long b = abs_bits(rhs[q]);
+            m = b > m ? b : m;
+        }
+        const unsigned long long b0 = block_max(m, red);
+        const double target = P.adj_tol * __longlong_as_double((long long)b0);
+        if (b0 == 0) return 0;
+        for (int it = 1; it <= P.adj_maxit; ++it) {
+            mg_apply(r, P.adj_inner);
+            for (int q = tid; q < nc; q += nt) lam[q] += (double)M0.dp[q];
+            __syncthreads();
+            unsigned long long mm = 0;
+            for (int q = tid; q < nc; q += nt) {
+                double v = rhs[q] - jt_apply(dE, dW, dN, dS, dg, lam, q);
+                r[q] = v;
+                unsigned long long b = abs_bits(v);
+                mm = b > mm ? b : mm;
+            }
+            const unsigned long long rb = block_max(mm, red);
+            if (rb > INF_BITS - 1) return P.adj_maxit + 1;
+            if (__longlong_as_double((long long)rb) <= target) return it;
+        }
+        return P.adj_maxit + 1;
+    }
+
+    // g -= (dR/dm)^T lam at the assembled state (m = ln Ks): interior faces
+    // contribute -g_cf (lam_c - lam_nb) dT_f/dm_c with dT_f/dm_c =
+    // (2/h^2) K_nb^2 K_c / (K_c + K_nb)^2; Dirichlet faces -g_b T_b lam_c
+    __device__ void adj_grad_update(const double* lam, double* g) {
+        const Lv64& F = L64[0];
+        for (int q = tid; q < nc; q += nt) {
+            int j = fdiv(q, nx, F.mnx), i = q - j * nx;
+            const double pc = p[q], kc = K[q], lc = lam[q];
+            double v = 0.0;
+            if (i < nx - 1) { double kn = K[q + 1], den = kc + kn;
+                v -= (p[q + 1] - pc) * (lc - lam[q + 1]) * (t2h * kn * kn * kc / (den * den)); }
+            if (i > 0)      { double kn = K[q - 1], den = kc + kn;
+                v -= (p[q - 1] - pc) * (lc - lam[q - 1]) * (t2h * kn * kn * kc / (den * den)); }
+            if (j < nz - 1) { double kn = K[q + nx], den = kc + kn;
+                v -= (p[q + nx] - pc + h) * (lc - lam[q + nx]) * (t2h * kn * kn * kc / (den * den)); }
+            else v -= (P.p_top - pc + h / 2.0) * F.Tbt[i] * lc;
+            if (j > 0)      { double kn = K[q - nx], den = kc + kn;
+                v -= (p[q - nx] - pc - h) * (lc - lam[q - nx]) * (t2h * kn * kn * kc / (den * den)); }
+            else v -= (P.p_bot - pc - h / 2.0) * F.Tbb[i] * lc;
+            g[q] -= v;
+        }
+        __syncthreads();
+    }
+};
+
+template <typename TM>
+__device__ __forceinline__ void init_levels(const FParams& P, char* slot, Lv64* L64, Lv<TM>* LM) {
+    constexpr bool SC = Scaled<TM>::value;
+    const int nlev = P.nlev;
+    if ((int)threadIdx.x < nlev) {
+        const int l = threadIdx.x;
+        Lv64& a = L64[l];
+        a.nx = P.nx[l]; a.nz = P.nz[l]; a.nc = a.nx * a.nz; a.mnx = P.mnx[l];
+        double** pp[N64] = {&a.Tx, &a.Tz, &a.Cdt, &a.D, &a.Tbt, &a.Tbb};
+        for (int k = 0; k < N64; ++k) *pp[k] = (double*)(slot + P.o64[l][k]);
+        Lv<TM>& b = LM[l];
+        b.nx = a.nx; b.nz = a.nz; b.hx = a.nx >> 1; b.nc = a.nc; b.mnx = P.mnx[l]; b.mhx = P.mhx[l];
+        TM** qq[NMG] = {&b.c0, &b.c1, &b.c2, &b.c3, &b.q, &b.f, &b.dp};
+        for (int k = 0; k < NMG; ++k) *qq[k] = P.omg[l][k] >= 0 ? (TM*)(slot + P.omg[l][k]) : nullptr;
+        if constexpr (SC) b.D = (TM*)a.D;                 // FP64: shares the operator diagonal
+        else { b.D = b.c3; b.c3 = nullptr; }              // FP32: its own copy
+    }
+    __syncthreads();
+}
+
+template <typename TM, int NT, bool WC, int CL>
+__global__ void __launch_bounds__(NT)
+k_fused(const FParams P) {
+    extern __shared__ unsigned char smraw[];
+    __shared__ unsigned long long red[33];
+    __shared__ int s_sample;
+    __shared__ Lv64 L64[MAXL];
+    __shared__ Lv<TM> LM[MAXL];
+    char* slot = P.scratch + (size_t)blockIdx.x * P.slot_bytes;
+    init_levels<TM>(P, slot, L64, LM);
+    Cta<TM, WC, CL> C(P, slot, L64, LM, reinterpret_cast<TM*>(smraw), red);
+    const int nc = C.nc, tid = C.tid, nt = C.nt;
+    for (;;) {
+        if (tid == 0) s_sample = atomicAdd(P.queue, 1);
+        __syncthreads();
+        const int s = s_sample;
+        __syncthreads();
+        if (s >= P.S) break;
+        C.setup(s);
+        int status = RICH_OK, maxpic = 0;
+        bool alive = true;
+        long long pic_tot = 0, mg_tot = 0;
+        for (int step = 0; step < P.nsteps && alive; ++step)
+            alive = C.time_step(pic_tot, mg_tot, maxpic, status);
+        if (tid < 32) {
+            const double q = C.qoi_warp0();
+            if (tid == 0) {
+                P.qoi[s] = alive ? q : __longlong_as_double(0x7FF8000000000000ll);
+                if (P.status) P.status[s] = status;
+                if (P.pic_total) P.pic_total[s] = pic_tot;
+                if (P.mg_total) P.mg_total[s] = mg_tot;
+                if (P.maxpic) P.maxpic[s] = maxpic;
+            }
+        }
+        if (P.p_final)
+            for (int q = tid; q < nc; q += nt) P.p_final[(size_t)s * nc + q] = C.p[q];
+        __syncthreads();
+    }
+}
+
+// Discrete adjoint of the converged time-stepped solve (one sample per CTA):
+// forward with a checkpoint of p every ckpt_every steps, then per segment
+// (last first) recompute its states from the checkpoint and step backwards:
+//   J_N^T lam_N = dQ/dp^N,  J_n^T lam_n = diag(C(p^n)/dt) lam_{n+1},
+//   dQ/dm = dQ/dm|explicit - sum_n (dR_n/dm)^T lam_n     (m = ln Ks).
+template <typename TM, bool WC>
+__global__ void __launch_bounds__(512)
+k_adjoint(const FParams P) {
+    extern __shared__ unsigned char smraw[];
+    __shared__ unsigned long long red[33];
+    __shared__ int s_sample;
+    __shared__ Lv64 L64[MAXL];
+    __shared__ Lv<TM> LM[MAXL];
+    char* slot = P.scratch + (size_t)blockIdx.x * P.slot_bytes;
+    init_levels<TM>(P, slot, L64, LM);
+    Cta<TM, WC> C(P, slot, L64, LM, reinterpret_cast<TM*>(smraw), red);
+    const int nc = C.nc, nx = C.nx, tid = C.tid, nt = C.nt;
+    const int CK = P.ckpt_every;
+    double* ckpt = (double*)(slot + P.o_ckpt);      // [nck][nc]
+    double* seg = (double*)(slot + P.o_seg);        // [CK][nc]
+    double* lam = (double*)(slot + P.o_lam);
+    double* rhs = (double*)(slot + P.o_rhs);
+    double* r = (double*)(slot + P.o_r);
+    double* dE = (double*)(slot + P.o_dE);
+    double* dW = (double*)(slot + P.o_dW);
+    double* dN = (double*)(slot + P.o_dN);
+    double* dS = (double*)(slot + P.o_dS);
+    double* dg = (double*)(slot + P.o_dg);
+    double* g = (double*)(slot + P.o_g);
+    const double NaN = __longlong_as_double(0x7FF8000000000000ll);
+    for (;;) {
+        if (tid == 0) s_sample = atomicAdd(P.queue, 1);
+        __syncthreads();
+        const int s = s_sample;
+        __syncthreads();
+        if (s >= P.S) break;
+        C.setup(s);
+        int status = RICH_OK, maxpic = 0;
+        bool alive = true;
+        long long pic_tot = 0, mg_tot = 0, adj_its = 0;
+        // ---- forward with checkpoints p^0, p^CK, p^2CK, ...
+        for (int n = 1; n <= P.nsteps && alive; ++n) {
+            if ((n - 1) % CK == 0) {
+                double* dst = ckpt + (size_t)((n - 1) / CK) * nc;
+                for (int q = tid; q < nc; q += nt) dst[q] = C.p[q];
+                __syncthreads();
+            }
+            alive = C.time_step(pic_tot, mg_tot, maxpic, status);
+        }
+        double qv = 0.0;
+        if (tid < 32) qv = C.qoi_warp0();
+        if (alive) {
+            // ---- dQ/dp^N (rhs) and the explicit dQ/dm (g), bottom cells
+            for (int q = tid; q < nc; q += nt) {
+                double gv = 0.0, rv = 0.0;
+                if (q < nx) {
+                    double kb = P.p_bot < 0.0 ? C.Ks[q] * exp(C.aa[q] * P.p_bot) : C.Ks[q];
+                    rv = kb * (2.0 / C.h) / nx;
+                    gv = kb * (2.0 * (C.p[q] - P.p_bot) / C.h + 1.0) / nx;
+                }
+                rhs[q] = rv;
+                g[q] = gv;
+            }
+            __syncthreads();
+            const int nck = (P.nsteps + CK - 1) / CK;
+            for (int sg = nck - 1; sg >= 0 && alive; --sg) {
+                const int n0 = sg * CK, n1 = min(n0 + CK, P.nsteps);
+                // recompute p^{n0+1..n1} from the checkpoint
+                for (int q = tid; q < nc; q += nt) C.p[q] = ckpt[(size_t)sg * nc + q];
+                __syncthreads();
+                long long dpic = 0, dmg = 0;
+                int dmax = 0, dst = RICH_OK;
+                for (int n = n0 + 1; n <= n1 && alive; ++n) {
+                    alive = C.time_step(dpic, dmg, dmax, dst);
+                    double* dstp = seg + (size_t)(n - n0 - 1) * nc;
+                    for (int q = tid; q < nc; q += nt) dstp[q] = C.p[q];
+                    __syncthreads();
+                }
+                if (!alive) { status = max(status, dst); break; }
+                for (int n = n1; n > n0; --n) {
+                    // state p^n, operator and Jacobian at p^n
+                    const double* pn = seg + (size_t)(n - n0 - 1) * nc;
+                    for (int q = tid; q < nc; q += nt) C.p[q] = pn[q];
+                    __syncthreads();
+                    C.assemble();
+                    if (n < P.nsteps) {       // rhs = diag(C(p^n)/dt) lam_{n+1}
+                        for (int q = tid; q < nc; q += nt) rhs[q] = L64[0].Cdt[q] * lam[q];
+                        __syncthreads();
+                    }
+                    C.adj_prepare(dE, dW, dN, dS, dg);
+                    const int its = C.adj_solve(dE, dW, dN, dS, dg, rhs, lam, r);
+                    adj_its += its;
+                    if (its > P.adj_maxit) status = max(status, (int)RICH_MG_MAXIT);
+                    C.adj_grad_update(lam, g);
+                }
+            }
+        }
+        if (tid == 0) {
+            P.qoi[s] = alive ? qv : NaN;
+            if (P.status) P.status[s] = status;
+            if (P.pic_total) P.pic_total[s] = pic_tot;
+            if (P.mg_total) P.mg_total[s] = adj_its;
+            if (P.maxpic) P.maxpic[s] = maxpic;
+        }
+        for (int q = tid; q < nc; q += nt) P.g_out[(size_t)s * nc + q] = alive ? g[q] : NaN;
+        __syncthreads();
+    }
+}
+
+}  // namespace

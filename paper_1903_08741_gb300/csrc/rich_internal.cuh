@@ -69,13 +69,22 @@ int rich_prof_harvest(rich_ctx* ctx);
 // ---- solver (solver.cu)
 int rich_samples_reserve(rich_ctx* ctx, int S);
 int rich_stage_reserve(rich_ctx* ctx, size_t bytes);
+// per-cell fields beyond ln Ks and alpha (van Genuchten-Mualem closure) and
+// the additive continuation shifts of alpha and n
+struct rich_soil_in {
+    const double* n = nullptr;
+    const double* theta_s = nullptr;
+    const double* theta_r = nullptr;
+    double alpha_shift = 0.0, n_shift = 0.0;
+};
 int rich_solve_device(rich_ctx* ctx, const rich_problem_t* pb, int S, const double* lnKs,
                       const double* alpha, double alpha_scale, double* qoi, double* p_final,
-                      int32_t* status, rich_stats_t* stats, cudaStream_t st);
+                      int32_t* status, rich_stats_t* stats, cudaStream_t st,
+                      const rich_soil_in* soil = nullptr);
 int rich_count_levels(int nx, int nz);
 int rich_solve_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const double* lnKs,
                      const double* alpha, double alpha_scale, double* qoi, double* p_final,
-                     int32_t* status, cudaStream_t st);
+                     int32_t* status, cudaStream_t st, const rich_soil_in* soil = nullptr);
 void rich_prof_amend(rich_ctx* ctx, double bytes, double flops);
 int rich_adjoint_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const double* lnKs,
                        const double* alpha, double alpha_scale, int ckpt_every, double adj_tol,
@@ -89,6 +98,9 @@ int rich_fields_pair_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int n
                             double* al_c, cudaStream_t st);
 int rich_fields_average(rich_ctx* ctx, int S, int nx, int nz, const double* lk, const double* al,
                         double* lkc, double* alc, cudaStream_t st);
+int rich_soil_device(rich_ctx* ctx, const rich_field_t* fd, const rich_soil_model_t* sm, int nx, int nz,
+                     uint32_t level, int64_t first, int S, int coarsen, const rich_soil_t* out,
+                     cudaStream_t st);
 int rich_fields_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int nz, uint32_t level,
                        int64_t first, int S, int coarsen, double* lnKs, double* alpha,
                        cudaStream_t st, const int64_t* first_dev = nullptr);

@@ -51,10 +51,11 @@ int rich_stage_reserve(rich_ctx* ctx, size_t bytes) {
 
 int rich_solve_device(rich_ctx* ctx, const rich_problem_t* pb, int S, const double* lnKs,
                       const double* alpha, double alpha_scale, double* qoi, double* p_final,
-                      int32_t* status, rich_stats_t* stats, cudaStream_t st) {
+                      int32_t* status, rich_stats_t* stats, cudaStream_t st, const rich_soil_in* soil) {
     auto t0 = std::chrono::steady_clock::now();
     if (int e = rich_samples_reserve(ctx, S)) return e;
-    if (int e = rich_solve_fused(ctx, pb, S, lnKs, alpha, alpha_scale, qoi, p_final, status, st)) return e;
+    if (int e = rich_solve_fused(ctx, pb, S, lnKs, alpha, alpha_scale, qoi, p_final, status, st, soil))
+        return e;
     rich_samplebuf& b = ctx->sb;
     std::vector<int32_t> hs(S), hmax(S);
     std::vector<int64_t> hp(S), hm(S);
