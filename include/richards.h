@@ -212,6 +212,14 @@ int rich_sample_soil(rich_ctx_t ctx, const rich_field_t* field, const rich_soil_
                      int32_t nx, int32_t nz, uint32_t level, int64_t first_sample,
                      int32_t nsamples, int32_t coarsen_times, const rich_soil_t* out, void* stream);
 
+/* The five soil fields as fine (nx x nz) / coarse (nx/2 x nz/2) couples by
+ * covariance upscaling (Appendix A, Eqs. averaging, cov_upscale), as
+ * rich_sample_fields_pair does for two: the fine members are the
+ * rich_sample_soil draws; the theta outputs of both members may be NULL. */
+int rich_sample_soil_pair(rich_ctx_t ctx, const rich_field_t* field, const rich_soil_model_t* soil,
+                          int32_t nx, int32_t nz, uint32_t level, int64_t first_sample, int32_t nsamples,
+                          const rich_soil_t* fine, const rich_soil_t* coarse, void* stream);
+
 /* As rich_solve_batch with per-cell soil fields (either closure) and the
  * additive continuation of Sec. 5: alpha_eff = alpha * alpha_scale +
  * alpha_shift, n_eff = n + n_shift (the paper's (grad alpha, grad n)
@@ -245,12 +253,25 @@ typedef struct {
                                  of ln Ks, alpha (cheap, not exact);
                                  2: covariance upscaling, rich_sample_fields_pair (exact,
                                  cheap; Appendix A)                                         */
-    int32_t continuation;     /* 1: alpha_l = alpha (l+1)/(L+1); 0: alpha on every level   */
+    int32_t continuation;     /* Gardner: 1 gives alpha_l = alpha (l+1)/(L+1); van Genuchten:
+                                 1 gives the additive (d_alpha, d_n) hierarchy below; 0: the
+                                 original parameters on every level                       */
     int32_t batch;            /* samples per batch, 0 = automatic                          */
     double eps;               /* RMSE target of the optimal-allocation report              */
     uint32_t key_offset;      /* added to the level in the noise key (independent reruns)  */
     int32_t tune_threads[RICH_MLMC_MAX_LEVELS];  /* per-level launch shape (0: context's)    */
     int32_t tune_inner[RICH_MLMC_MAX_LEVELS];    /* per-level FP32 cycles per defect (0: ctx) */
+    /* van Genuchten-Mualem levels (base.closure == RICH_VAN_GENUCHTEN): the
+     * five soil fields of `soil` (alpha's range is field.alpha_lo/span) and
+     * the additive continuation of Sec. 5.2: with k_l = max(0, L + 1 -
+     * fixed_levels - l), level l solves with alpha - k_l d_alpha and
+     * n + k_l d_n, so the fixed_levels finest levels (at least 1) keep the
+     * original parameters; continuation = 0 gives k_l = 0.  Theta fields are
+     * drawn when with_thetas is 1 (else the base problem's constants). */
+    rich_soil_model_t soil;
+    double d_alpha, d_n;
+    int32_t fixed_levels;
+    int32_t with_thetas;
 } rich_mlmc_cfg_t;
 
 typedef struct {

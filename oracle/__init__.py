@@ -138,6 +138,8 @@ def lib():
         L.orc_solve_one_soil.argtypes = [C.POINTER(Problem), C.c_int32, C.c_int32, C.POINTER(Soil),
                                          C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
                                          C.POINTER(Stats)]
+        L.orc_sample_soil_pair.argtypes = [C.c_uint64, C.POINTER(Cov), C.POINTER(SoilModel), C.c_int32,
+                                           C.c_int32, C.c_uint32, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p]
         L.orc_closure.argtypes = [C.c_int32] + [C.c_double] * 6 + [C.POINTER(C.c_double)] * 3
         L.orc_sample_soil.argtypes = [C.c_uint64, C.POINTER(Cov), C.POINTER(SoilModel), C.c_int32,
                                       C.c_int32, C.c_uint32, C.c_int64, C.c_int32, C.c_int32,
@@ -336,6 +338,22 @@ def sample_soil(nx, nz, nsamples, model, seed=0, level=0, first_sample=0, coarse
     return tuple(out)
 
 
+def sample_soil_pair(nx, nz, nsamples, model, seed=0, level=0, first_sample=0, sigma2=1.0, corr_len=0.3,
+                     corr_len_z=0.0, nu=0.0):
+    """The five soil fields as covariance-upscaled couples: (fine [5 arrays of
+    S, nz, nx], coarse [5 arrays of S, nz/2, nx/2])."""
+    fine = [np.empty((nsamples, nz, nx)) for _ in range(5)]
+    coarse = [np.empty((nsamples, nz // 2, nx // 2)) for _ in range(5)]
+    pf = (C.c_void_p * 5)(*[a.ctypes.data for a in fine])
+    pc = (C.c_void_p * 5)(*[a.ctypes.data for a in coarse])
+    cv = Cov(sigma2, corr_len, corr_len_z, nu)
+    rc = lib().orc_sample_soil_pair(seed, C.byref(cv), C.byref(model), nx, nz, level, first_sample, nsamples,
+                                    pf, pc)
+    if rc:
+        raise ValueError("invalid field arguments")
+    return tuple(fine), tuple(coarse)
+
+
 def picard_system(pb, lnKs, alpha, p, p_old, alpha_scale=1.0):
     """The Picard system at iterate p: (Tx, Tz, Tbt, Tbb, Cdt, f)."""
     lnKs, alpha, p, p_old = _f64(lnKs), _f64(alpha), _f64(p), _f64(p_old)
@@ -394,7 +412,8 @@ def optimal_samples(levels, eps):
 
 def mlmc_estimate(nsamples, n0, steps0, t_final, seed=0, coupling=0, continuation=1, key_offset=0,
                   sigma2=1.0, corr_len=0.3, alpha_lo=0.5, alpha_span=1.5, nthreads=None,
-                  corr_len_z=0.0, nu=0.0, **phys):
+                  corr_len_z=0.0, nu=0.0, soil=None, d_alpha=0.05, d_n=0.1, fixed_levels=1,
+                  with_thetas=True, **phys):
     """Parametric-continuation MLMC (Sec. 5) restated plainly: for level l draw
     N_l field pairs (coupling 0: on the finest grid, averaged down L-l times;
     coupling 1: on the level grid), solve the fine member on grid n0 2^l with
@@ -404,28 +423,48 @@ def mlmc_estimate(nsamples, n0, steps0, t_final, seed=0, coupling=0, continuatio
     NL = len(nsamples)
     L = NL - 1
     nL = n0 << L
+    vg = phys.get("closure", 0) == VAN_GENUCHTEN
     out = []
+
+    def vg_steps(k):        # Sec. 5.2: the fixed_levels finest levels keep alpha and n
+        return max(0, L + 1 - max(1, fixed_levels) - k) if continuation else 0
+
+    def solve(pb, flds, k):
+        if vg:
+            kk = vg_steps(k)
+            return solve_batch_soil(pb, *flds, alpha_shift=-kk * d_alpha, n_shift=kk * d_n, want_p=False,
+                                    nthreads=nthreads)
+        return solve_batch(pb, flds[0], flds[1], (k + 1) / NL if continuation else 1.0, want_p=False,
+                           nthreads=nthreads)
+
     for l in range(NL):
         M = n0 << l
-        scale = lambda k: (k + 1) / NL if continuation else 1.0
-        fm = dict(seed=seed, level=l + key_offset, sigma2=sigma2, corr_len=corr_len, corr_len_z=corr_len_z,
-                  nu=nu, alpha_lo=alpha_lo, alpha_span=alpha_span)
-        if coupling == 2 and l > 0:
-            lk, al, lkc_up, alc_up = sample_fields_pair(M, M, nsamples[l], **fm)
+        fm = dict(seed=seed, level=l + key_offset, sigma2=sigma2, corr_len=corr_len, corr_len_z=corr_len_z, nu=nu)
+        nf = 5 if with_thetas else 3
+        if vg and coupling == 2 and l > 0:
+            fine, crs = sample_soil_pair(M, M, nsamples[l], soil, **fm)
+            fine, crs = fine[:nf], crs[:nf]
+        elif vg:
+            ndraw, ct = (nL, L - l) if coupling == 0 else (M, 0)
+            fine = sample_soil(ndraw, ndraw, nsamples[l], soil, coarsen_times=ct, nthreads=nthreads, **fm)[:nf]
+        elif coupling == 2 and l > 0:
+            lk, al, lkc_up, alc_up = sample_fields_pair(M, M, nsamples[l], alpha_lo=alpha_lo,
+                                                        alpha_span=alpha_span, **fm)
+            fine, crs = (lk, al), (lkc_up, alc_up)
         elif coupling == 0:
-            lk, al = sample_fields(nL, nL, nsamples[l], coarsen_times=L - l, nthreads=nthreads, **fm)
+            fine = sample_fields(nL, nL, nsamples[l], coarsen_times=L - l, nthreads=nthreads, alpha_lo=alpha_lo,
+                                 alpha_span=alpha_span, **fm)
         else:
-            lk, al = sample_fields(M, M, nsamples[l], nthreads=nthreads, **fm)
+            fine = sample_fields(M, M, nsamples[l], nthreads=nthreads, alpha_lo=alpha_lo, alpha_span=alpha_span,
+                                 **fm)
         pf = make_problem(nsteps=steps0 << l, dt=t_final / (steps0 << l), **phys)
-        _, qf, sf, _ = solve_batch(pf, lk, al, scale(l), want_p=False, nthreads=nthreads)
+        _, qf, sf, _ = solve(pf, fine, l)
         if l > 0:
-            if coupling == 2:
-                lkc, alc = lkc_up, alc_up
-            else:
+            if coupling != 2:
                 blk = lambda x: x.reshape(x.shape[0], M // 2, 2, M // 2, 2).mean(axis=(2, 4))
-                lkc, alc = blk(lk), blk(al)
+                crs = tuple(blk(x) for x in fine)
             pc = make_problem(nsteps=steps0 << (l - 1), dt=t_final / (steps0 << (l - 1)), **phys)
-            _, qc, sc, _ = solve_batch(pc, lkc, alc, scale(l - 1), want_p=False, nthreads=nthreads)
+            _, qc, sc, _ = solve(pc, crs, l - 1)
         else:
             qc, sc = np.zeros_like(qf), np.zeros_like(sf)
         bad = np.isin(sf, (PICARD_MAXIT, NONFINITE)) | np.isin(sc, (PICARD_MAXIT, NONFINITE)) \

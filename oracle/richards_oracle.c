@@ -340,64 +340,82 @@ int orc_sample_soil(uint64_t seed, const orc_cov* cv, const orc_soil_model* sm, 
 /* y_c(I,J) = (1/2) * (sum of the 2x2 block of y) on the half-size torus gives  */
 /* the coarse field through the coarse grid's own spectrum (spacing 2h).       */
 /* ------------------------------------------------------------------------- */
-int orc_sample_fields_pair(uint64_t seed, const orc_cov* cv, double alpha_lo,
-                           double alpha_span, int32_t nx, int32_t nz, uint32_t level,
-                           int64_t first_sample, int32_t nsamples, double* lnKs_f, double* alpha_f,
-                           double* lnKs_c, double* alpha_c)
+static int sample_pair_n(uint64_t seed, const orc_cov* cv, int nf, double shift0, const double* lo,
+                         const double* span, double** outf, double** outc, int32_t nx, int32_t nz,
+                         uint32_t level, int64_t first_sample, int32_t nsamples)
 {
     if (nx < 2 || nz < 2 || nx % 2 || nz % 2 || nsamples < 0) return -1;
     double h = 1.0 / nz;
     int32_t px, pz;
     orc_torus_size(nx, nz, h, cv, &px, &pz);
     int pxc = px / 2, pzc = pz / 2, ncx = nx / 2, ncz = nz / 2;
-    size_t nf = (size_t)px * pz, nc = (size_t)pxc * pzc;
-    double* sqf = (double*)malloc(sizeof(double) * nf);
+    size_t nf_ = (size_t)px * pz, nc = (size_t)pxc * pzc;
+    double* sqf = (double*)malloc(sizeof(double) * nf_);
     double* sqc = (double*)malloc(sizeof(double) * nc);
     double ratio;
     orc_fftma_spectrum(px, pz, h, cv, sqf, &ratio);
     orc_fftma_spectrum(pxc, pzc, 2.0 * h, cv, sqc, &ratio);
-    double* y = (double*)malloc(sizeof(double) * nf);
-    double* re = (double*)malloc(sizeof(double) * nf);
-    double* im = (double*)malloc(sizeof(double) * nf);
+    double* y = (double*)malloc(sizeof(double) * nf_);
+    double* re = (double*)malloc(sizeof(double) * nf_);
+    double* im = (double*)malloc(sizeof(double) * nf_);
     double sig = sqrt(cv->sigma2);
     for (int k = 0; k < nsamples; ++k) {
         uint64_t sample = (uint64_t)(first_sample + k);
-        for (uint32_t fld = 0; fld < 2; ++fld) {
-            orc_white_noise(seed, level, sample, fld, (int64_t)nf, y);
-            /* fine member */
-            memcpy(re, y, sizeof(double) * nf);
-            memset(im, 0, sizeof(double) * nf);
-            orc_fft2(re, im, px, pz, 0);
-            for (size_t q = 0; q < nf; ++q) { re[q] *= sqf[q]; im[q] *= sqf[q]; }
-            orc_fft2(re, im, px, pz, 1);
-            for (int j = 0; j < nz; ++j)
-                for (int i = 0; i < nx; ++i) {
-                    double z = re[(size_t)j * px + i];
-                    size_t o = (size_t)k * nx * nz + (size_t)j * nx + i;
-                    if (fld == 0) lnKs_f[o] = z;
-                    else alpha_f[o] = alpha_lo + alpha_span * 0.5 * erfc(-(z / sig) / sqrt(2.0));
+        for (int fld = 0; fld < nf; ++fld) {
+            orc_white_noise(seed, level, sample, (uint32_t)fld, (int64_t)nf_, y);
+            for (int pass = 0; pass < 2; ++pass) {
+                /* pass 0: the fine member from y; pass 1: the coarse member
+                 * from y_c(I,J) = (1/2) (sum of the 2x2 block of y) */
+                int tx = pass ? pxc : px, tz = pass ? pzc : pz, ox = pass ? ncx : nx, oz = pass ? ncz : nz;
+                const double* sq = pass ? sqc : sqf;
+                double* out = (pass ? outc[fld] : outf[fld]) + (size_t)k * ox * oz;
+                if (pass == 0) {
+                    memcpy(re, y, sizeof(double) * nf_);
+                } else {
+                    for (int J = 0; J < pzc; ++J)
+                        for (int I = 0; I < pxc; ++I) {
+                            size_t a = (size_t)(2 * J) * px + 2 * I, b = a + px;
+                            re[(size_t)J * pxc + I] = 0.5 * (y[a] + y[a + 1] + y[b] + y[b + 1]);
+                        }
                 }
-            /* coarse member from the averaged noise */
-            for (int J = 0; J < pzc; ++J)
-                for (int I = 0; I < pxc; ++I) {
-                    size_t a = (size_t)(2 * J) * px + 2 * I, b = a + px;
-                    re[(size_t)J * pxc + I] = 0.5 * (y[a] + y[a + 1] + y[b] + y[b + 1]);
-                }
-            memset(im, 0, sizeof(double) * nc);
-            orc_fft2(re, im, pxc, pzc, 0);
-            for (size_t q = 0; q < nc; ++q) { re[q] *= sqc[q]; im[q] *= sqc[q]; }
-            orc_fft2(re, im, pxc, pzc, 1);
-            for (int j = 0; j < ncz; ++j)
-                for (int i = 0; i < ncx; ++i) {
-                    double z = re[(size_t)j * pxc + i];
-                    size_t o = (size_t)k * ncx * ncz + (size_t)j * ncx + i;
-                    if (fld == 0) lnKs_c[o] = z;
-                    else alpha_c[o] = alpha_lo + alpha_span * 0.5 * erfc(-(z / sig) / sqrt(2.0));
-                }
+                memset(im, 0, sizeof(double) * (size_t)tx * tz);
+                orc_fft2(re, im, tx, tz, 0);
+                for (size_t q = 0; q < (size_t)tx * tz; ++q) { re[q] *= sq[q]; im[q] *= sq[q]; }
+                orc_fft2(re, im, tx, tz, 1);
+                for (int j = 0; j < oz; ++j)
+                    for (int i = 0; i < ox; ++i) {
+                        double v = re[(size_t)j * tx + i];
+                        out[(size_t)j * ox + i] = fld == 0 ? shift0 + v
+                            : lo[fld] + span[fld] * 0.5 * erfc(-(v / sig) / sqrt(2.0));
+                    }
+            }
         }
     }
     free(sqf); free(sqc); free(y); free(re); free(im);
     return 0;
+}
+
+int orc_sample_fields_pair(uint64_t seed, const orc_cov* cv, double alpha_lo,
+                           double alpha_span, int32_t nx, int32_t nz, uint32_t level,
+                           int64_t first_sample, int32_t nsamples, double* lnKs_f, double* alpha_f,
+                           double* lnKs_c, double* alpha_c)
+{
+    double lo[2] = { 0.0, alpha_lo }, span[2] = { 0.0, alpha_span };
+    double* of[2] = { lnKs_f, alpha_f };
+    double* oc[2] = { lnKs_c, alpha_c };
+    return sample_pair_n(seed, cv, 2, 0.0, lo, span, of, oc, nx, nz, level, first_sample, nsamples);
+}
+
+/* The five soil fields as fine / coarse couples by covariance upscaling;
+ * outputs [5] arrays each, in the order ln Ks, alpha, n, theta_s, theta_r. */
+int orc_sample_soil_pair(uint64_t seed, const orc_cov* cv, const orc_soil_model* sm, int32_t nx, int32_t nz,
+                         uint32_t level, int64_t first_sample, int32_t nsamples, double** fine,
+                         double** coarse)
+{
+    double lo[5] = { 0.0, sm->alpha_lo, sm->n_lo, sm->theta_s_lo, sm->theta_r_lo };
+    double span[5] = { 0.0, sm->alpha_span, sm->n_span, sm->theta_s_span, sm->theta_r_span };
+    return sample_pair_n(seed, cv, 5, sm->lnks_mean, lo, span, fine, coarse, nx, nz, level, first_sample,
+                         nsamples);
 }
 
 /* ------------------------------------------------------------------------- */

@@ -96,6 +96,9 @@ int  orc_sample_soil(uint64_t seed, const orc_cov* cv, const orc_soil_model* sm,
                      uint32_t level, int64_t first_sample, int32_t nsamples, int32_t coarsen_times,
                      double* lnKs, double* alpha, double* n, double* theta_s, double* theta_r,
                      int32_t nthreads);
+int  orc_sample_soil_pair(uint64_t seed, const orc_cov* cv, const orc_soil_model* sm, int32_t nx, int32_t nz,
+                          uint32_t level, int64_t first_sample, int32_t nsamples, double** fine,
+                          double** coarse);
 int  orc_closure(int32_t kind, double Ks, double a, double n, double theta_r, double theta_s,
                  double p, double* K, double* theta, double* C);
 int  orc_solve_one_soil(const orc_problem* pb, int32_t nx, int32_t nz, const orc_soil* soil,

@@ -157,7 +157,8 @@ class _MlmcCfg(C.Structure):
                 ("nsamples", C.c_int32 * MLMC_MAX_LEVELS), ("coupling", C.c_int32),
                 ("continuation", C.c_int32), ("batch", C.c_int32), ("eps", C.c_double),
                 ("key_offset", C.c_uint32), ("tune_threads", C.c_int32 * MLMC_MAX_LEVELS),
-                ("tune_inner", C.c_int32 * MLMC_MAX_LEVELS)]
+                ("tune_inner", C.c_int32 * MLMC_MAX_LEVELS), ("soil", _SoilModel), ("d_alpha", C.c_double),
+                ("d_n", C.c_double), ("fixed_levels", C.c_int32), ("with_thetas", C.c_int32)]
 
 
 _LV = C.c_double * MLMC_MAX_LEVELS
@@ -189,6 +190,13 @@ class MlmcConfig:
     tune_inner: tuple = ()          # per level, 0 = the context's FP32 cycles per defect
     problem: Problem = field(default_factory=Problem)
     model: FieldModel = field(default_factory=FieldModel)
+    # van Genuchten levels (problem.closure == VAN_GENUCHTEN): soil fields and
+    # the additive (d_alpha, d_n) continuation of Sec. 5.2
+    soil: SoilModel = field(default_factory=SoilModel)
+    d_alpha: float = 0.05
+    d_n: float = 0.1
+    fixed_levels: int = 1
+    with_thetas: int = 1
 
     def _c(self):
         c = _MlmcCfg()
@@ -204,6 +212,8 @@ class MlmcConfig:
             c.tune_threads[l] = v
         for l, v in enumerate(self.tune_inner):
             c.tune_inner[l] = v
+        c.soil = self.soil._c()
+        c.d_alpha, c.d_n, c.fixed_levels, c.with_thetas = self.d_alpha, self.d_n, self.fixed_levels, self.with_thetas
         return c
 
 
@@ -251,6 +261,8 @@ def lib():
                                                vp, vp, C.POINTER(_Stats), vp]
         L.rich_sample_soil.argtypes = [vp, C.POINTER(_Field), C.POINTER(_SoilModel), i32, i32, u32, i64, i32,
                                        i32, C.POINTER(_Soil), vp]
+        L.rich_sample_soil_pair.argtypes = [vp, C.POINTER(_Field), C.POINTER(_SoilModel), i32, i32, u32, i64, i32,
+                                            C.POINTER(_Soil), C.POINTER(_Soil), vp]
         L.rich_solve_soil.argtypes = [vp, C.POINTER(_Problem), i32, C.POINTER(_Soil), dbl, dbl, dbl, vp, vp, vp,
                                       C.POINTER(_Stats), vp]
         L.rich_mlmc_estimate.argtypes = [vp, C.POINTER(_MlmcCfg), C.POINTER(_MlmcResult)]
@@ -265,7 +277,8 @@ def exported_symbols():
             "rich_mlmc_accumulate", "rich_profile", "rich_profile_read", "rich_launch_count",
             "rich_solve_batch_noalloc", "rich_mlmc_estimate", "rich_sample_fields_pair",
             "rich_kl_fields", "rich_solve_batch_adjoint", "rich_set_tuning", "rich_sample_fields_at",
-            "rich_solve_batch_async", "rich_mlmc_adaptive", "rich_sample_soil", "rich_solve_soil"]
+            "rich_solve_batch_async", "rich_mlmc_adaptive", "rich_sample_soil", "rich_solve_soil",
+            "rich_sample_soil_pair"]
 
 
 def _check(rc):
@@ -381,6 +394,24 @@ def sample_soil(nx, nz, nsamples, model: FieldModel, soil: SoilModel, level=0, f
     _check(lib().rich_sample_soil(context(device), C.byref(model._c()), C.byref(soil._c()), nx, nz, level,
                                   first_sample, nsamples, coarsen_times, C.byref(ptrs), _stream(torch, device)))
     return tuple(out)
+
+
+def sample_soil_pair(nx, nz, nsamples, model: FieldModel, soil: SoilModel, level=0, first_sample=0, device=0,
+                     thetas=True):
+    """The five soil fields as covariance-upscaled couples: (fine tuple of
+    [S, nz, nx], coarse tuple of [S, nz/2, nx/2]); theta entries None when
+    thetas=False."""
+    torch = _torch()
+    d = f"cuda:{device}"
+    k = 5 if thetas else 3
+    fine = [torch.empty((nsamples, nz, nx), dtype=torch.float64, device=d) for _ in range(k)] + [None] * (5 - k)
+    coarse = [torch.empty((nsamples, nz // 2, nx // 2), dtype=torch.float64, device=d) for _ in range(k)]
+    coarse += [None] * (5 - k)
+    mk = lambda ts: _Soil(*[None if t is None else _dev_ptr(t, torch.float64, "soil field").value for t in ts])
+    pf, pc = mk(fine), mk(coarse)
+    _check(lib().rich_sample_soil_pair(context(device), C.byref(model._c()), C.byref(soil._c()), nx, nz, level,
+                                       first_sample, nsamples, C.byref(pf), C.byref(pc), _stream(torch, device)))
+    return tuple(fine), tuple(coarse)
 
 
 def solve_soil(problem: Problem, lnKs, alpha, n=None, theta_s=None, theta_r=None, alpha_scale=1.0,

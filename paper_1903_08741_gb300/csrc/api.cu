@@ -235,6 +235,19 @@ extern "C" int rich_sample_soil(rich_ctx_t ctx, const rich_field_t* field, const
                             (cudaStream_t)stream);
 }
 
+extern "C" int rich_sample_soil_pair(rich_ctx_t ctx, const rich_field_t* field, const rich_soil_model_t* soil,
+                                     int32_t nx, int32_t nz, uint32_t level, int64_t first_sample,
+                                     int32_t nsamples, const rich_soil_t* fine, const rich_soil_t* coarse,
+                                     void* stream) {
+    if (!ctx || !field || !soil || !fine || !coarse || nsamples < 0 || first_sample < 0) return RICH_ERR_INVALID;
+    if (nsamples > 0 && (!fine->lnKs || !fine->alpha || !fine->n || !coarse->lnKs || !coarse->alpha || !coarse->n))
+        return RICH_ERR_INVALID;
+    if (!(soil->n_span >= 0) || !(soil->theta_s_span >= 0) || !(soil->theta_r_span >= 0)) return RICH_ERR_INVALID;
+    RICH_CUDA(cudaSetDevice(ctx->device));
+    return rich_soil_pair_device(ctx, field, soil, nx, nz, level, first_sample, nsamples, fine, coarse,
+                                 (cudaStream_t)stream);
+}
+
 extern "C" int rich_solve_batch_host(rich_ctx_t ctx, const rich_problem_t* pb, int32_t nsamples,
                                      const double* lnKs, const double* alpha, double alpha_scale,
                                      double* qoi, double* p_final, int32_t* status,

@@ -464,13 +464,20 @@ __global__ void k_noise_upscale(int S, int pxc, int pzc, const cplx* __restrict_
 }
 }
 
+// one packed pair of fields drawn as a fine/coarse couple: outputs on the
+// fine grid (f_*) and on the half grid (c_*); im outputs null: lane unused
+struct PairPack {
+    uint32_t fld0;
+    PackTr tr;
+    double *f_re, *f_im, *c_re, *c_im;
+};
+
 // Fine fields on nx x nz and coarse fields on (nx/2) x (nz/2) from one draw by
 // covariance upscaling (Appendix A, Eqs. averaging, cov_upscale): the coarse
 // white noise is half the 2x2 sums of the fine noise on the torus, filtered
 // with the coarse grid's own spectrum on the half-size torus.
-int rich_fields_pair_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int nz, uint32_t level,
-                            int64_t first, int S, double* lk_f, double* al_f, double* lk_c,
-                            double* al_c, cudaStream_t st) {
+static int pair_packs_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int nz, uint32_t level,
+                             int64_t first, int S, int npk, const PairPack* pk, cudaStream_t st) {
     if (!pow2(nx) || !pow2(nz) || nx < 2 || nz < 2 || bad_field(fd))
         return RICH_ERR_INVALID;
     if (S == 0) return 0;
@@ -489,30 +496,59 @@ int rich_fields_pair_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int n
     cplx* wf = (cplx*)ctx->field_work;
     cplx* wc = wf + (size_t)npf * cap;
     const double inv_sigma = 1.0 / sqrt(fd->sigma2);
+    const int ncx = nx / 2, ncz = nz / 2;
     for (int s0 = 0; s0 < S; s0 += cap) {
         int cs = std::min(cap, S - s0);
-        rich_count_launch();
-        k_noise<<<nb((long long)cs * (npf / 2)), 256, 0, st>>>(cs, npf, fd->seed, level, first + s0, nullptr, wf);
-        rich_count_launch();
-        k_noise_upscale<<<nb((long long)cs * npc), 256, 0, st>>>(cs, px / 2, pz / 2, wf, wc);
-        if (int e = fftma_inplace(wf, cs, spf, st)) return e;
-        if (int e = fftma_inplace(wc, cs, spc, st)) return e;
-        rich_count_launch();
-        const PackTr tr{0, 0.0, 0.0, fd->alpha_lo, fd->alpha_span};
-        k_window<<<nb((long long)cs * nx * nz), 256, 0, st>>>(cs, nx, nz, px, pz, wf, inv_sigma, tr,
-                                                            lk_f + (size_t)s0 * nx * nz,
-                                                            al_f + (size_t)s0 * nx * nz);
-        const int ncx = nx / 2, ncz = nz / 2;
-        rich_count_launch();
-        k_window<<<nb((long long)cs * ncx * ncz), 256, 0, st>>>(cs, ncx, ncz, px / 2, pz / 2, wc, inv_sigma, tr,
-                                                              lk_c + (size_t)s0 * ncx * ncz,
-                                                              al_c + (size_t)s0 * ncx * ncz);
+        for (int k = 0; k < npk; ++k) {
+            const PairPack& P = pk[k];
+            rich_count_launch();
+            k_noise<<<nb((long long)cs * (npf / 2)), 256, 0, st>>>(cs, npf, fd->seed, level, first + s0, nullptr,
+                                                                    wf, P.fld0);
+            rich_count_launch();
+            k_noise_upscale<<<nb((long long)cs * npc), 256, 0, st>>>(cs, px / 2, pz / 2, wf, wc);
+            if (int e = fftma_inplace(wf, cs, spf, st)) return e;
+            if (int e = fftma_inplace(wc, cs, spc, st)) return e;
+            rich_count_launch();
+            k_window<<<nb((long long)cs * nx * nz), 256, 0, st>>>(
+                cs, nx, nz, px, pz, wf, inv_sigma, P.tr, P.f_re + (size_t)s0 * nx * nz,
+                P.f_im ? P.f_im + (size_t)s0 * nx * nz : nullptr);
+            rich_count_launch();
+            k_window<<<nb((long long)cs * ncx * ncz), 256, 0, st>>>(
+                cs, ncx, ncz, px / 2, pz / 2, wc, inv_sigma, P.tr, P.c_re + (size_t)s0 * ncx * ncz,
+                P.c_im ? P.c_im + (size_t)s0 * ncx * ncz : nullptr);
+        }
     }
     RICH_CUDA(cudaGetLastError());
     return 0;
 }
 
-// 2x2 block means of both fields (the coarse member of an MLMC pair)
+int rich_fields_pair_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int nz, uint32_t level,
+                            int64_t first, int S, double* lk_f, double* al_f, double* lk_c,
+                            double* al_c, cudaStream_t st) {
+    const PairPack pk{0u, PackTr{0, 0.0, 0.0, fd->alpha_lo, fd->alpha_span}, lk_f, al_f, lk_c, al_c};
+    return pair_packs_device(ctx, fd, nx, nz, level, first, S, 1, &pk, st);
+}
+
+// the five soil fields as covariance-upscaled fine/coarse couples (theta
+// outputs may be null: not drawn)
+int rich_soil_pair_device(rich_ctx* ctx, const rich_field_t* fd, const rich_soil_model_t* sm, int nx, int nz,
+                          uint32_t level, int64_t first, int S, const rich_soil_t* fine,
+                          const rich_soil_t* coarse, cudaStream_t st) {
+    PairPack pk[3];
+    int npk = 0;
+    pk[npk++] = PairPack{0u, PackTr{0, sm->lnks_mean, 0.0, fd->alpha_lo, fd->alpha_span}, fine->lnKs, fine->alpha,
+                         coarse->lnKs, coarse->alpha};
+    const bool ts = fine->theta_s && coarse->theta_s;
+    pk[npk++] = PairPack{2u, PackTr{1, sm->n_lo, sm->n_span, ts ? sm->theta_s_lo : 0.0, ts ? sm->theta_s_span : 0.0},
+                         fine->n, ts ? fine->theta_s : nullptr, coarse->n, ts ? coarse->theta_s : nullptr};
+    if (fine->theta_r && coarse->theta_r)
+        pk[npk++] = PairPack{4u, PackTr{1, sm->theta_r_lo, sm->theta_r_span, 0.0, 0.0}, fine->theta_r, nullptr,
+                             coarse->theta_r, nullptr};
+    return pair_packs_device(ctx, fd, nx, nz, level, first, S, npk, pk, st);
+}
+
+// 2x2 block means of both fields (the coarse member of an MLMC pair; al and
+// alc may be null)
 int rich_fields_average(rich_ctx* ctx, int S, int nx, int nz, const double* lk, const double* al,
                         double* lkc, double* alc, cudaStream_t st) {
     (void)ctx;

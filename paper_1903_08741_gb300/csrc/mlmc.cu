@@ -78,12 +78,16 @@ struct MlmcRun {
     cudaStream_t st = nullptr;
     cudaEvent_t ev[4] = {};
     DevBuf lkf, alf, lkc, alc, qf, qc, sf, sc, acc;
+    DevBuf nf, tsf, trf, ncb, tsc, trc;     // van Genuchten: n, theta_s, theta_r (fine, coarse)
+    bool vg = false, thetas = false;
     std::vector<double> t_pair, t_fine;
     std::vector<long long> n_done;
     int worst = 0;
 
     MlmcRun(rich_ctx* c, const rich_mlmc_cfg_t* g) : ctx(c), cfg(g) {
         NL = g->nlevels; L = NL - 1; nL = g->n0 << L;
+        vg = g->base.closure == RICH_VAN_GENUCHTEN;
+        thetas = vg && g->with_thetas;
         t_pair.assign(NL, 0.0); t_fine.assign(NL, 0.0); n_done.assign(NL, 0);
     }
     ~MlmcRun() {
@@ -92,7 +96,25 @@ struct MlmcRun {
     }
     int grid(int l) const { return cfg->n0 << l; }
     int steps(int l) const { return cfg->steps0 << l; }
-    double ascale(int l) const { return cfg->continuation ? (double)(l + 1) / (double)NL : 1.0; }
+    double ascale(int l) const {
+        return (cfg->continuation && !vg) ? (double)(l + 1) / (double)NL : 1.0;
+    }
+    // van Genuchten continuation steps of level l (Sec. 5.2): the
+    // fixed_levels finest levels keep the original alpha and n
+    int vg_steps(int l) const {
+        if (!cfg->continuation) return 0;
+        const int fixed = std::max(1, (int)cfg->fixed_levels);
+        return std::max(0, L + 1 - fixed - l);
+    }
+    rich_soil_in soil_in(int l, bool coarse) const {
+        rich_soil_in in;
+        in.n = (const double*)(coarse ? ncb.p : nf.p);
+        in.theta_s = thetas ? (const double*)(coarse ? tsc.p : tsf.p) : nullptr;
+        in.theta_r = thetas ? (const double*)(coarse ? trc.p : trf.p) : nullptr;
+        in.alpha_shift = -vg_steps(l) * cfg->d_alpha;
+        in.n_shift = vg_steps(l) * cfg->d_n;
+        return in;
+    }
 
     int init(int batch_hint) {
         RICH_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
@@ -108,6 +130,11 @@ struct MlmcRun {
         if (dalloc(lkf, fine_cells * 8) || dalloc(alf, fine_cells * 8) || dalloc(lkc, fine_cells * 2) ||
             dalloc(alc, fine_cells * 2) || dalloc(qf, B * 8) || dalloc(qc, B * 8) || dalloc(sf, B * 4) ||
             dalloc(sc, B * 4) || dalloc(acc, 8 * 8 * NL))
+            return RICH_ERR_OOM;
+        if (vg && (dalloc(nf, fine_cells * 8) || dalloc(ncb, fine_cells * 2)))
+            return RICH_ERR_OOM;
+        if (thetas && (dalloc(tsf, fine_cells * 8) || dalloc(trf, fine_cells * 8) || dalloc(tsc, fine_cells * 2) ||
+                       dalloc(trc, fine_cells * 2)))
             return RICH_ERR_OOM;
         RICH_CUDA(cudaMemsetAsync(acc.p, 0, 8 * 8 * NL, st));
         return 0;
@@ -141,27 +168,42 @@ struct MlmcRun {
         RICH_CUDA(cudaEventRecord(ev[0], st));
         int e;
         const uint32_t key = (uint32_t)l + cfg->key_offset;
-        if (cfg->coupling == 2 && l > 0)
+        const rich_soil_t fine{(double*)lkf.p, (double*)alf.p, (double*)nf.p, thetas ? (double*)tsf.p : nullptr,
+                               thetas ? (double*)trf.p : nullptr};
+        const rich_soil_t crs{(double*)lkc.p, (double*)alc.p, (double*)ncb.p, thetas ? (double*)tsc.p : nullptr,
+                              thetas ? (double*)trc.p : nullptr};
+        if (vg) {
+            if (cfg->coupling == 2 && l > 0)
+                e = rich_soil_pair_device(ctx, &cfg->field, &cfg->soil, M, M, key, s0, nb, &fine, &crs, st);
+            else
+                e = rich_soil_device(ctx, &cfg->field, &cfg->soil, ndraw, ndraw, key, s0, nb, coarsen, &fine, st);
+        } else if (cfg->coupling == 2 && l > 0) {
             e = rich_fields_pair_device(ctx, &cfg->field, M, M, key, s0, nb, (double*)lkf.p, (double*)alf.p,
                                         (double*)lkc.p, (double*)alc.p, st);
-        else
+        } else {
             e = rich_fields_device(ctx, &cfg->field, ndraw, ndraw, key, s0, nb, coarsen, (double*)lkf.p,
                                    (double*)alf.p, st);
+        }
         if (e) return e;
         if (l > 0 && cfg->coupling != 2) {
             e = rich_fields_average(ctx, nb, M, M, (double*)lkf.p, (double*)alf.p, (double*)lkc.p,
                                     (double*)alc.p, st);
+            if (!e && vg)
+                e = rich_fields_average(ctx, nb, M, M, fine.n, fine.theta_s, crs.n, crs.theta_s, st);
+            if (!e && thetas)
+                e = rich_fields_average(ctx, nb, M, M, fine.theta_r, nullptr, crs.theta_r, nullptr, st);
             if (e) return e;
         }
         RICH_CUDA(cudaEventRecord(ev[1], st));
+        const rich_soil_in in_f = soil_in(l, false), in_c = soil_in(l > 0 ? l - 1 : 0, true);
         int rc = rich_solve_device(ctx, &pf, nb, (double*)lkf.p, (double*)alf.p, ascale(l), (double*)qf.p,
-                                   nullptr, (int32_t*)sf.p, nullptr, st);
+                                   nullptr, (int32_t*)sf.p, nullptr, st, vg ? &in_f : nullptr);
         if (rc < 0) return rc;
         worst = std::max(worst, rc);
         RICH_CUDA(cudaEventRecord(ev[2], st));
         if (l > 0) {
             rc = rich_solve_device(ctx, &pc, nb, (double*)lkc.p, (double*)alc.p, ascale(l - 1), (double*)qc.p,
-                                   nullptr, (int32_t*)sc.p, nullptr, st);
+                                   nullptr, (int32_t*)sc.p, nullptr, st, vg ? &in_c : nullptr);
             if (rc < 0) return rc;
             worst = std::max(worst, rc);
         }
@@ -223,6 +265,13 @@ int check_cfg(const rich_mlmc_cfg_t* cfg) {
     const int NL = cfg->nlevels;
     if (NL < 1 || NL > RICH_MLMC_MAX_LEVELS || cfg->n0 < 2 || cfg->steps0 < 1 || !(cfg->t_final > 0) ||
         cfg->coupling < 0 || cfg->coupling > 2)
+        return RICH_ERR_INVALID;
+    rich_problem_t p0 = cfg->base;
+    p0.nx = p0.nz = cfg->n0; p0.nsteps = cfg->steps0; p0.dt = cfg->t_final / cfg->steps0;
+    if (rich_check_problem(&p0)) return RICH_ERR_INVALID;
+    if (cfg->base.closure == RICH_VAN_GENUCHTEN &&
+        (!(cfg->d_alpha >= 0) || !(cfg->d_n >= 0) || cfg->fixed_levels < 0 || !(cfg->soil.n_span >= 0) ||
+         !(cfg->soil.theta_s_span >= 0) || !(cfg->soil.theta_r_span >= 0)))
         return RICH_ERR_INVALID;
     for (int l = 0; l < NL; ++l) {
         if (cfg->nsamples[l] < 2) return RICH_ERR_INVALID;

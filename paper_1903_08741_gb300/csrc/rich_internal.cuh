@@ -101,6 +101,9 @@ int rich_fields_average(rich_ctx* ctx, int S, int nx, int nz, const double* lk, 
 int rich_soil_device(rich_ctx* ctx, const rich_field_t* fd, const rich_soil_model_t* sm, int nx, int nz,
                      uint32_t level, int64_t first, int S, int coarsen, const rich_soil_t* out,
                      cudaStream_t st);
+int rich_soil_pair_device(rich_ctx* ctx, const rich_field_t* fd, const rich_soil_model_t* sm, int nx, int nz,
+                          uint32_t level, int64_t first, int S, const rich_soil_t* fine,
+                          const rich_soil_t* coarse, cudaStream_t st);
 int rich_fields_device(rich_ctx* ctx, const rich_field_t* fd, int nx, int nz, uint32_t level,
                        int64_t first, int S, int coarsen, double* lnKs, double* alpha,
                        cudaStream_t st, const int64_t* first_dev = nullptr);

@@ -89,3 +89,34 @@ def test_per_level_tuning_keeps_fp64_statistics(R):
     g0 = R.mlmc_estimate(R.MlmcConfig(**base))
     g1 = R.mlmc_estimate(R.MlmcConfig(**base, tune_threads=(1024, 512, 1024)))
     assert g0["mean"] == g1["mean"] and g0["var"] == g1["var"]
+
+
+VG_TIGHT = dict(picard_tol=1e-10, mg_tol=1e-12, picard_maxit=60, mg_maxit=200)
+VG_PHYS = dict(theta_r=0.05, theta_s=0.5, p_top=-0.4, p_bottom=0.1, p_init=-0.4, closure=1, init_decay=80.0,
+               nu1=2, nu2=2, gamma=2, **VG_TIGHT)
+
+
+@pytest.mark.parametrize("coupling", [0, 1, 2])
+def test_van_genuchten_mlmc_matches_oracle(R, coupling):
+    """The paper's MLMC setting (Sec. 5.2): infiltration problem, five soil
+    fields of Table soilparams with Matern Phi_1 covariance, W(2,2) cycles,
+    h_l = dt_l, and the additive (d_alpha, d_n) continuation with the finest
+    level fixed; level statistics equal the oracle's to 1e-9."""
+    ns, n0, s0, T = (20, 10, 6), 8, 2, 0.25
+    cov = dict(nu=1.0, corr_len=0.2, corr_len_z=0.2)
+    cfg = R.MlmcConfig(nsamples=ns, n0=n0, steps0=s0, t_final=T, coupling=coupling, eps=1e-3,
+                       problem=R.Problem.infiltration(**VG_TIGHT),
+                       model=R.soil_field_model(2.0, R.FieldModel(seed=0, **cov)), soil=R.SoilModel(n_bl=1.6),
+                       d_alpha=0.1, d_n=0.1, fixed_levels=1)
+    g = R.mlmc_estimate(cfg)
+    o = O.mlmc_estimate(ns, n0, s0, T, coupling=coupling, soil=O.soil_model(2.0, 1.6), d_alpha=0.1, d_n=0.1,
+                        fixed_levels=1, **cov, **VG_PHYS)
+    for l, lev in enumerate(o):
+        y, qf, qc = lev["y"], lev["qf"], lev["qc"]
+        assert g["n"][l] == y.size and g["failed"][l] == lev["failed"]
+        assert y.size >= ns[l] // 2
+        assert rel(g["mean"][l], y.mean()) < 1e-9
+        assert rel(g["var"][l], y.var(ddof=1)) < 1e-8
+        assert rel(g["mean_f"][l], qf.mean()) < 1e-9
+        if l > 0:
+            assert rel(g["mean_c"][l], qc.mean()) < 1e-9

@@ -109,22 +109,27 @@ def test_fields_pair_match_oracle(R, n):
 
 MATERN = {"phi1": dict(nu=1.0, corr_len=0.2, corr_len_z=0.2), "phi2": dict(nu=0.5, corr_len=0.1, corr_len_z=0.01),
           "nu2.5": dict(nu=2.5, corr_len=0.15, corr_len_z=0.3)}
+# The smooth nu = 2.5 kernel's circulant spectrum reaches 2e-9 of its maximum
+# on the 64^2 grid's torus, where sqrt(lambda) amplifies rounding: perturbing
+# the covariance entries by one ulp moves its fields by ~3e-12 (Phi_1, Phi_2:
+# < 1e-13), so its bar is 1e-10 instead of 1e-12.
+MATERN_TOL = {"phi1": 1e-12, "phi2": 1e-12, "nu2.5": 1e-10}
 
 
 @pytest.mark.parametrize("name", sorted(MATERN))
 @pytest.mark.parametrize("n", [32, 64])
 def test_matern_fields_match_oracle(R, name, n):
     """Matern fields (Eq. nonIsotropic; the paper's Phi_1, Phi_2 and a smooth
-    anisotropic case): GPU spectrum + FFT-MA against the oracle, to 1e-12."""
-    kw = MATERN[name]
+    anisotropic case): GPU spectrum + FFT-MA against the oracle."""
+    kw, tol = MATERN[name], MATERN_TOL[name]
     lk_o, al_o = O.sample_fields(n, n, 5, seed=13, level=1, first_sample=2, **kw)
     lk, al = R.sample_fields(n, n, 5, R.FieldModel(seed=13, **kw), level=1, first_sample=2)
-    assert np.abs(lk.cpu().numpy() - lk_o).max() < 1e-12
-    assert np.abs(al.cpu().numpy() - al_o).max() < 1e-12
+    assert np.abs(lk.cpu().numpy() - lk_o).max() < tol
+    assert np.abs(al.cpu().numpy() - al_o).max() < tol
     o = O.sample_fields_pair(n, n, 3, seed=13, level=2, **kw)
     g = R.sample_fields_pair(n, n, 3, R.FieldModel(seed=13, **kw), level=2)
     for a, b in zip(g, o):
-        assert np.abs(a.cpu().numpy() - b).max() < 1e-12
+        assert np.abs(a.cpu().numpy() - b).max() < tol
 
 
 def test_matern_presets_and_invalid(R):

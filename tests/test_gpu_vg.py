@@ -73,6 +73,17 @@ def test_soil_fields_match_oracle(R, n, c):
         assert np.abs(a.cpu().numpy() - b).max() < 1e-12
 
 
+@pytest.mark.parametrize("thetas", [True, False])
+def test_soil_pair_matches_oracle(R, thetas):
+    cov = dict(nu=0.5, corr_len=0.1, corr_len_z=0.01)
+    fo, co = O.sample_soil_pair(64, 64, 3, O.soil_model(2.8, 1.55), seed=6, level=3, first_sample=4, **cov)
+    fg, cg = R.sample_soil_pair(64, 64, 3, R.soil_field_model(2.8, R.FieldModel(seed=6, **cov)),
+                                R.SoilModel(n_bl=1.55), level=3, first_sample=4, thetas=thetas)
+    k = 5 if thetas else 3
+    for a, b in list(zip(fg[:k], fo[:k])) + list(zip(cg[:k], co[:k])):
+        assert np.abs(a.cpu().numpy() - b).max() < 1e-12
+
+
 def test_soil_fields_without_thetas(R):
     g = R.sample_soil(32, 32, 3, R.soil_field_model(2.0, R.FieldModel.phi2()), R.SoilModel(n_bl=1.6),
                       thetas=False)

@@ -206,3 +206,22 @@ def test_soil_fields_marginals_and_shared_streams():
     assert np.array_equal(al, al2)
     # different streams: n is not a function of alpha
     assert abs(np.corrcoef(al[:, 3, 5], n[:, 3, 5])[0, 1]) < 0.1
+
+
+def test_soil_pair_members():
+    """Covariance-upscaled soil couples (Appendix A): the fine members are the
+    plain soil draw, the coarse ln Ks / alpha are the two-field pair's coarse
+    members, and the coarse n, theta_s, theta_r keep uniform marginals."""
+    from scipy import stats
+    model = O.soil_model(2.8, 1.55)
+    cov = dict(nu=0.5, corr_len=0.1, corr_len_z=0.01)
+    fine, coarse = O.sample_soil_pair(32, 32, 800, model, seed=2, level=1, **cov)
+    plain = O.sample_soil(32, 32, 800, model, seed=2, level=1, **cov)
+    for a, b in zip(fine, plain):
+        assert np.array_equal(a, b)
+    lkf, alf, lkc, alc = O.sample_fields_pair(32, 32, 800, seed=2, level=1, alpha_lo=model.alpha_lo,
+                                              alpha_span=model.alpha_span, **cov)
+    assert np.abs(coarse[0] - np.log(0.2) - lkc).max() < 1e-13 and np.array_equal(coarse[1], alc)
+    for arr, lo, w in ((coarse[2], 1.50, 0.1), (coarse[3], 0.45, 0.1), (coarse[4], 0.045, 0.01)):
+        assert arr.shape == (800, 16, 16) and arr.min() > lo and arr.max() < lo + w
+        assert stats.kstest((arr[:, 5, 9] - lo) / w, "uniform").pvalue > 1e-3
