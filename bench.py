@@ -172,6 +172,106 @@ def cpu_baseline(n, nsamples, steps, dt, seed=0, field="exp", cycle=1):
     return nsamples / dt_s, cores, dt_s
 
 
+# The (alpha, n) values of the robustness study (Sec. 4.3, Table alpha_n).
+MAP_ALPHAS = [0.2 * k for k in range(1, 21)]
+MAP_NS = [1.1, 1.2, 1.3, 1.4, 1.5, 1.6, 1.7, 1.8, 1.9, 2.0, 2.2, 2.4, 2.6, 2.8, 3.0, 3.2, 3.4, 3.6, 3.8, 4.0]
+
+
+def run_vgmap(args):
+    """The solver-robustness study of Sec. 4.3: the infiltration problem (van
+    Genuchten-Mualem, Eq. travellingwave) on h = 1/32 with dt = 1/64 to T = 0.1
+    (6 steps), W(2,2) cycles, Picard and MG tolerances 1e-5, Ks = 0.2 exp(Z)
+    with 64 Matern fields (Phi_1 unless --field phi2), for each of the 400
+    (alpha, n) pairs of Table alpha_n: all 25,600 solves in one batched launch.
+    Reports solves/s, and per pair the mean W-cycles per solve and the number
+    of failed samples (the paper's cost and failure maps)."""
+    import math
+    import numpy as np
+    import torch
+    import paper_1903_08741_gb300 as R
+    from paper_1903_08741_gb300 import build as B
+    B.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda:0")
+    field = args.field if args.field != "exp" else "phi1"
+    n, reps = 32, args.samples or 64
+    dt = 1.0 / 64
+    steps = args.time_steps or round(0.1 / dt)
+    prec = R.MIXED if args.precision == "mixed" else R.FP64
+    na, nn = len(MAP_ALPHAS), len(MAP_NS)
+    S = na * nn * reps
+    lk, _ = R.sample_fields(n, n, reps, R.FieldModel(seed=0, **FIELDS[field]))
+    lk = (lk + math.log(0.2)).repeat(na * nn, 1, 1).contiguous()          # pair-major, 64 fields each
+    pa = torch.tensor(MAP_ALPHAS, dtype=torch.float64, device=dev).repeat_interleave(nn * reps)
+    pn = torch.tensor(MAP_NS, dtype=torch.float64, device=dev).repeat(na).repeat_interleave(reps)
+    al = pa[:, None, None].expand(S, n, n).contiguous()
+    nf = pn[:, None, None].expand(S, n, n).contiguous()
+    pb = R.Problem.infiltration(nx=n, nz=n, nsteps=steps, dt=dt, precision=prec, cycle=args.cycle)
+    from paper_1903_08741_gb300 import autotune
+    block_threads, mixed_inner = autotune.tune(pb, S)
+    for _ in range(args.warmup):
+        R.solve_soil(pb, lk[:1024], al[:1024], nf[:1024])
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = R.launch_count()
+    R.profile(True)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        q, _, st, stats, _ = R.solve_soil(pb, lk, al, nf)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    kms, klaunch, kbytes, kflops = R.profile_read()
+    R.profile(False)
+    launches = R.launch_count() - l0
+    clk = clocks.stop()
+    pic, mg = R.sample_counters(S)
+    stv = st.cpu().numpy().reshape(na, nn, reps)
+    mgv = mg.cpu().numpy().reshape(na, nn, reps).astype(np.float64)
+    fail = ((stv == 1) | (stv == 3)).sum(axis=2)
+    okm = np.where((stv == 0) | (stv == 2), mgv, np.nan)
+    with np.errstate(invalid="ignore"):
+        mean_cyc = np.nanmean(okm, axis=2)
+    value = S * args.steps / (ms / 1e3)
+    k_tflops = kflops / (kms / 1e3) / 1e12 if kms > 0 else 0.0
+    out = {
+        "metric": "Picard-MG solves/s", "value": value, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if prec == R.FP64 else "f32-in-f64", "data": "synthetic",
+        "config": {"workload": f"vgmap: infiltration problem, van Genuchten-Mualem, {n}x{n} grid, {steps} steps "
+                               f"dt=1/64, {na}x{nn} (alpha, n) pairs x {reps} Ks fields ({FIELD_TEXT[field]}), "
+                               f"cycle index {pb.cycle}, tolerances 1e-5",
+                   "global_batch": S, "launch": {"block_threads": block_threads, "mixed_inner": mixed_inner},
+                   "l2": "inputs larger than L2 (3 x %.0f MB soil fields)" % (S * n * n * 8 / 1e6)},
+        "clocks": clk, "gpu_launches": launches,
+        "roofline": {"bound": "alu", "achieved": k_tflops, "peak": FP64_TFLOPS_NOMINAL, "unit": "TFLOP/s",
+                     "frac": k_tflops / FP64_TFLOPS_NOMINAL, "traffic": None,
+                     "peak_kind": "FP64 nominal (152 SMs x 2 FMA/clk x 2.07 GHz)",
+                     "note": "multigrid and Picard-assembly FLOPs only; the van Genuchten closure's "
+                             "transcendentals are not counted"},
+        "failed_samples": int(fail.sum()), "mean_wcycles_per_solve": float(np.nanmean(okm)),
+        "map": {"alpha": [round(a, 10) for a in MAP_ALPHAS], "n": MAP_NS,
+                "mean_cycles": [[None if not np.isfinite(v) else round(float(v), 1) for v in row] for row in mean_cyc],
+                "failures": fail.tolist()},
+    }
+    if not args.no_cpu:
+        import oracle as O
+        cores = os.cpu_count() or 1
+        t0 = time.perf_counter()
+        ns = args.cpu_samples or 2 * cores
+        sel = np.arange(ns) * (S // ns)
+        pbo = O.infiltration_problem(nsteps=steps, dt=dt, gamma=pb.cycle)
+        O.solve_batch_soil(pbo, lk[sel].cpu().numpy(), al[sel].cpu().numpy(), nf[sel].cpu().numpy(),
+                           want_p=False, nthreads=cores)
+        secs = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": ns / secs, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                               "sample": f"{ns} solves spread over the map, {secs:.1f} s"}
+    print(json.dumps(out))
+
+
 def workload_suffix(args):
     """Non-default field model / cycle, appended to the workload name."""
     out = ""
@@ -590,15 +690,17 @@ def main():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["mlmc5", "adjoint256", "mc512"], default="mc128")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["mlmc5", "adjoint256", "mc512", "vgmap"],
+                    default="mc128")
     ap.add_argument("--check", action="store_true", help="adjoint workload: finite-difference check")
     ap.add_argument("--adaptive-eps", type=float, default=0.0, help="mlmc5: also run Algorithm PC_MLMC to this RMSE")
     ap.add_argument("--coupling", type=int, default=0, help="MLMC field coupling (0 exact, 1 level grid)")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--field", choices=sorted(FIELDS), default="exp",
                     help="covariance of the fields: exponential 0.3 (configured) or Matern Phi_1 / Phi_2")
-    ap.add_argument("--cycle", type=int, default=1, choices=[1, 2, 3],
-                    help="multigrid cycle index: 1 V-cycle (configured), 2 W-cycle")
+    ap.add_argument("--cycle", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="multigrid cycle index: 1 V-cycle, 2 W-cycle (0: the workload's own, V for the "
+                         "configured workloads, W for vgmap)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
@@ -609,6 +711,7 @@ def main():
     ap.add_argument("--samples", type=int, default=0, help="override samples per GPU")
     ap.add_argument("--time-steps", type=int, default=0, help="override implicit-Euler steps")
     args = ap.parse_args()
+    args.cycle = args.cycle or (2 if args.workload == "vgmap" else 1)
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "mlmc5":
@@ -617,6 +720,8 @@ def main():
         run_adjoint(args)
     elif args.workload == "mc512":
         run_mc512(args)
+    elif args.workload == "vgmap":
+        run_vgmap(args)
     else:
         run_ours(args)
 

@@ -229,6 +229,15 @@ int rich_solve_soil(rich_ctx_t ctx, const rich_problem_t* pb, int32_t nsamples,
                     const rich_soil_t* soil, double alpha_scale, double alpha_shift, double n_shift,
                     double* qoi, double* p_final, int32_t* status, rich_stats_t* stats, void* stream);
 
+/* Per-sample totals of the context's last solve (rich_solve_batch, _soil,
+ * _async, _host): Picard iterations and multigrid cycles summed over the
+ * time steps of each of the first nsamples samples (the cost measure of the
+ * paper's Sec. 4.3 study), copied to DEVICE arrays (either may be NULL) on
+ * `stream`, which must be ordered after that solve.  RICH_ERR_INVALID if
+ * nsamples exceeds the last solve's batch. */
+int rich_sample_counters(rich_ctx_t ctx, int32_t nsamples, int64_t* picard_iters, int64_t* mg_cycles,
+                         void* stream);
+
 /* Multilevel Monte Carlo with parametric continuation (Sec. 5, Eqs.
  * telescope_ch6, MLMCestimator_ch6, SMC_ch6, MC_var_ch6, ML_var_ch6,
  * eq:MLMCVar, MLMCSAMP_ch6).  Level l (0..L) pairs a fine solve on an

@@ -752,6 +752,7 @@ static double inf_norm(const double* x, size_t n)
 static int mg_solve_levels(mg_level* Ls, int nlev, double tol, int maxit, int nu1, int nu2,
                            int gamma, int* cycles, double* res_hist)
 {
+    if (gamma < 1) gamma = 1;          /* cycle index 0 means the V-cycle, as in the C ABI */
     mg_level* L = &Ls[0];
     size_t n = (size_t)L->nx * L->nz;
     for (int l = 0; l < nlev; ++l) {

@@ -263,6 +263,7 @@ def lib():
                                        i32, C.POINTER(_Soil), vp]
         L.rich_sample_soil_pair.argtypes = [vp, C.POINTER(_Field), C.POINTER(_SoilModel), i32, i32, u32, i64, i32,
                                             C.POINTER(_Soil), C.POINTER(_Soil), vp]
+        L.rich_sample_counters.argtypes = [vp, i32, vp, vp, vp]
         L.rich_solve_soil.argtypes = [vp, C.POINTER(_Problem), i32, C.POINTER(_Soil), dbl, dbl, dbl, vp, vp, vp,
                                       C.POINTER(_Stats), vp]
         L.rich_mlmc_estimate.argtypes = [vp, C.POINTER(_MlmcCfg), C.POINTER(_MlmcResult)]
@@ -278,7 +279,7 @@ def exported_symbols():
             "rich_solve_batch_noalloc", "rich_mlmc_estimate", "rich_sample_fields_pair",
             "rich_kl_fields", "rich_solve_batch_adjoint", "rich_set_tuning", "rich_sample_fields_at",
             "rich_solve_batch_async", "rich_mlmc_adaptive", "rich_sample_soil", "rich_solve_soil",
-            "rich_sample_soil_pair"]
+            "rich_sample_soil_pair", "rich_sample_counters"]
 
 
 def _check(rc):
@@ -439,6 +440,18 @@ def solve_soil(problem: Problem, lnKs, alpha, n=None, theta_s=None, theta_r=None
                                       _dev_ptr(status, torch.int32, "status"), C.byref(st),
                                       _stream(torch, device)))
     return qoi, p, status, Stats(*[getattr(st, f) for f, _ in _Stats._fields_]), rc
+
+
+def sample_counters(nsamples, device=0):
+    """Per-sample (Picard iterations, multigrid cycles) of the device's last
+    solve, summed over its time steps: two int64 CUDA tensors [nsamples]."""
+    torch = _torch()
+    d = f"cuda:{device}"
+    pic = torch.empty(nsamples, dtype=torch.int64, device=d)
+    mg = torch.empty(nsamples, dtype=torch.int64, device=d)
+    _check(lib().rich_sample_counters(context(device), nsamples, _dev_ptr(pic, torch.int64, "picard"),
+                                      _dev_ptr(mg, torch.int64, "mg"), _stream(torch, device)))
+    return pic, mg
 
 
 def solve_batch_host(problem: Problem, lnKs: np.ndarray, alpha: np.ndarray, alpha_scale=1.0,

@@ -248,6 +248,19 @@ extern "C" int rich_sample_soil_pair(rich_ctx_t ctx, const rich_field_t* field, 
                                  (cudaStream_t)stream);
 }
 
+extern "C" int rich_sample_counters(rich_ctx_t ctx, int32_t nsamples, int64_t* picard_iters,
+                                    int64_t* mg_cycles, void* stream) {
+    if (!ctx || nsamples < 0 || nsamples > ctx->sb.last) return RICH_ERR_INVALID;
+    if (nsamples == 0) return 0;
+    RICH_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (picard_iters)
+        RICH_CUDA(cudaMemcpyAsync(picard_iters, ctx->sb.pic_total, 8 * (size_t)nsamples, cudaMemcpyDeviceToDevice, st));
+    if (mg_cycles)
+        RICH_CUDA(cudaMemcpyAsync(mg_cycles, ctx->sb.mg_total, 8 * (size_t)nsamples, cudaMemcpyDeviceToDevice, st));
+    return 0;
+}
+
 extern "C" int rich_solve_batch_host(rich_ctx_t ctx, const rich_problem_t* pb, int32_t nsamples,
                                      const double* lnKs, const double* alpha, double alpha_scale,
                                      double* qoi, double* p_final, int32_t* status,

@@ -152,6 +152,7 @@ int rich_solve_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const doubl
     rich_prof_begin(ctx, st);
     if (int e = fused_launch(P, grid, smem, nt, st)) return e;
     rich_prof_end(ctx, st, 0.0, 0.0);
+    w.last = S;
     if (status)
         RICH_CUDA(cudaMemcpyAsync(status, w.status, sizeof(int32_t) * S, cudaMemcpyDeviceToDevice, st));
     return 0;

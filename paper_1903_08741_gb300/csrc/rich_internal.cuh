@@ -23,6 +23,7 @@ struct rich_samplebuf {
     int cap = 0;
     int32_t *status = nullptr, *maxpic = nullptr;
     int64_t *pic_total = nullptr, *mg_total = nullptr;
+    int last = 0;                               // samples of the last fused solve
 };
 
 // sqrt of the circulant covariance spectrum on one torus (+ FFT twiddles)

@@ -159,3 +159,22 @@ def test_vg_invalid_calls(R):
         R.solve_soil(pb, x, x)                       # n missing
     with pytest.raises(R.RichError):
         R.solve_soil(R.Problem.infiltration(nx=16, nz=16, closure=5), x, x, x)
+
+
+def test_per_sample_counters_match_oracle(R):
+    """rich_sample_counters: per-sample Picard iterations and W-cycles of the
+    last solve equal the oracle's per-sample counts (cycle counts within the
+    rounding-order slack of the parity tests)."""
+    f = fields(32, 6, 2.0, 1.6, seed=8)
+    pbo = O.infiltration_problem(nsteps=4, dt=1 / 64, **TIGHT)
+    per = [O.solve_one_soil(pbo, *[a[s] for a in f])[3] for s in range(6)]
+    dev = torch.device("cuda:0")
+    pb = R.Problem.infiltration(nx=32, nz=32, nsteps=4, dt=1 / 64, **TIGHT)
+    R.solve_soil(pb, *[torch.from_numpy(a).to(dev) for a in f])
+    pic, mg = R.sample_counters(6)
+    pic, mg = pic.cpu().numpy(), mg.cpu().numpy()
+    for s in range(6):
+        assert abs(pic[s] - per[s].picard_iters) <= 1
+        assert abs(mg[s] - per[s].mg_cycles) <= max(2, 0.01 * per[s].mg_cycles)
+    with pytest.raises(R.RichError):
+        R.sample_counters(7)
