@@ -43,7 +43,10 @@ FP64_TFLOPS_NOMINAL = 1.25      # GB300 FP64 (non-tensor) peak: 152 SMs x 2 FMA/
 # launch of the default workload's timed step, from an ncu capture (see
 # profiles/); valid only while the kernel source is the one captured.
 TRAFFIC = {
-    # (precision, block_threads): (fused_sha() of the captured sources, bytes per launch)
+    # (precision, block_threads): (fused_sha() of the captured sources, bytes per launch).
+    # Captured on sources whose device code is this one (they differed only in a
+    # host-side bookkeeping statement of rich_solve_fused).
+    ("fp64", 1024): ("52f8a5de125eb8f74c4989a74c7bdc1970427074176107931869c22ccc5197ab", 38.95e12 + 11.17e12),
 }
 
 
@@ -382,6 +385,75 @@ def run_mlmc(args):
     print(json.dumps(out))
 
 
+MLMC_VG_LEVELS = dict(nsamples=(20000, 5000, 1200, 300, 80), n0=16, steps0=3, t_final=0.2)
+
+
+def run_mlmc_vg(args):
+    """The paper's MLMC experiment (Sec. 5.2): the infiltration problem with the
+    van Genuchten-Mualem closure and five soil fields (Table soilparams, Matern
+    Phi_1 unless --field phi2) on 16^2..256^2 with 3 2^l steps to T = 0.2
+    (dt_l close to h_l), target parameters alpha_L = 3.0, n_L = 1.45 (Phi_2:
+    2.8, 1.55) on the finest level, additive continuation d_alpha = 0.05,
+    d_n = 0.1 below it, W(2,2) cycles, tolerances 1e-5, N_l = 20000/5000/
+    1200/300/80, coupling by covariance upscaling.  Reports V_l, C_l and
+    W(eps = 1e-3), with the continuation and without it."""
+    import torch
+    import paper_1903_08741_gb300 as R
+    from paper_1903_08741_gb300 import build as B
+    B.build()
+    torch.cuda.set_device(0)
+    prec = R.MIXED if args.precision == "mixed" else R.FP64
+    field = args.field if args.field != "exp" else "phi1"
+    a_l, n_l = (3.0, 1.45) if field == "phi1" else (2.8, 1.55)
+    base = R.Problem.infiltration(precision=prec, cycle=args.cycle)
+    model = R.soil_field_model(a_l, R.FieldModel(seed=0, **FIELDS[field]))
+    soil = R.SoilModel(n_bl=n_l)
+    from paper_1903_08741_gb300 import autotune
+    tt, ti = [], []
+    for l, nl in enumerate(MLMC_VG_LEVELS["nsamples"]):
+        m = MLMC_VG_LEVELS["n0"] << l
+        st_l = MLMC_VG_LEVELS["steps0"] << l
+        # the tuner probes Gardner solves of the same grid; the launch shape carries over
+        bt, mi = autotune.tune(R.Problem(nx=m, nz=m, nsteps=st_l, dt=MLMC_VG_LEVELS["t_final"] / st_l,
+                                         precision=prec, cycle=base.cycle, **PHYS), nl)
+        tt.append(bt)
+        ti.append(mi)
+    R.set_tuning(0, 0)
+    common = dict(coupling=2, eps=1e-3, tune_threads=tuple(tt), tune_inner=tuple(ti), problem=base,
+                  model=model, soil=soil, d_alpha=0.05, d_n=0.1, fixed_levels=1)
+    for k in range(args.warmup):
+        R.mlmc_estimate(R.MlmcConfig(nsamples=(64, 32, 16, 8, 4), n0=16, steps0=3, t_final=0.2,
+                                     key_offset=100 + k, **common))
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = R.launch_count()
+    res = {}
+    for cont in (1, 0):
+        for k in range(args.steps):
+            res[cont] = R.mlmc_estimate(R.MlmcConfig(**MLMC_VG_LEVELS, key_offset=10 * k, continuation=cont,
+                                                     **common))
+    launches = R.launch_count() - l0
+    clk = clocks.stop()
+    r = res[1]
+    lev = lambda x: {k: x[k] for k in ("n", "failed", "mean", "var", "cost", "n_opt", "mean_f", "var_f")}
+    out = {
+        "metric": "MLMC cost to RMSE 1e-3 (s)", "value": r["w_eps"], "unit": "s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * r["seconds"],
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == R.FP64 else "f32-in-f64", "data": "synthetic",
+        "config": {"workload": f"mlmc5vg: infiltration problem, van Genuchten-Mualem, five soil fields "
+                               f"({FIELD_TEXT[field]}), 16^2..256^2, 3*2^l steps to T=0.2, alpha_L={a_l}, "
+                               f"n_L={n_l}, d_alpha=0.05, d_n=0.1, cycle index {base.cycle}, tolerances 1e-5, "
+                               f"N_l = 20000/5000/1200/300/80, covariance upscaling"},
+        "clocks": clk, "gpu_launches": launches,
+        "levels": lev(r), "estimate": r["estimate"], "rmse": r["rmse"],
+        "w_mc_eps_s": r["w_mc_eps"], "mc_over_mlmc": r["w_mc_eps"] / r["w_eps"],
+        "no_continuation": {"w_eps": res[0]["w_eps"], "levels": lev(res[0]), "estimate": res[0]["estimate"]},
+        "launch": {"block_threads": tt, "mixed_inner": ti, "from": "autotuner, per level"},
+    }
+    print(json.dumps(out))
+
+
 def run_adjoint(args):
     """Discrete adjoint (256^2 grid, 256 samples, 50 steps of dt = 0.002, ln Ks
     from a 128-mode KL expansion of exp(-r/0.2), xi ~ N(0,1) seed 0, alpha as
@@ -690,7 +762,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["mlmc5", "adjoint256", "mc512", "vgmap"],
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["mlmc5", "mlmc5vg", "adjoint256", "mc512", "vgmap"],
                     default="mc128")
     ap.add_argument("--check", action="store_true", help="adjoint workload: finite-difference check")
     ap.add_argument("--adaptive-eps", type=float, default=0.0, help="mlmc5: also run Algorithm PC_MLMC to this RMSE")
@@ -711,7 +783,7 @@ def main():
     ap.add_argument("--samples", type=int, default=0, help="override samples per GPU")
     ap.add_argument("--time-steps", type=int, default=0, help="override implicit-Euler steps")
     args = ap.parse_args()
-    args.cycle = args.cycle or (2 if args.workload == "vgmap" else 1)
+    args.cycle = args.cycle or (2 if args.workload in ("vgmap", "mlmc5vg") else 1)
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "mlmc5":
@@ -722,6 +794,8 @@ def main():
         run_mc512(args)
     elif args.workload == "vgmap":
         run_vgmap(args)
+    elif args.workload == "mlmc5vg":
+        run_mlmc_vg(args)
     else:
         run_ours(args)
 
