@@ -413,9 +413,8 @@ def run_mlmc_vg(args):
     for l, nl in enumerate(MLMC_VG_LEVELS["nsamples"]):
         m = MLMC_VG_LEVELS["n0"] << l
         st_l = MLMC_VG_LEVELS["steps0"] << l
-        # the tuner probes Gardner solves of the same grid; the launch shape carries over
-        bt, mi = autotune.tune(R.Problem(nx=m, nz=m, nsteps=st_l, dt=MLMC_VG_LEVELS["t_final"] / st_l,
-                                         precision=prec, cycle=base.cycle, **PHYS), nl)
+        bt, mi = autotune.tune(R.Problem.infiltration(nx=m, nz=m, nsteps=st_l, dt=MLMC_VG_LEVELS["t_final"] / st_l,
+                                                      precision=prec, cycle=base.cycle), nl)
         tt.append(bt)
         ti.append(mi)
     R.set_tuning(0, 0)

@@ -35,7 +35,8 @@ def _bucket(n):
 def _key(problem, nsamples, device_name):
     prec = "mixed" if problem.precision else "fp64"
     cyc = "" if problem.cycle <= 1 else f"|W{problem.cycle}"    # V-cycle keys stay as they were
-    return f"{device_name}|{problem.nx}x{problem.nz}|{prec}|S{_bucket(nsamples)}{cyc}"
+    clo = "" if problem.closure == 0 else "|VG"
+    return f"{device_name}|{problem.nx}x{problem.nz}|{prec}|S{_bucket(nsamples)}{cyc}{clo}"
 
 
 def _load(path):
@@ -70,7 +71,14 @@ def tune(problem, nsamples, device=0, force=False, probe_steps=2, verbose=False)
         return bt, mi
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     S = max(1, min(nsamples, 4 * sms))
-    lk, al = R.sample_fields(problem.nx, problem.nz, S, R.FieldModel(seed=987654321), device=device)
+    if problem.closure == R.VAN_GENUCHTEN:
+        # van Genuchten kernels probe on soil fields of a mid-range soil
+        flds = R.sample_soil(problem.nx, problem.nz, S, R.soil_field_model(2.0, R.FieldModel(seed=987654321)),
+                             R.SoilModel(n_bl=1.6), device=device, thetas=False)[:3]
+        solve = lambda k: R.solve_soil(probe, *[f[:k].contiguous() for f in flds])
+    else:
+        lk, al = R.sample_fields(problem.nx, problem.nz, S, R.FieldModel(seed=987654321), device=device)
+        solve = lambda k: R.solve_batch(probe, lk[:k].contiguous(), al[:k].contiguous())
     probe = R.Problem(**{**problem.__dict__, "nsteps": max(1, min(problem.nsteps, probe_steps))})
     inners = [1, 2, 3, 4] if problem.precision else [0]
     timings = {}
@@ -78,10 +86,10 @@ def tune(problem, nsamples, device=0, force=False, probe_steps=2, verbose=False)
     for bt in (512, 1024):
         for mi in inners:
             R.set_tuning(bt, mi, device)
-            R.solve_batch(probe, lk[: min(S, 8)].contiguous(), al[: min(S, 8)].contiguous())
+            solve(min(S, 8))
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            R.solve_batch(probe, lk, al)
+            solve(S)
             e1.record(stream)
             torch.cuda.synchronize(dev)
             timings[f"{bt}/{mi}"] = e0.elapsed_time(e1)
