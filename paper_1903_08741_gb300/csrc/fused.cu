@@ -12,6 +12,28 @@ size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 }  // namespace
 
 // Slot layout and problem constants of the fused kernel (no device work).
+// Dynamic shared memory of a CTA: the coarsest level's dense matrix, then the
+// corrections dp of as many levels (coarsest first) as fit the budget of the
+// launch shape (one 1024-thread CTA per SM may use ~220 KB, two 512-thread
+// CTAs ~104 KB each), so that the Gauss-Seidel neighbour reads of those levels
+// stay on chip; levels that do not fit keep dp in the slot.  Results do not
+// depend on where dp lives.
+static void plan_smem(FParams& P, int nt) {
+    const size_t w = P.mixed ? 4 : 8;
+    const int c = P.nlev - 1;
+    const size_t nnc = (size_t)P.nx[c] * P.nz[c];
+    size_t off = (nnc * (nnc + 1) * w + 15) & ~(size_t)15;
+    const size_t budget = nt == 1024 ? 220 * 1024 : 104 * 1024;
+    for (int l = 0; l < MAXL; ++l) P.osm[l] = -1;
+    for (int l = c; l >= 0; --l) {
+        const size_t bytes = ((size_t)P.nx[l] * P.nz[l] * w + 15) & ~(size_t)15;
+        if (off + bytes > budget) break;
+        P.osm[l] = (long long)off;
+        off += bytes;
+    }
+    P.smem_bytes = (long long)off;
+}
+
 static int fused_setup(const rich_problem_t* pb, int S, FParams& P, int ckpt_every = 0) {
     P = FParams{};
     const int nlev = rich_count_levels(pb->nx, pb->nz);
@@ -71,10 +93,7 @@ static int fused_setup(const rich_problem_t* pb, int S, FParams& P, int ckpt_eve
     return 0;
 }
 
-static size_t fused_smem(const FParams& P) {
-    const int nnc = P.nx[P.nlev - 1] * P.nz[P.nlev - 1];
-    return (size_t)nnc * (nnc + 1) * (P.mixed ? 4 : 8);
-}
+static size_t fused_smem(const FParams& P) { return (size_t)P.smem_bytes; }
 
 // block shapes the fused kernel is built for: 512 threads (two resident CTAs
 // per SM at 64 registers) or 1024 (one; half the resident scratch slots)
@@ -83,8 +102,10 @@ static size_t fused_smem(const FParams& P) {
 template <int NT, bool WC>
 static int occ_nt(const FParams& P, size_t smem, int* occ) {
     if (P.mixed) {
+        if (int e = allow_dyn_smem((const void*)k_fused<float, NT, WC, 0>, smem)) return e;
         RICH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_fused<float, NT, WC, 0>, NT, smem));
     } else {
+        if (int e = allow_dyn_smem((const void*)k_fused<double, NT, WC, 0>, smem)) return e;
         RICH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_fused<double, NT, WC, 0>, NT, smem));
     }
     if (*occ < 1) *occ = 1;
@@ -124,14 +145,15 @@ int rich_solve_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const doubl
     rich_samplebuf& w = ctx->sb;
     FParams P;
     if (pb->closure == RICH_VAN_GENUCHTEN && (!soil || !soil->n)) return RICH_ERR_INVALID;
+    const int nt = ctx->tune_threads == 1024 ? 1024 : 512;
     if (int e = fused_setup(pb, S, P)) return e;
+    plan_smem(P, nt);
     if (soil) {
         P.n_in = soil->n; P.ts_in = soil->theta_s; P.tr_in = soil->theta_r;
         P.alpha_shift = soil->alpha_shift; P.n_shift = soil->n_shift;
     }
     const size_t off = (size_t)P.slot_bytes;
     const size_t smem = fused_smem(P);
-    const int nt = ctx->tune_threads == 1024 ? 1024 : 512;
     P.mixed_inner = ctx->tune_mixed_inner > 0 ? ctx->tune_mixed_inner : MIXED_INNER_DEFAULT;
     int occ = 0;
     if (int e = fused_occupancy(P, smem, nt, &occ)) return e;
@@ -166,12 +188,14 @@ int rich_adjoint_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const dou
     FParams P;
     if (ckpt_every < 1 || pb->closure != RICH_GARDNER) return RICH_ERR_INVALID;
     if (int e = fused_setup(pb, S, P, ckpt_every)) return e;
+    plan_smem(P, 512);
     P.adj_tol = adj_tol; P.adj_maxit = adj_maxit; P.adj_inner = pb->precision == RICH_MIXED ? 2 : 1;
     P.mixed_inner = ctx->tune_mixed_inner > 0 ? ctx->tune_mixed_inner : MIXED_INNER_DEFAULT;
     const size_t smem = fused_smem(P);
     int occ = 0;
     const void* kern = P.mixed ? (P.gamma > 1 ? (const void*)k_adjoint<float, true> : (const void*)k_adjoint<float, false>)
                                : (P.gamma > 1 ? (const void*)k_adjoint<double, true> : (const void*)k_adjoint<double, false>);
+    if (int e = allow_dyn_smem(kern, smem)) return e;
     RICH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 512, smem));
     occ = std::max(occ, 1);
     const int grid = std::max(1, std::min(S, ctx->sm_count * occ));
@@ -257,6 +281,7 @@ extern "C" int rich_solve_batch_noalloc(const rich_problem_t* pb, int32_t nsampl
         rich_set_error("unsupported grid", __FILE__, __LINE__);
         return e;
     }
+    plan_smem(P, 512);
     const size_t slot = (size_t)P.slot_bytes;
     const size_t slots = (RICH_NOALLOC_SCRATCH_BYTES - 256) / slot;
     if (slots < 1) {

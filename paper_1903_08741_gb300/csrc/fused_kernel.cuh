@@ -59,6 +59,9 @@ struct FParams {
     unsigned mnx[MAXL], mhx[MAXL];          // magic reciprocals of nx and nx/2
     long long o64[MAXL][N64];               // byte offsets in the slot (-1: absent)
     long long omg[MAXL][NMG];
+    long long osm[MAXL];                    // level's dp in dynamic shared memory at this
+                                            // byte offset (-1: in the slot)
+    long long smem_bytes;                   // dynamic shared memory of a CTA
     long long o_f64, o_dp64, o_p, o_thold, o_Ks, o_a, o_K, o_th;
     long long slot_bytes;
     char* scratch;
@@ -90,6 +93,24 @@ struct FParams {
     const double* tr_in;
     long long o_n, o_m, o_trc, o_tsc;
 };
+
+// allow a kernel `bytes` of dynamic shared memory above the 48 KB default; the
+// attribute is set once per (kernel, device, larger size)
+inline int allow_dyn_smem(const void* kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return 0;
+    struct Grant { const void* k; int dev; size_t bytes; };
+    static Grant grants[128];
+    static int ngrants = 0;
+    int dev = 0;
+    RICH_CUDA(cudaGetDevice(&dev));
+    int i = 0;
+    while (i < ngrants && !(grants[i].k == kernel && grants[i].dev == dev)) ++i;
+    if (i < ngrants && grants[i].bytes >= bytes) return 0;
+    RICH_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    if (i == ngrants && ngrants < 128) ++ngrants;
+    if (i < 128) grants[i] = Grant{kernel, dev, bytes};
+    return 0;
+}
 
 // launch shapes of the van Genuchten-Mualem instantiations (fused_vg.cu)
 int rich_vg_occupancy(const FParams& P, size_t smem, int nt, int* occ);
@@ -799,7 +820,8 @@ struct Cta {
 };
 
 template <typename TM>
-__device__ __forceinline__ void init_levels(const FParams& P, char* slot, Lv64* L64, Lv<TM>* LM) {
+__device__ __forceinline__ void init_levels(const FParams& P, char* slot, unsigned char* sm, Lv64* L64,
+                                            Lv<TM>* LM) {
     constexpr bool SC = Scaled<TM>::value;
     const int nlev = P.nlev;
     if ((int)threadIdx.x < nlev) {
@@ -812,6 +834,7 @@ __device__ __forceinline__ void init_levels(const FParams& P, char* slot, Lv64* 
         b.nx = a.nx; b.nz = a.nz; b.hx = a.nx >> 1; b.nc = a.nc; b.mnx = P.mnx[l]; b.mhx = P.mhx[l];
         TM** qq[NMG] = {&b.c0, &b.c1, &b.c2, &b.c3, &b.q, &b.f, &b.dp};
         for (int k = 0; k < NMG; ++k) *qq[k] = P.omg[l][k] >= 0 ? (TM*)(slot + P.omg[l][k]) : nullptr;
+        if (P.osm[l] >= 0) b.dp = (TM*)(sm + P.osm[l]);   // corrections of small levels on chip
         if constexpr (SC) b.D = (TM*)a.D;                 // FP64: shares the operator diagonal
         else { b.D = b.c3; b.c3 = nullptr; }              // FP32: its own copy
     }
@@ -827,7 +850,7 @@ k_fused(const FParams P) {
     __shared__ Lv64 L64[MAXL];
     __shared__ Lv<TM> LM[MAXL];
     char* slot = P.scratch + (size_t)blockIdx.x * P.slot_bytes;
-    init_levels<TM>(P, slot, L64, LM);
+    init_levels<TM>(P, slot, smraw, L64, LM);
     Cta<TM, WC, CL> C(P, slot, L64, LM, reinterpret_cast<TM*>(smraw), red);
     const int nc = C.nc, tid = C.tid, nt = C.nt;
     for (;;) {
@@ -872,7 +895,7 @@ k_adjoint(const FParams P) {
     __shared__ Lv64 L64[MAXL];
     __shared__ Lv<TM> LM[MAXL];
     char* slot = P.scratch + (size_t)blockIdx.x * P.slot_bytes;
-    init_levels<TM>(P, slot, L64, LM);
+    init_levels<TM>(P, slot, smraw, L64, LM);
     Cta<TM, WC> C(P, slot, L64, LM, reinterpret_cast<TM*>(smraw), red);
     const int nc = C.nc, nx = C.nx, tid = C.tid, nt = C.nt;
     const int CK = P.ckpt_every;

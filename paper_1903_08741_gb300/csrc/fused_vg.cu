@@ -8,8 +8,10 @@ namespace {
 template <int NT, bool WC>
 int occ_vg(const FParams& P, size_t smem, int* occ) {
     if (P.mixed) {
+        if (int e = allow_dyn_smem((const void*)k_fused<float, NT, WC, 1>, smem)) return e;
         RICH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_fused<float, NT, WC, 1>, NT, smem));
     } else {
+        if (int e = allow_dyn_smem((const void*)k_fused<double, NT, WC, 1>, smem)) return e;
         RICH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_fused<double, NT, WC, 1>, NT, smem));
     }
     if (*occ < 1) *occ = 1;
