@@ -43,10 +43,8 @@ FP64_TFLOPS_NOMINAL = 1.25      # GB300 FP64 (non-tensor) peak: 152 SMs x 2 FMA/
 # launch of the default workload's timed step, from an ncu capture (see
 # profiles/); valid only while the kernel source is the one captured.
 TRAFFIC = {
-    # (precision, block_threads): (fused_sha() of the captured sources, bytes per launch).
-    # Captured on sources whose device code is this one (they differed only in a
-    # host-side bookkeeping statement of rich_solve_fused).
-    ("fp64", 1024): ("52f8a5de125eb8f74c4989a74c7bdc1970427074176107931869c22ccc5197ab", 38.95e12 + 11.17e12),
+    # (precision, block_threads): (fused_sha() of the captured sources, bytes per launch)
+    ("fp64", 1024): ("bc4043f576f62d5250d78e2a1010858e8c688048faf291b2d1717d0c1fb0921d", 30.69e12 + 5.55e12),
 }
 
 
