@@ -417,7 +417,7 @@ def run_mlmc_vg(args):
         ti.append(mi)
     R.set_tuning(0, 0)
     common = dict(coupling=2, eps=1e-3, tune_threads=tuple(tt), tune_inner=tuple(ti), problem=base,
-                  model=model, soil=soil, d_alpha=0.05, d_n=0.1, fixed_levels=1)
+                  model=model, soil=soil, d_alpha=0.05, d_n=0.1, fixed_levels=args.fixed_levels)
     for k in range(args.warmup):
         R.mlmc_estimate(R.MlmcConfig(nsamples=(64, 32, 16, 8, 4), n0=16, steps0=3, t_final=0.2,
                                      key_offset=100 + k, **common))
@@ -440,7 +440,8 @@ def run_mlmc_vg(args):
         "dtype": "f64" if prec == R.FP64 else "f32-in-f64", "data": "synthetic",
         "config": {"workload": f"mlmc5vg: infiltration problem, van Genuchten-Mualem, five soil fields "
                                f"({FIELD_TEXT[field]}), 16^2..256^2, 3*2^l steps to T=0.2, alpha_L={a_l}, "
-                               f"n_L={n_l}, d_alpha=0.05, d_n=0.1, cycle index {base.cycle}, tolerances 1e-5, "
+                               f"n_L={n_l}, d_alpha=0.05, d_n=0.1, {args.fixed_levels} finest level(s) unperturbed, "
+                               f"cycle index {base.cycle}, tolerances 1e-5, "
                                f"N_l = 20000/5000/1200/300/80, covariance upscaling"},
         "clocks": clk, "gpu_launches": launches,
         "levels": lev(r), "estimate": r["estimate"], "rmse": r["rmse"],
@@ -767,6 +768,8 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--field", choices=sorted(FIELDS), default="exp",
                     help="covariance of the fields: exponential 0.3 (configured) or Matern Phi_1 / Phi_2")
+    ap.add_argument("--fixed-levels", type=int, default=1,
+                    help="mlmc5vg: finest levels solved with the original (alpha, n) (Sec. 5.2)")
     ap.add_argument("--cycle", type=int, default=0, choices=[0, 1, 2, 3],
                     help="multigrid cycle index: 1 V-cycle, 2 W-cycle (0: the workload's own, V for the "
                          "configured workloads, W for vgmap)")
