@@ -1,8 +1,9 @@
 """Autotuner of the fused solver's launch shape.
 
-Candidates: 512-thread CTAs (two resident per SM: more samples in flight) or
-1024-thread CTAs (one per SM: half the resident scratch slots, so more of the
-hierarchy stays in L2, and twice the threads per sample); for the mixed path
+Candidates: 256-thread CTAs (four resident per SM: small grids, whose levels
+give a large CTA too little work between barriers), 512-thread CTAs (two per
+SM) or 1024-thread CTAs (one per SM: the fewest resident scratch slots, so more
+of the hierarchy stays in L2, and the most threads per sample); for the mixed path
 also the number of FP32 V-cycles per FP64 defect (1..4).  Each candidate solves
 a probe batch of the same grid and precision (fresh seeded fields, two time
 steps) timed with CUDA events; the fastest is cached in a JSON file keyed by
@@ -83,7 +84,7 @@ def tune(problem, nsamples, device=0, force=False, probe_steps=2, verbose=False)
     inners = [1, 2, 3, 4] if problem.precision else [0]
     timings = {}
     stream = torch.cuda.current_stream(dev)
-    for bt in (512, 1024):
+    for bt in (256, 512, 1024):
         for mi in inners:
             R.set_tuning(bt, mi, device)
             solve(min(S, 8))

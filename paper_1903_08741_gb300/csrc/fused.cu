@@ -15,7 +15,7 @@ size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 // Dynamic shared memory of a CTA: the coarsest level's dense matrix, then the
 // corrections dp of as many levels (coarsest first) as fit the budget of the
 // launch shape (one 1024-thread CTA per SM may use ~220 KB, two 512-thread
-// CTAs ~104 KB each), so that the Gauss-Seidel neighbour reads of those levels
+// CTAs ~104 KB each, four 256-thread CTAs ~50 KB each), so that the Gauss-Seidel neighbour reads of those levels
 // stay on chip; levels that do not fit keep dp in the slot.  Results do not
 // depend on where dp lives.
 static void plan_smem(FParams& P, int nt) {
@@ -23,7 +23,7 @@ static void plan_smem(FParams& P, int nt) {
     const int c = P.nlev - 1;
     const size_t nnc = (size_t)P.nx[c] * P.nz[c];
     size_t off = (nnc * (nnc + 1) * w + 15) & ~(size_t)15;
-    const size_t budget = nt == 1024 ? 220 * 1024 : 104 * 1024;
+    const size_t budget = nt == 1024 ? 220 * 1024 : nt == 512 ? 104 * 1024 : 50 * 1024;
     for (int l = 0; l < MAXL; ++l) P.osm[l] = -1;
     for (int l = c; l >= 0; --l) {
         const size_t bytes = ((size_t)P.nx[l] * P.nz[l] * w + 15) & ~(size_t)15;
@@ -95,8 +95,9 @@ static int fused_setup(const rich_problem_t* pb, int S, FParams& P, int ckpt_eve
 
 static size_t fused_smem(const FParams& P) { return (size_t)P.smem_bytes; }
 
-// block shapes the fused kernel is built for: 512 threads (two resident CTAs
-// per SM at 64 registers) or 1024 (one; half the resident scratch slots)
+// block shapes the fused kernel is built for: 256 threads (four resident CTAs
+// per SM at 64 registers: small grids, where a CTA-wide barrier per half-sweep
+// dominates), 512 (two) or 1024 (one; the fewest resident scratch slots)
 // (and, per shape, the V-cycle and the gamma >= 2 cycle instantiations)
 // (the van Genuchten-Mualem instantiations live in fused_vg.cu)
 template <int NT, bool WC>
@@ -116,6 +117,7 @@ static int fused_occupancy(const FParams& P, size_t smem, int nt, int* occ) {
     if (P.closure == RICH_VAN_GENUCHTEN) return rich_vg_occupancy(P, smem, nt, occ);
     const bool wc = P.gamma > 1;
     if (nt == 1024) return wc ? occ_nt<1024, true>(P, smem, occ) : occ_nt<1024, false>(P, smem, occ);
+    if (nt == 256) return wc ? occ_nt<256, true>(P, smem, occ) : occ_nt<256, false>(P, smem, occ);
     return wc ? occ_nt<512, true>(P, smem, occ) : occ_nt<512, false>(P, smem, occ);
 }
 
@@ -131,6 +133,7 @@ static int fused_launch(const FParams& P, int grid, size_t smem, int nt, cudaStr
     const bool wc = P.gamma > 1;
     if (P.closure == RICH_VAN_GENUCHTEN) rich_vg_launch(P, grid, smem, nt, st);
     else if (nt == 1024) { if (wc) launch_nt<1024, true>(P, grid, smem, st); else launch_nt<1024, false>(P, grid, smem, st); }
+    else if (nt == 256) { if (wc) launch_nt<256, true>(P, grid, smem, st); else launch_nt<256, false>(P, grid, smem, st); }
     else if (wc) launch_nt<512, true>(P, grid, smem, st);
     else launch_nt<512, false>(P, grid, smem, st);
     RICH_CUDA(cudaGetLastError());
@@ -145,7 +148,7 @@ int rich_solve_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const doubl
     rich_samplebuf& w = ctx->sb;
     FParams P;
     if (pb->closure == RICH_VAN_GENUCHTEN && (!soil || !soil->n)) return RICH_ERR_INVALID;
-    const int nt = ctx->tune_threads == 1024 ? 1024 : 512;
+    const int nt = (ctx->tune_threads == 1024 || ctx->tune_threads == 256) ? ctx->tune_threads : 512;
     if (int e = fused_setup(pb, S, P)) return e;
     plan_smem(P, nt);
     if (soil) {

@@ -842,7 +842,7 @@ __device__ __forceinline__ void init_levels(const FParams& P, char* slot, unsign
 }
 
 template <typename TM, int NT, bool WC, int CL>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, NT <= 256 ? 4 : 1)
 k_fused(const FParams P) {
     extern __shared__ unsigned char smraw[];
     __shared__ unsigned long long red[33];

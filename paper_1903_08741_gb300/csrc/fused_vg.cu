@@ -31,12 +31,14 @@ namespace rich_fused {
 int rich_vg_occupancy(const FParams& P, size_t smem, int nt, int* occ) {
     const bool wc = P.gamma > 1;
     if (nt == 1024) return wc ? occ_vg<1024, true>(P, smem, occ) : occ_vg<1024, false>(P, smem, occ);
+    if (nt == 256) return wc ? occ_vg<256, true>(P, smem, occ) : occ_vg<256, false>(P, smem, occ);
     return wc ? occ_vg<512, true>(P, smem, occ) : occ_vg<512, false>(P, smem, occ);
 }
 
 void rich_vg_launch(const FParams& P, int grid, size_t smem, int nt, cudaStream_t st) {
     const bool wc = P.gamma > 1;
     if (nt == 1024) { if (wc) launch_vg<1024, true>(P, grid, smem, st); else launch_vg<1024, false>(P, grid, smem, st); }
+    else if (nt == 256) { if (wc) launch_vg<256, true>(P, grid, smem, st); else launch_vg<256, false>(P, grid, smem, st); }
     else if (wc) launch_vg<512, true>(P, grid, smem, st);
     else launch_vg<512, false>(P, grid, smem, st);
 }

@@ -248,7 +248,8 @@ def test_mc128_full_batch_sampled(R):
 
 
 def test_block_shape_does_not_change_fp64_results(R):
-    """The 1024-thread launch shape gives bit-identical FP64 results; the mixed
+    """The 256- and 1024-thread launch shapes give bit-identical FP64 results
+    (they also place different levels' corrections in shared memory); the mixed
     path with other inner-cycle counts stays within its 1e-6 QoI bound."""
     lk, al = O.sample_fields(32, 32, 10, seed=6)
     dev = torch.device("cuda:0")
@@ -257,13 +258,14 @@ def test_block_shape_does_not_change_fp64_results(R):
     try:
         R.set_tuning(512, 0)
         q1, p1, s1, _, _ = R.solve_batch(pb, *a, want_p=True)
-        R.set_tuning(1024, 0)
-        q2, p2, s2, _, _ = R.solve_batch(pb, *a, want_p=True)
-        assert torch.equal(s1, s2) and torch.equal(p1, p2)
         ok = s1 == 0
-        assert torch.equal(q1[ok], q2[ok])
+        for bt in (256, 1024):
+            R.set_tuning(bt, 0)
+            q2, p2, s2, _, _ = R.solve_batch(pb, *a, want_p=True)
+            assert torch.equal(s1, s2) and torch.equal(p1, p2)
+            assert torch.equal(q1[ok], q2[ok])
         pm = gpu_problem(R, 32, 32, 3, 0.01, precision=R.MIXED)
-        for bt, mi in ((512, 1), (1024, 4)):
+        for bt, mi in ((512, 1), (1024, 4), (256, 2)):
             R.set_tuning(bt, mi)
             qm, _, sm, _, _ = R.solve_batch(pm, *a)
             okm = ok & (sm == 0)
@@ -355,3 +357,21 @@ def test_invalid_cycle_index_rejected(R):
     with pytest.raises(R.RichError):
         R.solve_batch(gpu_problem(R, 8, 8, 1, 0.01, cycle=5), torch.from_numpy(lk).to(dev),
                       torch.from_numpy(al).to(dev), 1.0)
+
+
+def test_block_shapes_bitwise_at_128(R):
+    """At 128^2 the three launch shapes stage different levels in shared memory
+    (1024: all, 512: 64^2 and coarser, 256: 32^2 and coarser): same bits."""
+    lk, al = O.sample_fields(128, 128, 3, seed=12)
+    dev = torch.device("cuda:0")
+    a = (torch.from_numpy(lk).to(dev), torch.from_numpy(al).to(dev))
+    pb = gpu_problem(R, 128, 128, 2, 0.005)
+    out = {}
+    try:
+        for bt in (256, 512, 1024):
+            R.set_tuning(bt, 0)
+            out[bt] = R.solve_batch(pb, *a, want_p=True)
+    finally:
+        R.set_tuning(0, 0)
+    for bt in (256, 1024):
+        assert torch.equal(out[bt][1], out[512][1]) and torch.equal(out[bt][2], out[512][2])
