@@ -338,6 +338,8 @@ def run_mlmc(args):
     base = R.Problem(precision=prec, cycle=args.cycle, **PHYS)
     cfg = R.MlmcConfig(**MLMC_LEVELS, coupling=args.coupling, eps=1e-3, tune_threads=tuple(tt),
                        tune_inner=tuple(ti), problem=base, model=model)
+    if args.batch1:
+        return run_mlmc_batch1(args, R, cfg, prec)
     for k in range(args.warmup):
         small = R.MlmcConfig(nsamples=(64, 32, 16, 8, 4), n0=16, steps0=5, t_final=0.1,
                              coupling=args.coupling, key_offset=100 + k, problem=base, model=model)
@@ -450,6 +452,35 @@ def run_mlmc_vg(args):
         "launch": {"block_threads": tt, "mixed_inner": ti, "from": "autotuner, per level"},
     }
     print(json.dumps(out))
+
+
+def run_mlmc_batch1(args, R, cfg, prec):
+    """The same MLMC hierarchy with every sample solved on its own (one CTA per
+    launch, batch 1), on N_l scaled down to 200/50/12/3/2: the per-level costs
+    C_l of unbatched GPU solves, to set against the batched C_l (the level
+    variances are the batched run's, which these few samples cannot estimate)."""
+    cfg.nsamples = (200, 50, 12, 3, 2)
+    cfg.batch = 1
+    cfg.key_offset = 500
+    cfg.tune_threads = (1024,) * 5          # a lone sample gets the most threads
+    R.mlmc_estimate(R.MlmcConfig(nsamples=(2, 2), n0=16, steps0=5, t_final=0.1, batch=1,
+                                 coupling=cfg.coupling, key_offset=600, problem=cfg.problem, model=cfg.model))
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = R.launch_count()
+    r = R.mlmc_estimate(cfg)
+    launches = R.launch_count() - l0
+    clk = clocks.stop()
+    print(json.dumps({
+        "metric": "MLMC cost per pair, batch 1 (s)", "value": r["cost"][-1], "unit": "s", "n_gpus": 1,
+        "steps": 1, "warmup": 1, "ms_per_step": 1e3 * r["seconds"], "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == R.FP64 else "f32-in-f64",
+        "data": "synthetic",
+        "config": {"workload": "mlmc5 hierarchy with batch 1 (one sample per launch), N_l = 200/50/12/3/2, "
+                               f"coupling {cfg.coupling}"},
+        "clocks": clk, "gpu_launches": launches,
+        "levels": {k: r[k] for k in ("n", "failed", "cost", "cost_fine")},
+    }))
 
 
 def run_adjoint(args):
@@ -768,6 +799,8 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--field", choices=sorted(FIELDS), default="exp",
                     help="covariance of the fields: exponential 0.3 (configured) or Matern Phi_1 / Phi_2")
+    ap.add_argument("--batch1", action="store_true",
+                    help="mlmc5: per-level costs with one sample per launch (reduced N_l)")
     ap.add_argument("--fixed-levels", type=int, default=1,
                     help="mlmc5vg: finest levels solved with the original (alpha, n) (Sec. 5.2)")
     ap.add_argument("--cycle", type=int, default=0, choices=[0, 1, 2, 3],
