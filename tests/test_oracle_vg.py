@@ -225,3 +225,44 @@ def test_soil_pair_members():
     for arr, lo, w in ((coarse[2], 1.50, 0.1), (coarse[3], 0.45, 0.1), (coarse[4], 0.045, 0.01)):
         assert arr.shape == (800, 16, 16) and arr.min() > lo and arr.max() < lo + w
         assert stats.kstest((arr[:, 5, 9] - lo) / w, "uniform").pvalue > 1e-3
+
+
+# ------------------------------------------------------- van Genuchten MLMC
+VG_MLMC = dict(theta_r=0.05, theta_s=0.5, p_top=-0.4, p_bottom=0.1, p_init=-0.4, closure=1, init_decay=80.0,
+               gamma=2, picard_tol=1e-8, mg_tol=1e-10, nu=1.0, corr_len=0.2, corr_len_z=0.2)
+
+
+def test_vg_mlmc_continuation_reading():
+    """The additive continuation of Sec. 5.2 as read here: with every level
+    fixed (fixed_levels = L + 1) it is the estimator without continuation,
+    exactly; with it, the finest level still solves the original (alpha, n),
+    so its fine members equal a plain solve of the same fields."""
+    ns, n0, s0, T = (6, 4, 3), 8, 2, 0.25
+    model = O.soil_model(2.0, 1.6)
+    kw = dict(soil=model, d_alpha=0.1, d_n=0.1, coupling=0, **VG_MLMC)
+    a = O.mlmc_estimate(ns, n0, s0, T, continuation=0, **kw)
+    b = O.mlmc_estimate(ns, n0, s0, T, continuation=1, fixed_levels=3, **kw)
+    c = O.mlmc_estimate(ns, n0, s0, T, continuation=1, fixed_levels=1, **kw)
+    for la, lb in zip(a, b):
+        assert np.array_equal(la["qf"], lb["qf"]) and np.array_equal(la["qc"], lb["qc"])
+    assert np.array_equal(c[2]["qf"], a[2]["qf"])                  # finest: original parameters
+    assert not np.array_equal(c[1]["qf"], a[1]["qf"])              # below it: shifted
+    L = len(ns) - 1
+    fine = O.sample_soil(n0 << L, n0 << L, ns[L], model, level=L, nu=1.0, corr_len=0.2, corr_len_z=0.2)
+    pb = O.make_problem(nsteps=s0 << L, dt=T / (s0 << L), **{k: v for k, v in VG_MLMC.items()
+                                                            if k not in ("nu", "corr_len", "corr_len_z")})
+    _, q, st, _ = O.solve_batch_soil(pb, *fine, want_p=False)
+    assert np.array_equal(q[st == 0], c[L]["qf"])
+
+
+def test_vg_mlmc_telescoping_consistency():
+    """Coupling 0 (finest-grid draws averaged down): the fine member of pair l
+    and the coarse member of pair l+1 are the same grid, time step and shifted
+    parameters on fields of the same law, so their means agree within 4
+    standard errors (the telescoping sum of Eq. telescope_ch6 is exact)."""
+    ns = (600, 300)
+    out = O.mlmc_estimate(ns, 8, 2, 0.25, coupling=0, continuation=1, soil=O.soil_model(2.0, 1.6), d_alpha=0.2,
+                          d_n=0.2, **VG_MLMC)
+    f0, c1 = out[0]["qf"], out[1]["qc"]
+    se = np.sqrt(f0.var(ddof=1) / f0.size + c1.var(ddof=1) / c1.size)
+    assert abs(f0.mean() - c1.mean()) < 4 * se, (f0.mean(), c1.mean(), se)
