@@ -61,3 +61,44 @@ def test_adjoint_gradient_matches_finite_differences():
     # the oracle's own QoI agrees with the forward solve's
     p, q, rc, _ = O.solve_one(pb, lnks, alpha)
     assert abs(q - Q) <= 1e-12 * abs(q)
+
+
+@pytest.mark.parametrize("shape", [(4, 4), (8, 8)])
+def test_newton_on_tiny_grids_reaches_the_picard_solution(shape):
+    """Tiny-grid pin of the nonlinear solve: Newton's method with the analytic
+    (finite-difference-free) Jacobian of the discrete residual, globalised by
+    backtracking and started after five Picard iterations, converges quadratically to the exact discrete solution of
+    one implicit step, and modified Picard + CCMG reaches the same state to
+    within its tolerances."""
+    nz, nx = shape
+    lnks, alpha = O.sample_fields(nx, nz, 1, seed=21)
+    lnks, alpha = lnks[0], alpha[0]
+    pb = problem(nsteps=1, picard_tol=1e-13, picard_maxit=200, mg_tol=1e-14, mg_maxit=400)
+    p_pic, q, rc, _ = O.solve_one(pb, lnks, alpha)
+    assert rc == 0
+    h = 1.0 / nz
+    p_old = np.full(shape, PHYSICS["p_init"])
+    # Newton is sensitive to its starting point (Sec. 4.2): start from the state
+    # after 5 Picard iterations, still far from converged
+    p, _, rc5, _ = O.solve_one(problem(nsteps=1, picard_tol=1e-13, picard_maxit=5, mg_tol=1e-14, mg_maxit=400),
+                               lnks, alpha)
+    assert rc5 == O.PICARD_MAXIT and np.abs(p - p_pic).max() > 1e-3
+    steps = []
+    for it in range(60):
+        R = residual(pb, lnks, alpha, p, p_old)
+        J, _, _ = A.residual_jacobians(p, lnks, alpha, pb, h)
+        d = np.linalg.solve(J.toarray(), -R).reshape(shape)
+        # backtracking on ||R||_inf (Newton from the old state overshoots on this
+        # step); full steps near the root
+        t, r0 = 1.0, np.abs(R).max()
+        while t > 1e-6 and not np.abs(residual(pb, lnks, alpha, p + t * d, p_old)).max() < r0:
+            t *= 0.5
+        p = p + t * d
+        steps.append(np.abs(t * d).max())
+        if steps[-1] < 1e-14:
+            break
+    assert steps[-1] < 1e-14, steps
+    # quadratic convergence once close: each step at most C times the square of the previous
+    tail = [(b, a) for a, b in zip(steps[:-1], steps[1:]) if a < 1e-3 and b > 1e-15]
+    assert tail and all(b <= 50.0 * a * a for b, a in tail), steps
+    assert np.abs(p - p_pic).max() < 1e-10 * np.abs(p).max()
