@@ -278,6 +278,9 @@ def test_saturated_limit_dense_direct_solve(shape):
     p, q, rc, st = O.solve_one(problem(nsteps=1), lnks, np.zeros((nz, nx)))
     assert rc == 0
     assert np.abs(p - hydraulic_head_dense_solve(lnks)).max() < 1e-9
+    # linear problem: the first Picard update is the solution, the second only
+    # confirms it (||dp|| below the Picard tolerance)
+    assert st.picard_iters == 2, st.picard_iters
 
 
 # ------------------------------------------------------------ multigrid
@@ -295,7 +298,7 @@ def test_mg_poisson_matches_dense_and_contracts(n):
     assert rc == 0
     assert np.all(np.diff(hist) < 0)
     rho = (hist[-1] / hist[0]) ** (1.0 / cyc)
-    assert rho < 0.5, rho
+    assert rho < 0.2, rho              # V(2,2) with RB-GS: ~0.06-0.1 per cycle on these grids
     ref = np.linalg.solve(poisson_dense(n), f.reshape(-1)).reshape(n, n)
     assert np.abs(dp - ref).max() < 1e-10 * np.abs(ref).max()
 
@@ -466,6 +469,22 @@ def test_oracle_mlmc_telescoping():
     a, b = o[0]["qf"], o[1]["qc"]
     se = np.sqrt(a.var(ddof=1) / a.size + b.var(ddof=1) / b.size)
     assert abs(a.mean() - b.mean()) < 4 * se
+
+
+def test_oracle_mlmc_estimate_matches_plain_mc():
+    """The telescoping MLMC estimate (Eq. MLMCestimator_ch6, coupling 0) and a
+    plain MC estimate at the finest level with independent samples agree
+    within 3 standard errors."""
+    ns = (400, 120, 40)
+    o = O.mlmc_estimate(ns, 8, 2, 0.04, coupling=0, **PHYSICS, **SOLVER)
+    est = sum(lev["y"].mean() for lev in o)
+    var = sum(lev["y"].var(ddof=1) / lev["y"].size for lev in o)
+    lk, al = O.sample_fields(32, 32, 400, seed=0, level=77)
+    pb = O.make_problem(nsteps=8, dt=0.04 / 8, **PHYSICS, **SOLVER)
+    _, q, st, _ = O.solve_batch(pb, lk, al, want_p=False)
+    q = q[(st == 0) | (st == 2)]
+    se = np.sqrt(var + q.var(ddof=1) / q.size)
+    assert abs(est - q.mean()) < 3 * se, (est, q.mean(), se)
 
 
 def test_covariance_upscaling_pair_is_exact_on_both_grids():
