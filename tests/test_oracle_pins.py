@@ -173,6 +173,22 @@ def test_fields_anisotropic_empirical_covariance():
             assert abs(per.mean() - np.exp(-np.sqrt(2) * lag * h / lam)) < 5 * se + 1e-3, (axis, lag)
 
 
+@pytest.mark.parametrize("kw", [{}, dict(nu=1.0, corr_len=0.2, corr_len_z=0.2),
+                                dict(nu=0.5, corr_len=0.1, corr_len_z=0.01), dict(nu=2.5, corr_len=0.15, corr_len_z=0.3)])
+@pytest.mark.parametrize("n", [16, 32])
+def test_torus_is_the_smallest_admissible(kw, n):
+    """The FFT-MA torus (Appendix A): a power of two of at least twice the grid
+    per side whose circulant spectrum has no eigenvalue below -1e-12 max; when
+    it is larger than 2n, the torus of half its size has such an eigenvalue."""
+    px, pz = O.torus_size(n, n, **kw)
+    assert px == pz and px >= 2 * n and px & (px - 1) == 0
+    _, ratio = O.fftma_sqrt_spectrum(px, pz, 1.0 / n, **kw)
+    assert ratio >= -1e-12
+    if px > 2 * n:
+        _, half = O.fftma_sqrt_spectrum(px // 2, pz // 2, 1.0 / n, **kw)
+        assert half < -1e-12
+
+
 def test_fields_coarsening_is_2x2_mean():
     """coarsen_times = 1 returns the 2x2 block means of the fine draw."""
     lk, al = O.sample_fields(16, 16, 3, seed=5)
