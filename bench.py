@@ -37,7 +37,7 @@ WORKLOADS = {
 }
 PHYS = dict(theta_r=0.1, theta_s=0.5, p_top=-0.5, p_bottom=-5.0, p_init=-5.0,
             picard_tol=1e-8, picard_maxit=50, mg_tol=1e-10, mg_maxit=100, nu1=2, nu2=2)
-FP64_TFLOPS_NOMINAL = 1.25      # GB300 FP64 (non-tensor) peak: 152 SMs x 2 FMA/clk x 2070 MHz x 2
+FP64_TFLOPS_NOMINAL = 1.25      # GB300 FP64 (non-tensor) nominal: 152 SMs x 2 FMA/clk x 2070 MHz x 2
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one fused-solver
 # launch of the default workload's timed step, from an ncu capture (see
@@ -314,6 +314,70 @@ def run_reference(args):
 MLMC_LEVELS = dict(nsamples=(20000, 5000, 1200, 300, 80), n0=16, steps0=5, t_final=0.1)
 
 
+def mlmc_tuning(R, prec, cycle=1):
+    """Per-level launch shapes of the five-level hierarchy from the autotuner."""
+    from paper_1903_08741_gb300 import autotune
+    tt, ti = [], []
+    for l, nl in enumerate(MLMC_LEVELS["nsamples"]):
+        m = MLMC_LEVELS["n0"] << l
+        st_l = MLMC_LEVELS["steps0"] << l
+        bt, mi = autotune.tune(R.Problem(nx=m, nz=m, nsteps=st_l, dt=MLMC_LEVELS["t_final"] / st_l,
+                                         precision=prec, cycle=cycle, **PHYS), nl)
+        tt.append(bt)
+        ti.append(mi)
+    R.set_tuning(0, 0)
+    return tt, ti
+
+
+def mlmc_config(R, prec, coupling, field="exp", cycle=1, bias_pairs=0, key_offset=0):
+    tt, ti = mlmc_tuning(R, prec, cycle)
+    return R.MlmcConfig(**MLMC_LEVELS, coupling=coupling, eps=1e-3, tune_threads=tuple(tt), tune_inner=tuple(ti),
+                        problem=R.Problem(precision=prec, cycle=cycle, **PHYS),
+                        model=R.FieldModel(seed=0, **FIELDS[field]), bias_pairs=bias_pairs, key_offset=key_offset)
+
+
+def mlmc_warmup(R, cfg, k=0):
+    small = R.MlmcConfig(nsamples=(64, 32, 16, 8, 4), n0=16, steps0=5, t_final=0.1, coupling=cfg.coupling,
+                         key_offset=100 + k, problem=cfg.problem, model=cfg.model,
+                         tune_threads=cfg.tune_threads, tune_inner=cfg.tune_inner)
+    R.mlmc_estimate(small)
+
+
+def mlmc_report(r, cfg):
+    """The estimator's figures: level statistics, W(eps) (Eq. MLMCSAMP_ch6),
+    sampling RMSE, grid-only bias and total RMSE (Eqs. discErr, MSEMLMC_ch6)."""
+    out = {"w_eps_s": r["w_eps"], "eps": 1e-3,
+           "levels": {k: r[k] for k in ("n", "failed", "mean", "var", "cost", "cost_fine", "n_opt",
+                                        "mean_f", "var_f")},
+           "estimate": r["estimate"], "sampling_rmse": r["rmse"], "ml_variance": r["ml_variance"],
+           "w_mc_eps_s": r["w_mc_eps"], "mc_over_mlmc": r["w_mc_eps"] / r["w_eps"],
+           "bias_with_continuation_jump": r["bias_estimate"], "run_seconds": r["seconds"],
+           "launch": {"block_threads": list(cfg.tune_threads), "mixed_inner": list(cfg.tune_inner),
+                      "from": "autotuner, per level"}}
+    if r["bias_pairs"] > 0:
+        out.update({"bias_grid_only": r["bias_grid"], "bias_grid_only_se": r["bias_grid_se"],
+                    "bias_pairs": r["bias_pairs"], "total_rmse": r["total_rmse"],
+                    "levels_for_eps": r["levels_for_eps"]})
+    return out
+
+
+def mlmc_batch1(R, cfg):
+    """The hierarchy with one sample per launch (batch 1) on N_l = 200/50/12/3/2:
+    per-level costs of unbatched GPU solves; the level variances are the
+    batched run's, which these few samples cannot estimate."""
+    c1 = R.MlmcConfig(**{**MLMC_LEVELS, "nsamples": (200, 50, 12, 3, 2)}, coupling=cfg.coupling, eps=1e-3,
+                      batch=1, key_offset=500, tune_threads=(1024,) * 5, tune_inner=cfg.tune_inner,
+                      problem=cfg.problem, model=cfg.model)
+    R.mlmc_estimate(R.MlmcConfig(nsamples=(2, 2), n0=16, steps0=5, t_final=0.1, batch=1, coupling=cfg.coupling,
+                                 key_offset=600, problem=cfg.problem, model=cfg.model))
+    return R.mlmc_estimate(c1)
+
+
+def w_eps(var, cost, eps=1e-3):
+    import math
+    return sum(math.sqrt(max(v, 0.0) * c) for v, c in zip(var, cost)) ** 2 / eps ** 2
+
+
 def run_mlmc(args):
     """Parametric-continuation MLMC over 16^2..256^2 (5 levels, N_l = 20000, 5000,
     1200, 300, 80; 5 2^l steps to T = 0.1): reports V_l, C_l and the cost W(eps)
@@ -324,26 +388,11 @@ def run_mlmc(args):
     B.build()
     torch.cuda.set_device(0)
     prec = R.MIXED if args.precision == "mixed" else R.FP64
-    from paper_1903_08741_gb300 import autotune
-    tt, ti = [], []
-    for l, nl in enumerate(MLMC_LEVELS["nsamples"]):
-        m = MLMC_LEVELS["n0"] << l
-        st_l = MLMC_LEVELS["steps0"] << l
-        bt, mi = autotune.tune(R.Problem(nx=m, nz=m, nsteps=st_l, dt=MLMC_LEVELS["t_final"] / st_l,
-                                         precision=prec, cycle=args.cycle, **PHYS), nl)
-        tt.append(bt)
-        ti.append(mi)
-    R.set_tuning(0, 0)
-    model = R.FieldModel(seed=0, **FIELDS[args.field])
-    base = R.Problem(precision=prec, cycle=args.cycle, **PHYS)
-    cfg = R.MlmcConfig(**MLMC_LEVELS, coupling=args.coupling, eps=1e-3, tune_threads=tuple(tt),
-                       tune_inner=tuple(ti), problem=base, model=model)
+    cfg = mlmc_config(R, prec, args.coupling, args.field, args.cycle, bias_pairs=args.bias_pairs)
     if args.batch1:
         return run_mlmc_batch1(args, R, cfg, prec)
     for k in range(args.warmup):
-        small = R.MlmcConfig(nsamples=(64, 32, 16, 8, 4), n0=16, steps0=5, t_final=0.1,
-                             coupling=args.coupling, key_offset=100 + k, problem=base, model=model)
-        R.mlmc_estimate(small)
+        mlmc_warmup(R, cfg, k)
     clocks = ClockSampler(0)
     clocks.start()
     l0 = R.launch_count()
@@ -363,26 +412,24 @@ def run_mlmc(args):
         "config": {"workload": "mlmc5: 16^2..256^2, N_l = 20000/5000/1200/300/80, 5*2^l steps to T=0.1, "
                                f"alpha_l = alpha (l+1)/5, {FIELD_TEXT[args.field]}, seed 0"
                                + (f", cycle index {args.cycle}" if args.cycle > 1 else ""),
-                   "coupling": {0: "finest-grid draw, 2x2 averages of ln Ks and alpha",
-                                1: "level-grid draw, 2x2 averages of ln Ks and alpha",
-                                2: "covariance upscaling (2x2-averaged white noise)"}[args.coupling]},
+                   "coupling": COUPLING_TEXT[args.coupling]},
         "clocks": clk, "gpu_launches": launches,
-        "levels": {k: r[k] for k in ("n", "failed", "mean", "var", "cost", "cost_fine", "n_opt",
-                                     "mean_f", "var_f")},
-        "estimate": r["estimate"], "rmse": r["rmse"], "ml_variance": r["ml_variance"],
-        "w_mc_eps_s": r["w_mc_eps"], "mc_over_mlmc": r["w_mc_eps"] / r["w_eps"],
-        "bias_estimate": r["bias_estimate"], "run_seconds": secs,
-        "launch": {"block_threads": tt, "mixed_inner": ti, "from": "autotuner, per level"},
     }
+    out.update(mlmc_report(r, cfg))
     if args.adaptive_eps > 0:
         acfg = R.MlmcConfig(**{**MLMC_LEVELS, "nsamples": (512, 128, 32, 16, 8)}, coupling=args.coupling,
-                            eps=args.adaptive_eps, key_offset=1000, tune_threads=tuple(tt), tune_inner=tuple(ti),
-                            problem=base, model=model)
+                            eps=args.adaptive_eps, key_offset=1000, tune_threads=cfg.tune_threads,
+                            tune_inner=cfg.tune_inner, problem=cfg.problem, model=cfg.model)
         a = R.mlmc_adaptive(acfg, max_rounds=10)
         out["adaptive"] = {"eps": args.adaptive_eps, "rounds": a["rounds"], "n": a["n"], "failed": a["failed"],
                            "rmse": a["rmse"], "estimate": a["estimate"], "seconds": a["seconds"],
                            "var": a["var"], "cost": a["cost"], "w_eps_predicted": a["w_eps"]}
     print(json.dumps(out))
+
+
+COUPLING_TEXT = {0: "finest-grid draw, 2x2 averages of ln Ks and alpha",
+                 1: "level-grid draw, 2x2 averages of ln Ks and alpha",
+                 2: "covariance upscaling (2x2-averaged white noise)"}
 
 
 MLMC_VG_LEVELS = dict(nsamples=(20000, 5000, 1200, 300, 80), n0=16, steps0=3, t_final=0.2)
@@ -455,20 +502,11 @@ def run_mlmc_vg(args):
 
 
 def run_mlmc_batch1(args, R, cfg, prec):
-    """The same MLMC hierarchy with every sample solved on its own (one CTA per
-    launch, batch 1), on N_l scaled down to 200/50/12/3/2: the per-level costs
-    C_l of unbatched GPU solves, to set against the batched C_l (the level
-    variances are the batched run's, which these few samples cannot estimate)."""
-    cfg.nsamples = (200, 50, 12, 3, 2)
-    cfg.batch = 1
-    cfg.key_offset = 500
-    cfg.tune_threads = (1024,) * 5          # a lone sample gets the most threads
-    R.mlmc_estimate(R.MlmcConfig(nsamples=(2, 2), n0=16, steps0=5, t_final=0.1, batch=1,
-                                 coupling=cfg.coupling, key_offset=600, problem=cfg.problem, model=cfg.model))
+    """Per-level costs with one sample per launch (see mlmc_batch1)."""
     clocks = ClockSampler(0)
     clocks.start()
     l0 = R.launch_count()
-    r = R.mlmc_estimate(cfg)
+    r = mlmc_batch1(R, cfg)
     launches = R.launch_count() - l0
     clk = clocks.stop()
     print(json.dumps({
@@ -611,6 +649,97 @@ def run_mc512(args):
     print(json.dumps(out))
 
 
+def measure_fp64_rates(R, device):
+    """The library's FP64 microbenchmark, with the SM clocks sampled meanwhile."""
+    clocks = ClockSampler(device)
+    clocks.start()
+    r = R.measure_fp64(device)
+    r2 = R.measure_fp64(device)          # two passes: the sampler sees ~2 s of load
+    clk = clocks.stop()
+    best = max((r, r2), key=lambda x: x["dfma_flops"])
+    best["clocks"] = clk
+    return best
+
+
+def fp64_peak_tflops(fp64, clk):
+    """FP64 roofline denominator: the measured FMA rate, scaled to the median SM
+    clock of the timed region when the two clock readings differ; the nominal
+    unit-count figure when no measurement exists."""
+    if not fp64:
+        return FP64_TFLOPS_NOMINAL, "FP64 nominal (152 SMs x 2 FMA/clk x 2.07 GHz)"
+    peak = fp64["dfma_flops"] / 1e12
+    f_meas = (fp64.get("clocks") or {}).get("sm_mhz")
+    f_run = (clk or {}).get("sm_mhz")
+    if f_meas and f_run and abs(f_meas - f_run) > 1:
+        return peak * f_run / f_meas, (f"FP64 FMA microbenchmark (measured, {f_meas:.0f} MHz) "
+                                       f"scaled to the timed region's {f_run:.0f} MHz")
+    return peak, f"FP64 FMA microbenchmark (measured{f', %.0f MHz' % f_meas if f_meas else ''})"
+
+
+def bench_extras(R, args, pb, lk, al, q64, s64, clk):
+    """The rest of the headline metric on one GPU: (a) the mixed-precision
+    batched solve of the same workload on the e2e step's fields, with its QoI
+    error against the FP64 solve of those fields; (b) the five-level MLMC
+    (coupling 2) to RMSE 1e-3 in FP64 and in mixed precision, with grid-only
+    bias pairs and the total RMSE; (c) the per-level costs with one sample per
+    launch and the ratio of that FP64 batch-1 cost to the mixed batched cost."""
+    import numpy as np
+    import torch
+    from paper_1903_08741_gb300 import autotune
+    out = {}
+    dev = lk.device
+    stream = torch.cuda.current_stream(dev)
+    # (a) mixed precision, mc128
+    pm = R.Problem(**{**pb.__dict__, "precision": R.MIXED})
+    bt, mi = autotune.tune(pm, lk.shape[0])
+    R.solve_batch(pm, lk[:8].contiguous(), al[:8].contiguous())
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    qm, _, sm_, stm, _ = R.solve_batch(pm, lk, al)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    mclk = clocks.stop()
+    tm = e0.elapsed_time(e1)
+    S = lk.shape[0]
+    mixed = {"value": S / (tm / 1e3), "unit": "solves/s", "ms_per_step": tm, "clocks": mclk,
+             "launch": {"block_threads": bt, "mixed_inner": mi},
+             "failed_samples": stm.failed, "converged_solves_per_s": (S - stm.failed) / (tm / 1e3),
+             "what": "one batch (4096 samples, 128^2, 20 steps) on the e2e step's fields, FP32 V-cycles in "
+                     "FP64 defect correction"}
+    if q64 is not None:
+        qm, sm_ = qm.cpu().numpy(), sm_.cpu().numpy()
+        ok = (sm_ == 0) & (s64 == 0)
+        rel = np.abs(qm[ok] - q64[ok]) / np.abs(q64[ok])
+        mixed["qoi_rel_err_vs_fp64"] = {"max": float(rel.max()), "median": float(np.median(rel)),
+                                        "n": int(ok.sum()), "same_status": float((sm_ == s64).mean())}
+    out["mixed_mc128"] = mixed
+    # (b) MLMC, FP64 and mixed, coupling 2
+    res = {}
+    for name, prec in (("fp64", R.FP64), ("mixed", R.MIXED)):
+        cfg = mlmc_config(R, prec, 2, bias_pairs=152 if prec == R.FP64 else 0)
+        mlmc_warmup(R, cfg)
+        clocks = ClockSampler(dev.index or 0)
+        clocks.start()
+        r = R.mlmc_estimate(cfg)
+        rep = mlmc_report(r, cfg)
+        rep["clocks"] = clocks.stop()
+        res[name] = (r, cfg, rep)
+    out["mlmc5"] = {"workload": "mlmc5: 16^2..256^2, N_l = 20000/5000/1200/300/80, 5*2^l steps to T=0.1, "
+                                "alpha_l = alpha (l+1)/5, exp. cov. 0.3, seed 0, " + COUPLING_TEXT[2],
+                    "fp64": res["fp64"][2], "mixed": res["mixed"][2]}
+    # (c) batch-1 costs (FP64) and the ratio to the mixed batched cost
+    r1 = mlmc_batch1(R, res["fp64"][1])
+    w1 = w_eps(res["fp64"][0]["var"], r1["cost"])
+    out["mlmc5"]["fp64_batch1"] = {"cost": r1["cost"], "n": r1["n"], "w_eps_s": w1,
+                                   "note": "one sample per launch, N_l = 200/50/12/3/2; W(eps) from the "
+                                           "batched FP64 V_l"}
+    out["mlmc5"]["ratio_fp64_batch1_over_mixed_batched"] = w1 / res["mixed"][0]["w_eps"]
+    out["mlmc5"]["ratio_fp64_batched_over_mixed_batched"] = res["fp64"][0]["w_eps"] / res["mixed"][0]["w_eps"]
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -652,6 +781,10 @@ def run_ours(args):
     for k in range(args.warmup):
         step(k)
     torch.cuda.synchronize(dev)
+    default_run = (args.workload == "mc128" and not args.samples and not args.time_steps
+                   and args.field == "exp" and args.cycle == 1 and prec == R.FP64)
+    extras = ws == 1 and default_run and not args.no_extras
+    fp64 = measure_fp64_rates(R, local) if (prec == R.FP64 and ws == 1) else None
     if pg is not None:
         pg.barrier()
     clocks = ClockSampler(local)
@@ -713,6 +846,7 @@ def run_ours(args):
     # end to end through the host-buffer entry point: H2D of the fields, solve,
     # D2H of QoI and status, every step inside the timed region
     e2e = None
+    qh = sh = None
     if not args.no_e2e:
         R.sample_fields(n, n, S, model, level=0, first_sample=sample_base + 9_000_000, device=local,
                         out=(lk, al))
@@ -734,16 +868,16 @@ def run_ours(args):
     k_gbs = kbytes / (kms / 1e3) / 1e9 if kms > 0 else 0.0
     k_tflops = kflops / (kms / 1e3) / 1e12 if kms > 0 else 0.0
     frac_hbm = k_gbs / hbm_peak
-    frac_alu = k_tflops / FP64_TFLOPS_NOMINAL if prec == R.FP64 else 0.0
+    fp64_peak, fp64_kind = fp64_peak_tflops(fp64, clk)
+    frac_alu = k_tflops / fp64_peak if prec == R.FP64 else 0.0
     per_launch_bytes = kbytes / max(klaunch, 1)
     kname = f"k_fused<{'double' if prec == R.FP64 else 'float'},{block_threads}> (persistent fused solve)"
     default_workload = (args.workload == "mc128" and not args.samples and not args.time_steps
                         and args.field == "exp" and args.cycle == 1)
     traffic = captured_traffic("fp64" if prec == R.FP64 else "mixed", block_threads, default_workload)
     if prec == R.FP64 and frac_alu > frac_hbm:
-        roof = {"bound": "alu", "achieved": k_tflops, "peak": FP64_TFLOPS_NOMINAL, "unit": "TFLOP/s",
-                "frac": frac_alu, "traffic": traffic, "kernel": kname,
-                "peak_kind": "FP64 nominal (152 SMs x 2 FMA/clk x 2.07 GHz)",
+        roof = {"bound": "alu", "achieved": k_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": frac_alu, "traffic": traffic, "kernel": kname, "peak_kind": fp64_kind,
                 "hbm": {"achieved": k_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": frac_hbm,
                         "peak_kind": peak_kind}}
     else:
@@ -769,12 +903,19 @@ def run_ours(args):
         "picard_iters_per_sample": tot.picard_iters / (S * args.steps),
         "vcycles_per_sample": tot.mg_cycles / (S * args.steps),
         "failed_samples": tot.failed,
-        "mc_estimate": {"mean_qoi": a[0] / max(a[2], 1), "n": int(a[2]), "failed": int(a[3])},
+        "failed_fraction": tot.failed / total,
+        "converged_solves_per_s": (total - tot.failed) / (ms / 1e3),
+        "mc_estimate": {"mean_qoi": a[0] / max(a[2], 1), "n": int(a[2]), "failed": int(a[3]),
+                        "note": "mean over converged samples (failed samples, Sec. 4.3, are excluded)"},
     }
+    if fp64 is not None:
+        out["fp64_rates"] = fp64
     if e2e:
         out["e2e"] = e2e
     if graph:
         out["graph"] = graph
+    if extras:
+        out.update(bench_extras(R, args, pb, lk, al, qh, sh, clk))
     if not args.no_cpu and ws == 1:
         cores = os.cpu_count() or 1
         ns = args.cpu_samples or cores
@@ -810,6 +951,9 @@ def main():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload: skip the mixed-precision, MLMC and batch-1 measurements")
+    ap.add_argument("--bias-pairs", type=int, default=0, help="mlmc5: grid-only bias pairs (Eq. discErr)")
     ap.add_argument("--cpu-samples", type=int, default=0)
     ap.add_argument("--ref-samples", type=int, default=0)
     # profiling knobs (smaller cases for ncu captures; not bench workloads)

@@ -11,9 +11,12 @@
  * bottom of the unit-height domain; the mesh width is h = 1/nz (Eq. Grid_fine).
  *
  * Return codes: 0 = OK; < 0 = fatal error of the call (nothing is guaranteed
- * about the outputs); > 0 = the call completed and the value is the worst
- * per-sample status (RICH_PICARD_MAXIT, RICH_MG_MAXIT, RICH_NONFINITE), with
- * the per-sample details in the status array.  No C++ exception crosses the
+ * about the outputs); > 0 = the call completed and the value is the most
+ * severe per-sample status, in the order RICH_NONFINITE, RICH_PICARD_MAXIT
+ * (both: the sample failed, its QoI is NaN), RICH_MG_MAXIT (a multigrid solve
+ * stopped at its cycle cap; the sample's result is still usable), with the
+ * per-sample details in the status array.  A sample that fails after an
+ * earlier MG_MAXIT carries the failure status.  No C++ exception crosses the
  * ABI.  Streams are cudaStream_t passed as void* (NULL = legacy default).
  */
 #ifndef RICHARDS_H
@@ -281,6 +284,12 @@ typedef struct {
     double d_alpha, d_n;
     int32_t fixed_levels;
     int32_t with_thetas;
+    /* Grid-only bias estimate (Eq. discErr): after the levels, bias_pairs
+     * extra pairs of the finest level whose two members both use the original
+     * parameters (alpha scale 1, no additive shift), from their own noise
+     * stream; 0 = none.  With continuation the finest level's Y_L also holds
+     * the parameter jump, so |E Y_L| alone does not measure the grid bias. */
+    int32_t bias_pairs;
 } rich_mlmc_cfg_t;
 
 typedef struct {
@@ -297,9 +306,17 @@ typedef struct {
     double ml_variance;       /* sum V[Q_l] - V[Q_{l-1}] (Eq. ML_var_ch6)                */
     double w_eps;             /* eps^-2 (sum sqrt(V_l C_l))^2: seconds to RMSE eps        */
     double w_mc_eps;          /* plain MC at the finest level: V[Q_L] C_L,fine / eps^2   */
-    double bias_estimate;     /* |E Y_L| / (2^1 - 1): first-order bias bound (Eq. discErr) */
+    double bias_estimate;     /* |E Y_L| / (2^1 - 1) (Eq. discErr); with continuation it
+                                 mixes the grid bias with the finest parameter jump        */
     double seconds;           /* wall time of the call                                   */
     int32_t rounds;           /* sampling rounds (1 for rich_mlmc_estimate)              */
+    int64_t bias_pairs;       /* usable grid-only bias pairs (0: none requested)          */
+    double bias_grid;         /* |E[Q_L - Q_{L-1}]| / (2^1 - 1), both at the original
+                                 parameters (Eq. discErr, rate a = 1); NaN without pairs  */
+    double bias_grid_se;      /* standard error of E[Q_L - Q_{L-1}]                       */
+    double total_rmse;        /* sqrt(bias_grid^2 + sum V_l/N_l) (Eq. MSEMLMC_ch6)        */
+    int32_t levels_for_eps;   /* levels for which the grid bias (halving per level) falls
+                                 to eps/sqrt(2); 0 without bias pairs                      */
 } rich_mlmc_result_t;
 
 /* Run the estimator with the configured N_l and fill *out (HOST).  Synchronous;
@@ -365,13 +382,18 @@ int rich_solve_batch_adjoint(rich_ctx_t ctx, const rich_problem_t* pb, int32_t n
  * library-owned static device array of RICH_NOALLOC_SCRATCH_BYTES (16 MiB),
  * present on every GPU that loads the library until the process exits.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *     (cudaGetSymbolAddress, once per device, under a lock) with that device
+ *     current, and keeps it; make that first call before any stream capture.
+ *     The address dies with the device's context: do not call this entry
+ *     point again after cudaDeviceReset on that device.
  *   - Every call shares the one array: calls whose work overlaps on the GPU
  *     (other streams, other host threads) race and give wrong results; order
  *     them on one stream.  Each call clears the state that must start at zero.
  *   - The grid is limited to the CTA slots that fit in the array; a grid whose
- *     per-CTA slot exceeds it is rejected with RICH_ERR_INVALID (a 128^2 FP64
- *     problem needs about 2 MiB per CTA, so 8 CTAs run; 32^2 needs ~0.14 MiB).
+ *     per-CTA slot exceeds it is rejected with RICH_ERR_INVALID.  A slot holds
+ *     one sample's multigrid hierarchy and fine-grid state: a 128^2 FP64
+ *     problem needs 2.72 MiB per CTA, so 5 CTAs run; 32^2 FP64 needs
+ *     0.175 MiB (91 slots, more than the resident CTAs of one GPU).
  * Inputs lnKs, alpha [S][nz][nx] and outputs qoi[S], status[S] (status may be
  * NULL) are caller-owned DEVICE arrays.  The call is asynchronous on `stream`
  * and returns 0 once the work is enqueued (per-sample results are in status),
@@ -390,6 +412,20 @@ int rich_profile(rich_ctx_t ctx, int enable);
 int rich_profile_read(rich_ctx_t ctx, double* ms, int64_t* launches, double* alg_bytes,
                       double* alg_flops);
 int64_t rich_launch_count(void);
+
+/* FP64 arithmetic rates of the context's GPU, measured by microbenchmark
+ * kernels (independent FP64 chains on every SM, 256-thread CTAs, 8 per SM;
+ * one warm-up and one CUDA-event-timed launch each): FMA (counted as 2 FLOP),
+ * division and exp.  The fused FP64 solver is bound by the FP64 pipe, and
+ * dfma_flops is its roofline denominator.  Synchronous (a private stream);
+ * about a second of GPU time. */
+typedef struct {
+    double dfma_flops;        /* FP64 FLOP/s from FMA chains                      */
+    double div_per_s;         /* FP64 divisions per second                        */
+    double exp_per_s;         /* FP64 exp evaluations per second                  */
+    double ms_total;          /* timed milliseconds of the three kernels          */
+} rich_fp64_rates_t;
+int rich_measure_fp64(rich_ctx_t ctx, rich_fp64_rates_t* out);
 
 #ifdef __cplusplus
 }

@@ -56,6 +56,11 @@ class _Field(C.Structure):
                 ("corr_len_z", C.c_double)]
 
 
+class _Fp64Rates(C.Structure):
+    _fields_ = [("dfma_flops", C.c_double), ("div_per_s", C.c_double), ("exp_per_s", C.c_double),
+                ("ms_total", C.c_double)]
+
+
 class _Stats(C.Structure):
     _fields_ = [("picard_iters", C.c_int64), ("mg_cycles", C.c_int64), ("cell_vcycles", C.c_int64),
                 ("max_picard", C.c_int32), ("failed", C.c_int32), ("seconds", C.c_double)]
@@ -158,7 +163,8 @@ class _MlmcCfg(C.Structure):
                 ("continuation", C.c_int32), ("batch", C.c_int32), ("eps", C.c_double),
                 ("key_offset", C.c_uint32), ("tune_threads", C.c_int32 * MLMC_MAX_LEVELS),
                 ("tune_inner", C.c_int32 * MLMC_MAX_LEVELS), ("soil", _SoilModel), ("d_alpha", C.c_double),
-                ("d_n", C.c_double), ("fixed_levels", C.c_int32), ("with_thetas", C.c_int32)]
+                ("d_n", C.c_double), ("fixed_levels", C.c_int32), ("with_thetas", C.c_int32),
+                ("bias_pairs", C.c_int32)]
 
 
 _LV = C.c_double * MLMC_MAX_LEVELS
@@ -170,7 +176,9 @@ class _MlmcResult(C.Structure):
                 ("mean_f", _LV), ("var_f", _LV), ("mean_c", _LV), ("var_c", _LV), ("cost", _LV),
                 ("cost_fine", _LV), ("n_opt", _LV), ("estimate", C.c_double), ("rmse", C.c_double),
                 ("ml_variance", C.c_double), ("w_eps", C.c_double), ("w_mc_eps", C.c_double),
-                ("bias_estimate", C.c_double), ("seconds", C.c_double), ("rounds", C.c_int32)]
+                ("bias_estimate", C.c_double), ("seconds", C.c_double), ("rounds", C.c_int32),
+                ("bias_pairs", C.c_int64), ("bias_grid", C.c_double), ("bias_grid_se", C.c_double),
+                ("total_rmse", C.c_double), ("levels_for_eps", C.c_int32)]
 
 
 @dataclass
@@ -197,6 +205,9 @@ class MlmcConfig:
     d_n: float = 0.1
     fixed_levels: int = 1
     with_thetas: int = 1
+    # extra finest-level pairs at the original parameters for the grid-only
+    # bias estimate (Eq. discErr) and the total RMSE; 0 = none
+    bias_pairs: int = 0
 
     def _c(self):
         c = _MlmcCfg()
@@ -214,6 +225,7 @@ class MlmcConfig:
             c.tune_inner[l] = v
         c.soil = self.soil._c()
         c.d_alpha, c.d_n, c.fixed_levels, c.with_thetas = self.d_alpha, self.d_n, self.fixed_levels, self.with_thetas
+        c.bias_pairs = self.bias_pairs
         return c
 
 
@@ -268,6 +280,7 @@ def lib():
                                       C.POINTER(_Stats), vp]
         L.rich_mlmc_estimate.argtypes = [vp, C.POINTER(_MlmcCfg), C.POINTER(_MlmcResult)]
         L.rich_mlmc_adaptive.argtypes = [vp, C.POINTER(_MlmcCfg), i32, vp, C.POINTER(_MlmcResult)]
+        L.rich_measure_fp64.argtypes = [vp, C.POINTER(_Fp64Rates)]
         _lib = L
     return _lib
 
@@ -279,7 +292,7 @@ def exported_symbols():
             "rich_solve_batch_noalloc", "rich_mlmc_estimate", "rich_sample_fields_pair",
             "rich_kl_fields", "rich_solve_batch_adjoint", "rich_set_tuning", "rich_sample_fields_at",
             "rich_solve_batch_async", "rich_mlmc_adaptive", "rich_sample_soil", "rich_solve_soil",
-            "rich_sample_soil_pair", "rich_sample_counters"]
+            "rich_sample_soil_pair", "rich_sample_counters", "rich_measure_fp64"]
 
 
 def _check(rc):
@@ -499,27 +512,58 @@ def profile_read(device=0):
     return ms.value, n.value, b.value, f.value
 
 
+def measure_fp64(device=0):
+    """FP64 FMA FLOP/s, divisions/s and exp/s of the device, measured by the
+    library's microbenchmark kernels (the FP64 roofline denominator)."""
+    _torch()
+    r = _Fp64Rates()
+    _check(lib().rich_measure_fp64(context(device), C.byref(r)))
+    return {"dfma_flops": r.dfma_flops, "div_per_s": r.div_per_s, "exp_per_s": r.exp_per_s,
+            "ms": r.ms_total}
+
+
 def launch_count():
     """Kernels launched by librichards in this process so far."""
     return int(lib().rich_launch_count())
 
 
-def solve_batch_noalloc(problem: Problem, lnKs, alpha, alpha_scale=1.0, qoi=None, status=None):
-    """Allocation-free solve on the current device (see include/richards.h): the
-    library allocates nothing; the caller provides qoi [S] and status [S]
-    (created here when not given).  Asynchronous on the current stream."""
-    torch = _torch()
+def _check_noalloc_args(problem: Problem, lnKs, alpha, qoi, status):
+    """Shapes and devices of an allocation-free call, checked before anything
+    reaches the library: the kernel reads S x nz x nx cells of each field and
+    writes S entries of qoi and status, so a short or mis-shaped tensor would be
+    read or written out of bounds on the device."""
+    if lnKs.dim() != 3:
+        raise RichError("lnKs must be [S, nz, nx]")
     S = lnKs.shape[0]
+    if tuple(lnKs.shape) != (S, problem.nz, problem.nx) or tuple(alpha.shape) != tuple(lnKs.shape):
+        raise RichError("lnKs/alpha must be [S, nz, nx] of the problem's grid")
+    for name, t in (("qoi", qoi), ("status", status)):
+        if t is not None and t.numel() < S:
+            raise RichError(f"{name} must hold at least S = {S} entries")
+    devs = {t.device for t in (lnKs, alpha, qoi, status) if t is not None}
+    if len(devs) != 1:
+        raise RichError("lnKs, alpha, qoi and status must be on one device")
+    return S
+
+
+def solve_batch_noalloc(problem: Problem, lnKs, alpha, alpha_scale=1.0, qoi=None, status=None):
+    """Allocation-free solve (see include/richards.h): the library allocates
+    nothing; the caller provides qoi [S] and status [S] (created here when not
+    given).  Runs on lnKs's device, made current for the call; asynchronous on
+    that device's current stream."""
+    S = _check_noalloc_args(problem, lnKs, alpha, qoi, status)
+    torch = _torch()
     if qoi is None:
         qoi = torch.empty(S, dtype=torch.float64, device=lnKs.device)
     if status is None:
         status = torch.empty(S, dtype=torch.int32, device=lnKs.device)
-    _check(lib().rich_solve_batch_noalloc(C.byref(problem._c()), S,
-                                          _dev_ptr(lnKs, torch.float64, "lnKs"),
-                                          _dev_ptr(alpha, torch.float64, "alpha"), alpha_scale,
-                                          _dev_ptr(qoi, torch.float64, "qoi"),
-                                          _dev_ptr(status, torch.int32, "status"),
-                                          _stream(torch, lnKs.device.index)))
+    with torch.cuda.device(lnKs.device):
+        _check(lib().rich_solve_batch_noalloc(C.byref(problem._c()), S,
+                                              _dev_ptr(lnKs, torch.float64, "lnKs"),
+                                              _dev_ptr(alpha, torch.float64, "alpha"), alpha_scale,
+                                              _dev_ptr(qoi, torch.float64, "qoi"),
+                                              _dev_ptr(status, torch.int32, "status"),
+                                              _stream(torch, lnKs.device.index)))
     return qoi, status
 
 
@@ -528,7 +572,8 @@ def _mlmc_result(r, rc):
     out = {k: list(getattr(r, k))[:NL] for k in ("n", "failed", "mean", "var", "mean_f", "var_f", "mean_c",
                                                   "var_c", "cost", "cost_fine", "n_opt")}
     out.update({k: getattr(r, k) for k in ("estimate", "rmse", "ml_variance", "w_eps", "w_mc_eps",
-                                            "bias_estimate", "seconds", "rounds")})
+                                            "bias_estimate", "seconds", "rounds", "bias_pairs", "bias_grid",
+                                            "bias_grid_se", "total_rmse", "levels_for_eps")})
     out["nlevels"], out["rc"] = NL, rc
     return out
 
@@ -600,6 +645,11 @@ def _autograd():
 
         @staticmethod
         def forward(ctx, xi, alpha, basis, problem, alpha_scale=1.0, ckpt_every=10):
+            if not ctx.needs_input_grad[0]:
+                # no gradient wanted (torch.no_grad(), or xi without
+                # requires_grad): the forward solve alone
+                ctx.save_for_backward(None)
+                return solve_batch(problem, kl_fields(basis, xi.detach().contiguous()), alpha, alpha_scale)[0]
             qoi, dq, _, status, _, _ = solve_batch_adjoint(problem, basis, xi.detach().contiguous(),
                                                            alpha, alpha_scale, ckpt_every)
             ctx.save_for_backward(dq)
@@ -608,6 +658,8 @@ def _autograd():
         @staticmethod
         def backward(ctx, grad_qoi):
             (dq,) = ctx.saved_tensors
+            if dq is None:
+                return None, None, None, None, None, None
             return grad_qoi[:, None] * dq, None, None, None, None, None
 
     return RichardsQoI

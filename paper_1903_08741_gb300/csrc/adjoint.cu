@@ -100,7 +100,7 @@ extern "C" int rich_solve_batch_adjoint(rich_ctx_t ctx, const rich_problem_t* pb
     int worst = 0;
     rich_stats_t acc{};
     for (int s = 0; s < nsamples; ++s) {
-        worst = std::max(worst, (int)hs[s]);
+        worst = rich_status_worse(worst, (int)hs[s]);
         acc.picard_iters += hp[s];
         acc.mg_cycles += hm[s];          // adjoint: outer defect-correction iterations
         acc.max_picard = std::max(acc.max_picard, hmax[s]);

@@ -290,3 +290,95 @@ extern "C" int rich_solve_batch_host(rich_ctx_t ctx, const rich_problem_t* pb, i
     RICH_CUDA(cudaStreamSynchronize(st));
     return rc;
 }
+
+// ---------------------------------------------------------------------------
+// FP64 rate microbenchmark (the roofline denominator of the FP64-bound fused
+// solver): independent chains of FP64 FMAs, divisions and exp calls on every
+// SM, timed with CUDA events.  Chains are long enough to hide the pipeline
+// latency; the results feed a store behind a data-dependent test so that the
+// compiler keeps every operation.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int PK_TPB = 256;
+__device__ double g_peak_sink;
+
+__global__ void __launch_bounds__(PK_TPB) k_peak_dfma(int iters, double a, double b) {
+    double x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = 1.0 + 1e-3 * (threadIdx.x + k);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += x[k];
+    if (s == 1234.5678) g_peak_sink = s;
+}
+
+__global__ void __launch_bounds__(PK_TPB) k_peak_ddiv(int iters, double c) {
+    double x[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) x[k] = 1.0 + 1e-3 * (threadIdx.x + k);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) x[k] = c / (x[k] + 1.0);
+    }
+    const double s = x[0] + x[1] + x[2] + x[3];
+    if (s == 1234.5678) g_peak_sink = s;
+}
+
+__global__ void __launch_bounds__(PK_TPB) k_peak_dexp(int iters, double c) {
+    double x[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) x[k] = 1e-3 * (threadIdx.x + k);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) x[k] = exp(-c * x[k]);
+    }
+    const double s = x[0] + x[1] + x[2] + x[3];
+    if (s == 1234.5678) g_peak_sink = s;
+}
+}  // namespace
+
+extern "C" int rich_measure_fp64(rich_ctx_t ctx, rich_fp64_rates_t* out) {
+    if (!ctx || !out) return RICH_ERR_INVALID;
+    RICH_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = 0;
+    float ms[3] = {0, 0, 0};
+    const int grid = ctx->sm_count * (2048 / PK_TPB);
+    const double threads = (double)grid * PK_TPB;
+    const int it_fma = 1 << 16, it_div = 1 << 12, it_exp = 1 << 11;
+    auto run = [&](int which, float* t) -> int {
+        for (int rep = 0; rep < 2; ++rep) {      // first launch warms up, second is timed
+            RICH_CUDA(cudaEventRecord(e0, st));
+            rich_count_launch();
+            if (which == 0) k_peak_dfma<<<grid, PK_TPB, 0, st>>>(it_fma, 0.999999, 1e-7);
+            else if (which == 1) k_peak_ddiv<<<grid, PK_TPB, 0, st>>>(it_div, 0.75);
+            else k_peak_dexp<<<grid, PK_TPB, 0, st>>>(it_exp, 0.5);
+            RICH_CUDA(cudaGetLastError());
+            RICH_CUDA(cudaEventRecord(e1, st));
+            RICH_CUDA(cudaEventSynchronize(e1));
+            RICH_CUDA(cudaEventElapsedTime(t, e0, e1));
+        }
+        return 0;
+    };
+    RICH_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        rich_set_error("cudaEventCreate failed", __FILE__, __LINE__);
+        rc = RICH_ERR_CUDA;
+    }
+    for (int w = 0; w < 3 && rc == 0; ++w) rc = run(w, &ms[w]);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamDestroy(st);
+    if (rc) return rc;
+    out->dfma_flops = 2.0 * 8.0 * it_fma * threads / (1e-3 * ms[0]);
+    out->div_per_s = 4.0 * it_div * threads / (1e-3 * ms[1]);
+    out->exp_per_s = 4.0 * it_exp * threads / (1e-3 * ms[2]);
+    out->ms_total = ms[0] + ms[1] + ms[2];
+    return 0;
+}

@@ -3,6 +3,7 @@
 // fused_kernel.cuh).
 #include "fused_kernel.cuh"
 #include <algorithm>
+#include <mutex>
 
 namespace {
 
@@ -234,7 +235,11 @@ int rich_adjoint_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const dou
 // library is loaded and held by every GPU that loads it until the process
 // exits.  Host code may not use the array's name as a device address (on the
 // host it names a shadow object), so the address is looked up once per device
-// with cudaGetSymbolAddress and cached.
+// with cudaGetSymbolAddress and cached; the look-up runs under a mutex, so
+// first calls from several host threads resolve it once.  The cached address
+// belongs to the device's primary context: after cudaDeviceReset on that
+// device the array is gone and this entry point must not be called again in
+// the process.
 // ---------------------------------------------------------------------------
 static __device__ __align__(256) unsigned char g_noalloc_scratch[RICH_NOALLOC_SCRATCH_BYTES];
 
@@ -242,6 +247,7 @@ namespace {
 constexpr int NOALLOC_MAX_DEVICES = 64;
 void* g_noalloc_addr[NOALLOC_MAX_DEVICES];
 int g_noalloc_sms[NOALLOC_MAX_DEVICES];
+std::mutex g_noalloc_mu;
 }
 
 extern "C" int rich_solve_batch_noalloc(const rich_problem_t* pb, int32_t nsamples,
@@ -266,18 +272,26 @@ extern "C" int rich_solve_batch_noalloc(const rich_problem_t* pb, int32_t nsampl
         rich_set_error("device index beyond the allocation-free table", __FILE__, __LINE__);
         return RICH_ERR_INVALID;
     }
-    if (!g_noalloc_addr[dev]) {      // first call on this device: resolve the symbol
-        void* ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess || !ptr) {
-            cudaGetLastError();
-            rich_set_error(e != cudaSuccess ? cudaGetErrorString(e) : "null symbol address", __FILE__, __LINE__);
-            return RICH_ERR_CUDA;
+    char* base = nullptr;
+    int dev_sms = 0;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {      // first call on this device: resolve the symbol
+            void* ptr = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+            if (e != cudaSuccess || !ptr) {
+                cudaGetLastError();
+                rich_set_error(e != cudaSuccess ? cudaGetErrorString(e) : "null symbol address", __FILE__,
+                               __LINE__);
+                return RICH_ERR_CUDA;
+            }
+            int sms = 0;
+            RICH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            g_noalloc_sms[dev] = sms;
+            g_noalloc_addr[dev] = ptr;
         }
-        int sms = 0;
-        RICH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        g_noalloc_sms[dev] = sms;
-        g_noalloc_addr[dev] = ptr;
+        base = (char*)g_noalloc_addr[dev];
+        dev_sms = g_noalloc_sms[dev];
     }
     FParams P;
     if (int e = fused_setup(pb, nsamples, P)) {
@@ -296,9 +310,7 @@ extern "C" int rich_solve_batch_noalloc(const rich_problem_t* pb, int32_t nsampl
     P.mixed_inner = MIXED_INNER_DEFAULT;
     int occ = 0;
     if (int e = fused_occupancy(P, smem, 512, &occ)) return e;
-    const int grid = (int)std::min<long long>({(long long)nsamples, (long long)g_noalloc_sms[dev] * occ,
-                                              (long long)slots});
-    char* base = (char*)g_noalloc_addr[dev];
+    const int grid = (int)std::min<long long>({(long long)nsamples, (long long)dev_sms * occ, (long long)slots});
     P.queue = (int*)base;                 // cleared by fused_launch before the kernel
     P.scratch = base + 256;
     P.lnKs = lnKs; P.alpha = alpha; P.alpha_scale = alpha_scale;

@@ -665,15 +665,17 @@ struct Cta {
     }
 
     // one implicit-Euler step by modified Picard (Sec. 4.1); returns false if
-    // the sample failed (status set)
+    // the sample failed.  A failure (PICARD_MAXIT, NONFINITE) replaces any
+    // earlier MG_MAXIT flag: the sample's QoI is undefined, whatever happened
+    // in its multigrid solves before
     __device__ bool time_step(long long& pic_tot, long long& mg_tot, int& maxpic, int& status) {
         theta_old();
         int k = 0;
         bool alive = true;
         for (;;) {
             const unsigned long long fb = assemble();
-            if (fb > INF_BITS - 1) { status = max(status, (int)RICH_NONFINITE); alive = false; break; }
-            if (!mg_solve(fb, mg_tot, status)) { status = max(status, (int)RICH_NONFINITE); alive = false; break; }
+            if (fb > INF_BITS - 1) { status = RICH_NONFINITE; alive = false; break; }
+            if (!mg_solve(fb, mg_tot, status)) { status = RICH_NONFINITE; alive = false; break; }
             unsigned long long dm = 0;
             for (int q = tid; q < nc; q += nt) {
                 double d = dp64[q];
@@ -684,9 +686,9 @@ struct Cta {
             const unsigned long long db = block_max(dm, red);
             ++k;
             ++pic_tot;
-            if (db > INF_BITS - 1) { status = max(status, (int)RICH_NONFINITE); alive = false; break; }
+            if (db > INF_BITS - 1) { status = RICH_NONFINITE; alive = false; break; }
             if (__longlong_as_double((long long)db) < P.picard_tol) break;
-            if (k >= P.picard_maxit) { status = max(status, (int)RICH_PICARD_MAXIT); alive = false; break; }
+            if (k >= P.picard_maxit) { status = RICH_PICARD_MAXIT; alive = false; break; }
         }
         maxpic = max(maxpic, k);
         return alive;
@@ -959,7 +961,7 @@ k_adjoint(const FParams P) {
                     for (int q = tid; q < nc; q += nt) dstp[q] = C.p[q];
                     __syncthreads();
                 }
-                if (!alive) { status = max(status, dst); break; }
+                if (!alive) { status = dst; break; }
                 for (int n = n1; n > n0; --n) {
                     // state p^n, operator and Jacobian at p^n
                     const double* pn = seg + (size_t)(n - n0 - 1) * nc;

@@ -83,6 +83,11 @@ struct MlmcRun {
     std::vector<double> t_pair, t_fine;
     std::vector<long long> n_done;
     int worst = 0;
+    // grid-only bias pairs: both members of the finest pair with the original
+    // parameters (no continuation), own noise stream, own accumulator slot NL
+    bool bias_mode = false;
+    long long n_bias = 0;
+    static constexpr uint32_t BIAS_KEY = 64;
 
     MlmcRun(rich_ctx* c, const rich_mlmc_cfg_t* g) : ctx(c), cfg(g) {
         NL = g->nlevels; L = NL - 1; nL = g->n0 << L;
@@ -97,12 +102,12 @@ struct MlmcRun {
     int grid(int l) const { return cfg->n0 << l; }
     int steps(int l) const { return cfg->steps0 << l; }
     double ascale(int l) const {
-        return (cfg->continuation && !vg) ? (double)(l + 1) / (double)NL : 1.0;
+        return (cfg->continuation && !vg && !bias_mode) ? (double)(l + 1) / (double)NL : 1.0;
     }
     // van Genuchten continuation steps of level l (Sec. 5.2): the
     // fixed_levels finest levels keep the original alpha and n
     int vg_steps(int l) const {
-        if (!cfg->continuation) return 0;
+        if (!cfg->continuation || bias_mode) return 0;
         const int fixed = std::max(1, (int)cfg->fixed_levels);
         return std::max(0, L + 1 - fixed - l);
     }
@@ -129,14 +134,14 @@ struct MlmcRun {
         };
         if (dalloc(lkf, fine_cells * 8) || dalloc(alf, fine_cells * 8) || dalloc(lkc, fine_cells * 2) ||
             dalloc(alc, fine_cells * 2) || dalloc(qf, B * 8) || dalloc(qc, B * 8) || dalloc(sf, B * 4) ||
-            dalloc(sc, B * 4) || dalloc(acc, 8 * 8 * NL))
+            dalloc(sc, B * 4) || dalloc(acc, 8 * 8 * (NL + 1)))
             return RICH_ERR_OOM;
         if (vg && (dalloc(nf, fine_cells * 8) || dalloc(ncb, fine_cells * 2)))
             return RICH_ERR_OOM;
         if (thetas && (dalloc(tsf, fine_cells * 8) || dalloc(trf, fine_cells * 8) || dalloc(tsc, fine_cells * 2) ||
                        dalloc(trc, fine_cells * 2)))
             return RICH_ERR_OOM;
-        RICH_CUDA(cudaMemsetAsync(acc.p, 0, 8 * 8 * NL, st));
+        RICH_CUDA(cudaMemsetAsync(acc.p, 0, 8 * 8 * (NL + 1), st));
         return 0;
     }
 
@@ -160,14 +165,24 @@ struct MlmcRun {
         }
         ctx->tune_threads = save_t; ctx->tune_mixed_inner = save_i;
         if (rc_all < 0) return rc_all;
-        n_done[l] += count;
+        if (bias_mode) n_bias += count; else n_done[l] += count;
         return 0;
+    }
+    // `count` pairs (finest grid, next coarser grid) that differ only in the
+    // grid: the discretisation-bias estimate of Eq. discErr without the
+    // parameter jump that the continuation puts into the finest level
+    int run_bias(long long count) {
+        if (L < 1 || count < 1) return 0;
+        bias_mode = true;
+        const int e = run_level(L, n_bias, count);
+        bias_mode = false;
+        return e;
     }
     int batch(int l, long long s0, int nb, int M, int ndraw, int coarsen, const rich_problem_t& pf,
               const rich_problem_t& pc) {
         RICH_CUDA(cudaEventRecord(ev[0], st));
         int e;
-        const uint32_t key = (uint32_t)l + cfg->key_offset;
+        const uint32_t key = (bias_mode ? BIAS_KEY : (uint32_t)l) + cfg->key_offset;
         const rich_soil_t fine{(double*)lkf.p, (double*)alf.p, (double*)nf.p, thetas ? (double*)tsf.p : nullptr,
                                thetas ? (double*)trf.p : nullptr};
         const rich_soil_t crs{(double*)lkc.p, (double*)alc.p, (double*)ncb.p, thetas ? (double*)tsc.p : nullptr,
@@ -199,16 +214,17 @@ struct MlmcRun {
         int rc = rich_solve_device(ctx, &pf, nb, (double*)lkf.p, (double*)alf.p, ascale(l), (double*)qf.p,
                                    nullptr, (int32_t*)sf.p, nullptr, st, vg ? &in_f : nullptr);
         if (rc < 0) return rc;
-        worst = std::max(worst, rc);
+        worst = rich_status_worse(worst, rc);
         RICH_CUDA(cudaEventRecord(ev[2], st));
         if (l > 0) {
             rc = rich_solve_device(ctx, &pc, nb, (double*)lkc.p, (double*)alc.p, ascale(l - 1), (double*)qc.p,
                                    nullptr, (int32_t*)sc.p, nullptr, st, vg ? &in_c : nullptr);
             if (rc < 0) return rc;
-            worst = std::max(worst, rc);
+            worst = rich_status_worse(worst, rc);
         }
         e = rich_mlmc_accumulate(ctx, (double*)qf.p, l > 0 ? (double*)qc.p : nullptr, (int32_t*)sf.p,
-                                 l > 0 ? (int32_t*)sc.p : nullptr, nb, (double*)acc.p + 8 * l, st);
+                                 l > 0 ? (int32_t*)sc.p : nullptr, nb,
+                                 (double*)acc.p + 8 * (bias_mode ? NL : l), st);
         if (e) return e;
         RICH_CUDA(cudaEventRecord(ev[3], st));
         RICH_CUDA(cudaEventSynchronize(ev[3]));
@@ -216,6 +232,7 @@ struct MlmcRun {
         RICH_CUDA(cudaEventElapsedTime(&a, ev[0], ev[1]));
         RICH_CUDA(cudaEventElapsedTime(&b, ev[1], ev[2]));
         RICH_CUDA(cudaEventElapsedTime(&c, ev[2], ev[3]));
+        if (bias_mode) return 0;
         t_pair[l] += 1e-3 * (a + b + c);
         t_fine[l] += 1e-3 * (a + b);      // one draw + one fine solve (plain MC sample)
         return 0;
@@ -224,8 +241,8 @@ struct MlmcRun {
     // level statistics from the device sums (Eqs. SMC_ch6, MC_var_ch6,
     // eq:MLMCVar, ML_var_ch6, MLMCSAMP_ch6)
     int finalize(rich_mlmc_result_t* out) {
-        std::vector<double> h(8 * NL);
-        RICH_CUDA(cudaMemcpyAsync(h.data(), acc.p, 8 * 8 * NL, cudaMemcpyDeviceToHost, st));
+        std::vector<double> h(8 * (NL + 1));
+        RICH_CUDA(cudaMemcpyAsync(h.data(), acc.p, 8 * 8 * (NL + 1), cudaMemcpyDeviceToHost, st));
         RICH_CUDA(cudaStreamSynchronize(st));
         rich_mlmc_result_t r{};
         r.nlevels = NL;
@@ -256,6 +273,26 @@ struct MlmcRun {
             r.w_mc_eps = r.var_f[L] * r.cost_fine[L] / e2;
         }
         r.bias_estimate = L > 0 ? fabs(r.mean[L]) / (2.0 - 1.0) : NAN;
+        // grid-only bias (Eq. discErr with rate a = 1): |E[Q_L - Q_{L-1}]| at the
+        // original parameters / (2^a - 1); total RMSE sqrt(bias^2 + sum V_l/N_l)
+        // (Eq. MSEMLMC_ch6); levels needed so that the bias, halving per level,
+        // falls to eps / sqrt 2 (half of the MSE budget)
+        const double* b = &h[8 * NL];
+        r.bias_pairs = (int64_t)b[2];
+        if (b[2] > 0) {
+            const double m = b[0] / b[2];
+            r.bias_grid = fabs(m) / (2.0 - 1.0);
+            r.bias_grid_se = b[2] > 1 ? sqrt(std::max((b[1] - b[2] * m * m) / (b[2] - 1), 0.0) / b[2]) : NAN;
+            r.total_rmse = sqrt(r.bias_grid * r.bias_grid + rmse2);
+            if (cfg->eps > 0) {
+                const double lim = cfg->eps / sqrt(2.0);
+                int extra = 0;
+                for (double bb = r.bias_grid; bb > lim && extra < 64; bb *= 0.5) ++extra;
+                r.levels_for_eps = NL + extra;
+            }
+        } else {
+            r.bias_grid = r.bias_grid_se = r.total_rmse = NAN;
+        }
         *out = r;
         return 0;
     }
@@ -275,6 +312,7 @@ int check_cfg(const rich_mlmc_cfg_t* cfg) {
         return RICH_ERR_INVALID;
     for (int l = 0; l < NL; ++l) {
         if (cfg->nsamples[l] < 2) return RICH_ERR_INVALID;
+        if (cfg->bias_pairs < 0) return RICH_ERR_INVALID;
         if (cfg->tune_threads[l] != 0 && cfg->tune_threads[l] != 256 && cfg->tune_threads[l] != 512 &&
             cfg->tune_threads[l] != 1024)
             return RICH_ERR_INVALID;
@@ -295,6 +333,7 @@ extern "C" int rich_mlmc_estimate(rich_ctx_t ctx, const rich_mlmc_cfg_t* cfg, ri
     if (int e = run.init(maxN)) return e;
     for (int l = 0; l < cfg->nlevels; ++l)
         if (int e = run.run_level(l, 0, cfg->nsamples[l])) return e;
+    if (int e = run.run_bias(cfg->bias_pairs)) return e;
     if (int e = run.finalize(out)) return e;
     out->rounds = 1;
     out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -333,6 +372,10 @@ extern "C" int rich_mlmc_adaptive(rich_ctx_t ctx, const rich_mlmc_cfg_t* cfg, in
             if (add[l] > 0)
                 if (int e = run.run_level(l, run.n_done[l], add[l])) return e;
         ++rounds;
+    }
+    if (cfg->bias_pairs > 0) {
+        if (int e = run.run_bias(cfg->bias_pairs)) return e;
+        if (int e = run.finalize(out)) return e;
     }
     out->rounds = rounds;
     out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

@@ -17,6 +17,14 @@
 
 void rich_set_error(const char* msg, const char* file, int line);
 
+// The more severe of two per-sample statuses: NONFINITE, then PICARD_MAXIT
+// (the sample failed, its QoI is NaN), then MG_MAXIT (a multigrid solve hit
+// its cycle cap but the sample's result is usable), then OK.
+inline int rich_status_worse(int a, int b) {
+    auto rank = [](int s) { return s == RICH_NONFINITE ? 3 : s == RICH_PICARD_MAXIT ? 2 : s == RICH_MG_MAXIT ? 1 : 0; };
+    return rank(b) > rank(a) ? b : a;
+}
+
 // per-sample status and counters of the last fused solve
 struct rich_samplebuf {
     void* base = nullptr;

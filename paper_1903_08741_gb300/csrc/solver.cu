@@ -67,7 +67,7 @@ int rich_solve_device(rich_ctx* ctx, const rich_problem_t* pb, int S, const doub
     int worst = 0;
     rich_stats_t acc{};
     for (int s = 0; s < S; ++s) {
-        worst = std::max(worst, (int)hs[s]);
+        worst = rich_status_worse(worst, (int)hs[s]);
         acc.picard_iters += hp[s];
         acc.mg_cycles += hm[s];
         acc.max_picard = std::max(acc.max_picard, hmax[s]);

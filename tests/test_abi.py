@@ -57,11 +57,32 @@ def test_struct_layouts_match_c(tmp_path):
                    ' offsetof(rich_stats_t, seconds), offsetof(rich_problem_t, cycle),'
                    ' offsetof(rich_field_t, nu), offsetof(rich_field_t, corr_len_z),'
                    ' sizeof(rich_mlmc_cfg_t), offsetof(rich_mlmc_cfg_t, tune_inner),'
-                   ' sizeof(rich_mlmc_result_t)); return 0;}\n')
+                   ' sizeof(rich_mlmc_result_t)); printf("%zu %zu %zu\\n", offsetof(rich_mlmc_cfg_t, bias_pairs),'
+                   ' offsetof(rich_mlmc_result_t, total_rmse), offsetof(rich_mlmc_result_t, levels_for_eps));'
+                   ' return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     vals = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     assert vals == [C.sizeof(R._Problem), C.sizeof(R._Field), C.sizeof(R._Stats),
                     R._Problem.precision.offset, R._Stats.seconds.offset, R._Problem.cycle.offset,
                     R._Field.nu.offset, R._Field.corr_len_z.offset, C.sizeof(R._MlmcCfg),
-                    R._MlmcCfg.tune_inner.offset, C.sizeof(R._MlmcResult)]
+                    R._MlmcCfg.tune_inner.offset, C.sizeof(R._MlmcResult), R._MlmcCfg.bias_pairs.offset,
+                    R._MlmcResult.total_rmse.offset, R._MlmcResult.levels_for_eps.offset]
+
+
+def test_noalloc_wrapper_rejects_bad_shapes_on_host():
+    """The allocation-free wrapper checks grid shape, alpha shape and the
+    lengths of qoi / status before anything reaches the library (CPU tensors
+    here: the check runs before any device is touched)."""
+    torch = pytest.importorskip("torch")
+    pb = R.Problem(nx=16, nz=16, nsteps=1, dt=0.01)
+    x = torch.zeros((4, 16, 16), dtype=torch.float64)
+    bad = ((torch.zeros((4, 16, 8), dtype=torch.float64), x, None, None),
+           (x, torch.zeros((3, 16, 16), dtype=torch.float64), None, None),
+           (torch.zeros((16, 16), dtype=torch.float64), x, None, None),
+           (x, x, torch.zeros(3, dtype=torch.float64), None),
+           (x, x, None, torch.zeros(2, dtype=torch.int32)))
+    for lk, al, q, s in bad:
+        with pytest.raises(R.RichError):
+            R.solve_batch_noalloc(pb, lk, al, qoi=q, status=s)
+    assert R._check_noalloc_args(pb, x, x, None, None) == 4

@@ -112,3 +112,22 @@ def test_autograd_function(R):
     _, dq, _, _, _, _ = R.solve_batch_adjoint(pb, Bd, xid, ald)
     expect = dq * torch.tensor([[2.0], [-1.0]], dtype=torch.float64, device=q.device)
     assert torch.allclose(x.grad, expect, rtol=0, atol=0)
+
+
+def test_autograd_forward_only_without_grad(R):
+    """Under torch.no_grad() (or with xi not requiring grad) the wrapper runs the
+    forward solve alone: no adjoint launch, the same QoI as the adjoint's forward."""
+    n, nkl, S, steps, dt = 16, 4, 3, 3, 0.005
+    B, xi, al, (Bd, xid, ald) = setup_case(R, n, nkl, S, 12)
+    pb = gpu_pb(R, n, steps, dt)
+    q_adj, _, _, st, _, _ = R.solve_batch_adjoint(pb, Bd, xid, ald)
+    l0 = R.launch_count()
+    with torch.no_grad():
+        q = R.RichardsQoI.apply(xid.clone().requires_grad_(True), ald, Bd, pb)
+    l1 = R.launch_count()
+    q2 = R.RichardsQoI.apply(xid, ald, Bd, pb)
+    ok = st == 0
+    assert torch.equal(q[ok], q_adj[ok]) and torch.equal(q2[ok], q_adj[ok])
+    assert not q.requires_grad
+    # the forward path launches the KL field kernel and the fused solve only
+    assert l1 - l0 <= 2

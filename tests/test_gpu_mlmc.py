@@ -48,6 +48,74 @@ def test_mlmc_matches_oracle(R, coupling):
     assert all(c > 0 for c in g["cost"])
 
 
+def close(a, b, tol):
+    """Relative agreement; two NaNs (a level with fewer than two usable pairs
+    has no variance) agree."""
+    if np.isnan(a) or np.isnan(b):
+        return np.isnan(a) and np.isnan(b)
+    return rel(a, b) < tol
+
+
+@pytest.mark.slow
+def test_mlmc_configured_hierarchy_matches_oracle(R):
+    """The configured five-level hierarchy (16^2 ... 256^2 with 5 2^l steps to
+    T = 0.1, alpha_l = alpha (l+1)/5, covariance upscaling, Sec. 5 Eq.
+    MLMCestimator_ch6) with N_l reduced to 16/8/4/2/2: the GPU's level
+    statistics equal the oracle's restatement of the estimator."""
+    ns, n0, s0, T = (16, 8, 4, 2, 2), 16, 5, 0.1
+    cfg = R.MlmcConfig(nsamples=ns, n0=n0, steps0=s0, t_final=T, coupling=2, eps=1e-3,
+                       problem=R.Problem(**PHYSICS, **SOLVER))
+    g = R.mlmc_estimate(cfg)
+    o = O.mlmc_estimate(ns, n0, s0, T, coupling=2, **PHYSICS, **SOLVER)
+    for l, lev in enumerate(o):
+        y, qf, qc = lev["y"], lev["qf"], lev["qc"]
+        assert g["n"][l] == y.size and g["failed"][l] == lev["failed"]
+        assert close(g["mean"][l], y.mean() if y.size else np.nan, 1e-9)
+        assert close(g["var"][l], y.var(ddof=1) if y.size > 1 else np.nan, 1e-8)
+        assert close(g["mean_f"][l], qf.mean() if y.size else np.nan, 1e-9)
+        if l > 0:
+            assert close(g["mean_c"][l], qc.mean() if y.size else np.nan, 1e-9)
+    assert sum(g["n"]) >= sum(ns) // 2
+
+
+@pytest.mark.parametrize("coupling", [0, 2])
+def test_mlmc_grid_only_bias_matches_oracle(R, coupling):
+    """Grid-only bias pairs (Eq. discErr): finest-level pairs with both members
+    at the original alpha, from their own noise stream (level key 64); the
+    bias |E[Q_L - Q_{L-1}]| and the total RMSE sqrt(bias^2 + sum V_l/N_l) (Eq.
+    MSEMLMC_ch6) equal the oracle's restatement, and the level statistics do
+    not change when the pairs are added."""
+    ns, n0, s0, T, nb = (12, 6, 4), 8, 2, 0.04, 6
+    base = dict(nsamples=ns, n0=n0, steps0=s0, t_final=T, coupling=coupling, eps=1e-3,
+                problem=R.Problem(**PHYSICS, **SOLVER))
+    g = R.mlmc_estimate(R.MlmcConfig(**base, bias_pairs=nb))
+    g0 = R.mlmc_estimate(R.MlmcConfig(**base))
+    assert g0["mean"] == g["mean"] and g0["var"] == g["var"] and g0["bias_pairs"] == 0
+    L = len(ns) - 1
+    M = n0 << L
+    if coupling == 2:
+        lk, al, lkc, alc = O.sample_fields_pair(M, M, nb, seed=0, level=64)
+    else:
+        lk, al = O.sample_fields(M, M, nb, seed=0, level=64)
+        blk = lambda x: x.reshape(nb, M // 2, 2, M // 2, 2).mean(axis=(2, 4))
+        lkc, alc = blk(lk), blk(al)
+    pf = O.make_problem(nsteps=s0 << L, dt=T / (s0 << L), **PHYSICS, **SOLVER)
+    pc = O.make_problem(nsteps=s0 << (L - 1), dt=T / (s0 << (L - 1)), **PHYSICS, **SOLVER)
+    _, qf, sf, _ = O.solve_batch(pf, lk, al, 1.0, want_p=False)
+    _, qc, sc, _ = O.solve_batch(pc, lkc, alc, 1.0, want_p=False)
+    bad = np.isin(sf, (1, 3)) | np.isin(sc, (1, 3))
+    y = (qf - qc)[~bad]
+    assert g["bias_pairs"] == y.size >= nb // 2
+    assert rel(g["bias_grid"], abs(y.mean())) < 1e-9
+    assert rel(g["total_rmse"], np.sqrt(abs(y.mean()) ** 2 + g["rmse"] ** 2)) < 1e-9
+    assert rel(g["bias_grid_se"], y.std(ddof=1) / np.sqrt(y.size)) < 1e-7
+    extra = 0
+    b = abs(y.mean())
+    while b > 1e-3 / np.sqrt(2):
+        b, extra = b / 2, extra + 1
+    assert g["levels_for_eps"] == len(ns) + extra
+
+
 def test_mlmc_telescoping_consistency(R):
     """Exact coupling: the level-l fine member (pair l) and the level-l coarse
     member (pair l+1) have the same law, so their means agree within 4 sigma."""

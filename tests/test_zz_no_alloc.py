@@ -18,14 +18,19 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def test_noalloc_matches_solve_batch_twice():
+@pytest.fixture(scope="module")
+def R():
     import paper_1903_08741_gb300 as R
     from paper_1903_08741_gb300 import build
-    from tests.inputs import PHYSICS, SOLVER
     build.build()
     assert torch.cuda.is_available()
+    torch.cuda.set_device(torch.device("cuda:0"))
+    return R
+
+
+def test_noalloc_matches_solve_batch_twice(R):
+    from tests.inputs import PHYSICS, SOLVER
     dev = torch.device("cuda:0")
-    torch.cuda.set_device(dev)
     pb = R.Problem(nx=32, nz=32, nsteps=3, dt=0.01, **PHYSICS, **SOLVER)
     for call, seed in enumerate((21, 22)):
         lk, al = O.sample_fields(32, 32, 12, seed=seed)
@@ -45,11 +50,27 @@ def test_noalloc_matches_solve_batch_twice():
         assert np.all(np.isnan(q[(s_ref == 1) | (s_ref == 3)]))
 
 
-def test_noalloc_rejects_oversized_grid():
-    import paper_1903_08741_gb300 as R
+def test_noalloc_rejects_oversized_grid(R):
     from tests.inputs import PHYSICS, SOLVER
     dev = torch.device("cuda:0")
     pb = R.Problem(nx=1024, nz=1024, nsteps=1, dt=0.01, **PHYSICS, **SOLVER)
     x = torch.zeros((1, 1024, 1024), dtype=torch.float64, device=dev)
     with pytest.raises(R.RichError):
         R.solve_batch_noalloc(pb, x, x)
+
+
+def test_noalloc_rejects_bad_shapes_before_launch(R):
+    """A field of another grid, a mismatched alpha, or a qoi / status shorter
+    than the batch raise before the library is called."""
+    from tests.inputs import PHYSICS, SOLVER
+    dev = torch.device("cuda:0")
+    pb = R.Problem(nx=16, nz=16, nsteps=1, dt=0.01, **PHYSICS, **SOLVER)
+    x = torch.zeros((4, 16, 16), dtype=torch.float64, device=dev)
+    l0 = R.launch_count()
+    for args, kw in (((torch.zeros((4, 16, 8), dtype=torch.float64, device=dev), x), {}),
+                     ((x, torch.zeros((3, 16, 16), dtype=torch.float64, device=dev)), {}),
+                     ((x, x), dict(qoi=torch.zeros(3, dtype=torch.float64, device=dev))),
+                     ((x, x), dict(status=torch.zeros(2, dtype=torch.int32, device=dev)))):
+        with pytest.raises(R.RichError):
+            R.solve_batch_noalloc(pb, *args, **kw)
+    assert R.launch_count() == l0
