@@ -39,12 +39,14 @@ PHYS = dict(theta_r=0.1, theta_s=0.5, p_top=-0.5, p_bottom=-5.0, p_init=-5.0,
             picard_tol=1e-8, picard_maxit=50, mg_tol=1e-10, mg_maxit=100, nu1=2, nu2=2)
 FP64_TFLOPS_NOMINAL = 1.25      # GB300 FP64 (non-tensor) nominal: 152 SMs x 2 FMA/clk x 2070 MHz x 2
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one fused-solver
-# launch of the default workload's timed step, from an ncu capture (see
-# profiles/); valid only while the kernel source is the one captured.
+# DRAM traffic of the fused solver per algorithmic byte: (dram__bytes_read.sum +
+# dram__bytes_write.sum) of one launch of a reduced case of the workload (304
+# samples, 2 time steps; ncu, see profiles/), divided by that launch's
+# algorithmic bytes (the library's count).  The bench scales it by the timed
+# launch's algorithmic bytes.  Valid only while the kernel sources are the
+# ones captured (fused_sha()).
 TRAFFIC = {
-    # (precision, block_threads): (fused_sha() of the captured sources, bytes per launch)
-    ("fp64", 1024): ("bc4043f576f62d5250d78e2a1010858e8c688048faf291b2d1717d0c1fb0921d", 30.69e12 + 5.55e12),
+    # (precision, block_threads): (fused_sha() of the captured sources, DRAM bytes per algorithmic byte)
 }
 
 
@@ -58,11 +60,11 @@ def fused_sha():
     return h.hexdigest()
 
 
-def captured_traffic(prec_name, block_threads, default_workload):
+def captured_traffic(prec_name, block_threads, alg_bytes_per_launch):
     ent = TRAFFIC.get((prec_name, block_threads))
-    if not default_workload or ent is None or ent[0] != fused_sha():
+    if ent is None or ent[0] != fused_sha():
         return None
-    return ent[1]
+    return ent[1] * alg_bytes_per_launch
 
 
 def load_peaks():
@@ -347,8 +349,12 @@ def mlmc_report(r, cfg):
     """The estimator's figures: level statistics, W(eps) (Eq. MLMCSAMP_ch6),
     sampling RMSE, grid-only bias and total RMSE (Eqs. discErr, MSEMLMC_ch6)."""
     out = {"w_eps_s": r["w_eps"], "eps": 1e-3,
-           "levels": {k: r[k] for k in ("n", "failed", "mean", "var", "cost", "cost_fine", "n_opt",
+           "w_eps_full_gpu_s": r["w_eps_sm"],
+           "levels": {k: r[k] for k in ("n", "failed", "mean", "var", "cost", "cost_sm", "cost_fine", "n_opt",
                                         "mean_f", "var_f")},
+           "cost_note": "cost: wall seconds per pair of this run's batches; cost_sm: GPU-seconds per pair on a "
+                        "fully occupied GPU (field time + the solves' SM-seconds / SMs), the per-pair cost that "
+                        "W(eps) assumes once N_l fills the GPU",
            "estimate": r["estimate"], "sampling_rmse": r["rmse"], "ml_variance": r["ml_variance"],
            "w_mc_eps_s": r["w_mc_eps"], "mc_over_mlmc": r["w_mc_eps"] / r["w_eps"],
            "bias_with_continuation_jump": r["bias_estimate"], "run_seconds": r["seconds"],
@@ -872,9 +878,7 @@ def run_ours(args):
     frac_alu = k_tflops / fp64_peak if prec == R.FP64 else 0.0
     per_launch_bytes = kbytes / max(klaunch, 1)
     kname = f"k_fused<{'double' if prec == R.FP64 else 'float'},{block_threads}> (persistent fused solve)"
-    default_workload = (args.workload == "mc128" and not args.samples and not args.time_steps
-                        and args.field == "exp" and args.cycle == 1)
-    traffic = captured_traffic("fp64" if prec == R.FP64 else "mixed", block_threads, default_workload)
+    traffic = captured_traffic("fp64" if prec == R.FP64 else "mixed", block_threads, per_launch_bytes)
     if prec == R.FP64 and frac_alu > frac_hbm:
         roof = {"bound": "alu", "achieved": k_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
                 "frac": frac_alu, "traffic": traffic, "kernel": kname, "peak_kind": fp64_kind,

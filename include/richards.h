@@ -97,6 +97,10 @@ typedef struct {
     int32_t max_picard;      /* largest Picard count of one step of one sample    */
     int32_t failed;          /* samples with status PICARD_MAXIT or NONFINITE     */
     double seconds;          /* wall time of the call                             */
+    double sm_seconds;       /* SM-seconds the solves held: sum over samples of the
+                                sample's solve time on its CTA / the CTAs resident
+                                per SM (the cost on a fully occupied GPU is
+                                sm_seconds / the number of SMs)                   */
 } rich_stats_t;
 
 /* Create a context on CUDA device `device`.  The context owns its device
@@ -317,6 +321,11 @@ typedef struct {
     double total_rmse;        /* sqrt(bias_grid^2 + sum V_l/N_l) (Eq. MSEMLMC_ch6)        */
     int32_t levels_for_eps;   /* levels for which the grid bias (halving per level) falls
                                  to eps/sqrt(2); 0 without bias pairs                      */
+    double cost_sm[RICH_MLMC_MAX_LEVELS];  /* GPU-seconds per pair on a fully occupied GPU:
+                                 field time + the solves' SM-seconds (rich_stats_t
+                                 sm_seconds) / the number of SMs, per pair; equals cost[]
+                                 when a level's batches fill the GPU                       */
+    double w_eps_sm;          /* eps^-2 (sum sqrt(V_l cost_sm_l))^2                        */
 } rich_mlmc_result_t;
 
 /* Run the estimator with the configured N_l and fill *out (HOST).  Synchronous;

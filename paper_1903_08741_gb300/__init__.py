@@ -63,7 +63,8 @@ class _Fp64Rates(C.Structure):
 
 class _Stats(C.Structure):
     _fields_ = [("picard_iters", C.c_int64), ("mg_cycles", C.c_int64), ("cell_vcycles", C.c_int64),
-                ("max_picard", C.c_int32), ("failed", C.c_int32), ("seconds", C.c_double)]
+                ("max_picard", C.c_int32), ("failed", C.c_int32), ("seconds", C.c_double),
+                ("sm_seconds", C.c_double)]
 
 
 @dataclass
@@ -178,7 +179,8 @@ class _MlmcResult(C.Structure):
                 ("ml_variance", C.c_double), ("w_eps", C.c_double), ("w_mc_eps", C.c_double),
                 ("bias_estimate", C.c_double), ("seconds", C.c_double), ("rounds", C.c_int32),
                 ("bias_pairs", C.c_int64), ("bias_grid", C.c_double), ("bias_grid_se", C.c_double),
-                ("total_rmse", C.c_double), ("levels_for_eps", C.c_int32)]
+                ("total_rmse", C.c_double), ("levels_for_eps", C.c_int32), ("cost_sm", _LV),
+                ("w_eps_sm", C.c_double)]
 
 
 @dataclass
@@ -237,6 +239,7 @@ class Stats:
     max_picard: int = 0
     failed: int = 0
     seconds: float = 0.0
+    sm_seconds: float = 0.0
 
 
 _lib = None
@@ -570,10 +573,10 @@ def solve_batch_noalloc(problem: Problem, lnKs, alpha, alpha_scale=1.0, qoi=None
 def _mlmc_result(r, rc):
     NL = r.nlevels
     out = {k: list(getattr(r, k))[:NL] for k in ("n", "failed", "mean", "var", "mean_f", "var_f", "mean_c",
-                                                  "var_c", "cost", "cost_fine", "n_opt")}
+                                                  "var_c", "cost", "cost_fine", "n_opt", "cost_sm")}
     out.update({k: getattr(r, k) for k in ("estimate", "rmse", "ml_variance", "w_eps", "w_mc_eps",
                                             "bias_estimate", "seconds", "rounds", "bias_pairs", "bias_grid",
-                                            "bias_grid_se", "total_rmse", "levels_for_eps")})
+                                            "bias_grid_se", "total_rmse", "levels_for_eps", "w_eps_sm")})
     out["nlevels"], out["rc"] = NL, rc
     return out
 
@@ -643,11 +646,17 @@ def _autograd():
         bottom-flux QoI of each sample with ln Ks = basis^T xi; backward returns
         grad_qoi[:, None] * dQ/dxi from the discrete adjoint."""
 
+        @classmethod
+        def apply(cls, xi, alpha, basis, problem, alpha_scale=1.0, ckpt_every=10):
+            if not (torch.is_grad_enabled() and xi.requires_grad):
+                # no gradient can flow (torch.no_grad(), or xi without
+                # requires_grad): the forward solve alone, no adjoint sweep
+                return solve_batch(problem, kl_fields(basis, xi.detach().contiguous()), alpha, alpha_scale)[0]
+            return super().apply(xi, alpha, basis, problem, alpha_scale, ckpt_every)
+
         @staticmethod
         def forward(ctx, xi, alpha, basis, problem, alpha_scale=1.0, ckpt_every=10):
             if not ctx.needs_input_grad[0]:
-                # no gradient wanted (torch.no_grad(), or xi without
-                # requires_grad): the forward solve alone
                 ctx.save_for_backward(None)
                 return solve_batch(problem, kl_fields(basis, xi.detach().contiguous()), alpha, alpha_scale)[0]
             qoi, dq, _, status, _, _ = solve_batch_adjoint(problem, basis, xi.detach().contiguous(),

@@ -12,22 +12,50 @@ size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
 
-// Slot layout and problem constants of the fused kernel (no device work).
-// Dynamic shared memory of a CTA: the coarsest level's dense matrix, then the
-// corrections dp of as many levels (coarsest first) as fit the budget of the
-// launch shape (one 1024-thread CTA per SM may use ~220 KB, two 512-thread
-// CTAs ~104 KB each, four 256-thread CTAs ~50 KB each), so that the Gauss-Seidel neighbour reads of those levels
+// Dynamic shared memory of a CTA (no device work): the coarsest level's dense
+// matrix; then the arrays that the cycles read on the small coarse levels
+// that warp 0 runs alone (levels l >= 1 with at most WARP_CELLS cells: the
+// multigrid arrays, and for FP64 the diagonal and the coarsest level's faces,
+// which the direct solve assembles); then the corrections dp of as many of the other levels
+// (coarsest first) as fit the budget of the launch shape (one 1024-thread CTA
+// per SM may use ~220 KB, two 512-thread CTAs ~104 KB each, four 256-thread
+// CTAs ~50 KB each), so that the Gauss-Seidel neighbour reads of those levels
 // stay on chip; levels that do not fit keep dp in the slot.  Results do not
-// depend on where dp lives.
+// depend on where an array lives.
+constexpr int WARP_CELLS = 256;
+
 static void plan_smem(FParams& P, int nt) {
     const size_t w = P.mixed ? 4 : 8;
     const int c = P.nlev - 1;
     const size_t nnc = (size_t)P.nx[c] * P.nz[c];
-    size_t off = (nnc * (nnc + 1) * w + 15) & ~(size_t)15;
+    auto al16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    size_t off = al16(nnc * (nnc + 1) * w);
     const size_t budget = nt == 1024 ? 220 * 1024 : nt == 512 ? 104 * 1024 : 50 * 1024;
-    for (int l = 0; l < MAXL; ++l) P.osm[l] = -1;
-    for (int l = c; l >= 0; --l) {
-        const size_t bytes = ((size_t)P.nx[l] * P.nz[l] * w + 15) & ~(size_t)15;
+    for (int l = 0; l < MAXL; ++l) {
+        P.osm[l] = -1;
+        for (int k = 0; k < N64; ++k) P.s64[l][k] = -1;
+        for (int k = 0; k < NMG; ++k) P.smg[l][k] = -1;
+    }
+    P.lw = P.nlev;
+    for (int l = 1; l < P.nlev; ++l)
+        if ((size_t)P.nx[l] * P.nz[l] <= (size_t)WARP_CELLS) { P.lw = l; break; }
+    for (int l = P.lw; l < P.nlev; ++l) {
+        const size_t nc = (size_t)P.nx[l] * P.nz[l];
+        if (!P.mixed) {
+            for (int k = 0; k < N64; ++k) {
+                if (k != A_D && !(l == c && (k == A_TX || k == A_TZ))) continue;
+                P.s64[l][k] = (long long)off;
+                off = al16(off + nc * 8);
+            }
+        }
+        for (int k = 0; k < NMG; ++k) {
+            if (P.omg[l][k] < 0) continue;
+            P.smg[l][k] = (long long)off;
+            off = al16(off + nc * w);
+        }
+    }
+    for (int l = P.lw - 1; l >= 0; --l) {
+        const size_t bytes = al16((size_t)P.nx[l] * P.nz[l] * w);
         if (off + bytes > budget) break;
         P.osm[l] = (long long)off;
         off += bytes;
@@ -174,7 +202,10 @@ int rich_solve_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const doubl
     P.queue = (int*)ctx->fused_scratch;
     P.lnKs = lnKs; P.alpha = alpha; P.alpha_scale = alpha_scale;
     P.qoi = qoi; P.p_final = p_final; P.status = w.status;
-    P.pic_total = w.pic_total; P.mg_total = w.mg_total; P.maxpic = w.maxpic;
+    P.pic_total = w.pic_total; P.mg_total = w.mg_total; P.maxpic = w.maxpic; P.t_ns = w.t_ns;
+    // CTAs that share an SM during the solve: a grid smaller than the GPU's
+    // resident capacity is spread over the SMs first
+    w.last_occ = std::max(1, std::min(occ, (grid + ctx->sm_count - 1) / std::max(ctx->sm_count, 1)));
     rich_prof_begin(ctx, st);
     if (int e = fused_launch(P, grid, smem, nt, st)) return e;
     rich_prof_end(ctx, st, 0.0, 0.0);

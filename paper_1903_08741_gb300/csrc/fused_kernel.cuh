@@ -38,6 +38,7 @@
 #pragma once
 #include "rich_internal.cuh"
 #include <math.h>
+#include <type_traits>
 
 // launch parameters and slot layout, shared across translation units
 namespace rich_fused {
@@ -61,6 +62,9 @@ struct FParams {
     long long omg[MAXL][NMG];
     long long osm[MAXL];                    // level's dp in dynamic shared memory at this
                                             // byte offset (-1: in the slot)
+    int lw;                                 // first level run by warp 0 alone (nlev: none)
+    long long s64[MAXL][N64];               // levels >= lw: every array in dynamic shared
+    long long smg[MAXL][NMG];               // memory at these byte offsets (-1: not there)
     long long smem_bytes;                   // dynamic shared memory of a CTA
     long long o_f64, o_dp64, o_p, o_thold, o_Ks, o_a, o_K, o_th;
     long long slot_bytes;
@@ -73,6 +77,7 @@ struct FParams {
     int32_t* status;
     int64_t* pic_total;
     int64_t* mg_total;
+    int64_t* t_ns;                          // per-sample solve time on its CTA (ns; may be null)
     int32_t* maxpic;
     int* queue;
     int nsteps, picard_maxit, mg_maxit, nu1, nu2, gamma;
@@ -126,6 +131,13 @@ __device__ __forceinline__ int fdiv(int c, int d, unsigned m) {
     return d == 1 ? c : (int)__umulhi((unsigned)c, m);
 }
 
+// the GPU's global nanosecond timer (per-sample solve times)
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 __device__ __forceinline__ unsigned long long abs_bits(double x) {
     return (unsigned long long)__double_as_longlong(x) & ABS_MASK;
 }
@@ -174,181 +186,276 @@ struct Lv {
 
 template <typename T> struct Scaled { static constexpr bool value = sizeof(T) == 8; };
 
-// Gauss-Seidel value of cell P from its current neighbours
+// Thread groups that run a level's loops: the whole CTA (barrier
+// __syncthreads), or warp 0 alone (barrier __syncwarp) on the small coarse
+// levels, whose few hundred cells do not pay for CTA-wide barriers; those
+// levels keep every array in shared memory.  Each level function ends with
+// its group synchronised.
+struct GCta {
+    static __device__ __forceinline__ int rank() { return threadIdx.x; }
+    static __device__ __forceinline__ int size() { return blockDim.x; }
+    static __device__ __forceinline__ void sync() { __syncthreads(); }
+};
+struct GWarp {
+    static __device__ __forceinline__ int rank() { return threadIdx.x & 31; }
+    static __device__ __forceinline__ int size() { return 32; }
+    static __device__ __forceinline__ void sync() { __syncwarp(); }
+};
+
+// Gauss-Seidel value of cell P from its current neighbours, with the level's
+// arrays passed as restrict-qualified pointers: every caller reads dp only at
+// cells that it does not write in the same pass (see rbgs_cells), so the
+// compiler may keep several cells' loads in flight ahead of the stores.
+//   FP64 (scaled): c0..c3 = wE, wW, wN, wS; value f + sum w dp_nb.
+//   FP32 (unscaled): c0 = Tx, c1 = Tz; value (f + sum T dp_nb) / D.
 template <typename T>
-__device__ __forceinline__ T gs_value(const Lv<T>& L, int P, int i, int j) {
+__device__ __forceinline__ T gs_at(int P, int i, int j, int nx, int nz, const T* __restrict__ f,
+                                   const T* __restrict__ c0, const T* __restrict__ c1,
+                                   const T* __restrict__ c2, const T* __restrict__ c3,
+                                   const T* __restrict__ q, const T* __restrict__ dp) {
     if constexpr (Scaled<T>::value) {
-        T v = L.f[P];
-        if (i < L.nx - 1) v += L.c0[P] * L.dp[P + 1];
-        if (i > 0)        v += L.c1[P] * L.dp[P - 1];
-        if (j < L.nz - 1) v += L.c2[P] * L.dp[P + L.nx];
-        if (j > 0)        v += L.c3[P] * L.dp[P - L.nx];
+        T v = f[P];
+        if (i < nx - 1) v += c0[P] * dp[P + 1];
+        if (i > 0)      v += c1[P] * dp[P - 1];
+        if (j < nz - 1) v += c2[P] * dp[P + nx];
+        if (j > 0)      v += c3[P] * dp[P - nx];
         return v;
     } else {
-        T s = T(0);
-        if (i < L.nx - 1) s += L.c0[P] * L.dp[P + 1];
-        if (i > 0)        s += L.c0[P - 1] * L.dp[P - 1];
-        if (j < L.nz - 1) s += L.c1[P] * L.dp[P + L.nx];
-        if (j > 0)        s += L.c1[P - L.nx] * L.dp[P - L.nx];
-        return (L.f[P] + s) * L.q[P];
+        T t = T(0);
+        if (i < nx - 1) t += c0[P] * dp[P + 1];
+        if (i > 0)      t += c0[P - 1] * dp[P - 1];
+        if (j < nz - 1) t += c1[P] * dp[P + nx];
+        if (j > 0)      t += c1[P - nx] * dp[P - nx];
+        return (f[P] + t) * q[P];
     }
 }
 
-// residual f - A dp at cell P (unscaled)
+// residual f - A dp at cell P (unscaled): FP64 D (value - dp_P), FP32
+// f - (D dp_P - sum T dp_nb)
 template <typename T>
-__device__ __forceinline__ T residual(const Lv<T>& L, int P, int i, int j) {
+__device__ __forceinline__ T resid_at(int P, int i, int j, int nx, int nz, const T* __restrict__ f,
+                                      const T* __restrict__ c0, const T* __restrict__ c1,
+                                      const T* __restrict__ c2, const T* __restrict__ c3,
+                                      const T* __restrict__ q, const T* __restrict__ D,
+                                      const T* __restrict__ dp) {
     if constexpr (Scaled<T>::value) {
-        return L.D[P] * (gs_value(L, P, i, j) - L.dp[P]);
+        return D[P] * (gs_at<T>(P, i, j, nx, nz, f, c0, c1, c2, c3, q, dp) - dp[P]);
     } else {
-        T s = T(0);
-        if (i < L.nx - 1) s += L.c0[P] * L.dp[P + 1];
-        if (i > 0)        s += L.c0[P - 1] * L.dp[P - 1];
-        if (j < L.nz - 1) s += L.c1[P] * L.dp[P + L.nx];
-        if (j > 0)        s += L.c1[P - L.nx] * L.dp[P - L.nx];
-        return L.f[P] - (L.D[P] * L.dp[P] - s);
+        T t = T(0);
+        if (i < nx - 1) t += c0[P] * dp[P + 1];
+        if (i > 0)      t += c0[P - 1] * dp[P - 1];
+        if (j < nz - 1) t += c1[P] * dp[P + nx];
+        if (j > 0)      t += c1[P - nx] * dp[P - nx];
+        return f[P] - (D[P] * dp[P] - t);
     }
 }
 
-// one colour of red-black Gauss-Seidel over the level (red: i + j even)
-template <typename T>
-__device__ __forceinline__ void rbgs(const Lv<T>& L, int colour) {
-    const int n = L.hx * L.nz;
-    for (int c = threadIdx.x; c < n; c += blockDim.x) {
-        int j = fdiv(c, L.hx, L.mhx);
-        int i = 2 * (c - j * L.hx) + ((j + colour) & 1);
-        L.dp[j * L.nx + i] = gs_value(L, j * L.nx + i, i, j);
+// one colour of red-black Gauss-Seidel over the level (red: i + j even).  The
+// corrections are read through one restrict-qualified view and written through
+// another: a half-sweep writes cells of one colour and reads only cells of the
+// other, so the two views never touch the same element.
+template <typename T, typename G>
+__device__ __forceinline__ void rbgs_cells(int n, int nx, int nz, int hx, unsigned mhx, int colour,
+                                           const T* __restrict__ f, const T* __restrict__ c0,
+                                           const T* __restrict__ c1, const T* __restrict__ c2,
+                                           const T* __restrict__ c3, const T* __restrict__ q,
+                                           const T* __restrict__ dpr, T* __restrict__ dpw) {
+#pragma unroll 4
+    for (int c = G::rank(); c < n; c += G::size()) {
+        const int j = fdiv(c, hx, mhx);
+        const int i = 2 * (c - j * hx) + ((j + colour) & 1);
+        const int P = j * nx + i;
+        dpw[P] = gs_at<T>(P, i, j, nx, nz, f, c0, c1, c2, c3, q, dpr);
     }
-    __syncthreads();
+    G::sync();
+}
+
+template <typename T, typename G>
+__device__ __forceinline__ void rbgs(const Lv<T>& L, int colour) {
+    rbgs_cells<T, G>(L.hx * L.nz, L.nx, L.nz, L.hx, L.mhx, colour, L.f, L.c0, L.c1, L.c2, L.c3, L.q, L.dp, L.dp);
+}
+
+template <typename T, typename G>
+__device__ __forceinline__ void smooth(const Lv<T>& L, int nu) {
+    for (int it = 0; it < nu; ++it) { rbgs<T, G>(L, 0); rbgs<T, G>(L, 1); }
 }
 
 // restricted residual (Eq. transfer, R = 1/4 sum of the children); after a
-// black half-sweep only the two red children carry a residual
-template <typename T>
-__device__ __forceinline__ void resid_restrict(const Lv<T>& F, const Lv<T>& C, bool red_only,
-                                               bool coarsest) {
-    for (int c = threadIdx.x; c < C.nc; c += blockDim.x) {
-        int J = fdiv(c, C.nx, C.mnx), I = c - J * C.nx;
-        int i = 2 * I, j = 2 * J, P = j * F.nx + i;
-        T r00 = residual(F, P, i, j);
-        T r11 = residual(F, P + F.nx + 1, i + 1, j + 1);
+// black half-sweep only the two red children carry a residual.  Reads the
+// fine level, writes the coarse one (distinct arrays: restrict views).
+template <typename T, typename G>
+__device__ __forceinline__ void restrict_cells(const Lv<T>& F, int cnx, int cnc, unsigned cmnx, bool red_only,
+                                               bool scale, const T* __restrict__ f, const T* __restrict__ c0,
+                                               const T* __restrict__ c1, const T* __restrict__ c2,
+                                               const T* __restrict__ c3, const T* __restrict__ q,
+                                               const T* __restrict__ D, const T* __restrict__ dp,
+                                               const T* __restrict__ cq, T* __restrict__ cf, T* __restrict__ cdp) {
+    const int nx = F.nx, nz = F.nz;
+#pragma unroll 2
+    for (int c = G::rank(); c < cnc; c += G::size()) {
+        const int J = fdiv(c, cnx, cmnx), I = c - J * cnx;
+        const int i = 2 * I, j = 2 * J, P = j * nx + i;
+        const T r00 = resid_at<T>(P, i, j, nx, nz, f, c0, c1, c2, c3, q, D, dp);
+        const T r11 = resid_at<T>(P + nx + 1, i + 1, j + 1, nx, nz, f, c0, c1, c2, c3, q, D, dp);
         T sum;
         if (red_only) {
             sum = r00 + r11;
         } else {
-            T r10 = residual(F, P + 1, i + 1, j);
-            T r01 = residual(F, P + F.nx, i, j + 1);
+            const T r10 = resid_at<T>(P + 1, i + 1, j, nx, nz, f, c0, c1, c2, c3, q, D, dp);
+            const T r01 = resid_at<T>(P + nx, i, j + 1, nx, nz, f, c0, c1, c2, c3, q, D, dp);
             sum = r00 + r10 + r01 + r11;
         }
         T fc = T(0.25) * sum;
-        if constexpr (Scaled<T>::value) { if (!coarsest) fc *= C.q[c]; }
-        C.f[c] = fc;
-        C.dp[c] = T(0);
+        if (scale) fc *= cq[c];
+        cf[c] = fc;
+        cdp[c] = T(0);
     }
-    __syncthreads();
+    G::sync();
 }
 
-template <typename T>
+template <typename T, typename G>
+__device__ __forceinline__ void resid_restrict(const Lv<T>& F, const Lv<T>& C, bool red_only, bool coarsest) {
+    restrict_cells<T, G>(F, C.nx, C.nc, C.mnx, red_only, Scaled<T>::value && !coarsest, F.f, F.c0, F.c1, F.c2,
+                         F.c3, F.q, F.D, F.dp, C.q, C.f, C.dp);
+}
+
+// piecewise-constant prolongation and correction: each coarse cell adds its
+// value to its own four children, so no two iterations touch one element
+template <typename T, typename G>
 __device__ __forceinline__ void prolong(const Lv<T>& F, const Lv<T>& C) {
-    for (int c = threadIdx.x; c < C.nc; c += blockDim.x) {
-        int J = fdiv(c, C.nx, C.mnx), I = c - J * C.nx;
-        T e = C.dp[c];
-        int P = (2 * J) * F.nx + 2 * I;
-        F.dp[P] += e; F.dp[P + 1] += e; F.dp[P + F.nx] += e; F.dp[P + F.nx + 1] += e;
+    const T* __restrict__ e = C.dp;
+    T* __restrict__ d = F.dp;
+    const int fx = F.nx;
+#pragma unroll 2
+    for (int c = G::rank(); c < C.nc; c += G::size()) {
+        const int J = fdiv(c, C.nx, C.mnx), I = c - J * C.nx;
+        const T v = e[c];
+        const int P = (2 * J) * fx + 2 * I;
+        d[P] += v; d[P + 1] += v; d[P + fx] += v; d[P + fx + 1] += v;
     }
-    __syncthreads();
+    G::sync();
 }
 
 // exact coarsest solve: Gaussian elimination of the assembled five-point
-// matrix by warp 0 in shared memory (symmetric, diagonally dominant)
+// matrix by one warp in shared memory (symmetric, diagonally dominant); run
+// by warp 0 only, synchronised with __syncwarp
 template <typename T>
-__device__ __forceinline__ void coarse_solve(int nx, int nz, const T* Tx, const T* Tz, const T* D,
-                                             const T* f, T* dp, T* A) {
-    if (threadIdx.x < 32) {
-        const int nn = nx * nz, ld = nn + 1, lane = threadIdx.x;
-        for (int r = lane; r < nn; r += 32) {
-            for (int c = 0; c < nn; ++c) A[r * ld + c] = T(0);
-            int j = r / nx, i = r - j * nx;
-            A[r * ld + r] = D[r];
-            if (i < nx - 1) A[r * ld + r + 1] = -Tx[r];
-            if (i > 0)      A[r * ld + r - 1] = -Tx[r - 1];
-            if (j < nz - 1) A[r * ld + r + nx] = -Tz[r];
-            if (j > 0)      A[r * ld + r - nx] = -Tz[r - nx];
-            A[r * ld + nn] = f[r];
-        }
-        __syncwarp();
-        for (int k = 0; k < nn; ++k) {
-            for (int r = k + 1 + lane; r < nn; r += 32) {
-                T m = A[r * ld + k] / A[k * ld + k];
-                for (int c = k; c <= nn; ++c) A[r * ld + c] -= m * A[k * ld + c];
-            }
-            __syncwarp();
-        }
-        if (lane == 0) {
-            for (int k = nn - 1; k >= 0; --k) {
-                T sum = A[k * ld + nn];
-                for (int c = k + 1; c < nn; ++c) sum -= A[k * ld + c] * A[c * ld + nn];
-                A[k * ld + nn] = sum / A[k * ld + k];
-            }
-        }
-        __syncwarp();
-        for (int r = lane; r < nn; r += 32) dp[r] = A[r * ld + nn];
+__device__ __forceinline__ void coarse_solve_warp(int nx, int nz, const T* Tx, const T* Tz, const T* D,
+                                                  const T* f, T* dp, T* A) {
+    const int nn = nx * nz, ld = nn + 1, lane = threadIdx.x & 31;
+    for (int r = lane; r < nn; r += 32) {
+        for (int c = 0; c < nn; ++c) A[r * ld + c] = T(0);
+        int j = r / nx, i = r - j * nx;
+        A[r * ld + r] = D[r];
+        if (i < nx - 1) A[r * ld + r + 1] = -Tx[r];
+        if (i > 0)      A[r * ld + r - 1] = -Tx[r - 1];
+        if (j < nz - 1) A[r * ld + r + nx] = -Tz[r];
+        if (j > 0)      A[r * ld + r - nx] = -Tz[r - nx];
+        A[r * ld + nn] = f[r];
     }
-    __syncthreads();
+    __syncwarp();
+    for (int k = 0; k < nn; ++k) {
+        for (int r = k + 1 + lane; r < nn; r += 32) {
+            T m = A[r * ld + k] / A[k * ld + k];
+            for (int c = k; c <= nn; ++c) A[r * ld + c] -= m * A[k * ld + c];
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        for (int k = nn - 1; k >= 0; --k) {
+            T sum = A[k * ld + nn];
+            for (int c = k + 1; c < nn; ++c) sum -= A[k * ld + c] * A[c * ld + nn];
+            A[k * ld + nn] = sum / A[k * ld + k];
+        }
+    }
+    __syncwarp();
+    for (int r = lane; r < nn; r += 32) dp[r] = A[r * ld + nn];
+    __syncwarp();
 }
 
-// f0: unscaled finest right-hand side, used by the direct solve when the
-// finest grid is also the coarsest (FP64 levels keep f/D otherwise)
 // exact solve on the coarsest level c (FP64 levels: the unscaled FP64
-// operator; f0 is the unscaled right-hand side when c is the finest level)
-template <typename T>
+// operator; f0 is the unscaled right-hand side when c is the finest level),
+// by warp 0; the CTA group waits for it at a barrier
+template <typename T, typename G>
 __device__ __forceinline__ void coarsest(const Lv<T>* L, const Lv64* L64, int c, T* A, const T* f0) {
-    if constexpr (Scaled<T>::value)
-        coarse_solve<T>(L64[c].nx, L64[c].nz, L64[c].Tx, L64[c].Tz, L64[c].D, c == 0 ? f0 : L[c].f,
-                        L[c].dp, A);
-    else
-        coarse_solve<T>(L[c].nx, L[c].nz, L[c].c0, L[c].c1, L[c].D, L[c].f, L[c].dp, A);
+    if (threadIdx.x < 32) {
+        if constexpr (Scaled<T>::value)
+            coarse_solve_warp<T>(L64[c].nx, L64[c].nz, L64[c].Tx, L64[c].Tz, L64[c].D, c == 0 ? f0 : L[c].f,
+                                 L[c].dp, A);
+        else
+            coarse_solve_warp<T>(L[c].nx, L[c].nz, L[c].c0, L[c].c1, L[c].D, L[c].f, L[c].dp, A);
+    }
+    if constexpr (std::is_same<G, GCta>::value) __syncthreads();
 }
 
-// one cycle of index gamma >= 2 (W-cycle for gamma = 2, the paper's cycle,
-// Sec. 4.2): every visit of level l < nlev-2 runs gamma cycles on level l+1,
-// the visit of nlev-2 one exact coarsest solve.  The recursion is unrolled
-// into a depth-first walk whose per-level visit counts sit in 4-bit fields of
-// one register (no device stack); called uniformly by the whole CTA.
-template <typename T>
-__device__ void gcycle(const Lv<T>* L, const Lv64* L64, int nlev, int nu1, int nu2, int gamma, T* A,
-                       const T* f0) {
+// One multigrid cycle rooted at level `root`: V-cycle for gamma = 1, else the
+// cycle of index gamma (W-cycle for gamma = 2, the paper's cycle, Sec. 4.2):
+// every visit of level l < nlev-2 runs gamma cycles on level l+1, the visit
+// of nlev-2 one exact coarsest solve.  The recursion is unrolled into a
+// depth-first walk whose per-level visit counts sit in 4-bit fields of one
+// register (no device stack).  Run by the CTA, each visit of level lw (the
+// first small level) is handed to warp 0 as a complete cycle rooted at lw.
+template <typename T, typename G>
+__device__ __forceinline__ void gwalk(const Lv<T>* L, const Lv64* L64, int root, int nlev, int lw, int nu1, int nu2, int gamma,
+                      T* A, const T* f0) {
     static_assert(RICH_MAX_LEVELS * 4 <= 64, "visit counters must fit one 64-bit word");
     unsigned long long cnt = 0;
-    int l = 0;
+    int l = root;
     for (;;) {
-        for (; l < nlev - 1; ++l) {                       // enter l: pre-smooth, restrict
-            for (int it = 0; it < nu1; ++it) { rbgs(L[l], 0); rbgs(L[l], 1); }
-            resid_restrict(L[l], L[l + 1], nu1 > 0, l + 1 == nlev - 1);
+        for (; l < nlev - 1 && l != lw; ++l) {            // enter l: pre-smooth, restrict
+            smooth<T, G>(L[l], nu1);
+            resid_restrict<T, G>(L[l], L[l + 1], nu1 > 0, l + 1 == nlev - 1);
             cnt &= ~(15ull << (4 * l));
         }
-        coarsest<T>(L, L64, nlev - 1, A, f0);
+        if constexpr (std::is_same<G, GCta>::value) {
+            if (l == lw && lw < nlev - 1) {
+                if (threadIdx.x < 32) gwalk<T, GWarp>(L, L64, lw, nlev, nlev, nu1, nu2, gamma, A, f0);
+                __syncthreads();
+            } else {
+                coarsest<T, G>(L, L64, nlev - 1, A, f0);
+            }
+        } else {
+            coarsest<T, G>(L, L64, nlev - 1, A, f0);
+        }
         for (;;) {                                        // leave l+1, back on l
-            if (--l < 0) return;
+            if (--l < root) return;
             cnt += 1ull << (4 * l);
             const int reps = (l + 1 == nlev - 1) ? 1 : gamma;
             if ((int)((cnt >> (4 * l)) & 15) < reps) { ++l; break; }   // cycle l+1 again
-            prolong(L[l], L[l + 1]);
-            for (int it = 0; it < nu2; ++it) { rbgs(L[l], 0); rbgs(L[l], 1); }
+            prolong<T, G>(L[l], L[l + 1]);
+            smooth<T, G>(L[l], nu2);
         }
     }
 }
 
+// V-cycle with the levels from lw down handed to warp 0 (lw = nlev: none)
 template <typename T>
-__device__ void vcycle(const Lv<T>* L, const Lv64* L64, int nlev, int nu1, int nu2, T* A,
+__device__ __forceinline__ void vcycle(const Lv<T>* L, const Lv64* L64, int nlev, int lw, int nu1, int nu2, T* A,
                        const T* f0) {
-    for (int l = 0; l < nlev - 1; ++l) {
-        for (int it = 0; it < nu1; ++it) { rbgs(L[l], 0); rbgs(L[l], 1); }
-        resid_restrict(L[l], L[l + 1], nu1 > 0, l + 1 == nlev - 1);
+    const int top = min(lw, nlev - 1);       // levels 0 .. top-1 run on the whole CTA
+    for (int l = 0; l < top; ++l) {
+        smooth<T, GCta>(L[l], nu1);
+        resid_restrict<T, GCta>(L[l], L[l + 1], nu1 > 0, l + 1 == nlev - 1);
     }
-    coarsest<T>(L, L64, nlev - 1, A, f0);
-    for (int l = nlev - 2; l >= 0; --l) {
-        prolong(L[l], L[l + 1]);
-        for (int it = 0; it < nu2; ++it) { rbgs(L[l], 0); rbgs(L[l], 1); }
+    if (lw < nlev - 1) {
+        if (threadIdx.x < 32) {
+            for (int l = lw; l < nlev - 1; ++l) {
+                smooth<T, GWarp>(L[l], nu1);
+                resid_restrict<T, GWarp>(L[l], L[l + 1], nu1 > 0, l + 1 == nlev - 1);
+            }
+            coarsest<T, GWarp>(L, L64, nlev - 1, A, f0);
+            for (int l = nlev - 2; l >= lw; --l) {
+                prolong<T, GWarp>(L[l], L[l + 1]);
+                smooth<T, GWarp>(L[l], nu2);
+            }
+        }
+        __syncthreads();
+    } else {
+        coarsest<T, GCta>(L, L64, nlev - 1, A, f0);
+    }
+    for (int l = top - 1; l >= 0; --l) {
+        prolong<T, GCta>(L[l], L[l + 1]);
+        smooth<T, GCta>(L[l], nu2);
     }
 }
 
@@ -358,18 +465,22 @@ template <typename T>
 __device__ __forceinline__ unsigned long long resid_norm(const Lv<T>& L, bool red_only,
                                                          unsigned long long* red) {
     unsigned long long m = 0;
+    const int nx = L.nx, nz = L.nz;
     if (red_only) {
         const int n = L.hx * L.nz;
+#pragma unroll 2
         for (int c = threadIdx.x; c < n; c += blockDim.x) {
-            int j = fdiv(c, L.hx, L.mhx);
-            int i = 2 * (c - j * L.hx) + (j & 1);
-            unsigned long long b = abs_bits((double)residual(L, j * L.nx + i, i, j));
+            const int j = fdiv(c, L.hx, L.mhx);
+            const int i = 2 * (c - j * L.hx) + (j & 1);
+            const unsigned long long b = abs_bits(
+                (double)resid_at<T>(j * nx + i, i, j, nx, nz, L.f, L.c0, L.c1, L.c2, L.c3, L.q, L.D, L.dp));
             m = b > m ? b : m;
         }
     } else {
-        for (int q = threadIdx.x; q < L.nc; q += blockDim.x) {
-            int j = fdiv(q, L.nx, L.mnx), i = q - j * L.nx;
-            unsigned long long b = abs_bits((double)residual(L, q, i, j));
+        for (int c = threadIdx.x; c < L.nc; c += blockDim.x) {
+            const int j = fdiv(c, L.nx, L.mnx), i = c - j * L.nx;
+            const unsigned long long b = abs_bits(
+                (double)resid_at<T>(c, i, j, nx, nz, L.f, L.c0, L.c1, L.c2, L.c3, L.q, L.D, L.dp));
             m = b > m ? b : m;
         }
     }
@@ -606,20 +717,42 @@ struct Cta {
     // instantiation so the V kernels keep their register allocation) the
     // cycle of index P.gamma
     __device__ void mgcycle(const TM* f0) {
-        if constexpr (WC) gcycle<TM>(LM, L64, nlev, P.nu1, P.nu2, P.gamma, Amat, f0);
-        else vcycle<TM>(LM, L64, nlev, P.nu1, P.nu2, Amat, f0);
+        if constexpr (WC) gwalk<TM, GCta>(LM, L64, 0, nlev, P.lw, P.nu1, P.nu2, P.gamma, Amat, f0);
+        else vcycle<TM>(LM, L64, nlev, P.lw, P.nu1, P.nu2, Amat, f0);
     }
 
-    // FP64 residual f - A x of the finest operator at cell q
-    __device__ __forceinline__ double resid64(const double* f, const double* x, int q) const {
-        const Lv64& F = L64[0];
-        int j = fdiv(q, nx, F.mnx), i = q - j * nx;
-        double sn = 0.0;
-        if (i < nx - 1) sn += F.Tx[q] * x[q + 1];
-        if (i > 0)      sn += F.Tx[q - 1] * x[q - 1];
-        if (j < nz - 1) sn += F.Tz[q] * x[q + nx];
-        if (j > 0)      sn += F.Tz[q - nx] * x[q - nx];
-        return f[q] - (F.D[q] * x[q] - sn);
+    // x += e (FP64 += FP32 correction), then the CTA synchronises
+    __device__ __forceinline__ void add_correction(double* __restrict__ x, const TM* __restrict__ e) const {
+#pragma unroll 4
+        for (int q = tid; q < nc; q += nt) x[q] += (double)e[q];
+        __syncthreads();
+    }
+
+    // FP64 defect r = f - A x of the finest operator, stored as the next FP32
+    // right-hand side rf (with the FP32 correction ef cleared); returns this
+    // thread's max |r| as a bit pattern (distinct arrays: restrict views)
+    __device__ __forceinline__ unsigned long long defect(const double* __restrict__ f, const double* __restrict__ x,
+                                                         const double* __restrict__ Tx,
+                                                         const double* __restrict__ Tz,
+                                                         const double* __restrict__ D, TM* __restrict__ rf,
+                                                         TM* __restrict__ ef) const {
+        const unsigned mnx = L64[0].mnx;
+        unsigned long long mm = 0;
+#pragma unroll 2
+        for (int q = tid; q < nc; q += nt) {
+            const int j = fdiv(q, nx, mnx), i = q - j * nx;
+            double sn = 0.0;
+            if (i < nx - 1) sn += Tx[q] * x[q + 1];
+            if (i > 0)      sn += Tx[q - 1] * x[q - 1];
+            if (j < nz - 1) sn += Tz[q] * x[q + nx];
+            if (j > 0)      sn += Tz[q - nx] * x[q - nx];
+            const double r = f[q] - (D[q] * x[q] - sn);
+            rf[q] = (TM)r;
+            ef[q] = TM(0);
+            const unsigned long long b = abs_bits(r);
+            mm = b > mm ? b : mm;
+        }
+        return mm;
     }
 
     // multigrid solve of A dp = f from dp = 0 (set up by assemble()); stops
@@ -644,17 +777,8 @@ struct Cta {
                 }
                 // dp += e in FP64, then the FP64 defect: stopping norm and the
                 // next FP32 right-hand side
-                unsigned long long mm = 0;
-                for (int q = tid; q < nc; q += nt) dp64[q] += (double)M0.dp[q];
-                __syncthreads();
-                for (int q = tid; q < nc; q += nt) {
-                    double r = resid64(f64, dp64, q);
-                    M0.f[q] = (TM)r;
-                    M0.dp[q] = TM(0);
-                    unsigned long long b = abs_bits(r);
-                    mm = b > mm ? b : mm;
-                }
-                rb = block_max(mm, red);
+                add_correction(dp64, M0.dp);
+                rb = block_max(defect(f64, dp64, L64[0].Tx, L64[0].Tz, L64[0].D, M0.f, M0.dp), red);
             }
             if (rb > INF_BITS - 1) { mg_tot += cyc; return false; }
             rn = __longlong_as_double((long long)rb);
@@ -831,11 +955,14 @@ __device__ __forceinline__ void init_levels(const FParams& P, char* slot, unsign
         Lv64& a = L64[l];
         a.nx = P.nx[l]; a.nz = P.nz[l]; a.nc = a.nx * a.nz; a.mnx = P.mnx[l];
         double** pp[N64] = {&a.Tx, &a.Tz, &a.Cdt, &a.D, &a.Tbt, &a.Tbb};
-        for (int k = 0; k < N64; ++k) *pp[k] = (double*)(slot + P.o64[l][k]);
+        for (int k = 0; k < N64; ++k)
+            *pp[k] = P.s64[l][k] >= 0 ? (double*)(sm + P.s64[l][k]) : (double*)(slot + P.o64[l][k]);
         Lv<TM>& b = LM[l];
         b.nx = a.nx; b.nz = a.nz; b.hx = a.nx >> 1; b.nc = a.nc; b.mnx = P.mnx[l]; b.mhx = P.mhx[l];
         TM** qq[NMG] = {&b.c0, &b.c1, &b.c2, &b.c3, &b.q, &b.f, &b.dp};
-        for (int k = 0; k < NMG; ++k) *qq[k] = P.omg[l][k] >= 0 ? (TM*)(slot + P.omg[l][k]) : nullptr;
+        for (int k = 0; k < NMG; ++k)
+            *qq[k] = P.smg[l][k] >= 0 ? (TM*)(sm + P.smg[l][k])
+                   : P.omg[l][k] >= 0 ? (TM*)(slot + P.omg[l][k]) : nullptr;
         if (P.osm[l] >= 0) b.dp = (TM*)(sm + P.osm[l]);   // corrections of small levels on chip
         if constexpr (SC) b.D = (TM*)a.D;                 // FP64: shares the operator diagonal
         else { b.D = b.c3; b.c3 = nullptr; }              // FP32: its own copy
@@ -844,7 +971,7 @@ __device__ __forceinline__ void init_levels(const FParams& P, char* slot, unsign
 }
 
 template <typename TM, int NT, bool WC, int CL>
-__global__ void __launch_bounds__(NT, NT <= 256 ? 4 : 1)
+__global__ void __launch_bounds__(NT, NT <= 256 ? 4 : NT == 512 ? 2 : 1)
 k_fused(const FParams P) {
     extern __shared__ unsigned char smraw[];
     __shared__ unsigned long long red[33];
@@ -861,6 +988,7 @@ k_fused(const FParams P) {
         const int s = s_sample;
         __syncthreads();
         if (s >= P.S) break;
+        const unsigned long long t0 = globaltimer_ns();
         C.setup(s);
         int status = RICH_OK, maxpic = 0;
         bool alive = true;
@@ -875,6 +1003,7 @@ k_fused(const FParams P) {
                 if (P.pic_total) P.pic_total[s] = pic_tot;
                 if (P.mg_total) P.mg_total[s] = mg_tot;
                 if (P.maxpic) P.maxpic[s] = maxpic;
+                if (P.t_ns) P.t_ns[s] = (int64_t)(globaltimer_ns() - t0);
             }
         }
         if (P.p_final)

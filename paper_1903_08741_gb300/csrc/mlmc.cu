@@ -80,7 +80,7 @@ struct MlmcRun {
     DevBuf lkf, alf, lkc, alc, qf, qc, sf, sc, acc;
     DevBuf nf, tsf, trf, ncb, tsc, trc;     // van Genuchten: n, theta_s, theta_r (fine, coarse)
     bool vg = false, thetas = false;
-    std::vector<double> t_pair, t_fine;
+    std::vector<double> t_pair, t_fine, t_sm;   // wall time; GPU-seconds at full occupancy
     std::vector<long long> n_done;
     int worst = 0;
     // grid-only bias pairs: both members of the finest pair with the original
@@ -93,7 +93,7 @@ struct MlmcRun {
         NL = g->nlevels; L = NL - 1; nL = g->n0 << L;
         vg = g->base.closure == RICH_VAN_GENUCHTEN;
         thetas = vg && g->with_thetas;
-        t_pair.assign(NL, 0.0); t_fine.assign(NL, 0.0); n_done.assign(NL, 0);
+        t_pair.assign(NL, 0.0); t_fine.assign(NL, 0.0); t_sm.assign(NL, 0.0); n_done.assign(NL, 0);
     }
     ~MlmcRun() {
         for (auto& e : ev) if (e) cudaEventDestroy(e);
@@ -215,12 +215,14 @@ struct MlmcRun {
                                    nullptr, (int32_t*)sf.p, nullptr, st, vg ? &in_f : nullptr);
         if (rc < 0) return rc;
         worst = rich_status_worse(worst, rc);
+        double sm_s = ctx->last_sm_seconds;
         RICH_CUDA(cudaEventRecord(ev[2], st));
         if (l > 0) {
             rc = rich_solve_device(ctx, &pc, nb, (double*)lkc.p, (double*)alc.p, ascale(l - 1), (double*)qc.p,
                                    nullptr, (int32_t*)sc.p, nullptr, st, vg ? &in_c : nullptr);
             if (rc < 0) return rc;
             worst = rich_status_worse(worst, rc);
+            sm_s += ctx->last_sm_seconds;
         }
         e = rich_mlmc_accumulate(ctx, (double*)qf.p, l > 0 ? (double*)qc.p : nullptr, (int32_t*)sf.p,
                                  l > 0 ? (int32_t*)sc.p : nullptr, nb,
@@ -233,6 +235,7 @@ struct MlmcRun {
         RICH_CUDA(cudaEventElapsedTime(&b, ev[1], ev[2]));
         RICH_CUDA(cudaEventElapsedTime(&c, ev[2], ev[3]));
         if (bias_mode) return 0;
+        t_sm[l] += 1e-3 * a + sm_s / std::max(ctx->sm_count, 1);
         t_pair[l] += 1e-3 * (a + b + c);
         t_fine[l] += 1e-3 * (a + b);      // one draw + one fine solve (plain MC sample)
         return 0;
@@ -246,7 +249,7 @@ struct MlmcRun {
         RICH_CUDA(cudaStreamSynchronize(st));
         rich_mlmc_result_t r{};
         r.nlevels = NL;
-        double rmse2 = 0, ssum = 0;
+        double rmse2 = 0, ssum = 0, ssum_sm = 0;
         for (int l = 0; l < NL; ++l) {
             const double* a = &h[8 * l];
             const double n = a[2];
@@ -260,16 +263,19 @@ struct MlmcRun {
             if (l > 0) mv(a[6], a[7], &r.mean_c[l], &r.var_c[l]);
             r.cost[l] = n_done[l] > 0 ? t_pair[l] / n_done[l] : NAN;
             r.cost_fine[l] = n_done[l] > 0 ? t_fine[l] / n_done[l] : NAN;
+            r.cost_sm[l] = n_done[l] > 0 ? t_sm[l] / n_done[l] : NAN;
             r.estimate += r.mean[l];
             rmse2 += r.var[l] / n;
             r.ml_variance += r.var_f[l] - (l > 0 ? r.var_c[l] : 0.0);
             ssum += sqrt(std::max(r.var[l], 0.0) * r.cost[l]);
+            ssum_sm += sqrt(std::max(r.var[l], 0.0) * r.cost_sm[l]);
         }
         r.rmse = sqrt(rmse2);
         if (cfg->eps > 0) {
             const double e2 = cfg->eps * cfg->eps;
             for (int l = 0; l < NL; ++l) r.n_opt[l] = ssum * sqrt(std::max(r.var[l], 0.0) / r.cost[l]) / e2;
             r.w_eps = ssum * ssum / e2;
+            r.w_eps_sm = ssum_sm * ssum_sm / e2;
             r.w_mc_eps = r.var_f[L] * r.cost_fine[L] / e2;
         }
         r.bias_estimate = L > 0 ? fabs(r.mean[L]) / (2.0 - 1.0) : NAN;

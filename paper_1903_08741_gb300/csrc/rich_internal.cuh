@@ -31,7 +31,9 @@ struct rich_samplebuf {
     int cap = 0;
     int32_t *status = nullptr, *maxpic = nullptr;
     int64_t *pic_total = nullptr, *mg_total = nullptr;
+    int64_t* t_ns = nullptr;                    // per-sample solve time on its CTA
     int last = 0;                               // samples of the last fused solve
+    int last_occ = 1;                           // resident CTAs per SM of the last fused launch
 };
 
 // sqrt of the circulant covariance spectrum on one torus (+ FFT twiddles)
@@ -68,6 +70,7 @@ struct rich_ctx {
     size_t stage_bytes = 0;
     int tune_threads = 0;                       // fused-kernel block size (0: default 512)
     int tune_mixed_inner = 0;                   // FP32 V-cycles per FP64 defect (0: default 2)
+    double last_sm_seconds = 0;                 // SM-seconds of the last rich_solve_device
 };
 
 void rich_count_launch();

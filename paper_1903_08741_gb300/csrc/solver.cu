@@ -29,11 +29,12 @@ int rich_samples_reserve(rich_ctx* ctx, int S) {
     const size_t o_mx = off; off = al256(off + 4 * n);
     const size_t o_pt = off; off = al256(off + 8 * n);
     const size_t o_mt = off; off = al256(off + 8 * n);
+    const size_t o_tn = off; off = al256(off + 8 * n);
     cudaError_t e = cudaMalloc(&b.base, off);
     if (e != cudaSuccess) { cudaGetLastError(); b.base = nullptr; return RICH_ERR_OOM; }
     char* c = (char*)b.base;
     b.status = (int32_t*)(c + o_st); b.maxpic = (int32_t*)(c + o_mx);
-    b.pic_total = (int64_t*)(c + o_pt); b.mg_total = (int64_t*)(c + o_mt);
+    b.pic_total = (int64_t*)(c + o_pt); b.mg_total = (int64_t*)(c + o_mt); b.t_ns = (int64_t*)(c + o_tn);
     b.cap = (int)n;
     return 0;
 }
@@ -58,7 +59,8 @@ int rich_solve_device(rich_ctx* ctx, const rich_problem_t* pb, int S, const doub
         return e;
     rich_samplebuf& b = ctx->sb;
     std::vector<int32_t> hs(S), hmax(S);
-    std::vector<int64_t> hp(S), hm(S);
+    std::vector<int64_t> hp(S), hm(S), ht(S);
+    RICH_CUDA(cudaMemcpyAsync(ht.data(), b.t_ns, 8 * (size_t)S, cudaMemcpyDeviceToHost, st));
     RICH_CUDA(cudaMemcpyAsync(hs.data(), b.status, 4 * (size_t)S, cudaMemcpyDeviceToHost, st));
     RICH_CUDA(cudaMemcpyAsync(hmax.data(), b.maxpic, 4 * (size_t)S, cudaMemcpyDeviceToHost, st));
     RICH_CUDA(cudaMemcpyAsync(hp.data(), b.pic_total, 8 * (size_t)S, cudaMemcpyDeviceToHost, st));
@@ -66,6 +68,11 @@ int rich_solve_device(rich_ctx* ctx, const rich_problem_t* pb, int S, const doub
     RICH_CUDA(cudaStreamSynchronize(st));
     int worst = 0;
     rich_stats_t acc{};
+    double cta_ns = 0;
+    for (int s = 0; s < S; ++s) cta_ns += (double)ht[s];
+    // SM-seconds: each sample held 1/occ of an SM for its solve time
+    ctx->last_sm_seconds = 1e-9 * cta_ns / std::max(b.last_occ, 1);
+    acc.sm_seconds = ctx->last_sm_seconds;
     for (int s = 0; s < S; ++s) {
         worst = rich_status_worse(worst, (int)hs[s]);
         acc.picard_iters += hp[s];

@@ -46,6 +46,11 @@ def test_mlmc_matches_oracle(R, coupling):
     s = sum(np.sqrt(v * c) for v, c in zip(g["var"], g["cost"]))
     assert rel(g["w_eps"], s * s / 1e-6) < 1e-12
     assert all(c > 0 for c in g["cost"])
+    # full-occupancy cost: the solves' SM-seconds spread over the GPU; these
+    # small batches leave most SMs idle, so it is below the wall-clock cost
+    assert all(0 < cs <= 1.05 * c for cs, c in zip(g["cost_sm"], g["cost"]))
+    s_sm = sum(np.sqrt(v * c) for v, c in zip(g["var"], g["cost_sm"]))
+    assert rel(g["w_eps_sm"], s_sm * s_sm / 1e-6) < 1e-12
 
 
 def close(a, b, tol):

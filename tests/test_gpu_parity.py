@@ -155,6 +155,9 @@ def test_solve_mc32_full(R):
     """The 32^2 x 64-sample, 10-step workload, every sample and cell."""
     q, q_o, s, st, st_o = compare(R, 32, 32, 64, 10, 0.01)
     assert (s == 0).sum() > 32
+    # SM-seconds of the solves: positive, and no more than the call's wall
+    # time times the SMs in use
+    assert 0 < st.sm_seconds <= st.seconds * torch.cuda.get_device_properties(0).multi_processor_count
 
 
 @pytest.mark.parametrize("nx,nz,S,steps", [(48, 32, 5, 3), (24, 40, 3, 2), (8, 8, 7, 4), (3, 3, 2, 2),
