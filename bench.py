@@ -765,7 +765,13 @@ def run_ours(args):
     prec = R.MIXED if args.precision == "mixed" else R.FP64
     pb = R.Problem(nx=n, nz=n, nsteps=steps, dt=dt, precision=prec, cycle=args.cycle, **PHYS)
     from paper_1903_08741_gb300 import autotune
-    block_threads, mixed_inner = autotune.tune(pb, S, device=local)
+    if args.launch:
+        block_threads, mixed_inner = (int(x) for x in args.launch.split("/"))
+        R.set_tuning(block_threads, mixed_inner, local)
+        launch_from = "--launch"
+    else:
+        launch_from = "autotuner (" + autotune.source(pb, S, local) + ")"
+        block_threads, mixed_inner = autotune.tune(pb, S, device=local)
     model = R.FieldModel(seed=0, **FIELDS[args.field])
     lk = torch.empty((S, n, n), dtype=torch.float64, device=dev)
     al = torch.empty_like(lk)
@@ -898,7 +904,7 @@ def run_ours(args):
                                f"{'FP64' if prec == R.FP64 else 'FP32 V-cycles in FP64 defect correction'}"
                                + workload_suffix(args),
                    "global_batch": S * ws, "grid": [n, n], "time_steps": steps,
-                   "launch": {"block_threads": block_threads, "mixed_inner": mixed_inner, "from": "autotuner"},
+                   "launch": {"block_threads": block_threads, "mixed_inner": mixed_inner, "from": launch_from},
                    "l2": "inputs larger than L2 (2 x %.0f MB fields per step, fresh samples each step)"
                          % (S * n * n * 8 / 1e6)},
         "clocks": clk, "gpu_launches": launches, "roofline": roof,
@@ -955,6 +961,8 @@ def main():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--launch", default="", help="mc workloads: launch shape block_threads/mixed_inner "
+                                                 "(e.g. 512/4) instead of the autotuner's")
     ap.add_argument("--no-extras", action="store_true",
                     help="default workload: skip the mixed-precision, MLMC and batch-1 measurements")
     ap.add_argument("--bias-pairs", type=int, default=0, help="mlmc5: grid-only bias pairs (Eq. discErr)")

@@ -369,9 +369,10 @@ int rich_kl_fields(rich_ctx_t ctx, const double* kl_basis, int32_t n_kl, int32_t
  *   J_N^T lam_N = dQ/dp^N,  J_n^T lam_n = diag(C(p^n)/dt) lam_{n+1},
  *   dQ/dm = dQ/dm|explicit - sum_n (dR_n/dm)^T lam_n,  dQ/dxi_j = <basis_j, dQ/dm>,
  * J_n the full Newton Jacobian (K'(p) inside the harmonic means included).
- * J^T systems are solved by defect correction preconditioned with CCMG V-cycles
- * of the Picard operator (FP32 V-cycles when pb->precision is RICH_MIXED) to a
- * relative residual of 1e-11.  Memory: the states are checkpointed every
+ * J^T systems are solved by BiCGStab (or defect correction, see
+ * rich_set_adjoint_method) preconditioned with CCMG V-cycles of the Picard
+ * operator (FP32 V-cycles when pb->precision is RICH_MIXED) to a relative
+ * residual of 1e-11.  Memory: the states are checkpointed every
  * ckpt_every steps and each segment is recomputed during the reverse sweep.
  * dq_dlnKs [S][nz][nx] (device) may be NULL.  A J^T solve that stops at its
  * iteration limit sets RICH_MG_MAXIT.  Synchronous (returns when done). */
@@ -380,6 +381,14 @@ int rich_solve_batch_adjoint(rich_ctx_t ctx, const rich_problem_t* pb, int32_t n
                              const double* alpha, double alpha_scale, int32_t ckpt_every,
                              double* qoi, double* dq_dxi, double* dq_dlnKs, int32_t* status,
                              rich_stats_t* stats, void* stream);
+
+/* Solver of the adjoint's J^T systems in this context's rich_solve_batch_adjoint
+ * calls: 1 (default) BiCGStab (van der Vorst 1992) right-preconditioned with
+ * the CCMG cycles of the Picard operator, stopped on the true residual; 0 the
+ * plain defect correction lam += M^{-1}(rhs - J^T lam).  Both stop at a relative
+ * residual of 1e-11 or 400 preconditioner applications (then RICH_MG_MAXIT);
+ * rich_stats_t.mg_cycles counts the applications.  RICH_ERR_INVALID otherwise. */
+int rich_set_adjoint_method(rich_ctx_t ctx, int32_t method);
 
 /* Allocation-free solve.  The paper has no counterpart: this entry point exists
  * for callers that cannot call cudaMalloc -- code embedded in a host framework

@@ -284,6 +284,7 @@ def lib():
         L.rich_mlmc_estimate.argtypes = [vp, C.POINTER(_MlmcCfg), C.POINTER(_MlmcResult)]
         L.rich_mlmc_adaptive.argtypes = [vp, C.POINTER(_MlmcCfg), i32, vp, C.POINTER(_MlmcResult)]
         L.rich_measure_fp64.argtypes = [vp, C.POINTER(_Fp64Rates)]
+        L.rich_set_adjoint_method.argtypes = [vp, i32]
         _lib = L
     return _lib
 
@@ -295,7 +296,8 @@ def exported_symbols():
             "rich_solve_batch_noalloc", "rich_mlmc_estimate", "rich_sample_fields_pair",
             "rich_kl_fields", "rich_solve_batch_adjoint", "rich_set_tuning", "rich_sample_fields_at",
             "rich_solve_batch_async", "rich_mlmc_adaptive", "rich_sample_soil", "rich_solve_soil",
-            "rich_sample_soil_pair", "rich_sample_counters", "rich_measure_fp64"]
+            "rich_sample_soil_pair", "rich_sample_counters", "rich_measure_fp64",
+            "rich_set_adjoint_method"]
 
 
 def _check(rc):
@@ -513,6 +515,14 @@ def profile_read(device=0):
     ms, n, b, f = C.c_double(), C.c_int64(), C.c_double(), C.c_double()
     _check(lib().rich_profile_read(context(device), C.byref(ms), C.byref(n), C.byref(b), C.byref(f)))
     return ms.value, n.value, b.value, f.value
+
+
+BICGSTAB, DEFECT_CORRECTION = 1, 0
+
+
+def set_adjoint_method(method=BICGSTAB, device=0):
+    """J^T solver of the device's adjoint solves: BICGSTAB (default) or DEFECT_CORRECTION."""
+    _check(lib().rich_set_adjoint_method(context(device), method))
 
 
 def measure_fp64(device=0):

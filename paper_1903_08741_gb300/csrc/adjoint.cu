@@ -79,9 +79,9 @@ extern "C" int rich_solve_batch_adjoint(rich_ctx_t ctx, const rich_problem_t* pb
     if (int e = rich_kl_fields(ctx, kl_basis, n_kl, nc, xi, nsamples, lk, stream)) return e;
     if (int e = rich_samples_reserve(ctx, nsamples)) return e;
     auto t0 = std::chrono::steady_clock::now();
-    // adjoint linear solves to 1e-11 relative, at most 200 outer iterations
-    if (int e = rich_adjoint_fused(ctx, pb, nsamples, lk, alpha, alpha_scale, ckpt_every, 1e-11, 200,
-                                   qoi, g, st))
+    // adjoint linear solves to 1e-11 relative, at most 400 preconditioner applications
+    if (int e = rich_adjoint_fused(ctx, pb, nsamples, lk, alpha, alpha_scale, ckpt_every, 1e-11, 400,
+                                   ctx->adj_method, qoi, g, st))
         return e;
     dim3 grid(n_kl, nsamples);
     rich_count_launch();
@@ -102,11 +102,17 @@ extern "C" int rich_solve_batch_adjoint(rich_ctx_t ctx, const rich_problem_t* pb
     for (int s = 0; s < nsamples; ++s) {
         worst = rich_status_worse(worst, (int)hs[s]);
         acc.picard_iters += hp[s];
-        acc.mg_cycles += hm[s];          // adjoint: outer defect-correction iterations
+        acc.mg_cycles += hm[s];          // adjoint: preconditioner applications of the J^T solves
         acc.max_picard = std::max(acc.max_picard, hmax[s]);
         if (hs[s] == RICH_PICARD_MAXIT || hs[s] == RICH_NONFINITE) acc.failed++;
     }
     acc.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (stats) *stats = acc;
     return worst;
+}
+
+extern "C" int rich_set_adjoint_method(rich_ctx_t ctx, int32_t method) {
+    if (!ctx || method < 0 || method > 1) return RICH_ERR_INVALID;
+    ctx->adj_method = method;
+    return 0;
 }

@@ -15,7 +15,7 @@ size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 // Dynamic shared memory of a CTA (no device work): the coarsest level's dense
 // matrix; then the arrays that the cycles read on the small coarse levels
 // that warp 0 runs alone (levels l >= 1 with at most WARP_CELLS cells: the
-// multigrid arrays, and for FP64 the diagonal and the coarsest level's faces,
+// multigrid arrays, and for FP64 the coarsest level's faces and diagonal,
 // which the direct solve assembles); then the corrections dp of as many of the other levels
 // (coarsest first) as fit the budget of the launch shape (one 1024-thread CTA
 // per SM may use ~220 KB, two 512-thread CTAs ~104 KB each, four 256-thread
@@ -43,7 +43,7 @@ static void plan_smem(FParams& P, int nt) {
         const size_t nc = (size_t)P.nx[l] * P.nz[l];
         if (!P.mixed) {
             for (int k = 0; k < N64; ++k) {
-                if (k != A_D && !(l == c && (k == A_TX || k == A_TZ))) continue;
+                if (!(l == c && (k == A_TX || k == A_TZ || k == A_D))) continue;
                 P.s64[l][k] = (long long)off;
                 off = al16(off + nc * 8);
             }
@@ -82,8 +82,8 @@ static int fused_setup(const rich_problem_t* pb, int S, FParams& P, int ckpt_eve
             P.o64[l][k] = (long long)off; off = al256(off + bytes);
         }
         for (int k = 0; k < NMG; ++k) {
-            // FP64: wE wW wN wS q f dp ; FP32: Tx Tz - D q f dp (slot B_2 unused)
-            if (mixed && k == B_2) { P.omg[l][k] = -1; continue; }
+            // FP64: wE wW wN wS q f dp D ; FP32: Tx Tz - D q f dp - (slots B_2, B_7 unused)
+            if (mixed && (k == B_2 || k == B_7)) { P.omg[l][k] = -1; continue; }
             P.omg[l][k] = (long long)off; off = al256(off + nc * w);
         }
         lx /= 2; lz /= 2;
@@ -109,7 +109,8 @@ static int fused_setup(const rich_problem_t* pb, int S, FParams& P, int ckpt_eve
         P.ckpt_every = ckpt_every;
         P.o_ckpt = off; off = al256(off + nc8 * std::max(nck, 1));
         P.o_seg = off; off = al256(off + nc8 * ckpt_every);
-        long long* adj[] = {&P.o_lam, &P.o_rhs, &P.o_r, &P.o_dE, &P.o_dW, &P.o_dN, &P.o_dS, &P.o_dg, &P.o_g};
+        long long* adj[] = {&P.o_lam, &P.o_rhs, &P.o_r, &P.o_dE, &P.o_dW, &P.o_dN, &P.o_dS, &P.o_dg, &P.o_g,
+                            &P.o_rh, &P.o_pk, &P.o_v, &P.o_t, &P.o_ph, &P.o_sh};
         for (long long* o : adj) { *o = (long long)off; off = al256(off + nc8); }
     }
     P.slot_bytes = (long long)off;
@@ -218,13 +219,14 @@ int rich_solve_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const doubl
 // Discrete adjoint of S samples: QoI and dQ/d ln Ks [S][nz][nx] (g_out).
 int rich_adjoint_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const double* lnKs,
                        const double* alpha, double alpha_scale, int ckpt_every, double adj_tol,
-                       int adj_maxit, double* qoi, double* g_out, cudaStream_t st) {
+                       int adj_maxit, int adj_method, double* qoi, double* g_out, cudaStream_t st) {
     rich_samplebuf& w = ctx->sb;
     FParams P;
     if (ckpt_every < 1 || pb->closure != RICH_GARDNER) return RICH_ERR_INVALID;
     if (int e = fused_setup(pb, S, P, ckpt_every)) return e;
     plan_smem(P, 512);
     P.adj_tol = adj_tol; P.adj_maxit = adj_maxit; P.adj_inner = pb->precision == RICH_MIXED ? 2 : 1;
+    P.adj_method = adj_method;
     P.mixed_inner = ctx->tune_mixed_inner > 0 ? ctx->tune_mixed_inner : MIXED_INNER_DEFAULT;
     const size_t smem = fused_smem(P);
     int occ = 0;

@@ -50,9 +50,9 @@ constexpr int MIXED_INNER_DEFAULT = 2;   // FP32 V-cycles per FP64 defect evalua
 
 // FP64 unscaled operator (all levels): faces, mass term, diagonal, Dirichlet faces
 enum { A_TX, A_TZ, A_CDT, A_D, A_TBT, A_TBB, N64 };
-// multigrid arrays in the cycle precision.  FP64: wE wW wN wS q=1/D fh dp
-// (D shared with the FP64 operator).  FP32: Tx Tz D 1/D f dp.
-enum { B_0, B_1, B_2, B_3, B_4, B_5, B_6, NMG };
+// multigrid arrays in the cycle precision, colour-split on every level but
+// the coarsest.  FP64: wE wW wN wS q=1/D fh dp D.  FP32: Tx Tz - D 1/D f dp -.
+enum { B_0, B_1, B_2, B_3, B_4, B_5, B_6, B_7, NMG };
 
 struct FParams {
     int S, nlev, mixed;
@@ -87,6 +87,8 @@ struct FParams {
     int ckpt_every, adj_maxit, adj_inner;
     double adj_tol;
     long long o_ckpt, o_seg, o_lam, o_rhs, o_r, o_dE, o_dW, o_dN, o_dS, o_dg, o_g;
+    int adj_method;             // J^T solver: 0 defect correction, 1 BiCGStab
+    long long o_rh, o_pk, o_v, o_t, o_ph, o_sh;   // BiCGStab vectors
     double* g_out;
     // closure 1 (van Genuchten-Mualem): per-cell n, theta_s, theta_r inputs
     // (theta arrays may be null: the problem's constants), continuation
@@ -151,6 +153,26 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
     return v;
 }
 
+// block-wide sum of v in a fixed order (warp trees, then the warp partials in
+// warp order), returned to every thread
+__device__ __forceinline__ double block_sum(double v, double* red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < nw ? red[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[32] = v;
+    }
+    __syncthreads();
+    const double r = red[32];
+    __syncthreads();
+    return r;
+}
+
 // block-wide max of v, returned to every thread
 __device__ __forceinline__ unsigned long long block_max(unsigned long long v, unsigned long long* red) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -177,12 +199,38 @@ struct Lv64 {
 // multigrid level in cycle precision T.  FP64 (scaled): c = {wE, wW, wN, wS},
 // q = 1/D, f = f/D (the coarsest level keeps f unscaled for the direct solve).
 // FP32 (unscaled): c = {Tx, Tz, -, -}, q = 1/D, f = f.
+// Layout: every level that is smoothed stores its cells colour-split, the red
+// cells ((i + j) even) first and then the black ones, each half row-major with
+// hx = nx/2 cells per row: cell (i, j) sits at ((i + j) & 1) H + j hx + i/2
+// (H = hx nz).  A half-sweep then reads its own cells, and the neighbours of
+// the other colour, at unit stride (no shared-memory bank conflicts, full
+// sectors from L2).  The coarsest level (direct solve; its sides may be odd)
+// keeps the natural row-major order (H = 0).
 template <typename T>
 struct Lv {
-    int nx, nz, hx, nc;
+    int nx, nz, hx, nc, H;
     unsigned mnx, mhx;
     T *c0, *c1, *c2, *c3, *D, *q, *f, *dp;
 };
+
+// storage index of cell (i, j) on a level
+template <typename T>
+__device__ __forceinline__ int sidx(const Lv<T>& L, int i, int j) {
+    return L.H ? ((i + j) & 1) * L.H + j * L.hx + (i >> 1) : j * L.nx + i;
+}
+
+// storage indices of cell (i, j) and of its east, west, north and south
+// neighbours (valid where the neighbour exists)
+struct Nb { int own, e, w, n, s; };
+template <typename T>
+__device__ __forceinline__ Nb nb_of(const Lv<T>& L, int i, int j) {
+    if (L.H) {
+        const int col = (i + j) & 1, c = j * L.hx + (i >> 1), oth = (1 - col) * L.H + c;
+        return Nb{col * L.H + c, oth + (i & 1), oth - 1 + (i & 1), oth + L.hx, oth - L.hx};
+    }
+    const int P = j * L.nx + i;
+    return Nb{P, P + 1, P - 1, P + L.nx, P - L.nx};
+}
 
 template <typename T> struct Scaled { static constexpr bool value = sizeof(T) == 8; };
 
@@ -202,77 +250,86 @@ struct GWarp {
     static __device__ __forceinline__ void sync() { __syncwarp(); }
 };
 
-// Gauss-Seidel value of cell P from its current neighbours, with the level's
-// arrays passed as restrict-qualified pointers: every caller reads dp only at
-// cells that it does not write in the same pass (see rbgs_cells), so the
-// compiler may keep several cells' loads in flight ahead of the stores.
+// Gauss-Seidel value of a cell (storage indices b) from its current
+// neighbours, with the level's arrays passed as restrict-qualified pointers:
+// every caller reads dp only at cells that it does not write in the same pass
+// (see rbgs_cells), so the compiler may keep several cells' loads in flight
+// ahead of the stores.
 //   FP64 (scaled): c0..c3 = wE, wW, wN, wS; value f + sum w dp_nb.
-//   FP32 (unscaled): c0 = Tx, c1 = Tz; value (f + sum T dp_nb) / D.
+//   FP32 (unscaled): c0 = Tx (east face), c1 = Tz (north face); the west and
+//   south faces are the neighbours'; value (f + sum T dp_nb) / D.
 template <typename T>
-__device__ __forceinline__ T gs_at(int P, int i, int j, int nx, int nz, const T* __restrict__ f,
+__device__ __forceinline__ T gs_at(const Nb& b, bool hE, bool hW, bool hN, bool hS, const T* __restrict__ f,
                                    const T* __restrict__ c0, const T* __restrict__ c1,
                                    const T* __restrict__ c2, const T* __restrict__ c3,
                                    const T* __restrict__ q, const T* __restrict__ dp) {
     if constexpr (Scaled<T>::value) {
-        T v = f[P];
-        if (i < nx - 1) v += c0[P] * dp[P + 1];
-        if (i > 0)      v += c1[P] * dp[P - 1];
-        if (j < nz - 1) v += c2[P] * dp[P + nx];
-        if (j > 0)      v += c3[P] * dp[P - nx];
+        T v = f[b.own];
+        if (hE) v += c0[b.own] * dp[b.e];
+        if (hW) v += c1[b.own] * dp[b.w];
+        if (hN) v += c2[b.own] * dp[b.n];
+        if (hS) v += c3[b.own] * dp[b.s];
         return v;
     } else {
         T t = T(0);
-        if (i < nx - 1) t += c0[P] * dp[P + 1];
-        if (i > 0)      t += c0[P - 1] * dp[P - 1];
-        if (j < nz - 1) t += c1[P] * dp[P + nx];
-        if (j > 0)      t += c1[P - nx] * dp[P - nx];
-        return (f[P] + t) * q[P];
+        if (hE) t += c0[b.own] * dp[b.e];
+        if (hW) t += c0[b.w] * dp[b.w];
+        if (hN) t += c1[b.own] * dp[b.n];
+        if (hS) t += c1[b.s] * dp[b.s];
+        return (f[b.own] + t) * q[b.own];
     }
 }
 
-// residual f - A dp at cell P (unscaled): FP64 D (value - dp_P), FP32
-// f - (D dp_P - sum T dp_nb)
+// residual f - A dp at a cell (unscaled): FP64 D (value - dp), FP32
+// f - (D dp - sum T dp_nb)
 template <typename T>
-__device__ __forceinline__ T resid_at(int P, int i, int j, int nx, int nz, const T* __restrict__ f,
-                                      const T* __restrict__ c0, const T* __restrict__ c1,
-                                      const T* __restrict__ c2, const T* __restrict__ c3,
-                                      const T* __restrict__ q, const T* __restrict__ D,
-                                      const T* __restrict__ dp) {
+__device__ __forceinline__ T resid_at(const Nb& b, bool hE, bool hW, bool hN, bool hS,
+                                      const T* __restrict__ f, const T* __restrict__ c0,
+                                      const T* __restrict__ c1, const T* __restrict__ c2,
+                                      const T* __restrict__ c3, const T* __restrict__ q,
+                                      const T* __restrict__ D, const T* __restrict__ dp) {
     if constexpr (Scaled<T>::value) {
-        return D[P] * (gs_at<T>(P, i, j, nx, nz, f, c0, c1, c2, c3, q, dp) - dp[P]);
+        return D[b.own] * (gs_at<T>(b, hE, hW, hN, hS, f, c0, c1, c2, c3, q, dp) - dp[b.own]);
     } else {
         T t = T(0);
-        if (i < nx - 1) t += c0[P] * dp[P + 1];
-        if (i > 0)      t += c0[P - 1] * dp[P - 1];
-        if (j < nz - 1) t += c1[P] * dp[P + nx];
-        if (j > 0)      t += c1[P - nx] * dp[P - nx];
-        return f[P] - (D[P] * dp[P] - t);
+        if (hE) t += c0[b.own] * dp[b.e];
+        if (hW) t += c0[b.w] * dp[b.w];
+        if (hN) t += c1[b.own] * dp[b.n];
+        if (hS) t += c1[b.s] * dp[b.s];
+        return f[b.own] - (D[b.own] * dp[b.own] - t);
     }
 }
 
-// one colour of red-black Gauss-Seidel over the level (red: i + j even).  The
-// corrections are read through one restrict-qualified view and written through
-// another: a half-sweep writes cells of one colour and reads only cells of the
-// other, so the two views never touch the same element.
+template <typename T>
+__device__ __forceinline__ T resid_cell(const Lv<T>& L, int i, int j) {
+    return resid_at<T>(nb_of(L, i, j), i < L.nx - 1, i > 0, j < L.nz - 1, j > 0, L.f, L.c0, L.c1, L.c2, L.c3,
+                       L.q, L.D, L.dp);
+}
+
+// one colour of red-black Gauss-Seidel over a colour-split level (red:
+// i + j even).  The corrections are read through one restrict-qualified view
+// and written through another: a half-sweep writes cells of one colour and
+// reads only cells of the other, so the two views never touch one element.
 template <typename T, typename G>
-__device__ __forceinline__ void rbgs_cells(int n, int nx, int nz, int hx, unsigned mhx, int colour,
+__device__ __forceinline__ void rbgs_cells(int nx, int nz, int hx, int H, unsigned mhx, int colour,
                                            const T* __restrict__ f, const T* __restrict__ c0,
                                            const T* __restrict__ c1, const T* __restrict__ c2,
                                            const T* __restrict__ c3, const T* __restrict__ q,
                                            const T* __restrict__ dpr, T* __restrict__ dpw) {
 #pragma unroll 4
-    for (int c = G::rank(); c < n; c += G::size()) {
+    for (int c = G::rank(); c < H; c += G::size()) {
         const int j = fdiv(c, hx, mhx);
         const int i = 2 * (c - j * hx) + ((j + colour) & 1);
-        const int P = j * nx + i;
-        dpw[P] = gs_at<T>(P, i, j, nx, nz, f, c0, c1, c2, c3, q, dpr);
+        const int oth = (1 - colour) * H + c;
+        const Nb b{colour * H + c, oth + (i & 1), oth - 1 + (i & 1), oth + hx, oth - hx};
+        dpw[b.own] = gs_at<T>(b, i < nx - 1, i > 0, j < nz - 1, j > 0, f, c0, c1, c2, c3, q, dpr);
     }
     G::sync();
 }
 
 template <typename T, typename G>
 __device__ __forceinline__ void rbgs(const Lv<T>& L, int colour) {
-    rbgs_cells<T, G>(L.hx * L.nz, L.nx, L.nz, L.hx, L.mhx, colour, L.f, L.c0, L.c1, L.c2, L.c3, L.q, L.dp, L.dp);
+    rbgs_cells<T, G>(L.nx, L.nz, L.hx, L.H, L.mhx, colour, L.f, L.c0, L.c1, L.c2, L.c3, L.q, L.dp, L.dp);
 }
 
 template <typename T, typename G>
@@ -282,41 +339,49 @@ __device__ __forceinline__ void smooth(const Lv<T>& L, int nu) {
 
 // restricted residual (Eq. transfer, R = 1/4 sum of the children); after a
 // black half-sweep only the two red children carry a residual.  Reads the
-// fine level, writes the coarse one (distinct arrays: restrict views).
+// fine level, writes the coarse one (distinct arrays: restrict views).  The
+// fine level is colour-split: the children of coarse cell (I, J) are the red
+// cells r0 = 2J hx + I and r0 + hx and the black cells H + r0, H + r0 + hx.
 template <typename T, typename G>
-__device__ __forceinline__ void restrict_cells(const Lv<T>& F, int cnx, int cnc, unsigned cmnx, bool red_only,
-                                               bool scale, const T* __restrict__ f, const T* __restrict__ c0,
+__device__ __forceinline__ void restrict_cells(const Lv<T>& F, const Lv<T>& C, bool red_only, bool scale,
+                                               const T* __restrict__ f, const T* __restrict__ c0,
                                                const T* __restrict__ c1, const T* __restrict__ c2,
                                                const T* __restrict__ c3, const T* __restrict__ q,
                                                const T* __restrict__ D, const T* __restrict__ dp,
                                                const T* __restrict__ cq, T* __restrict__ cf, T* __restrict__ cdp) {
-    const int nx = F.nx, nz = F.nz;
-#pragma unroll 2
-    for (int c = G::rank(); c < cnc; c += G::size()) {
-        const int J = fdiv(c, cnx, cmnx), I = c - J * cnx;
-        const int i = 2 * I, j = 2 * J, P = j * nx + i;
-        const T r00 = resid_at<T>(P, i, j, nx, nz, f, c0, c1, c2, c3, q, D, dp);
-        const T r11 = resid_at<T>(P + nx + 1, i + 1, j + 1, nx, nz, f, c0, c1, c2, c3, q, D, dp);
+    const int nx = F.nx, nz = F.nz, hx = F.hx, H = F.H;
+#pragma unroll 1
+    for (int c = G::rank(); c < C.nc; c += G::size()) {
+        const int J = fdiv(c, C.nx, C.mnx), I = c - J * C.nx;
+        const int i = 2 * I, j = 2 * J, r0 = j * hx + I;
+        // red (i, j): neighbours black; red (i+1, j+1) likewise
+        const Nb b00{r0, H + r0, H + r0 - 1, H + r0 + hx, H + r0 - hx};
+        const Nb b11{r0 + hx, H + r0 + hx + 1, H + r0 + hx, H + r0 + 2 * hx, H + r0};
+        const T r00 = resid_at<T>(b00, true, i > 0, true, j > 0, f, c0, c1, c2, c3, q, D, dp);
+        const T r11 = resid_at<T>(b11, i + 1 < nx - 1, true, j + 1 < nz - 1, true, f, c0, c1, c2, c3, q, D, dp);
         T sum;
         if (red_only) {
             sum = r00 + r11;
         } else {
-            const T r10 = resid_at<T>(P + 1, i + 1, j, nx, nz, f, c0, c1, c2, c3, q, D, dp);
-            const T r01 = resid_at<T>(P + nx, i, j + 1, nx, nz, f, c0, c1, c2, c3, q, D, dp);
+            const Nb b10{H + r0, r0 + 1, r0, r0 + hx, r0 - hx};
+            const Nb b01{H + r0 + hx, r0 + hx, r0 + hx - 1, r0 + 2 * hx, r0};
+            const T r10 = resid_at<T>(b10, i + 1 < nx - 1, true, true, j > 0, f, c0, c1, c2, c3, q, D, dp);
+            const T r01 = resid_at<T>(b01, true, i > 0, j + 1 < nz - 1, true, f, c0, c1, c2, c3, q, D, dp);
             sum = r00 + r10 + r01 + r11;
         }
+        const int cs = sidx(C, I, J);
         T fc = T(0.25) * sum;
-        if (scale) fc *= cq[c];
-        cf[c] = fc;
-        cdp[c] = T(0);
+        if (scale) fc *= cq[cs];
+        cf[cs] = fc;
+        cdp[cs] = T(0);
     }
     G::sync();
 }
 
 template <typename T, typename G>
 __device__ __forceinline__ void resid_restrict(const Lv<T>& F, const Lv<T>& C, bool red_only, bool coarsest) {
-    restrict_cells<T, G>(F, C.nx, C.nc, C.mnx, red_only, Scaled<T>::value && !coarsest, F.f, F.c0, F.c1, F.c2,
-                         F.c3, F.q, F.D, F.dp, C.q, C.f, C.dp);
+    restrict_cells<T, G>(F, C, red_only, Scaled<T>::value && !coarsest, F.f, F.c0, F.c1, F.c2, F.c3, F.q, F.D,
+                         F.dp, C.q, C.f, C.dp);
 }
 
 // piecewise-constant prolongation and correction: each coarse cell adds its
@@ -325,13 +390,13 @@ template <typename T, typename G>
 __device__ __forceinline__ void prolong(const Lv<T>& F, const Lv<T>& C) {
     const T* __restrict__ e = C.dp;
     T* __restrict__ d = F.dp;
-    const int fx = F.nx;
+    const int hx = F.hx, H = F.H;
 #pragma unroll 2
     for (int c = G::rank(); c < C.nc; c += G::size()) {
         const int J = fdiv(c, C.nx, C.mnx), I = c - J * C.nx;
-        const T v = e[c];
-        const int P = (2 * J) * fx + 2 * I;
-        d[P] += v; d[P + 1] += v; d[P + fx] += v; d[P + fx + 1] += v;
+        const T v = e[sidx(C, I, J)];
+        const int r0 = 2 * J * hx + I;
+        d[r0] += v; d[r0 + hx] += v; d[H + r0] += v; d[H + r0 + hx] += v;
     }
     G::sync();
 }
@@ -465,22 +530,19 @@ template <typename T>
 __device__ __forceinline__ unsigned long long resid_norm(const Lv<T>& L, bool red_only,
                                                          unsigned long long* red) {
     unsigned long long m = 0;
-    const int nx = L.nx, nz = L.nz;
     if (red_only) {
         const int n = L.hx * L.nz;
 #pragma unroll 2
         for (int c = threadIdx.x; c < n; c += blockDim.x) {
             const int j = fdiv(c, L.hx, L.mhx);
             const int i = 2 * (c - j * L.hx) + (j & 1);
-            const unsigned long long b = abs_bits(
-                (double)resid_at<T>(j * nx + i, i, j, nx, nz, L.f, L.c0, L.c1, L.c2, L.c3, L.q, L.D, L.dp));
+            const unsigned long long b = abs_bits((double)resid_cell(L, i, j));
             m = b > m ? b : m;
         }
     } else {
         for (int c = threadIdx.x; c < L.nc; c += blockDim.x) {
             const int j = fdiv(c, L.nx, L.mnx), i = c - j * L.nx;
-            const unsigned long long b = abs_bits(
-                (double)resid_at<T>(c, i, j, nx, nz, L.f, L.c0, L.c1, L.c2, L.c3, L.q, L.D, L.dp));
+            const unsigned long long b = abs_bits((double)resid_cell(L, i, j));
             m = b > m ? b : m;
         }
     }
@@ -667,15 +729,16 @@ struct Cta {
             F.D[q] = d;
             f64[q] = -R;
             dp64[q] = 0.0;
+            const int sq = sidx(M0, i, j);
             if constexpr (SC) {
                 double inv = 1.0 / d;
-                M0.q[q] = inv;
-                M0.c0[q] = te * inv; M0.c1[q] = tw * inv; M0.c2[q] = tn * inv; M0.c3[q] = tsf * inv;
-                M0.f[q] = -R * inv;
+                M0.q[sq] = inv; M0.D[sq] = d;
+                M0.c0[sq] = te * inv; M0.c1[sq] = tw * inv; M0.c2[sq] = tn * inv; M0.c3[sq] = tsf * inv;
+                M0.f[sq] = -R * inv;
             } else {
-                M0.c0[q] = (TM)te; M0.c1[q] = (TM)tn; M0.D[q] = (TM)d;
-                M0.q[q] = (TM)(1.0f / (float)d);
-                M0.f[q] = (TM)(-R); M0.dp[q] = TM(0);
+                M0.c0[sq] = (TM)te; M0.c1[sq] = (TM)tn; M0.D[sq] = (TM)d;
+                M0.q[sq] = (TM)(1.0f / (float)d);
+                M0.f[sq] = (TM)(-R); M0.dp[q] = TM(0);
             }
             unsigned long long b = abs_bits(R);
             m = b > m ? b : m;
@@ -699,13 +762,14 @@ struct Cta {
                 if (J > 0)         { tsf = 0.25 * (0.5 * (Fl.Tz[f00 - fx] + Fl.Tz[f00 - fx + 1])); d += tsf; }
                 else d += Cl.Tbb[I];
                 Cl.Tx[c] = te; Cl.Tz[c] = tn; Cl.Cdt[c] = cd; Cl.D[c] = d;
+                const int sc = sidx(Ml, I, J);
                 if constexpr (SC) {
                     double inv = 1.0 / d;
-                    Ml.q[c] = inv;
-                    Ml.c0[c] = te * inv; Ml.c1[c] = tw * inv; Ml.c2[c] = tn * inv; Ml.c3[c] = tsf * inv;
+                    Ml.q[sc] = inv; Ml.D[sc] = d;
+                    Ml.c0[sc] = te * inv; Ml.c1[sc] = tw * inv; Ml.c2[sc] = tn * inv; Ml.c3[sc] = tsf * inv;
                 } else {
-                    Ml.c0[c] = (TM)te; Ml.c1[c] = (TM)tn; Ml.D[c] = (TM)d;
-                    Ml.q[c] = (TM)(1.0f / (float)d);
+                    Ml.c0[sc] = (TM)te; Ml.c1[sc] = (TM)tn; Ml.D[sc] = (TM)d;
+                    Ml.q[sc] = (TM)(1.0f / (float)d);
                 }
             }
             __syncthreads();
@@ -721,10 +785,16 @@ struct Cta {
         else vcycle<TM>(LM, L64, nlev, P.lw, P.nu1, P.nu2, Amat, f0);
     }
 
-    // x += e (FP64 += FP32 correction), then the CTA synchronises
+    // x += e (FP64, natural order += FP32 finest-level correction), then the
+    // CTA synchronises
     __device__ __forceinline__ void add_correction(double* __restrict__ x, const TM* __restrict__ e) const {
+        const Lv<TM>& M0 = LM[0];
+        const unsigned mnx = L64[0].mnx;
 #pragma unroll 4
-        for (int q = tid; q < nc; q += nt) x[q] += (double)e[q];
+        for (int q = tid; q < nc; q += nt) {
+            const int j = fdiv(q, nx, mnx), i = q - j * nx;
+            x[q] += (double)e[sidx(M0, i, j)];
+        }
         __syncthreads();
     }
 
@@ -747,8 +817,9 @@ struct Cta {
             if (j < nz - 1) sn += Tz[q] * x[q + nx];
             if (j > 0)      sn += Tz[q - nx] * x[q - nx];
             const double r = f[q] - (D[q] * x[q] - sn);
-            rf[q] = (TM)r;
-            ef[q] = TM(0);
+            const int sq = sidx(LM[0], i, j);
+            rf[sq] = (TM)r;
+            ef[sq] = TM(0);
             const unsigned long long b = abs_bits(r);
             mm = b > mm ? b : mm;
         }
@@ -802,7 +873,13 @@ struct Cta {
             if (!mg_solve(fb, mg_tot, status)) { status = RICH_NONFINITE; alive = false; break; }
             unsigned long long dm = 0;
             for (int q = tid; q < nc; q += nt) {
-                double d = dp64[q];
+                double d;
+                if constexpr (SC) {
+                    const int j = fdiv(q, nx, L64[0].mnx);
+                    d = dp64[sidx(LM[0], q - j * nx, j)];
+                } else {
+                    d = dp64[q];
+                }
                 p[q] += d;
                 unsigned long long b = abs_bits(d);
                 dm = b > dm ? b : dm;
@@ -875,8 +952,9 @@ struct Cta {
     __device__ void mg_apply(const double* r, int ninner) {
         const Lv<TM>& M0 = LM[0];
         for (int q = tid; q < nc; q += nt) {
-            if constexpr (SC) M0.f[q] = r[q] * M0.q[q];
-            else M0.f[q] = (TM)r[q];
+            const int j = fdiv(q, nx, L64[0].mnx), sq = sidx(M0, q - j * nx, j);
+            if constexpr (SC) M0.f[sq] = r[q] * M0.q[sq];
+            else M0.f[sq] = (TM)r[q];
             M0.dp[q] = TM(0);
         }
         __syncthreads();
@@ -904,7 +982,10 @@ struct Cta {
         if (b0 == 0) return 0;
         for (int it = 1; it <= P.adj_maxit; ++it) {
             mg_apply(r, P.adj_inner);
-            for (int q = tid; q < nc; q += nt) lam[q] += (double)M0.dp[q];
+            for (int q = tid; q < nc; q += nt) {
+                const int j = fdiv(q, nx, L64[0].mnx);
+                lam[q] += (double)M0.dp[sidx(M0, q - j * nx, j)];
+            }
             __syncthreads();
             unsigned long long mm = 0;
             for (int q = tid; q < nc; q += nt) {
@@ -918,6 +999,133 @@ struct Cta {
             if (__longlong_as_double((long long)rb) <= target) return it;
         }
         return P.adj_maxit + 1;
+    }
+
+    // e = M^{-1} r: ninner cycles of the Picard operator A from zero (a fixed
+    // linear operator: the same cycles on the same matrix), copied to out
+    __device__ void precond(const double* r, double* out) {
+        mg_apply(r, P.adj_inner);
+        const TM* e = LM[0].dp;
+        for (int q = tid; q < nc; q += nt) {
+            const int j = fdiv(q, nx, L64[0].mnx), sq = sidx(LM[0], q - j * nx, j);
+            out[q] = (double)e[sq];
+        }
+        __syncthreads();
+    }
+
+    // y = J^T x over all cells, then the CTA synchronises
+    __device__ void jt_vec(const double* dE, const double* dW, const double* dN, const double* dS,
+                           const double* dg, const double* x, double* y) {
+        for (int q = tid; q < nc; q += nt) y[q] = jt_apply(dE, dW, dN, dS, dg, x, q);
+        __syncthreads();
+    }
+
+    // J^T lam = rhs by BiCGStab (van der Vorst 1992) right-preconditioned with
+    // the CCMG cycles of A: converged when the TRUE residual ||rhs - J^T lam||
+    // <= adj_tol ||rhs|| (checked explicitly whenever the recursive residual
+    // says so; a mismatch restarts the recurrence from the true residual).
+    // Returns the number of preconditioner applications (adj_maxit + 1 when
+    // not converged); w holds the vectors r (also s), r^, p, v, t, p^, s^.
+    __device__ int adj_solve_bicgstab(const double* dE, const double* dW, const double* dN, const double* dS,
+                                      const double* dg, const double* rhs, double* lam, double* r, double* rh,
+                                      double* pk, double* v, double* t, double* ph, double* sh) {
+        double* redd = reinterpret_cast<double*>(red);
+        unsigned long long m = 0;
+        for (int q = tid; q < nc; q += nt) {
+            lam[q] = 0.0;
+            unsigned long long b = abs_bits(rhs[q]);
+            m = b > m ? b : m;
+        }
+        const unsigned long long b0 = block_max(m, red);
+        if (b0 == 0) return 0;
+        const double target = P.adj_tol * __longlong_as_double((long long)b0);
+        int apps = 0;
+        bool restart = true;
+        double rho = 1.0, alpha = 1.0, omega = 1.0;
+        while (apps < P.adj_maxit) {
+            if (restart) {                          // r = r^ = rhs - J^T lam, p = v = 0
+                unsigned long long rm = 0;
+                for (int q = tid; q < nc; q += nt) {
+                    const double rv = rhs[q] - jt_apply(dE, dW, dN, dS, dg, lam, q);
+                    r[q] = rv; rh[q] = rv; pk[q] = 0.0; v[q] = 0.0;
+                    unsigned long long b = abs_bits(rv);
+                    rm = b > rm ? b : rm;
+                }
+                const unsigned long long rb = block_max(rm, red);
+                if (rb > INF_BITS - 1) break;
+                if (__longlong_as_double((long long)rb) <= target) return apps;
+                rho = alpha = omega = 1.0;
+                restart = false;
+                if (apps > 0) ++apps;               // a restart counts as one application
+            }
+            double s1 = 0.0;
+            for (int q = tid; q < nc; q += nt) s1 += rh[q] * r[q];
+            const double rho_new = block_sum(s1, redd);
+            if (!(fabs(rho_new) > 0.0) || !isfinite(rho_new)) { restart = true; if (!isfinite(rho_new)) break; continue; }
+            const double beta = (rho_new / rho) * (alpha / omega);
+            for (int q = tid; q < nc; q += nt) pk[q] = r[q] + beta * (pk[q] - omega * v[q]);
+            __syncthreads();
+            precond(pk, ph); ++apps;
+            jt_vec(dE, dW, dN, dS, dg, ph, v);
+            double s2 = 0.0;
+            for (int q = tid; q < nc; q += nt) s2 += rh[q] * v[q];
+            const double den = block_sum(s2, redd);
+            if (!(fabs(den) > 0.0) || !isfinite(den)) { restart = true; if (!isfinite(den)) break; continue; }
+            alpha = rho_new / den;
+            unsigned long long sm = 0;
+            for (int q = tid; q < nc; q += nt) {
+                const double sv = r[q] - alpha * v[q];
+                r[q] = sv;                                  // r now holds s
+                unsigned long long b = abs_bits(sv);
+                sm = b > sm ? b : sm;
+            }
+            const unsigned long long sb = block_max(sm, red);
+            if (sb > INF_BITS - 1) break;
+            if (__longlong_as_double((long long)sb) <= target) {
+                for (int q = tid; q < nc; q += nt) lam[q] += alpha * ph[q];
+                __syncthreads();
+                if (true_resid_ok(dE, dW, dN, dS, dg, rhs, lam, target)) return apps;
+                restart = true;
+                continue;
+            }
+            precond(r, sh); ++apps;
+            jt_vec(dE, dW, dN, dS, dg, sh, t);
+            double s3 = 0.0, s4 = 0.0;
+            for (int q = tid; q < nc; q += nt) { s3 += t[q] * r[q]; s4 += t[q] * t[q]; }
+            const double ts = block_sum(s3, redd);
+            const double tt = block_sum(s4, redd);
+            omega = tt > 0.0 ? ts / tt : 0.0;
+            unsigned long long rm = 0;
+            for (int q = tid; q < nc; q += nt) {
+                lam[q] += alpha * ph[q] + omega * sh[q];
+                const double rv = r[q] - omega * t[q];
+                r[q] = rv;
+                unsigned long long b = abs_bits(rv);
+                rm = b > rm ? b : rm;
+            }
+            const unsigned long long rb = block_max(rm, red);
+            if (rb > INF_BITS - 1) break;
+            if (__longlong_as_double((long long)rb) <= target) {
+                if (true_resid_ok(dE, dW, dN, dS, dg, rhs, lam, target)) return apps;
+                restart = true;
+                continue;
+            }
+            if (!(omega != 0.0)) restart = true;
+            rho = rho_new;
+        }
+        return P.adj_maxit + 1;
+    }
+
+    // ||rhs - J^T lam||_inf <= target (the true residual)
+    __device__ bool true_resid_ok(const double* dE, const double* dW, const double* dN, const double* dS,
+                                  const double* dg, const double* rhs, const double* lam, double target) {
+        unsigned long long m = 0;
+        for (int q = tid; q < nc; q += nt) {
+            unsigned long long b = abs_bits(rhs[q] - jt_apply(dE, dW, dN, dS, dg, lam, q));
+            m = b > m ? b : m;
+        }
+        const unsigned long long rb = block_max(m, red);
+        return rb <= INF_BITS - 1 && __longlong_as_double((long long)rb) <= target;
     }
 
     // g -= (dR/dm)^T lam at the assembled state (m = ln Ks): interior faces
@@ -959,13 +1167,13 @@ __device__ __forceinline__ void init_levels(const FParams& P, char* slot, unsign
             *pp[k] = P.s64[l][k] >= 0 ? (double*)(sm + P.s64[l][k]) : (double*)(slot + P.o64[l][k]);
         Lv<TM>& b = LM[l];
         b.nx = a.nx; b.nz = a.nz; b.hx = a.nx >> 1; b.nc = a.nc; b.mnx = P.mnx[l]; b.mhx = P.mhx[l];
-        TM** qq[NMG] = {&b.c0, &b.c1, &b.c2, &b.c3, &b.q, &b.f, &b.dp};
+        b.H = l < nlev - 1 ? b.hx * b.nz : 0;             // colour-split unless coarsest
+        TM** qq[NMG] = {&b.c0, &b.c1, &b.c2, &b.c3, &b.q, &b.f, &b.dp, &b.D};
         for (int k = 0; k < NMG; ++k)
             *qq[k] = P.smg[l][k] >= 0 ? (TM*)(sm + P.smg[l][k])
                    : P.omg[l][k] >= 0 ? (TM*)(slot + P.omg[l][k]) : nullptr;
         if (P.osm[l] >= 0) b.dp = (TM*)(sm + P.osm[l]);   // corrections of small levels on chip
-        if constexpr (SC) b.D = (TM*)a.D;                 // FP64: shares the operator diagonal
-        else { b.D = b.c3; b.c3 = nullptr; }              // FP32: its own copy
+        if constexpr (!SC) { b.D = b.c3; b.c3 = nullptr; }   // FP32: D in the c3 slot
     }
     __syncthreads();
 }
@@ -1102,7 +1310,12 @@ k_adjoint(const FParams P) {
                         __syncthreads();
                     }
                     C.adj_prepare(dE, dW, dN, dS, dg);
-                    const int its = C.adj_solve(dE, dW, dN, dS, dg, rhs, lam, r);
+                    const int its = P.adj_method == 1
+                        ? C.adj_solve_bicgstab(dE, dW, dN, dS, dg, rhs, lam, r, (double*)(slot + P.o_rh),
+                                               (double*)(slot + P.o_pk), (double*)(slot + P.o_v),
+                                               (double*)(slot + P.o_t), (double*)(slot + P.o_ph),
+                                               (double*)(slot + P.o_sh))
+                        : C.adj_solve(dE, dW, dN, dS, dg, rhs, lam, r);
                     adj_its += its;
                     if (its > P.adj_maxit) status = max(status, (int)RICH_MG_MAXIT);
                     C.adj_grad_update(lam, g);

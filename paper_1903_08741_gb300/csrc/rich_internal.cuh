@@ -71,6 +71,7 @@ struct rich_ctx {
     int tune_threads = 0;                       // fused-kernel block size (0: default 512)
     int tune_mixed_inner = 0;                   // FP32 V-cycles per FP64 defect (0: default 2)
     double last_sm_seconds = 0;                 // SM-seconds of the last rich_solve_device
+    int adj_method = 1;                         // adjoint J^T solver: 0 defect correction, 1 BiCGStab
 };
 
 void rich_count_launch();
@@ -100,7 +101,7 @@ int rich_solve_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const doubl
 void rich_prof_amend(rich_ctx* ctx, double bytes, double flops);
 int rich_adjoint_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const double* lnKs,
                        const double* alpha, double alpha_scale, int ckpt_every, double adj_tol,
-                       int adj_maxit, double* qoi, double* g_out, cudaStream_t st);
+                       int adj_maxit, int adj_method, double* qoi, double* g_out, cudaStream_t st);
 int rich_check_problem(const rich_problem_t* pb);
 
 // ---- fields (fields.cu)
