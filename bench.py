@@ -746,6 +746,35 @@ def bench_extras(R, args, pb, lk, al, q64, s64, clk):
     return out
 
 
+def run_tunecheck(args):
+    """The autotuner against the full batch: for the 128^2 workload (FP64 and
+    mixed) and every level of the five-level MLMC hierarchy, time each launch
+    shape on the whole batch (2 time steps, fresh fields) and report how far
+    the tuner's choice is from the fastest."""
+    import torch
+    import paper_1903_08741_gb300 as R
+    from paper_1903_08741_gb300 import autotune
+    from paper_1903_08741_gb300 import build as B
+    B.build()
+    torch.cuda.set_device(0)
+    steps = args.time_steps or 2
+    cases = []
+    for prec in (R.FP64, R.MIXED):
+        cases.append((R.Problem(nx=128, nz=128, nsteps=20, dt=0.005, precision=prec, **PHYS), 4096, "mc128"))
+        for l, nl in enumerate(MLMC_LEVELS["nsamples"]):
+            m, st_l = MLMC_LEVELS["n0"] << l, MLMC_LEVELS["steps0"] << l
+            cases.append((R.Problem(nx=m, nz=m, nsteps=st_l, dt=MLMC_LEVELS["t_final"] / st_l, precision=prec,
+                                    **PHYS), nl, f"mlmc5 level {l}"))
+    out = []
+    for pb, S, name in cases:
+        src = autotune.source(pb, S)
+        r = autotune.check(pb, S, steps=steps)
+        r.update({"case": name, "tuner_source": src})
+        out.append(r)
+    print(json.dumps({"metric": "autotuner shortfall vs best shape on the full batch", "steps": steps,
+                      "max_shortfall": max(r["tuner_shortfall"] for r in out), "cases": out}))
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -942,7 +971,8 @@ def main():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["mlmc5", "mlmc5vg", "adjoint256", "mc512", "vgmap"],
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["mlmc5", "mlmc5vg", "adjoint256", "mc512", "vgmap",
+                                                               "tunecheck"],
                     default="mc128")
     ap.add_argument("--check", action="store_true", help="adjoint workload: finite-difference check")
     ap.add_argument("--adaptive-eps", type=float, default=0.0, help="mlmc5: also run Algorithm PC_MLMC to this RMSE")
@@ -985,6 +1015,8 @@ def main():
         run_vgmap(args)
     elif args.workload == "mlmc5vg":
         run_mlmc_vg(args)
+    elif args.workload == "tunecheck":
+        run_tunecheck(args)
     else:
         run_ours(args)
 

@@ -410,8 +410,8 @@ int rich_set_adjoint_method(rich_ctx_t ctx, int32_t method);
  *   - The grid is limited to the CTA slots that fit in the array; a grid whose
  *     per-CTA slot exceeds it is rejected with RICH_ERR_INVALID.  A slot holds
  *     one sample's multigrid hierarchy and fine-grid state: a 128^2 FP64
- *     problem needs 2.72 MiB per CTA, so 5 CTAs run; 32^2 FP64 needs
- *     0.175 MiB (91 slots, more than the resident CTAs of one GPU).
+ *     problem needs 2.88 MiB per CTA, so 5 CTAs run (mixed precision: 2.18 MiB,
+ *     7 CTAs); 32^2 FP64 needs 0.19 MiB (86 slots).
  * Inputs lnKs, alpha [S][nz][nx] and outputs qoi[S], status[S] (status may be
  * NULL) are caller-owned DEVICE arrays.  The call is asynchronous on `stream`
  * and returns 0 once the work is enqueued (per-sample results are in status),

@@ -126,3 +126,46 @@ def tune(problem, nsamples, device=0, force=False, probe_steps=1, verbose=False,
     _save(path, data)
     R.set_tuning(bt, mi, device)
     return bt, mi
+
+
+def check(problem, nsamples, device=0, steps=None, verbose=False):
+    """Time every candidate launch shape on the FULL batch (fresh seeded
+    fields, `steps` time steps, default the problem's own) and compare the
+    fastest with the shape tune() chooses.  Returns a dict with the
+    per-candidate milliseconds, the best shape, the tuner's shape and the
+    tuner's shortfall (its time / the best time - 1)."""
+    import torch
+    import paper_1903_08741_gb300 as R
+    dev = torch.device(f"cuda:{device}")
+    chosen = tune(problem, nsamples, device=device)
+    pb = R.Problem(**{**problem.__dict__, "nsteps": steps or problem.nsteps})
+    if problem.closure == R.VAN_GENUCHTEN:
+        flds = R.sample_soil(problem.nx, problem.nz, nsamples, R.soil_field_model(2.0, R.FieldModel(seed=123457)),
+                             R.SoilModel(n_bl=1.6), device=device, thetas=False)[:3]
+        solve = lambda k: R.solve_soil(pb, *[f[:k].contiguous() for f in flds])
+    else:
+        lk, al = R.sample_fields(problem.nx, problem.nz, nsamples, R.FieldModel(seed=123457), device=device)
+        solve = lambda k: R.solve_batch(pb, lk[:k].contiguous(), al[:k].contiguous())
+    inners = [1, 2, 3, 4, 6] if problem.precision else [0]
+    stream = torch.cuda.current_stream(dev)
+    ms = {}
+    try:
+        for bt in (256, 512, 1024):
+            for mi in inners:
+                R.set_tuning(bt, mi, device)
+                solve(min(nsamples, 8))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                solve(nsamples)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                ms[f"{bt}/{mi}"] = e0.elapsed_time(e1)
+                if verbose:
+                    print(f"check {problem.nx}x{problem.nz} S{nsamples}: {bt}/{mi} {ms[f'{bt}/{mi}']:.1f} ms")
+    finally:
+        R.set_tuning(*chosen, device)
+    best = min(ms, key=ms.get)
+    key = f"{chosen[0]}/{chosen[1]}"
+    return {"grid": [problem.nx, problem.nz], "precision": "mixed" if problem.precision else "fp64",
+            "samples": nsamples, "steps": pb.nsteps, "ms": ms, "best": best, "tuner": key,
+            "tuner_shortfall": ms[key] / ms[best] - 1.0}

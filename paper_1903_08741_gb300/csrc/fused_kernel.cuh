@@ -333,8 +333,23 @@ __device__ __forceinline__ void rbgs(const Lv<T>& L, int colour) {
 }
 
 template <typename T, typename G>
-__device__ __forceinline__ void smooth(const Lv<T>& L, int nu) {
-    for (int it = 0; it < nu; ++it) { rbgs<T, G>(L, 0); rbgs<T, G>(L, 1); }
+__device__ __forceinline__ void prolong(const Lv<T>& F, const Lv<T>& C);
+
+// nu red-black sweeps; with seeded true the first red half-sweep is skipped
+// because the restriction already stored its result (see restrict_cells)
+template <typename T, typename G>
+__device__ __forceinline__ void smooth(const Lv<T>& L, int nu, bool seeded = false) {
+    for (int it = 0; it < nu; ++it) {
+        if (!(seeded && it == 0)) rbgs<T, G>(L, 0);
+        rbgs<T, G>(L, 1);
+    }
+}
+
+// prolongation and post-smoothing of level l from level l+1
+template <typename T, typename G>
+__device__ __forceinline__ void prolong_smooth(const Lv<T>& F, const Lv<T>& C, int nu2) {
+    prolong<T, G>(F, C);
+    smooth<T, G>(F, nu2);
 }
 
 // restricted residual (Eq. transfer, R = 1/4 sum of the children); after a
@@ -342,15 +357,19 @@ __device__ __forceinline__ void smooth(const Lv<T>& L, int nu) {
 // fine level, writes the coarse one (distinct arrays: restrict views).  The
 // fine level is colour-split: the children of coarse cell (I, J) are the red
 // cells r0 = 2J hx + I and r0 + hx and the black cells H + r0, H + r0 + hx.
+// The coarse correction starts at zero; when the coarse level is smoothed
+// next (seed), its red cells get at once the value the first red half-sweep
+// would compute from all-zero neighbours, f q (FP64: the scaled f), so that
+// half-sweep is skipped.
 template <typename T, typename G>
-__device__ __forceinline__ void restrict_cells(const Lv<T>& F, const Lv<T>& C, bool red_only, bool scale,
+__device__ __forceinline__ void restrict_cells(const Lv<T>& F, const Lv<T>& C, bool red_only, bool scale, bool seed,
                                                const T* __restrict__ f, const T* __restrict__ c0,
                                                const T* __restrict__ c1, const T* __restrict__ c2,
                                                const T* __restrict__ c3, const T* __restrict__ q,
                                                const T* __restrict__ D, const T* __restrict__ dp,
                                                const T* __restrict__ cq, T* __restrict__ cf, T* __restrict__ cdp) {
     const int nx = F.nx, nz = F.nz, hx = F.hx, H = F.H;
-#pragma unroll 1
+#pragma unroll(Scaled<T>::value ? 1 : 2)
     for (int c = G::rank(); c < C.nc; c += G::size()) {
         const int J = fdiv(c, C.nx, C.mnx), I = c - J * C.nx;
         const int i = 2 * I, j = 2 * J, r0 = j * hx + I;
@@ -373,15 +392,21 @@ __device__ __forceinline__ void restrict_cells(const Lv<T>& F, const Lv<T>& C, b
         T fc = T(0.25) * sum;
         if (scale) fc *= cq[cs];
         cf[cs] = fc;
-        cdp[cs] = T(0);
+        T d0 = T(0);
+        if (seed && !((I + J) & 1)) {
+            if constexpr (Scaled<T>::value) d0 = fc;
+            else d0 = fc * cq[cs];
+        }
+        cdp[cs] = d0;
     }
     G::sync();
 }
 
 template <typename T, typename G>
-__device__ __forceinline__ void resid_restrict(const Lv<T>& F, const Lv<T>& C, bool red_only, bool coarsest) {
-    restrict_cells<T, G>(F, C, red_only, Scaled<T>::value && !coarsest, F.f, F.c0, F.c1, F.c2, F.c3, F.q, F.D,
-                         F.dp, C.q, C.f, C.dp);
+__device__ __forceinline__ void resid_restrict(const Lv<T>& F, const Lv<T>& C, bool red_only, bool coarsest,
+                                               bool seed = false) {
+    restrict_cells<T, G>(F, C, red_only, Scaled<T>::value && !coarsest, seed && !coarsest, F.f, F.c0, F.c1, F.c2,
+                         F.c3, F.q, F.D, F.dp, C.q, C.f, C.dp);
 }
 
 // piecewise-constant prolongation and correction: each coarse cell adds its
@@ -460,21 +485,28 @@ __device__ __forceinline__ void coarsest(const Lv<T>* L, const Lv64* L64, int c,
 // depth-first walk whose per-level visit counts sit in 4-bit fields of one
 // register (no device stack).  Run by the CTA, each visit of level lw (the
 // first small level) is handed to warp 0 as a complete cycle rooted at lw.
+// A level entered right after the restriction into it (fresh) skips its
+// first red half-sweep, which the restriction seeded; a level cycled again
+// (gamma > 1) starts from its previous correction and smooths in full.
 template <typename T, typename G>
-__device__ __forceinline__ void gwalk(const Lv<T>* L, const Lv64* L64, int root, int nlev, int lw, int nu1, int nu2, int gamma,
-                      T* A, const T* f0) {
+__device__ __forceinline__ void gwalk(const Lv<T>* L, const Lv64* L64, int root, int nlev, int lw, int nu1, int nu2,
+                                      int gamma, T* A, const T* f0, bool root_fresh) {
     static_assert(RICH_MAX_LEVELS * 4 <= 64, "visit counters must fit one 64-bit word");
     unsigned long long cnt = 0;
     int l = root;
+    bool fresh = root_fresh;
+    const bool seed = nu1 > 0;
     for (;;) {
         for (; l < nlev - 1 && l != lw; ++l) {            // enter l: pre-smooth, restrict
-            smooth<T, G>(L[l], nu1);
-            resid_restrict<T, G>(L[l], L[l + 1], nu1 > 0, l + 1 == nlev - 1);
+            smooth<T, G>(L[l], nu1, fresh && seed);
+            resid_restrict<T, G>(L[l], L[l + 1], nu1 > 0, l + 1 == nlev - 1, seed);
             cnt &= ~(15ull << (4 * l));
+            fresh = true;
         }
         if constexpr (std::is_same<G, GCta>::value) {
             if (l == lw && lw < nlev - 1) {
-                if (threadIdx.x < 32) gwalk<T, GWarp>(L, L64, lw, nlev, nlev, nu1, nu2, gamma, A, f0);
+                if (threadIdx.x < 32)
+                    gwalk<T, GWarp>(L, L64, lw, nlev, nlev, nu1, nu2, gamma, A, f0, fresh && seed);
                 __syncthreads();
             } else {
                 coarsest<T, G>(L, L64, nlev - 1, A, f0);
@@ -486,42 +518,37 @@ __device__ __forceinline__ void gwalk(const Lv<T>* L, const Lv64* L64, int root,
             if (--l < root) return;
             cnt += 1ull << (4 * l);
             const int reps = (l + 1 == nlev - 1) ? 1 : gamma;
-            if ((int)((cnt >> (4 * l)) & 15) < reps) { ++l; break; }   // cycle l+1 again
-            prolong<T, G>(L[l], L[l + 1]);
-            smooth<T, G>(L[l], nu2);
+            if ((int)((cnt >> (4 * l)) & 15) < reps) { ++l; fresh = false; break; }   // cycle l+1 again
+            prolong_smooth<T, G>(L[l], L[l + 1], nu2);
         }
     }
 }
 
-// V-cycle with the levels from lw down handed to warp 0 (lw = nlev: none)
+// V-cycle with the levels from lw down handed to warp 0 (lw = nlev: none);
+// every level below the finest is fresh (seeded by its restriction)
 template <typename T>
 __device__ __forceinline__ void vcycle(const Lv<T>* L, const Lv64* L64, int nlev, int lw, int nu1, int nu2, T* A,
-                       const T* f0) {
+                                       const T* f0) {
+    const bool seed = nu1 > 0;
     const int top = min(lw, nlev - 1);       // levels 0 .. top-1 run on the whole CTA
     for (int l = 0; l < top; ++l) {
-        smooth<T, GCta>(L[l], nu1);
-        resid_restrict<T, GCta>(L[l], L[l + 1], nu1 > 0, l + 1 == nlev - 1);
+        smooth<T, GCta>(L[l], nu1, l > 0 && seed);
+        resid_restrict<T, GCta>(L[l], L[l + 1], nu1 > 0, l + 1 == nlev - 1, seed);
     }
     if (lw < nlev - 1) {
         if (threadIdx.x < 32) {
             for (int l = lw; l < nlev - 1; ++l) {
-                smooth<T, GWarp>(L[l], nu1);
-                resid_restrict<T, GWarp>(L[l], L[l + 1], nu1 > 0, l + 1 == nlev - 1);
+                smooth<T, GWarp>(L[l], nu1, seed);
+                resid_restrict<T, GWarp>(L[l], L[l + 1], nu1 > 0, l + 1 == nlev - 1, seed);
             }
             coarsest<T, GWarp>(L, L64, nlev - 1, A, f0);
-            for (int l = nlev - 2; l >= lw; --l) {
-                prolong<T, GWarp>(L[l], L[l + 1]);
-                smooth<T, GWarp>(L[l], nu2);
-            }
+            for (int l = nlev - 2; l >= lw; --l) prolong_smooth<T, GWarp>(L[l], L[l + 1], nu2);
         }
         __syncthreads();
     } else {
         coarsest<T, GCta>(L, L64, nlev - 1, A, f0);
     }
-    for (int l = top - 1; l >= 0; --l) {
-        prolong<T, GCta>(L[l], L[l + 1]);
-        smooth<T, GCta>(L[l], nu2);
-    }
+    for (int l = top - 1; l >= 0; --l) prolong_smooth<T, GCta>(L[l], L[l + 1], nu2);
 }
 
 // ||f - A dp||_inf on a level after a cycle ending with a black half-sweep
@@ -781,7 +808,7 @@ struct Cta {
     // instantiation so the V kernels keep their register allocation) the
     // cycle of index P.gamma
     __device__ void mgcycle(const TM* f0) {
-        if constexpr (WC) gwalk<TM, GCta>(LM, L64, 0, nlev, P.lw, P.nu1, P.nu2, P.gamma, Amat, f0);
+        if constexpr (WC) gwalk<TM, GCta>(LM, L64, 0, nlev, P.lw, P.nu1, P.nu2, P.gamma, Amat, f0, false);
         else vcycle<TM>(LM, L64, nlev, P.lw, P.nu1, P.nu2, Amat, f0);
     }
 
@@ -1226,7 +1253,7 @@ k_fused(const FParams P) {
 //   J_N^T lam_N = dQ/dp^N,  J_n^T lam_n = diag(C(p^n)/dt) lam_{n+1},
 //   dQ/dm = dQ/dm|explicit - sum_n (dR_n/dm)^T lam_n     (m = ln Ks).
 template <typename TM, bool WC>
-__global__ void __launch_bounds__(512)
+__global__ void __maxnreg__(128)
 k_adjoint(const FParams P) {
     extern __shared__ unsigned char smraw[];
     __shared__ unsigned long long red[33];
