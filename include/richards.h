@@ -113,8 +113,8 @@ const char* rich_last_error(void);
 
 /* Launch tuning of this context's solves (set by the autotuner of the Python
  * package, which times the candidates and caches the choice per grid,
- * precision and batch): block_threads 256 (four resident CTAs per SM), 512
- * (two) or 1024 (one), 0 = default 512; mixed_inner = FP32 V-cycles per FP64 defect in
+ * precision and batch): block_threads 128 (eight resident CTAs per SM), 256
+ * (four), 512 (two) or 1024 (one), 0 = default 512; mixed_inner = FP32 V-cycles per FP64 defect in
  * RICH_MIXED solves, 0 = default 2 (1..16).  The computed solution does not
  * depend on block_threads; mixed_inner changes how often the FP64 stopping
  * test is evaluated (the FP64 tolerance holds either way). */

@@ -1,12 +1,13 @@
 """Autotuner of the fused solver's launch shape.
 
-Candidates: 256-thread CTAs (four resident per SM: small grids, whose levels
-give a large CTA too little work between barriers), 512-thread CTAs (two per
+Candidates: 128- and 256-thread CTAs (eight or four resident per SM: small
+grids, whose levels give a large CTA too little work between barriers),
+512-thread CTAs (two per
 SM) or 1024-thread CTAs (one per SM: the fewest resident scratch slots, so more
 of the hierarchy stays in L2, and the most threads per sample); for the mixed path
 also the number of FP32 V-cycles per FP64 defect (1, 2, 3, 4, 6).  Each
 candidate solves a probe batch of the same grid and precision (fresh seeded
-fields, one time step) timed with CUDA events.  The probe is the production
+fields, two time steps) timed with CUDA events.  The probe is the production
 batch itself, up to 64 samples per SM: the persistent kernel balances samples
 of unequal cost through its queue, so a probe with only a few samples per CTA
 is set by its slowest samples and misranks the shapes.  The fastest candidate
@@ -75,7 +76,7 @@ def source(problem, nsamples, device=0):
     return "shipped" if key in _load(SHIPPED) else "measure"
 
 
-def tune(problem, nsamples, device=0, force=False, probe_steps=1, verbose=False, shipped=True):
+def tune(problem, nsamples, device=0, force=False, probe_steps=2, verbose=False, shipped=True):
     """Return (block_threads, mixed_inner) for this grid/precision/batch and
     apply it to the device's context; measures and caches when neither the
     user cache nor (with shipped=True) the package's defaults hold the key."""
@@ -106,7 +107,7 @@ def tune(problem, nsamples, device=0, force=False, probe_steps=1, verbose=False,
     inners = [1, 2, 3, 4, 6] if problem.precision else [0]
     timings = {}
     stream = torch.cuda.current_stream(dev)
-    for bt in (256, 512, 1024):
+    for bt in (128, 256, 512, 1024):
         for mi in inners:
             R.set_tuning(bt, mi, device)
             solve(min(S, 8))
@@ -150,7 +151,7 @@ def check(problem, nsamples, device=0, steps=None, verbose=False):
     stream = torch.cuda.current_stream(dev)
     ms = {}
     try:
-        for bt in (256, 512, 1024):
+        for bt in (128, 256, 512, 1024):
             for mi in inners:
                 R.set_tuning(bt, mi, device)
                 solve(min(nsamples, 8))

@@ -13,7 +13,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "librichards.so")
-SOURCES = ["api.cu", "solver.cu", "fused.cu", "fused_vg.cu", "fields.cu", "mlmc.cu", "adjoint.cu"]
+SOURCES = ["api.cu", "solver.cu", "fused.cu", "fused_g64.cu", "fused_g32.cu", "fused_vg64.cu", "fused_vg32.cu",
+           "fused_adj64.cu", "fused_adj32.cu", "fields.cu", "mlmc.cu", "adjoint.cu"]
 HEADERS = [os.path.join(CSRC, "rich_internal.cuh"), os.path.join(CSRC, "fused_kernel.cuh"),
            os.path.join(ROOT, "include", "richards.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -43,6 +44,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if verbose:
             sys.stdout.write(r.stdout + r.stderr)
 
+    # longest translation units first (the kernel instantiations)
+    jobs.sort(key=lambda c: 0 if "fused_" in c[-3] else 1)
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         list(ex.map(run, jobs))
     objs = [os.path.join(BUILD, s.replace(".cu", ".o")) for s in SOURCES]

@@ -19,7 +19,8 @@ size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 // which the direct solve assembles); then the corrections dp of as many of the other levels
 // (coarsest first) as fit the budget of the launch shape (one 1024-thread CTA
 // per SM may use ~220 KB, two 512-thread CTAs ~104 KB each, four 256-thread
-// CTAs ~50 KB each), so that the Gauss-Seidel neighbour reads of those levels
+// CTAs ~50 KB each, eight 128-thread CTAs ~24 KB each), so that the
+// Gauss-Seidel neighbour reads of those levels
 // stay on chip; levels that do not fit keep dp in the slot.  Results do not
 // depend on where an array lives.
 constexpr int WARP_CELLS = 256;
@@ -30,7 +31,7 @@ static void plan_smem(FParams& P, int nt) {
     const size_t nnc = (size_t)P.nx[c] * P.nz[c];
     auto al16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
     size_t off = al16(nnc * (nnc + 1) * w);
-    const size_t budget = nt == 1024 ? 220 * 1024 : nt == 512 ? 104 * 1024 : 50 * 1024;
+    const size_t budget = nt == 1024 ? 220 * 1024 : nt == 512 ? 104 * 1024 : nt == 256 ? 50 * 1024 : 24 * 1024;
     for (int l = 0; l < MAXL; ++l) {
         P.osm[l] = -1;
         for (int k = 0; k < N64; ++k) P.s64[l][k] = -1;
@@ -125,47 +126,25 @@ static int fused_setup(const rich_problem_t* pb, int S, FParams& P, int ckpt_eve
 
 static size_t fused_smem(const FParams& P) { return (size_t)P.smem_bytes; }
 
-// block shapes the fused kernel is built for: 256 threads (four resident CTAs
-// per SM at 64 registers: small grids, where a CTA-wide barrier per half-sweep
-// dominates), 512 (two) or 1024 (one; the fewest resident scratch slots)
-// (and, per shape, the V-cycle and the gamma >= 2 cycle instantiations)
-// (the van Genuchten-Mualem instantiations live in fused_vg.cu)
-template <int NT, bool WC>
-static int occ_nt(const FParams& P, size_t smem, int* occ) {
-    if (P.mixed) {
-        if (int e = allow_dyn_smem((const void*)k_fused<float, NT, WC, 0>, smem)) return e;
-        RICH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_fused<float, NT, WC, 0>, NT, smem));
-    } else {
-        if (int e = allow_dyn_smem((const void*)k_fused<double, NT, WC, 0>, smem)) return e;
-        RICH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_fused<double, NT, WC, 0>, NT, smem));
-    }
-    if (*occ < 1) *occ = 1;
-    return 0;
-}
-
+// the fused kernel's instantiations live in one translation unit per (cycle
+// precision, closure): fused_g64.cu, fused_g32.cu, fused_vg64.cu, fused_vg32.cu
 static int fused_occupancy(const FParams& P, size_t smem, int nt, int* occ) {
-    if (P.closure == RICH_VAN_GENUCHTEN) return rich_vg_occupancy(P, smem, nt, occ);
-    const bool wc = P.gamma > 1;
-    if (nt == 1024) return wc ? occ_nt<1024, true>(P, smem, occ) : occ_nt<1024, false>(P, smem, occ);
-    if (nt == 256) return wc ? occ_nt<256, true>(P, smem, occ) : occ_nt<256, false>(P, smem, occ);
-    return wc ? occ_nt<512, true>(P, smem, occ) : occ_nt<512, false>(P, smem, occ);
-}
-
-template <int NT, bool WC>
-static void launch_nt(const FParams& P, int grid, size_t smem, cudaStream_t st) {
-    if (P.mixed) k_fused<float, NT, WC, 0><<<grid, NT, smem, st>>>(P);
-    else k_fused<double, NT, WC, 0><<<grid, NT, smem, st>>>(P);
+    if (P.closure == RICH_VAN_GENUCHTEN)
+        return P.mixed ? rich_occ_vg32(P, smem, nt, occ) : rich_occ_vg64(P, smem, nt, occ);
+    return P.mixed ? rich_occ_g32(P, smem, nt, occ) : rich_occ_g64(P, smem, nt, occ);
 }
 
 static int fused_launch(const FParams& P, int grid, size_t smem, int nt, cudaStream_t st) {
     RICH_CUDA(cudaMemsetAsync(P.queue, 0, sizeof(int), st));
     rich_count_launch();
-    const bool wc = P.gamma > 1;
-    if (P.closure == RICH_VAN_GENUCHTEN) rich_vg_launch(P, grid, smem, nt, st);
-    else if (nt == 1024) { if (wc) launch_nt<1024, true>(P, grid, smem, st); else launch_nt<1024, false>(P, grid, smem, st); }
-    else if (nt == 256) { if (wc) launch_nt<256, true>(P, grid, smem, st); else launch_nt<256, false>(P, grid, smem, st); }
-    else if (wc) launch_nt<512, true>(P, grid, smem, st);
-    else launch_nt<512, false>(P, grid, smem, st);
+    if (P.closure == RICH_VAN_GENUCHTEN) {
+        if (P.mixed) rich_launch_vg32(P, grid, smem, nt, st);
+        else rich_launch_vg64(P, grid, smem, nt, st);
+    } else if (P.mixed) {
+        rich_launch_g32(P, grid, smem, nt, st);
+    } else {
+        rich_launch_g64(P, grid, smem, nt, st);
+    }
     RICH_CUDA(cudaGetLastError());
     return 0;
 }
@@ -178,7 +157,8 @@ int rich_solve_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const doubl
     rich_samplebuf& w = ctx->sb;
     FParams P;
     if (pb->closure == RICH_VAN_GENUCHTEN && (!soil || !soil->n)) return RICH_ERR_INVALID;
-    const int nt = (ctx->tune_threads == 1024 || ctx->tune_threads == 256) ? ctx->tune_threads : 512;
+    const int nt = (ctx->tune_threads == 1024 || ctx->tune_threads == 256 || ctx->tune_threads == 128)
+                       ? ctx->tune_threads : 512;
     if (int e = fused_setup(pb, S, P)) return e;
     plan_smem(P, nt);
     if (soil) {
@@ -230,8 +210,7 @@ int rich_adjoint_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const dou
     P.mixed_inner = ctx->tune_mixed_inner > 0 ? ctx->tune_mixed_inner : MIXED_INNER_DEFAULT;
     const size_t smem = fused_smem(P);
     int occ = 0;
-    const void* kern = P.mixed ? (P.gamma > 1 ? (const void*)k_adjoint<float, true> : (const void*)k_adjoint<float, false>)
-                               : (P.gamma > 1 ? (const void*)k_adjoint<double, true> : (const void*)k_adjoint<double, false>);
+    const void* kern = P.mixed ? rich_adjoint_kernel32(P.gamma > 1) : rich_adjoint_kernel64(P.gamma > 1);
     if (int e = allow_dyn_smem(kern, smem)) return e;
     RICH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 512, smem));
     occ = std::max(occ, 1);
@@ -252,11 +231,8 @@ int rich_adjoint_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const dou
     RICH_CUDA(cudaMemsetAsync(P.queue, 0, sizeof(int), st));
     rich_count_launch();
     rich_prof_begin(ctx, st);
-    if (P.mixed) {
-        if (P.gamma > 1) k_adjoint<float, true><<<grid, 512, smem, st>>>(P);
-        else k_adjoint<float, false><<<grid, 512, smem, st>>>(P);
-    } else if (P.gamma > 1) k_adjoint<double, true><<<grid, 512, smem, st>>>(P);
-    else k_adjoint<double, false><<<grid, 512, smem, st>>>(P);
+    if (P.mixed) rich_adjoint_launch32(P, grid, smem, st);
+    else rich_adjoint_launch64(P, grid, smem, st);
     rich_prof_end(ctx, st, 0.0, 0.0);
     RICH_CUDA(cudaGetLastError());
     return 0;

@@ -119,9 +119,24 @@ inline int allow_dyn_smem(const void* kernel, size_t bytes) {
     return 0;
 }
 
-// launch shapes of the van Genuchten-Mualem instantiations (fused_vg.cu)
-int rich_vg_occupancy(const FParams& P, size_t smem, int nt, int* occ);
-void rich_vg_launch(const FParams& P, int grid, size_t smem, int nt, cudaStream_t st);
+// Occupancy query and launch of the fused kernel's instantiations, one
+// translation unit per (cycle precision, closure) so that they compile in
+// parallel: fused_g64.cu (FP64, Gardner), fused_g32.cu (mixed, Gardner),
+// fused_vg64.cu, fused_vg32.cu (van Genuchten-Mualem).
+int rich_occ_g64(const FParams& P, size_t smem, int nt, int* occ);
+int rich_occ_g32(const FParams& P, size_t smem, int nt, int* occ);
+int rich_occ_vg64(const FParams& P, size_t smem, int nt, int* occ);
+int rich_occ_vg32(const FParams& P, size_t smem, int nt, int* occ);
+void rich_launch_g64(const FParams& P, int grid, size_t smem, int nt, cudaStream_t st);
+void rich_launch_g32(const FParams& P, int grid, size_t smem, int nt, cudaStream_t st);
+void rich_launch_vg64(const FParams& P, int grid, size_t smem, int nt, cudaStream_t st);
+void rich_launch_vg32(const FParams& P, int grid, size_t smem, int nt, cudaStream_t st);
+// the adjoint kernel's instantiations (fused_adj64.cu, fused_adj32.cu): the
+// kernel's address (occupancy queries) and its launch with 512 threads
+const void* rich_adjoint_kernel64(bool wcycle);
+const void* rich_adjoint_kernel32(bool wcycle);
+void rich_adjoint_launch64(const FParams& P, int grid, size_t smem, cudaStream_t st);
+void rich_adjoint_launch32(const FParams& P, int grid, size_t smem, cudaStream_t st);
 
 }  // namespace rich_fused
 
@@ -1206,7 +1221,7 @@ __device__ __forceinline__ void init_levels(const FParams& P, char* slot, unsign
 }
 
 template <typename TM, int NT, bool WC, int CL>
-__global__ void __launch_bounds__(NT, NT <= 256 ? 4 : NT == 512 ? 2 : 1)
+__global__ void __launch_bounds__(NT, NT <= 128 ? 8 : NT <= 256 ? 4 : NT == 512 ? 2 : 1)
 k_fused(const FParams P) {
     extern __shared__ unsigned char smraw[];
     __shared__ unsigned long long red[33];
@@ -1361,4 +1376,43 @@ k_adjoint(const FParams P) {
     }
 }
 
+}  // namespace
+
+namespace {
+// launch shapes of one (cycle precision, closure) pair: 128, 256, 512 or 1024
+// threads, each with the V-cycle and the gamma >= 2 cycle instantiation
+template <typename TM, int NT, bool WC, int CL>
+int occ_one(const FParams& P, size_t smem, int* occ) {
+    if (int e = allow_dyn_smem((const void*)k_fused<TM, NT, WC, CL>, smem)) return e;
+    RICH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_fused<TM, NT, WC, CL>, NT, smem));
+    if (*occ < 1) *occ = 1;
+    return 0;
+}
+
+template <typename TM, int CL>
+int occ_shapes(const FParams& P, size_t smem, int nt, int* occ) {
+    const bool wc = P.gamma > 1;
+    if (nt == 1024) return wc ? occ_one<TM, 1024, true, CL>(P, smem, occ) : occ_one<TM, 1024, false, CL>(P, smem, occ);
+    if (nt == 256) return wc ? occ_one<TM, 256, true, CL>(P, smem, occ) : occ_one<TM, 256, false, CL>(P, smem, occ);
+    if (nt == 128) return wc ? occ_one<TM, 128, true, CL>(P, smem, occ) : occ_one<TM, 128, false, CL>(P, smem, occ);
+    return wc ? occ_one<TM, 512, true, CL>(P, smem, occ) : occ_one<TM, 512, false, CL>(P, smem, occ);
+}
+
+template <typename TM, int CL>
+void launch_shapes(const FParams& P, int grid, size_t smem, int nt, cudaStream_t st) {
+    const bool wc = P.gamma > 1;
+    if (nt == 1024) {
+        if (wc) k_fused<TM, 1024, true, CL><<<grid, 1024, smem, st>>>(P);
+        else k_fused<TM, 1024, false, CL><<<grid, 1024, smem, st>>>(P);
+    } else if (nt == 256) {
+        if (wc) k_fused<TM, 256, true, CL><<<grid, 256, smem, st>>>(P);
+        else k_fused<TM, 256, false, CL><<<grid, 256, smem, st>>>(P);
+    } else if (nt == 128) {
+        if (wc) k_fused<TM, 128, true, CL><<<grid, 128, smem, st>>>(P);
+        else k_fused<TM, 128, false, CL><<<grid, 128, smem, st>>>(P);
+    } else {
+        if (wc) k_fused<TM, 512, true, CL><<<grid, 512, smem, st>>>(P);
+        else k_fused<TM, 512, false, CL><<<grid, 512, smem, st>>>(P);
+    }
+}
 }  // namespace

@@ -81,12 +81,19 @@ int rich_solve_device(rich_ctx* ctx, const rich_problem_t* pb, int S, const doub
         if (hs[s] == RICH_PICARD_MAXIT || hs[s] == RICH_NONFINITE) acc.failed++;
     }
     acc.cell_vcycles = acc.mg_cycles * (int64_t)pb->nx * pb->nz;
-    // algorithmic work of the fused launch (for the live roofline): per fine cell
-    // and V-cycle 74 FLOP and 16.7 words (two fused passes per level, hierarchy
-    // factor 4/3); per Picard iteration 56 FLOP and 10 FP64 words per cell
+    // algorithmic work of the fused launch (for the live roofline), per fine
+    // cell.  V-cycle (V(2,2), FMA = 2 FLOP): on the finest level 2 x 2 sweeps of
+    // 8 FLOP per cell (4 FMA per Gauss-Seidel update) = 32, the red-only
+    // residual restriction 23 per coarse cell = 5.75, prolongation 1: 38.75;
+    // each coarser level the same less the seeded first red half-sweep (4):
+    // 34.75, hierarchy factor 1/3; the red-only stopping norm 5: 55 FLOP.
+    // Picard iteration: closure 6 (+ one exp), harmonic faces 8, mixed-form
+    // residual 20, scaled coefficients 6, coarse operators ~26 per coarse cell
+    // (8.7), update 1: 51 FLOP.  Bytes: the two-fused-passes model, 16.7 words
+    // per cell and V-cycle and 10 FP64 words per cell and Picard iteration.
     const double nc = (double)pb->nx * pb->nz;
     const double w8 = pb->precision == RICH_MIXED ? 4.0 : 8.0;
-    const double flops = nc * (74.0 * acc.mg_cycles + 56.0 * acc.picard_iters);
+    const double flops = nc * (55.0 * acc.mg_cycles + 51.0 * acc.picard_iters);
     const double bytes = nc * (16.7 * w8 * acc.mg_cycles + 10.0 * 8.0 * acc.picard_iters);
     rich_prof_amend(ctx, bytes, flops);
     acc.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
