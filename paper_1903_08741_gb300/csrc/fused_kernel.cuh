@@ -595,19 +595,21 @@ __device__ __forceinline__ unsigned long long resid_norm(const Lv<T>& L, bool re
 // m = 1 - 1/n and an = (a|p|)^n: S = (1 + an)^-m, K_rw = S^(1/2) (1 - (an /
 // (1 + an))^m)^2 (1 - S^(1/m) = an/(1 + an) exactly) and dS/dp = m n S an /
 // ((1 + an) |p|), the Eq. sc_van capacity divided by theta_s - theta_r.  In
-// logarithms: l = log(a|p|), an = exp(n l), S = exp(-m log1p(an)) and
-// (an / (1 + an))^m = exp(m (n l - log1p(an))).
+// logarithms: an = exp(n log(a|p|)), S = exp(-m log1p(an)), and since
+// m n = n - 1, (an / (1 + an))^m = an^m S = (an / (a|p|)) S: one exp fewer
+// than exp(m (n log(a|p|) - log1p(an))), and no cancellation between the two
+// logarithms in the dry limit.
 __device__ __forceinline__ double vg_sat(double a, double n, double m, double p) {
     return exp(-m * log1p(exp(n * log(-a * p))));
 }
 
 __device__ __forceinline__ void vg_eval(double a, double n, double m, double p, double& S, double& krw,
                                         double& dS) {
-    const double nl = n * log(-a * p);
-    const double an = exp(nl);
+    const double ap = -a * p;
+    const double an = exp(n * log(ap));
     const double l1 = log1p(an);
     S = exp(-m * l1);
-    const double b = 1.0 - exp(m * (nl - l1));
+    const double b = 1.0 - S * (an / ap);
     krw = sqrt(S) * b * b;
     dS = m * n * S * an / ((1.0 + an) * (-p));
 }

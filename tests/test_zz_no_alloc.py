@@ -50,6 +50,30 @@ def test_noalloc_matches_solve_batch_twice(R):
         assert np.all(np.isnan(q[(s_ref == 1) | (s_ref == 3)]))
 
 
+@pytest.mark.parametrize("n,prec", [(32, "mixed"), (128, "fp64")])
+def test_noalloc_other_precisions_and_grids(R, n, prec):
+    """Mixed precision (FP32 cycles, QoI within the mixed path's 1e-6) and a
+    128^2 FP64 grid, whose 2.9 MiB slots let only five CTAs share the array
+    (bit-identical results to the regular entry point at any CTA count)."""
+    from tests.inputs import PHYSICS, SOLVER
+    dev = torch.device("cuda:0")
+    kw = dict(precision=R.MIXED) if prec == "mixed" else {}
+    pb = R.Problem(nx=n, nz=n, nsteps=2, dt=0.005, **PHYSICS, **SOLVER, **kw)
+    S = 12
+    lk, al = O.sample_fields(n, n, S, seed=31)
+    lk_d, al_d = torch.from_numpy(lk).to(dev), torch.from_numpy(al).to(dev)
+    q_ref, _, s_ref, _, _ = R.solve_batch(pb, lk_d, al_d)
+    for call in range(2):
+        q, s = R.solve_batch_noalloc(pb, lk_d, al_d)
+        torch.cuda.synchronize(dev)
+        ok = (s_ref == 0) & (s == 0)
+        assert ok.sum() >= S // 2
+        if prec == "mixed":
+            assert (torch.abs(q[ok] - q_ref[ok]) / torch.abs(q_ref[ok])).max() <= 1e-6, call
+        else:
+            assert torch.equal(s, s_ref) and torch.equal(q[ok], q_ref[ok]), call
+
+
 def test_noalloc_rejects_oversized_grid(R):
     from tests.inputs import PHYSICS, SOLVER
     dev = torch.device("cuda:0")
