@@ -548,6 +548,8 @@ def run_adjoint(args):
     xi = torch.from_numpy(np.random.default_rng(0).normal(size=(S, nkl))).to(dev)
     _, al = R.sample_fields(n, n, S, R.FieldModel(seed=0))
     pb = R.Problem(nx=n, nz=n, nsteps=steps, dt=dt, precision=prec, **PHYS)
+    method = {"bicgstab": R.BICGSTAB, "gmres": R.GMRES, "dc": R.DEFECT_CORRECTION}[args.adjoint_method]
+    R.set_adjoint_method(method)
     for k in range(args.warmup):
         small = R.Problem(nx=n, nz=n, nsteps=2, dt=dt, precision=prec, **PHYS)
         R.solve_batch_adjoint(small, Bd, xi[:8].contiguous(), al[:8].contiguous(), ckpt_every=10)
@@ -573,12 +575,13 @@ def run_adjoint(args):
         "dtype": "f64" if prec == R.FP64 else "f32-in-f64", "data": "synthetic",
         "config": {"workload": f"adjoint{n}: {n}x{n} grid, {S} samples, {steps} steps dt={dt}, "
                                f"ln Ks = 128-mode KL (exp. cov. 0.2), checkpoint every 10 steps",
+                   "jt_solver": args.adjoint_method,
                    "kl_variance_captured": float(lam.sum() / (n * n))},
         "clocks": clk, "gpu_launches": launches,
         "failed_samples": int(((stv == 1) | (stv == 3)).sum()),
         "adjoint_linear_solve_limit_hit": int((stv == 2).sum()),
         "picard_iters_per_sample": stats.picard_iters / S,
-        "adjoint_outer_iters_per_sample": stats.mg_cycles / S,
+        "adjoint_preconditioner_applications_per_sample": stats.mg_cycles / S,
         "mean_qoi": float(np.nanmean(q.cpu().numpy())),
         "mean_abs_grad": float(np.nanmean(np.abs(dq.cpu().numpy()))),
     }
@@ -975,6 +978,8 @@ def main():
                                                                "tunecheck"],
                     default="mc128")
     ap.add_argument("--check", action="store_true", help="adjoint workload: finite-difference check")
+    ap.add_argument("--adjoint-method", choices=["bicgstab", "gmres", "dc"], default="bicgstab",
+                    help="adjoint workload: solver of the J^T systems")
     ap.add_argument("--adaptive-eps", type=float, default=0.0, help="mlmc5: also run Algorithm PC_MLMC to this RMSE")
     ap.add_argument("--coupling", type=int, default=0, help="MLMC field coupling (0 exact, 1 level grid)")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")

@@ -384,8 +384,10 @@ int rich_solve_batch_adjoint(rich_ctx_t ctx, const rich_problem_t* pb, int32_t n
 
 /* Solver of the adjoint's J^T systems in this context's rich_solve_batch_adjoint
  * calls: 1 (default) BiCGStab (van der Vorst 1992) right-preconditioned with
- * the CCMG cycles of the Picard operator, stopped on the true residual; 0 the
- * plain defect correction lam += M^{-1}(rhs - J^T lam).  Both stop at a relative
+ * the CCMG cycles of the Picard operator, stopped on the true residual; 2
+ * restarted GMRES(12) (Saad & Schultz 1986) with the same preconditioner,
+ * stopped on the true residual; 0 the plain defect correction
+ * lam += M^{-1}(rhs - J^T lam).  Both stop at a relative
  * residual of 1e-11 or 400 preconditioner applications (then RICH_MG_MAXIT);
  * rich_stats_t.mg_cycles counts the applications.  RICH_ERR_INVALID otherwise. */
 int rich_set_adjoint_method(rich_ctx_t ctx, int32_t method);

@@ -517,11 +517,11 @@ def profile_read(device=0):
     return ms.value, n.value, b.value, f.value
 
 
-BICGSTAB, DEFECT_CORRECTION = 1, 0
+BICGSTAB, DEFECT_CORRECTION, GMRES = 1, 0, 2
 
 
 def set_adjoint_method(method=BICGSTAB, device=0):
-    """J^T solver of the device's adjoint solves: BICGSTAB (default) or DEFECT_CORRECTION."""
+    """J^T solver of the device's adjoint solves: BICGSTAB (default), GMRES or DEFECT_CORRECTION."""
     _check(lib().rich_set_adjoint_method(context(device), method))
 
 

@@ -112,7 +112,7 @@ extern "C" int rich_solve_batch_adjoint(rich_ctx_t ctx, const rich_problem_t* pb
 }
 
 extern "C" int rich_set_adjoint_method(rich_ctx_t ctx, int32_t method) {
-    if (!ctx || method < 0 || method > 1) return RICH_ERR_INVALID;
+    if (!ctx || method < 0 || method > 2) return RICH_ERR_INVALID;
     ctx->adj_method = method;
     return 0;
 }

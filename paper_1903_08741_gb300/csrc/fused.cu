@@ -113,6 +113,7 @@ static int fused_setup(const rich_problem_t* pb, int S, FParams& P, int ckpt_eve
         long long* adj[] = {&P.o_lam, &P.o_rhs, &P.o_r, &P.o_dE, &P.o_dW, &P.o_dN, &P.o_dS, &P.o_dg, &P.o_g,
                             &P.o_rh, &P.o_pk, &P.o_v, &P.o_t, &P.o_ph, &P.o_sh};
         for (long long* o : adj) { *o = (long long)off; off = al256(off + nc8); }
+        P.o_kry = (long long)off; off = al256(off + nc8 * (2 * ADJ_M + 1));
     }
     P.slot_bytes = (long long)off;
     P.nsteps = pb->nsteps; P.picard_maxit = pb->picard_maxit; P.mg_maxit = pb->mg_maxit;

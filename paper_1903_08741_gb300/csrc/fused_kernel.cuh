@@ -47,6 +47,7 @@ constexpr unsigned long long ABS_MASK = 0x7FFFFFFFFFFFFFFFull;
 constexpr unsigned long long INF_BITS = 0x7FF0000000000000ull;
 constexpr int MAXL = RICH_MAX_LEVELS;
 constexpr int MIXED_INNER_DEFAULT = 2;   // FP32 V-cycles per FP64 defect evaluation
+constexpr int ADJ_M = 12;                // GMRES restart length of the adjoint's J^T solves
 
 // FP64 unscaled operator (all levels): faces, mass term, diagonal, Dirichlet faces
 enum { A_TX, A_TZ, A_CDT, A_D, A_TBT, A_TBB, N64 };
@@ -87,8 +88,9 @@ struct FParams {
     int ckpt_every, adj_maxit, adj_inner;
     double adj_tol;
     long long o_ckpt, o_seg, o_lam, o_rhs, o_r, o_dE, o_dW, o_dN, o_dS, o_dg, o_g;
-    int adj_method;             // J^T solver: 0 defect correction, 1 BiCGStab
+    int adj_method;             // J^T solver: 0 defect correction, 1 BiCGStab, 2 GMRES(ADJ_M)
     long long o_rh, o_pk, o_v, o_t, o_ph, o_sh;   // BiCGStab vectors
+    long long o_kry;                              // GMRES: ADJ_M + 1 Krylov and ADJ_M preconditioned vectors
     double* g_out;
     // closure 1 (van Genuchten-Mualem): per-cell n, theta_s, theta_r inputs
     // (theta arrays may be null: the problem's constants), continuation
@@ -1160,6 +1162,114 @@ struct Cta {
         return P.adj_maxit + 1;
     }
 
+    // J^T lam = rhs by restarted GMRES(ADJ_M) (Saad & Schultz 1986), right-
+    // preconditioned with the CCMG cycles of A, modified Gram-Schmidt, Givens
+    // rotations; each cycle ends with the update lam += Z y and the TRUE
+    // residual ||rhs - J^T lam||_inf <= adj_tol ||rhs||_inf decides.  The
+    // Hessenberg matrix and rotations are computed by every thread from the
+    // same block sums (uniform control flow).  Returns the number of
+    // preconditioner applications (adj_maxit + 1 when not converged).
+    __device__ int adj_solve_gmres(const double* dE, const double* dW, const double* dN, const double* dS,
+                                   const double* dg, const double* rhs, double* lam, double* kry) {
+        // Hessenberg matrix, rotations, right-hand side and solution of the
+        // small least-squares problem: one copy per CTA, updated by thread 0
+        __shared__ double sH[ADJ_M + 1][ADJ_M], scs[ADJ_M], ssn[ADJ_M], sg[ADJ_M + 1], sy[ADJ_M];
+        double* redd = reinterpret_cast<double*>(red);
+        double* V = kry;                                  // [ADJ_M + 1][nc]
+        double* Z = kry + (size_t)(ADJ_M + 1) * nc;       // [ADJ_M][nc]
+        unsigned long long m = 0;
+        for (int q = tid; q < nc; q += nt) {
+            lam[q] = 0.0;
+            unsigned long long b = abs_bits(rhs[q]);
+            m = b > m ? b : m;
+        }
+        const unsigned long long b0 = block_max(m, red);
+        if (b0 == 0) return 0;
+        const double target = P.adj_tol * __longlong_as_double((long long)b0);
+        int apps = 0;
+        while (apps < P.adj_maxit) {
+            // r = rhs - J^T lam (the true residual), its inf-norm and 2-norm
+            unsigned long long rm = 0;
+            double s2 = 0.0;
+            for (int q = tid; q < nc; q += nt) {
+                const double rv = rhs[q] - jt_apply(dE, dW, dN, dS, dg, lam, q);
+                V[q] = rv;
+                s2 += rv * rv;
+                unsigned long long b = abs_bits(rv);
+                rm = b > rm ? b : rm;
+            }
+            const unsigned long long rb = block_max(rm, red);
+            const double beta = sqrt(block_sum(s2, redd));
+            if (rb > INF_BITS - 1 || !(beta > 0.0)) break;
+            if (__longlong_as_double((long long)rb) <= target) return apps;
+            const double ib = 1.0 / beta;
+            for (int q = tid; q < nc; q += nt) V[q] *= ib;
+            if (tid == 0) {
+                for (int i = 0; i <= ADJ_M; ++i) sg[i] = 0.0;
+                sg[0] = beta;
+            }
+            __syncthreads();
+            int k = 0;
+            for (; k < ADJ_M && apps < P.adj_maxit; ++k) {
+                double* vk = V + (size_t)k * nc;
+                double* zk = Z + (size_t)k * nc;
+                double* w = V + (size_t)(k + 1) * nc;
+                precond(vk, zk); ++apps;
+                jt_vec(dE, dW, dN, dS, dg, zk, w);
+                for (int i = 0; i <= k; ++i) {                  // modified Gram-Schmidt
+                    const double* vi = V + (size_t)i * nc;
+                    double d = 0.0;
+                    for (int q = tid; q < nc; q += nt) d += w[q] * vi[q];
+                    const double h = block_sum(d, redd);
+                    if (tid == 0) sH[i][k] = h;
+                    for (int q = tid; q < nc; q += nt) w[q] -= h * vi[q];
+                    __syncthreads();
+                }
+                double d = 0.0;
+                for (int q = tid; q < nc; q += nt) d += w[q] * w[q];
+                const double hn = sqrt(block_sum(d, redd));
+                if (hn > 0.0) {
+                    const double ih = 1.0 / hn;
+                    for (int q = tid; q < nc; q += nt) w[q] *= ih;
+                }
+                if (tid == 0) {                                  // rotations on column k
+                    sH[k + 1][k] = hn;
+                    for (int i = 0; i < k; ++i) {
+                        const double a = sH[i][k], b = sH[i + 1][k];
+                        sH[i][k] = scs[i] * a + ssn[i] * b;
+                        sH[i + 1][k] = -ssn[i] * a + scs[i] * b;
+                    }
+                    const double a = sH[k][k], b = sH[k + 1][k];
+                    const double rr = sqrt(a * a + b * b);
+                    scs[k] = rr > 0.0 ? a / rr : 1.0;
+                    ssn[k] = rr > 0.0 ? b / rr : 0.0;
+                    sH[k][k] = rr; sH[k + 1][k] = 0.0;
+                    sg[k + 1] = -ssn[k] * sg[k];
+                    sg[k] = scs[k] * sg[k];
+                }
+                __syncthreads();
+                const double gk = sg[k + 1];
+                // the 2-norm estimate bounds the inf-norm: the cycle may stop early
+                if (!(hn > 0.0) || !isfinite(gk) || fabs(gk) <= target) { ++k; break; }
+            }
+            if (tid == 0) {                                      // y = H^{-1} g, k x k upper triangular
+                for (int i = k - 1; i >= 0; --i) {
+                    double t = sg[i];
+                    for (int j = i + 1; j < k; ++j) t -= sH[i][j] * sy[j];
+                    sy[i] = sH[i][i] != 0.0 ? t / sH[i][i] : 0.0;
+                }
+            }
+            __syncthreads();
+            for (int q = tid; q < nc; q += nt) {
+                double acc = lam[q];
+                for (int j = 0; j < k; ++j) acc += sy[j] * Z[(size_t)j * nc + q];
+                lam[q] = acc;
+            }
+            __syncthreads();
+        }
+        return true_resid_ok(dE, dW, dN, dS, dg, rhs, lam, target) ? apps : P.adj_maxit + 1;
+    }
+
     // ||rhs - J^T lam||_inf <= target (the true residual)
     __device__ bool true_resid_ok(const double* dE, const double* dW, const double* dN, const double* dS,
                                   const double* dg, const double* rhs, const double* lam, double target) {
@@ -1354,7 +1464,9 @@ k_adjoint(const FParams P) {
                         __syncthreads();
                     }
                     C.adj_prepare(dE, dW, dN, dS, dg);
-                    const int its = P.adj_method == 1
+                    const int its = P.adj_method == 2
+                        ? C.adj_solve_gmres(dE, dW, dN, dS, dg, rhs, lam, (double*)(slot + P.o_kry))
+                        : P.adj_method == 1
                         ? C.adj_solve_bicgstab(dE, dW, dN, dS, dg, rhs, lam, r, (double*)(slot + P.o_rh),
                                                (double*)(slot + P.o_pk), (double*)(slot + P.o_v),
                                                (double*)(slot + P.o_t), (double*)(slot + P.o_ph),

@@ -134,26 +134,29 @@ def test_autograd_forward_only_without_grad(R):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_bicgstab_and_defect_correction_agree(R, prec):
-    """Both J^T solvers stop at a true relative residual of 1e-11, so their
-    gradients agree to the 1e-7 the oracle comparison uses; BiCGStab needs fewer preconditioner
-    applications (rich_stats_t.mg_cycles counts them) and none hits the cap."""
+def test_krylov_solvers_and_defect_correction_agree(R, prec):
+    """The three J^T solvers stop at a true relative residual of 1e-11, so their
+    gradients agree to the 1e-7 the oracle comparison uses; BiCGStab and
+    GMRES need fewer preconditioner applications than defect correction
+    (rich_stats_t.mg_cycles counts them) and none hits the cap."""
     n, nkl, S, steps, dt = 64, 6, 4, 4, 0.002
     B, xi, al, (Bd, xid, ald) = setup_case(R, n, nkl, S, 13)
     kw = {} if prec == "fp64" else dict(precision=R.MIXED)
     pb = gpu_pb(R, n, steps, dt, **kw)
     out = {}
     try:
-        for m in (R.DEFECT_CORRECTION, R.BICGSTAB):
+        for m in (R.DEFECT_CORRECTION, R.BICGSTAB, R.GMRES):
             R.set_adjoint_method(m)
             out[m] = R.solve_batch_adjoint(pb, Bd, xid, ald, ckpt_every=2)
     finally:
         R.set_adjoint_method(R.BICGSTAB)
-    (qd, dqd, _, sd, std, _), (qb, dqb, _, sb, stb, _) = out[R.DEFECT_CORRECTION], out[R.BICGSTAB]
-    ok = (sd.cpu().numpy() == 0) & (sb.cpu().numpy() == 0)
-    assert ok.sum() >= 3
-    assert torch.equal(qd[ok], qb[ok])
-    a, b = dqd.cpu().numpy()[ok], dqb.cpu().numpy()[ok]
-    assert np.abs(a - b).max() <= 1e-7 * np.abs(a).max()
-    assert stb.mg_cycles < std.mg_cycles
-    assert not (sb.cpu().numpy() == R.MG_MAXIT).any()
+    qd, dqd, _, sd, std, _ = out[R.DEFECT_CORRECTION]
+    for m in (R.BICGSTAB, R.GMRES):
+        qk, dqk, _, sk, stk, _ = out[m]
+        ok = (sd.cpu().numpy() == 0) & (sk.cpu().numpy() == 0)
+        assert ok.sum() >= 3
+        assert torch.equal(qd[ok], qk[ok])
+        a, b = dqd.cpu().numpy()[ok], dqk.cpu().numpy()[ok]
+        assert np.abs(a - b).max() <= 1e-7 * np.abs(a).max(), m
+        assert stk.mg_cycles < std.mg_cycles, m
+        assert not (sk.cpu().numpy() == R.MG_MAXIT).any(), m

@@ -436,3 +436,18 @@ def test_block_shapes_bitwise_at_128(R):
         R.set_tuning(0, 0)
     for bt in (256, 1024):
         assert torch.equal(out[bt][1], out[512][1]) and torch.equal(out[bt][2], out[512][2])
+
+
+def test_fp64_microbenchmark_rates(R):
+    """The FP64 rate microbenchmark (the FP64 roofline's denominator): positive,
+    finite rates, FMA FLOP/s above the division and exp rates, and the FMA rate
+    below the SMs x 4 FLOP x clock ceiling of an FP64 pipe issuing two FMAs
+    per clock (GB300's rate; reaching most of it shows the chains are not
+    optimised away)."""
+    r = R.measure_fp64()
+    for k in ("dfma_flops", "div_per_s", "exp_per_s", "ms"):
+        assert np.isfinite(r[k]) and r[k] > 0, (k, r)
+    assert r["dfma_flops"] > r["div_per_s"] > 0 and r["dfma_flops"] > r["exp_per_s"]
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert r["dfma_flops"] < sms * 4 * 2.5e9
+    assert r["dfma_flops"] > 0.3 * sms * 4 * 2.07e9
