@@ -47,6 +47,8 @@ FP64_TFLOPS_NOMINAL = 1.25      # GB300 FP64 (non-tensor) nominal: 152 SMs x 2 F
 # ones captured (fused_sha()).
 TRAFFIC = {
     # (precision, block_threads): (fused_sha() of the captured sources, DRAM bytes per algorithmic byte)
+    ("fp64", 512): ("06f0e930f14ff8a6b70bd5efe0fec7ffca9193b6964b2da20cad31627185dc85", 1.9235),
+    ("mixed", 512): ("06f0e930f14ff8a6b70bd5efe0fec7ffca9193b6964b2da20cad31627185dc85", 0.7079),
 }
 
 
@@ -211,7 +213,11 @@ def run_vgmap(args):
     nf = pn[:, None, None].expand(S, n, n).contiguous()
     pb = R.Problem.infiltration(nx=n, nz=n, nsteps=steps, dt=dt, precision=prec, cycle=args.cycle)
     from paper_1903_08741_gb300 import autotune
-    block_threads, mixed_inner = autotune.tune(pb, S)
+    if args.launch:
+        block_threads, mixed_inner = (int(x) for x in args.launch.split("/"))
+        R.set_tuning(block_threads, mixed_inner)
+    else:
+        block_threads, mixed_inner = autotune.tune(pb, S)
     for _ in range(args.warmup):
         R.solve_soil(pb, lk[:1024], al[:1024], nf[:1024])
     torch.cuda.synchronize(dev)
@@ -996,7 +1002,7 @@ def main():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--launch", default="", help="mc workloads: launch shape block_threads/mixed_inner "
+    ap.add_argument("--launch", default="", help="mc and vgmap workloads: launch shape block_threads/mixed_inner "
                                                  "(e.g. 512/4) instead of the autotuner's")
     ap.add_argument("--no-extras", action="store_true",
                     help="default workload: skip the mixed-precision, MLMC and batch-1 measurements")
