@@ -77,6 +77,13 @@ struct MlmcRun {
     int NL, L, nL, B = 0;
     cudaStream_t st = nullptr;
     cudaEvent_t ev[4] = {};
+    // the coarse member of each pair is solved at the same time as the fine
+    // one, by a second context on a second stream: the two solves are
+    // independent, and a level with fewer samples than the GPU has SMs
+    // (e.g. 80 pairs at 256^2) would otherwise leave SMs idle twice
+    rich_ctx* ctx2 = nullptr;
+    cudaStream_t st2 = nullptr;
+    cudaEvent_t evc = nullptr;
     DevBuf lkf, alf, lkc, alc, qf, qc, sf, sc, acc;
     DevBuf nf, tsf, trf, ncb, tsc, trc;     // van Genuchten: n, theta_s, theta_r (fine, coarse)
     bool vg = false, thetas = false;
@@ -97,7 +104,10 @@ struct MlmcRun {
     }
     ~MlmcRun() {
         for (auto& e : ev) if (e) cudaEventDestroy(e);
+        if (evc) cudaEventDestroy(evc);
         if (st) cudaStreamDestroy(st);
+        if (st2) cudaStreamDestroy(st2);
+        if (ctx2) rich_destroy(ctx2);
     }
     int grid(int l) const { return cfg->n0 << l; }
     int steps(int l) const { return cfg->steps0 << l; }
@@ -123,7 +133,10 @@ struct MlmcRun {
 
     int init(int batch_hint) {
         RICH_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        RICH_CUDA(cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking));
         for (auto& e : ev) RICH_CUDA(cudaEventCreate(&e));
+        RICH_CUDA(cudaEventCreateWithFlags(&evc, cudaEventDisableTiming));
+        if (int e = rich_create(&ctx2, ctx->device)) return e;
         B = cfg->batch > 0 ? cfg->batch : (int)std::max<long long>(1, (1ll << 31) / (16ll * nL * nL));
         B = std::max(1, std::min(B, batch_hint));
         const size_t fine_cells = (size_t)B * nL * nL;       // worst case: level L fine member
@@ -211,18 +224,22 @@ struct MlmcRun {
         }
         RICH_CUDA(cudaEventRecord(ev[1], st));
         const rich_soil_in in_f = soil_in(l, false), in_c = soil_in(l > 0 ? l - 1 : 0, true);
-        int rc = rich_solve_device(ctx, &pf, nb, (double*)lkf.p, (double*)alf.p, ascale(l), (double*)qf.p,
-                                   nullptr, (int32_t*)sf.p, nullptr, st, vg ? &in_f : nullptr);
+        // fine member on (ctx, st); coarse member on (ctx2, st2) once the fields exist
+        if (int e2 = rich_samples_reserve(ctx, nb)) return e2;
+        int rc = rich_solve_fused(ctx, &pf, nb, (double*)lkf.p, (double*)alf.p, ascale(l), (double*)qf.p, nullptr,
+                                  (int32_t*)sf.p, st, vg ? &in_f : nullptr);
         if (rc < 0) return rc;
-        worst = rich_status_worse(worst, rc);
-        double sm_s = ctx->last_sm_seconds;
         RICH_CUDA(cudaEventRecord(ev[2], st));
         if (l > 0) {
-            rc = rich_solve_device(ctx, &pc, nb, (double*)lkc.p, (double*)alc.p, ascale(l - 1), (double*)qc.p,
-                                   nullptr, (int32_t*)sc.p, nullptr, st, vg ? &in_c : nullptr);
+            if (int e2 = rich_samples_reserve(ctx2, nb)) return e2;
+            ctx2->tune_threads = cfg->tune_threads[l - 1] ? cfg->tune_threads[l - 1] : ctx->tune_threads;
+            ctx2->tune_mixed_inner = cfg->tune_inner[l - 1] ? cfg->tune_inner[l - 1] : ctx->tune_mixed_inner;
+            RICH_CUDA(cudaStreamWaitEvent(st2, ev[1], 0));
+            rc = rich_solve_fused(ctx2, &pc, nb, (double*)lkc.p, (double*)alc.p, ascale(l - 1), (double*)qc.p,
+                                  nullptr, (int32_t*)sc.p, st2, vg ? &in_c : nullptr);
             if (rc < 0) return rc;
-            worst = rich_status_worse(worst, rc);
-            sm_s += ctx->last_sm_seconds;
+            RICH_CUDA(cudaEventRecord(evc, st2));
+            RICH_CUDA(cudaStreamWaitEvent(st, evc, 0));
         }
         e = rich_mlmc_accumulate(ctx, (double*)qf.p, l > 0 ? (double*)qc.p : nullptr, (int32_t*)sf.p,
                                  l > 0 ? (int32_t*)sc.p : nullptr, nb,
@@ -230,6 +247,19 @@ struct MlmcRun {
         if (e) return e;
         RICH_CUDA(cudaEventRecord(ev[3], st));
         RICH_CUDA(cudaEventSynchronize(ev[3]));
+        // most severe status of the batch, and the solves' SM-seconds
+        {
+            std::vector<int32_t> hs(2 * (size_t)nb, 0);
+            RICH_CUDA(cudaMemcpy(hs.data(), sf.p, 4 * (size_t)nb, cudaMemcpyDeviceToHost));
+            if (l > 0) RICH_CUDA(cudaMemcpy(hs.data() + nb, sc.p, 4 * (size_t)nb, cudaMemcpyDeviceToHost));
+            for (int32_t v : hs) worst = rich_status_worse(worst, (int)v);
+        }
+        double sm_s = 0.0, sm_c = 0.0;
+        if (int e2 = rich_sm_seconds(ctx, nb, st, &sm_s)) return e2;
+        if (l > 0) {
+            if (int e2 = rich_sm_seconds(ctx2, nb, st2, &sm_c)) return e2;
+            sm_s += sm_c;
+        }
         float a = 0, b = 0, c = 0;
         RICH_CUDA(cudaEventElapsedTime(&a, ev[0], ev[1]));
         RICH_CUDA(cudaEventElapsedTime(&b, ev[1], ev[2]));

@@ -95,6 +95,7 @@ int rich_solve_device(rich_ctx* ctx, const rich_problem_t* pb, int S, const doub
                       int32_t* status, rich_stats_t* stats, cudaStream_t st,
                       const rich_soil_in* soil = nullptr);
 int rich_count_levels(int nx, int nz);
+int rich_sm_seconds(rich_ctx* ctx, int S, cudaStream_t st, double* out);
 int rich_solve_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const double* lnKs,
                      const double* alpha, double alpha_scale, double* qoi, double* p_final,
                      int32_t* status, cudaStream_t st, const rich_soil_in* soil = nullptr);

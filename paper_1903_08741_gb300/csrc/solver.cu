@@ -50,6 +50,18 @@ int rich_stage_reserve(rich_ctx* ctx, size_t bytes) {
     return 0;
 }
 
+// SM-seconds of the context's last fused solve of S samples: each sample held
+// 1/occ of an SM for its solve time on its CTA (synchronises `st`)
+int rich_sm_seconds(rich_ctx* ctx, int S, cudaStream_t st, double* out) {
+    std::vector<int64_t> ht(std::max(S, 1));
+    if (S > 0) RICH_CUDA(cudaMemcpyAsync(ht.data(), ctx->sb.t_ns, 8 * (size_t)S, cudaMemcpyDeviceToHost, st));
+    RICH_CUDA(cudaStreamSynchronize(st));
+    double cta_ns = 0;
+    for (int s = 0; s < S; ++s) cta_ns += (double)ht[s];
+    *out = 1e-9 * cta_ns / std::max(ctx->sb.last_occ, 1);
+    return 0;
+}
+
 int rich_solve_device(rich_ctx* ctx, const rich_problem_t* pb, int S, const double* lnKs,
                       const double* alpha, double alpha_scale, double* qoi, double* p_final,
                       int32_t* status, rich_stats_t* stats, cudaStream_t st, const rich_soil_in* soil) {

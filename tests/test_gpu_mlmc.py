@@ -121,6 +121,20 @@ def test_mlmc_grid_only_bias_matches_oracle(R, coupling):
     assert g["levels_for_eps"] == len(ns) + extra
 
 
+def test_mixed_precision_mlmc_close_to_fp64(R):
+    """The estimator with FP32 V-cycles inside FP64 defect correction: every
+    level's pair counts equal the FP64 run's and its means of Q_l and of
+    Y_l agree with them to 1e-6 of the QoI scale (the mixed path's QoI bar)."""
+    base = dict(nsamples=(24, 12, 6), n0=8, steps0=2, t_final=0.04, coupling=2, eps=1e-3)
+    g64 = R.mlmc_estimate(R.MlmcConfig(**base, problem=R.Problem(**PHYSICS, **SOLVER)))
+    g32 = R.mlmc_estimate(R.MlmcConfig(**base, problem=R.Problem(precision=R.MIXED, **PHYSICS, **SOLVER)))
+    scale = max(abs(v) for v in g64["mean_f"])
+    assert g64["n"] == g32["n"] and g64["failed"] == g32["failed"]
+    for l in range(3):
+        assert abs(g32["mean"][l] - g64["mean"][l]) <= 1e-6 * scale, l
+        assert abs(g32["mean_f"][l] - g64["mean_f"][l]) <= 1e-6 * scale, l
+
+
 def test_mlmc_telescoping_consistency(R):
     """Exact coupling: the level-l fine member (pair l) and the level-l coarse
     member (pair l+1) have the same law, so their means agree within 4 sigma."""
