@@ -585,7 +585,8 @@ def run_adjoint(args):
                    "kl_variance_captured": float(lam.sum() / (n * n))},
         "clocks": clk, "gpu_launches": launches,
         "failed_samples": int(((stv == 1) | (stv == 3)).sum()),
-        "adjoint_linear_solve_limit_hit": int((stv == 2).sum()),
+        "adjoint_linear_solve_limit_hit": int((stv == R.ADJ_MAXIT).sum()),
+        "forward_mg_limit_hit": int((stv == R.MG_MAXIT).sum()),
         "picard_iters_per_sample": stats.picard_iters / S,
         "adjoint_preconditioner_applications_per_sample": stats.mg_cycles / S,
         "mean_qoi": float(np.nanmean(q.cpu().numpy())),

@@ -13,10 +13,11 @@
  * Return codes: 0 = OK; < 0 = fatal error of the call (nothing is guaranteed
  * about the outputs); > 0 = the call completed and the value is the most
  * severe per-sample status, in the order RICH_NONFINITE, RICH_PICARD_MAXIT
- * (both: the sample failed, its QoI is NaN), RICH_MG_MAXIT (a multigrid solve
- * stopped at its cycle cap; the sample's result is still usable), with the
- * per-sample details in the status array.  A sample that fails after an
- * earlier MG_MAXIT carries the failure status.  No C++ exception crosses the
+ * (both: the sample failed, its QoI is NaN), RICH_ADJ_MAXIT (an adjoint J^T
+ * solve stopped at its cap; QoI usable, gradient not to tolerance),
+ * RICH_MG_MAXIT (a multigrid solve stopped at its cycle cap; the sample's
+ * result is still usable), with the per-sample details in the status array.
+ * A sample that fails after an earlier MG_MAXIT carries the failure status.  No C++ exception crosses the
  * ABI.  Streams are cudaStream_t passed as void* (NULL = legacy default).
  */
 #ifndef RICHARDS_H
@@ -32,6 +33,7 @@ enum {
     RICH_PICARD_MAXIT = 1, /* a time step needed more Picard iterations than allowed (Sec. 4.3) */
     RICH_MG_MAXIT = 2,     /* an MG solve stopped at mg_maxit cycles above tolerance           */
     RICH_NONFINITE = 3,    /* NaN/Inf met in a residual or correction                          */
+    RICH_ADJ_MAXIT = 4,    /* an adjoint J^T solve stopped at its cap above tolerance          */
     RICH_ERR_INVALID = -1, /* bad argument: sizes, pointers, unsupported grid                  */
     RICH_ERR_CUDA = -2,    /* a CUDA runtime call failed                                       */
     RICH_ERR_OOM = -3      /* device workspace could not be allocated                          */
@@ -387,10 +389,19 @@ int rich_solve_batch_adjoint(rich_ctx_t ctx, const rich_problem_t* pb, int32_t n
  * the CCMG cycles of the Picard operator, stopped on the true residual; 2
  * restarted GMRES(12) (Saad & Schultz 1986) with the same preconditioner,
  * stopped on the true residual; 0 the plain defect correction
- * lam += M^{-1}(rhs - J^T lam).  Both stop at a relative
- * residual of 1e-11 or 400 preconditioner applications (then RICH_MG_MAXIT);
+ * lam += M^{-1}(rhs - J^T lam).  All stop at the limits of
+ * rich_set_adjoint_limits (default: relative residual 1e-11, 400
+ * preconditioner applications, then RICH_ADJ_MAXIT);
  * rich_stats_t.mg_cycles counts the applications.  RICH_ERR_INVALID otherwise. */
 int rich_set_adjoint_method(rich_ctx_t ctx, int32_t method);
+
+/* Stopping rule of this context's adjoint J^T solves (any method): converged
+ * when ||rhs - J^T lam||_inf <= rel_tol ||rhs||_inf, given up after
+ * max_applications preconditioner applications (defect correction: outer
+ * iterations), which sets RICH_ADJ_MAXIT for the sample (its QoI and its
+ * not fully converged gradient are still returned).  Defaults 1e-11 and 400.
+ * RICH_ERR_INVALID unless 0 < rel_tol < 1 and 1 <= max_applications <= 1e6. */
+int rich_set_adjoint_limits(rich_ctx_t ctx, double rel_tol, int32_t max_applications);
 
 /* Allocation-free solve.  The paper has no counterpart: this entry point exists
  * for callers that cannot call cudaMalloc -- code embedded in a host framework

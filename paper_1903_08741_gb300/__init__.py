@@ -21,7 +21,7 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "librichards.so")
 
-OK, PICARD_MAXIT, MG_MAXIT, NONFINITE = 0, 1, 2, 3
+OK, PICARD_MAXIT, MG_MAXIT, NONFINITE, ADJ_MAXIT = 0, 1, 2, 3, 4
 FP64, MIXED = 0, 1
 GARDNER, VAN_GENUCHTEN = 0, 1
 
@@ -285,6 +285,7 @@ def lib():
         L.rich_mlmc_adaptive.argtypes = [vp, C.POINTER(_MlmcCfg), i32, vp, C.POINTER(_MlmcResult)]
         L.rich_measure_fp64.argtypes = [vp, C.POINTER(_Fp64Rates)]
         L.rich_set_adjoint_method.argtypes = [vp, i32]
+        L.rich_set_adjoint_limits.argtypes = [vp, dbl, i32]
         _lib = L
     return _lib
 
@@ -297,7 +298,7 @@ def exported_symbols():
             "rich_kl_fields", "rich_solve_batch_adjoint", "rich_set_tuning", "rich_sample_fields_at",
             "rich_solve_batch_async", "rich_mlmc_adaptive", "rich_sample_soil", "rich_solve_soil",
             "rich_sample_soil_pair", "rich_sample_counters", "rich_measure_fp64",
-            "rich_set_adjoint_method"]
+            "rich_set_adjoint_method", "rich_set_adjoint_limits"]
 
 
 def _check(rc):
@@ -523,6 +524,12 @@ BICGSTAB, DEFECT_CORRECTION, GMRES = 1, 0, 2
 def set_adjoint_method(method=BICGSTAB, device=0):
     """J^T solver of the device's adjoint solves: BICGSTAB (default), GMRES or DEFECT_CORRECTION."""
     _check(lib().rich_set_adjoint_method(context(device), method))
+
+
+def set_adjoint_limits(rel_tol=1e-11, max_applications=400, device=0):
+    """Stopping rule of the device's adjoint J^T solves: relative residual
+    target and cap on preconditioner applications (then status ADJ_MAXIT)."""
+    _check(lib().rich_set_adjoint_limits(context(device), float(rel_tol), int(max_applications)))
 
 
 def measure_fp64(device=0):

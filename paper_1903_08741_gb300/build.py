@@ -16,6 +16,7 @@ LIB = os.path.join(PKG, "librichards.so")
 SOURCES = ["api.cu", "solver.cu", "fused.cu", "fused_g64.cu", "fused_g32.cu", "fused_vg64.cu", "fused_vg32.cu",
            "fused_adj64.cu", "fused_adj32.cu", "fields.cu", "mlmc.cu", "adjoint.cu"]
 HEADERS = [os.path.join(CSRC, "rich_internal.cuh"), os.path.join(CSRC, "fused_kernel.cuh"),
+           os.path.join(CSRC, "fused_adjoint.cuh"),
            os.path.join(ROOT, "include", "richards.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-diag-suppress", "177"]

@@ -79,8 +79,9 @@ extern "C" int rich_solve_batch_adjoint(rich_ctx_t ctx, const rich_problem_t* pb
     if (int e = rich_kl_fields(ctx, kl_basis, n_kl, nc, xi, nsamples, lk, stream)) return e;
     if (int e = rich_samples_reserve(ctx, nsamples)) return e;
     auto t0 = std::chrono::steady_clock::now();
-    // adjoint linear solves to 1e-11 relative, at most 400 preconditioner applications
-    if (int e = rich_adjoint_fused(ctx, pb, nsamples, lk, alpha, alpha_scale, ckpt_every, 1e-11, 400,
+    // adjoint linear solves to the context's relative residual (default 1e-11),
+    // at most its cap of preconditioner applications (default 400)
+    if (int e = rich_adjoint_fused(ctx, pb, nsamples, lk, alpha, alpha_scale, ckpt_every, ctx->adj_tol, ctx->adj_cap,
                                    ctx->adj_method, qoi, g, st))
         return e;
     dim3 grid(n_kl, nsamples);
@@ -114,5 +115,13 @@ extern "C" int rich_solve_batch_adjoint(rich_ctx_t ctx, const rich_problem_t* pb
 extern "C" int rich_set_adjoint_method(rich_ctx_t ctx, int32_t method) {
     if (!ctx || method < 0 || method > 2) return RICH_ERR_INVALID;
     ctx->adj_method = method;
+    return 0;
+}
+
+extern "C" int rich_set_adjoint_limits(rich_ctx_t ctx, double rel_tol, int32_t max_applications) {
+    if (!ctx || !(rel_tol > 0.0 && rel_tol < 1.0) || max_applications < 1 || max_applications > 1000000)
+        return RICH_ERR_INVALID;
+    ctx->adj_tol = rel_tol;
+    ctx->adj_cap = max_applications;
     return 0;
 }

@@ -92,6 +92,7 @@ extern "C" const char* rich_status_str(int code) {
         case RICH_PICARD_MAXIT: return "picard iteration limit reached";
         case RICH_MG_MAXIT: return "multigrid cycle limit reached";
         case RICH_NONFINITE: return "non-finite residual or correction";
+        case RICH_ADJ_MAXIT: return "adjoint linear-solve limit reached";
         case RICH_ERR_INVALID: return "invalid argument";
         case RICH_ERR_CUDA: return "CUDA error";
         case RICH_ERR_OOM: return "out of device memory";

@@ -1,7 +1,7 @@
 // FP64 instantiations of the discrete-adjoint kernel (V-cycle and
 // cycle-index-gamma preconditioners), in a translation unit of their own so
 // that they compile in parallel with the rest of the library.
-#include "fused_kernel.cuh"
+#include "fused_adjoint.cuh"
 
 namespace rich_fused {
 

@@ -6,33 +6,63 @@ namespace {
 
 constexpr int ACC_TPB = 1024;
 
-// One block, fixed summation order (strided per-thread sums, then a fixed
-// tree), so that repeated calls give bit-identical sums.  Sample i counts when
-// both statuses are RICH_OK or RICH_MG_MAXIT (the QoI is defined); failed
-// samples are counted separately and excluded from the sums.
-__global__ void __launch_bounds__(ACC_TPB)
-k_accumulate(int n, const double* __restrict__ qf, const double* __restrict__ qc,
-             const int32_t* __restrict__ sf, const int32_t* __restrict__ sc, double* acc) {
-    double v[7] = {0, 0, 0, 0, 0, 0, 0};   // sum Y, sum Y^2, count, sum Qf, sum Qf^2, sum Qc, sum Qc^2
-    double nfail = 0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        bool bad = (sf && (sf[i] == RICH_PICARD_MAXIT || sf[i] == RICH_NONFINITE)) ||
-                   (qc && sc && (sc[i] == RICH_PICARD_MAXIT || sc[i] == RICH_NONFINITE));
-        double f = qf[i], c = qc ? qc[i] : 0.0;
-        if (bad || !isfinite(f) || !isfinite(c)) { nfail += 1; continue; }
-        double y = f - c;
-        v[0] += y; v[1] += y * y; v[2] += 1;
-        v[3] += f; v[4] += f * f; v[5] += c; v[6] += c * c;
-    }
-    __shared__ double sm[8][ACC_TPB];
-    for (int k = 0; k < 7; ++k) sm[k][threadIdx.x] = v[k];
-    sm[7][threadIdx.x] = nfail;
+// Sums of eight per-thread values over the block in a fixed order (strided
+// per-thread sums, then a fixed tree), so that repeated calls give
+// bit-identical sums; the totals are in sm[k][0] for every thread on return.
+__device__ void tree_sum8(const double (&v)[8], double (*sm)[ACC_TPB]) {
+    for (int k = 0; k < 8; ++k) sm[k][threadIdx.x] = v[k];
     __syncthreads();
     for (int w = ACC_TPB / 2; w > 0; w >>= 1) {
         if ((int)threadIdx.x < w)
             for (int k = 0; k < 8; ++k) sm[k][threadIdx.x] += sm[k][threadIdx.x + w];
         __syncthreads();
     }
+}
+
+// One block.  Sample i counts when both statuses are RICH_OK, RICH_MG_MAXIT
+// or RICH_ADJ_MAXIT (the QoI is defined); failed samples are counted
+// separately and excluded from the sums.  With `shift` (the estimator's own
+// statistics) the sums are of Y - K_Y, Qf - K_f, Qc - K_c about shifts fixed
+// by the means of the first batch that has a defined sample (shift[3] = 1
+// once set): the variance (S2 - S1^2/n)/(n - 1) of shifted data does not
+// cancel when |mean| >> standard deviation (Chan, Golub & LeVeque 1983).
+// Without it: plain sums, the layout of rich_mlmc_accumulate.
+__global__ void __launch_bounds__(ACC_TPB)
+k_accumulate(int n, const double* __restrict__ qf, const double* __restrict__ qc,
+             const int32_t* __restrict__ sf, const int32_t* __restrict__ sc, double* acc, double* shift) {
+    __shared__ double sm[8][ACC_TPB];
+    auto bad = [&](int i) {
+        return (sf && (sf[i] == RICH_PICARD_MAXIT || sf[i] == RICH_NONFINITE)) ||
+               (qc && sc && (sc[i] == RICH_PICARD_MAXIT || sc[i] == RICH_NONFINITE)) || !isfinite(qf[i]) ||
+               (qc && !isfinite(qc[i]));
+    };
+    double ky = 0.0, kf = 0.0, kc = 0.0;
+    if (shift) {
+        if (shift[3] == 0.0) {                  // first defined batch: its means become the shifts
+            double m[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                if (bad(i)) continue;
+                const double f = qf[i], c = qc ? qc[i] : 0.0;
+                m[0] += f - c; m[1] += f; m[2] += c; m[3] += 1;
+            }
+            tree_sum8(m, sm);
+            const double cnt = sm[3][0];
+            if (cnt > 0) { ky = sm[0][0] / cnt; kf = sm[1][0] / cnt; kc = sm[2][0] / cnt; }
+            __syncthreads();
+            if (threadIdx.x == 0 && cnt > 0) { shift[0] = ky; shift[1] = kf; shift[2] = kc; shift[3] = 1.0; }
+        } else {
+            ky = shift[0]; kf = shift[1]; kc = shift[2];
+        }
+    }
+    double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};    // Y, Y^2, count, Qf, Qf^2, Qc, Qc^2, failed
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        if (bad(i)) { v[7] += 1; continue; }
+        const double f = qf[i], c = qc ? qc[i] : 0.0;
+        const double y = (f - c) - ky, fs = f - kf, cs = c - kc;
+        v[0] += y; v[1] += y * y; v[2] += 1;
+        v[3] += fs; v[4] += fs * fs; v[5] += cs; v[6] += cs * cs;
+    }
+    tree_sum8(v, sm);
     if (threadIdx.x == 0) {
         acc[0] += sm[0][0]; acc[1] += sm[1][0]; acc[2] += sm[2][0]; acc[3] += sm[7][0];
         acc[4] += sm[3][0]; acc[5] += sm[4][0]; acc[6] += sm[5][0]; acc[7] += sm[6][0];
@@ -49,10 +79,22 @@ extern "C" int rich_mlmc_accumulate(rich_ctx_t ctx, const double* qoi_fine, cons
     RICH_CUDA(cudaSetDevice(ctx->device));
     rich_count_launch();
     k_accumulate<<<1, ACC_TPB, 0, (cudaStream_t)stream>>>(n, qoi_fine, qoi_coarse, status_fine,
-                                                         status_coarse, acc);
+                                                         status_coarse, acc, nullptr);
     RICH_CUDA(cudaGetLastError());
     return 0;
 }
+
+namespace {
+// the estimator's accumulation: shifted sums (acc[8]) about shift[4]
+int accumulate_shifted(const double* qf, const double* qc, const int32_t* sf, const int32_t* sc, int n,
+                       double* acc, double* shift, cudaStream_t st) {
+    if (n == 0) return 0;
+    rich_count_launch();
+    k_accumulate<<<1, ACC_TPB, 0, st>>>(n, qf, qc, sf, sc, acc, shift);
+    RICH_CUDA(cudaGetLastError());
+    return 0;
+}
+}  // namespace
 
 // ------------------------------------------------------------------ estimator
 #include <chrono>
@@ -61,6 +103,16 @@ extern "C" int rich_mlmc_accumulate(rich_ctx_t ctx, const double* qoi_fine, cons
 #include <algorithm>
 
 namespace {
+
+// per level (and the bias pairs): 8 shifted sums (k_accumulate) + 4 shift values
+constexpr int ACC_W = 12;
+
+// mean and unbiased variance of n values from the sums s1, s2 of their
+// deviations from the shift k (Eqs. SMC_ch6, MC_var_ch6)
+void mean_var(double s1, double s2, double n, double k, double* m, double* v) {
+    *m = n > 0 ? k + s1 / n : NAN;
+    *v = n > 1 ? (s2 - s1 * (s1 / n)) / (n - 1) : NAN;
+}
 
 struct DevBuf {
     void* p = nullptr;
@@ -147,14 +199,14 @@ struct MlmcRun {
         };
         if (dalloc(lkf, fine_cells * 8) || dalloc(alf, fine_cells * 8) || dalloc(lkc, fine_cells * 2) ||
             dalloc(alc, fine_cells * 2) || dalloc(qf, B * 8) || dalloc(qc, B * 8) || dalloc(sf, B * 4) ||
-            dalloc(sc, B * 4) || dalloc(acc, 8 * 8 * (NL + 1)))
+            dalloc(sc, B * 4) || dalloc(acc, 8 * ACC_W * (NL + 1)))
             return RICH_ERR_OOM;
         if (vg && (dalloc(nf, fine_cells * 8) || dalloc(ncb, fine_cells * 2)))
             return RICH_ERR_OOM;
         if (thetas && (dalloc(tsf, fine_cells * 8) || dalloc(trf, fine_cells * 8) || dalloc(tsc, fine_cells * 2) ||
                        dalloc(trc, fine_cells * 2)))
             return RICH_ERR_OOM;
-        RICH_CUDA(cudaMemsetAsync(acc.p, 0, 8 * 8 * (NL + 1), st));
+        RICH_CUDA(cudaMemsetAsync(acc.p, 0, 8 * ACC_W * (NL + 1), st));
         return 0;
     }
 
@@ -241,9 +293,9 @@ struct MlmcRun {
             RICH_CUDA(cudaEventRecord(evc, st2));
             RICH_CUDA(cudaStreamWaitEvent(st, evc, 0));
         }
-        e = rich_mlmc_accumulate(ctx, (double*)qf.p, l > 0 ? (double*)qc.p : nullptr, (int32_t*)sf.p,
-                                 l > 0 ? (int32_t*)sc.p : nullptr, nb,
-                                 (double*)acc.p + 8 * (bias_mode ? NL : l), st);
+        double* lacc = (double*)acc.p + ACC_W * (bias_mode ? NL : l);
+        e = accumulate_shifted((double*)qf.p, l > 0 ? (double*)qc.p : nullptr, (int32_t*)sf.p,
+                               l > 0 ? (int32_t*)sc.p : nullptr, nb, lacc, lacc + 8, st);
         if (e) return e;
         RICH_CUDA(cudaEventRecord(ev[3], st));
         RICH_CUDA(cudaEventSynchronize(ev[3]));
@@ -274,23 +326,19 @@ struct MlmcRun {
     // level statistics from the device sums (Eqs. SMC_ch6, MC_var_ch6,
     // eq:MLMCVar, ML_var_ch6, MLMCSAMP_ch6)
     int finalize(rich_mlmc_result_t* out) {
-        std::vector<double> h(8 * (NL + 1));
-        RICH_CUDA(cudaMemcpyAsync(h.data(), acc.p, 8 * 8 * (NL + 1), cudaMemcpyDeviceToHost, st));
+        std::vector<double> h(ACC_W * (NL + 1));
+        RICH_CUDA(cudaMemcpyAsync(h.data(), acc.p, 8 * ACC_W * (NL + 1), cudaMemcpyDeviceToHost, st));
         RICH_CUDA(cudaStreamSynchronize(st));
         rich_mlmc_result_t r{};
         r.nlevels = NL;
         double rmse2 = 0, ssum = 0, ssum_sm = 0;
         for (int l = 0; l < NL; ++l) {
-            const double* a = &h[8 * l];
+            const double* a = &h[ACC_W * l];
             const double n = a[2];
             r.n[l] = (int64_t)n; r.failed[l] = (int64_t)a[3];
-            auto mv = [&](double s1, double s2, double* m, double* v) {
-                *m = n > 0 ? s1 / n : NAN;
-                *v = n > 1 ? (s2 - n * (*m) * (*m)) / (n - 1) : NAN;
-            };
-            mv(a[0], a[1], &r.mean[l], &r.var[l]);
-            mv(a[4], a[5], &r.mean_f[l], &r.var_f[l]);
-            if (l > 0) mv(a[6], a[7], &r.mean_c[l], &r.var_c[l]);
+            mean_var(a[0], a[1], n, a[8], &r.mean[l], &r.var[l]);
+            mean_var(a[4], a[5], n, a[9], &r.mean_f[l], &r.var_f[l]);
+            if (l > 0) mean_var(a[6], a[7], n, a[10], &r.mean_c[l], &r.var_c[l]);
             r.cost[l] = n_done[l] > 0 ? t_pair[l] / n_done[l] : NAN;
             r.cost_fine[l] = n_done[l] > 0 ? t_fine[l] / n_done[l] : NAN;
             r.cost_sm[l] = n_done[l] > 0 ? t_sm[l] / n_done[l] : NAN;
@@ -313,12 +361,13 @@ struct MlmcRun {
         // original parameters / (2^a - 1); total RMSE sqrt(bias^2 + sum V_l/N_l)
         // (Eq. MSEMLMC_ch6); levels needed so that the bias, halving per level,
         // falls to eps / sqrt 2 (half of the MSE budget)
-        const double* b = &h[8 * NL];
+        const double* b = &h[ACC_W * NL];
         r.bias_pairs = (int64_t)b[2];
         if (b[2] > 0) {
-            const double m = b[0] / b[2];
+            double m, v;
+            mean_var(b[0], b[1], b[2], b[8], &m, &v);
             r.bias_grid = fabs(m) / (2.0 - 1.0);
-            r.bias_grid_se = b[2] > 1 ? sqrt(std::max((b[1] - b[2] * m * m) / (b[2] - 1), 0.0) / b[2]) : NAN;
+            r.bias_grid_se = b[2] > 1 ? sqrt(std::max(v, 0.0) / b[2]) : NAN;
             r.total_rmse = sqrt(r.bias_grid * r.bias_grid + rmse2);
             if (cfg->eps > 0) {
                 const double lim = cfg->eps / sqrt(2.0);

@@ -18,10 +18,13 @@
 void rich_set_error(const char* msg, const char* file, int line);
 
 // The more severe of two per-sample statuses: NONFINITE, then PICARD_MAXIT
-// (the sample failed, its QoI is NaN), then MG_MAXIT (a multigrid solve hit
-// its cycle cap but the sample's result is usable), then OK.
+// (the sample failed, its QoI is NaN), then ADJ_MAXIT (an adjoint J^T solve
+// hit its cap: the gradient is not to tolerance), then MG_MAXIT (a multigrid
+// solve hit its cycle cap but the sample's result is usable), then OK.
 inline int rich_status_worse(int a, int b) {
-    auto rank = [](int s) { return s == RICH_NONFINITE ? 3 : s == RICH_PICARD_MAXIT ? 2 : s == RICH_MG_MAXIT ? 1 : 0; };
+    auto rank = [](int s) {
+        return s == RICH_NONFINITE ? 4 : s == RICH_PICARD_MAXIT ? 3 : s == RICH_ADJ_MAXIT ? 2 : s == RICH_MG_MAXIT ? 1 : 0;
+    };
     return rank(b) > rank(a) ? b : a;
 }
 
@@ -72,6 +75,8 @@ struct rich_ctx {
     int tune_mixed_inner = 0;                   // FP32 V-cycles per FP64 defect (0: default 2)
     double last_sm_seconds = 0;                 // SM-seconds of the last rich_solve_device
     int adj_method = 1;                         // adjoint J^T solver: 0 defect correction, 1 BiCGStab
+    double adj_tol = 1e-11;                     // J^T solves: relative residual target ...
+    int adj_cap = 400;                          // ... and cap on preconditioner applications
 };
 
 void rich_count_launch();

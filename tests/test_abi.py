@@ -45,6 +45,8 @@ def test_status_strings_without_gpu(libpath):
     L = R.lib()
     assert L.rich_status_str(0) == b"ok"
     assert b"picard" in L.rich_status_str(1)
+    assert b"adjoint" in L.rich_status_str(4)
+    assert L.rich_set_adjoint_limits(None, 1e-11, 400) == -1
     h = C.c_void_p()
     assert L.rich_create(C.byref(h), 0) in (0, -2)   # -2 when no CUDA device is present
 

@@ -159,4 +159,31 @@ def test_krylov_solvers_and_defect_correction_agree(R, prec):
         a, b = dqd.cpu().numpy()[ok], dqk.cpu().numpy()[ok]
         assert np.abs(a - b).max() <= 1e-7 * np.abs(a).max(), m
         assert stk.mg_cycles < std.mg_cycles, m
-        assert not (sk.cpu().numpy() == R.MG_MAXIT).any(), m
+        assert not (sk.cpu().numpy() == R.ADJ_MAXIT).any(), m
+
+
+def test_adjoint_cap_sets_its_own_status(R):
+    """A J^T solve stopped at the cap of rich_set_adjoint_limits flags its sample
+    ADJ_MAXIT (not the forward solver's MG_MAXIT), the call returns that code,
+    and the QoI (the forward solve) is unchanged; a tolerance the solver
+    cannot reach in one application is forced by a cap of 1."""
+    n, nkl, S, steps, dt = 32, 6, 4, 3, 0.002
+    B, xi, al, (Bd, xid, ald) = setup_case(R, n, nkl, S, 17)
+    pb = gpu_pb(R, n, steps, dt)
+    q0, dq0, _, s0, st0, rc0 = R.solve_batch_adjoint(pb, Bd, xid, ald, ckpt_every=2)
+    assert np.isin(s0.cpu().numpy(), (R.OK, R.MG_MAXIT)).all() and rc0 in (0, R.MG_MAXIT)
+    assert not (s0.cpu().numpy() == R.ADJ_MAXIT).any()
+    try:
+        R.set_adjoint_limits(1e-11, 1)
+        q1, dq1, _, s1, st1, rc1 = R.solve_batch_adjoint(pb, Bd, xid, ald, ckpt_every=2)
+    finally:
+        R.set_adjoint_limits()
+    assert (s1.cpu().numpy() == R.ADJ_MAXIT).all() and rc1 == R.ADJ_MAXIT
+    assert torch.equal(q0, q1)
+    assert torch.isfinite(dq1).all()
+    # every J^T solve (one per step) stops at the cap and counts cap + 1
+    assert st1.mg_cycles == S * steps * 2
+    with pytest.raises(R.RichError):
+        R.set_adjoint_limits(0.0, 10)
+    with pytest.raises(R.RichError):
+        R.set_adjoint_limits(1e-11, 0)

@@ -53,6 +53,31 @@ def test_mlmc_matches_oracle(R, coupling):
     assert rel(g["w_eps_sm"], s_sm * s_sm / 1e-6) < 1e-12
 
 
+def test_level_variances_of_a_nearly_constant_qoi(R):
+    """With sigma^2 = 1e-16 and a constant alpha every sample solves nearly the
+    same problem: mean^2 / var of Y_l and Q_l is ~1e16, where a one-pass
+    (sum Y^2 - n mean^2) variance is quantised in steps (~1e-15) larger than
+    the variance itself (it returns 0, negative values or a multiple).  The
+    estimator's shifted sums still give the oracle's two-pass variances;
+    the 25 % bound covers the GPU/oracle difference of single QoIs (~1e-13
+    relative) against a sample spread of ~2e-8."""
+    ns, n0, s0, T = (24, 12, 6), 8, 2, 0.04
+    cfg = R.MlmcConfig(nsamples=ns, n0=n0, steps0=s0, t_final=T, coupling=0, eps=1e-3,
+                       model=R.FieldModel(sigma2=1e-16, alpha_span=0.0),
+                       problem=R.Problem(**PHYSICS, **SOLVER))
+    g = R.mlmc_estimate(cfg)
+    o = O.mlmc_estimate(ns, n0, s0, T, coupling=0, sigma2=1e-16, alpha_span=0.0, **PHYSICS, **SOLVER)
+    for l, lev in enumerate(o):
+        y, qf = lev["y"], lev["qf"]
+        assert g["n"][l] == y.size and g["failed"][l] == 0
+        assert y.mean() ** 2 / y.var(ddof=1) > 1e14
+        assert rel(g["mean"][l], y.mean()) < 1e-9 and rel(g["mean_f"][l], qf.mean()) < 1e-9
+        assert g["var"][l] > 0 and g["var_f"][l] > 0
+        if y.size >= 12:
+            assert rel(g["var"][l], y.var(ddof=1)) < 0.25
+            assert rel(g["var_f"][l], qf.var(ddof=1)) < 0.25
+
+
 def close(a, b, tol):
     """Relative agreement; two NaNs (a level with fewer than two usable pairs
     has no variance) agree."""
