@@ -115,7 +115,8 @@ const char* rich_last_error(void);
 
 /* Launch tuning of this context's solves (set by the autotuner of the Python
  * package, which times the candidates and caches the choice per grid,
- * precision and batch): block_threads 128 (eight resident CTAs per SM), 256
+ * precision and batch): block_threads 32 (thirty-two resident CTAs per SM,
+ * one warp per sample, every level in the sample's slot), 128 (eight), 256
  * (four), 512 (two) or 1024 (one), 0 = default 512; mixed_inner = FP32 V-cycles per FP64 defect in
  * RICH_MIXED solves, 0 = default 2 (1..16).  The computed solution does not
  * depend on block_threads; mixed_inner changes how often the FP64 stopping
@@ -351,7 +352,10 @@ int rich_mlmc_adaptive(rich_ctx_t ctx, const rich_mlmc_cfg_t* cfg, int32_t max_r
  *   acc[4] += sum Qf, acc[5] += sum Qf^2, acc[6] += sum Qc, acc[7] += sum Qc^2.
  * A sample is failed (counted, excluded from the sums) when either status is
  * RICH_PICARD_MAXIT or RICH_NONFINITE or a QoI is not finite; statuses may be
- * NULL.  Deterministic summation order.  Asynchronous on `stream`. */
+ * NULL.  Deterministic summation order.  Asynchronous on `stream`.  Plain
+ * sums (ranks merge them by adding); the variance (S2 - S1^2/n)/(n - 1)
+ * loses digits when |mean| >> std, so for such data subtract a shift from
+ * the QoIs first (rich_mlmc_estimate does this internally per level). */
 int rich_mlmc_accumulate(rich_ctx_t ctx, const double* qoi_fine, const double* qoi_coarse,
                          const int32_t* status_fine, const int32_t* status_coarse, int32_t n,
                          double* acc, void* stream);

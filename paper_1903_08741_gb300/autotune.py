@@ -1,7 +1,9 @@
 """Autotuner of the fused solver's launch shape.
 
-Candidates: 128- and 256-thread CTAs (eight or four resident per SM: small
-grids, whose levels give a large CTA too little work between barriers),
+Candidates: 32-thread CTAs (grids up to 32^2: a sample per warp, 32 resident
+per SM, no CTA-wide barrier), 128- and 256-thread CTAs (eight or four resident
+per SM: small grids, whose levels give a large CTA too little work between
+barriers),
 512-thread CTAs (two per
 SM) or 1024-thread CTAs (one per SM: the fewest resident scratch slots, so more
 of the hierarchy stays in L2, and the most threads per sample); for the mixed path
@@ -66,6 +68,14 @@ def _save(path, data):
     os.replace(tmp, path)
 
 
+def shapes(problem):
+    """Candidate CTA sizes: one-warp CTAs (32 per SM, a whole sample on one
+    warp) only for grids of at most 32^2 cells, where a larger CTA spends its
+    time at barriers between a few cells of work; 128 ... 1024 for all."""
+    small = problem.nx * problem.nz <= 32 * 32
+    return ((32,) if small else ()) + (128, 256, 512, 1024)
+
+
 def source(problem, nsamples, device=0):
     """Where tune() would take this key's choice from: "cache", "shipped" or
     "measure"."""
@@ -107,7 +117,7 @@ def tune(problem, nsamples, device=0, force=False, probe_steps=2, verbose=False,
     inners = [1, 2, 3, 4, 6] if problem.precision else [0]
     timings = {}
     stream = torch.cuda.current_stream(dev)
-    for bt in (128, 256, 512, 1024):
+    for bt in shapes(problem):
         for mi in inners:
             R.set_tuning(bt, mi, device)
             solve(min(S, 8))
@@ -151,7 +161,7 @@ def check(problem, nsamples, device=0, steps=None, verbose=False):
     stream = torch.cuda.current_stream(dev)
     ms = {}
     try:
-        for bt in (128, 256, 512, 1024):
+        for bt in shapes(problem):
             for mi in inners:
                 R.set_tuning(bt, mi, device)
                 solve(min(nsamples, 8))

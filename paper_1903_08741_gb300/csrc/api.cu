@@ -142,8 +142,8 @@ int rich_check_problem(const rich_problem_t* pb) {
 }
 
 extern "C" int rich_set_tuning(rich_ctx_t ctx, int32_t block_threads, int32_t mixed_inner) {
-    if (!ctx || (block_threads != 0 && block_threads != 128 && block_threads != 256 && block_threads != 512 &&
-                 block_threads != 1024) ||
+    if (!ctx || (block_threads != 0 && block_threads != 32 && block_threads != 128 && block_threads != 256 &&
+                 block_threads != 512 && block_threads != 1024) ||
         mixed_inner < 0 ||
         mixed_inner > 16)
         return RICH_ERR_INVALID;

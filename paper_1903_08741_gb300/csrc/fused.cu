@@ -31,14 +31,18 @@ static void plan_smem(FParams& P, int nt) {
     const size_t nnc = (size_t)P.nx[c] * P.nz[c];
     auto al16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
     size_t off = al16(nnc * (nnc + 1) * w);
-    const size_t budget = nt == 1024 ? 220 * 1024 : nt == 512 ? 104 * 1024 : nt == 256 ? 50 * 1024 : 24 * 1024;
+    const size_t budget = nt == 1024 ? 220 * 1024 : nt == 512 ? 104 * 1024 : nt == 256 ? 50 * 1024
+                        : nt == 128 ? 24 * 1024 : 3 * 1024;
     for (int l = 0; l < MAXL; ++l) {
         P.osm[l] = -1;
         for (int k = 0; k < N64; ++k) P.s64[l][k] = -1;
         for (int k = 0; k < NMG; ++k) P.smg[l][k] = -1;
     }
+    // small levels below the finest run on warp 0 with their arrays on chip;
+    // a one-warp CTA (32 threads, 32 CTAs per SM) runs every level itself and
+    // keeps them in its slot: on-chip copies would cost it its occupancy
     P.lw = P.nlev;
-    for (int l = 1; l < P.nlev; ++l)
+    for (int l = 1; l < P.nlev && nt > 32; ++l)
         if ((size_t)P.nx[l] * P.nz[l] <= (size_t)WARP_CELLS) { P.lw = l; break; }
     for (int l = P.lw; l < P.nlev; ++l) {
         const size_t nc = (size_t)P.nx[l] * P.nz[l];
@@ -158,7 +162,8 @@ int rich_solve_fused(rich_ctx* ctx, const rich_problem_t* pb, int S, const doubl
     rich_samplebuf& w = ctx->sb;
     FParams P;
     if (pb->closure == RICH_VAN_GENUCHTEN && (!soil || !soil->n)) return RICH_ERR_INVALID;
-    const int nt = (ctx->tune_threads == 1024 || ctx->tune_threads == 256 || ctx->tune_threads == 128)
+    const int nt = (ctx->tune_threads == 1024 || ctx->tune_threads == 256 || ctx->tune_threads == 128 ||
+                    ctx->tune_threads == 32)
                        ? ctx->tune_threads : 512;
     if (int e = fused_setup(pb, S, P)) return e;
     plan_smem(P, nt);

@@ -176,6 +176,10 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (nw == 1) {              // one-warp CTA: every lane holds the sum (the
+        __syncwarp();           // second stage would add zeros); the warp
+        return v;               // barrier keeps the CTA barrier's ordering
+    }
     if (lane == 0) red[wid] = v;
     __syncthreads();
     if (wid == 0) {
@@ -194,6 +198,10 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 __device__ __forceinline__ unsigned long long block_max(unsigned long long v, unsigned long long* red) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     v = warp_max_u64(v);
+    if (nw == 1) {
+        __syncwarp();
+        return v;
+    }
     if (lane == 0) red[wid] = v;
     __syncthreads();
     if (wid == 0) {
@@ -1333,7 +1341,7 @@ __device__ __forceinline__ void init_levels(const FParams& P, char* slot, unsign
 }
 
 template <typename TM, int NT, bool WC, int CL>
-__global__ void __launch_bounds__(NT, NT <= 128 ? 8 : NT <= 256 ? 4 : NT == 512 ? 2 : 1)
+__global__ void __launch_bounds__(NT, NT == 32 ? 32 : NT <= 128 ? 8 : NT <= 256 ? 4 : NT == 512 ? 2 : 1)
 k_fused(const FParams P) {
     extern __shared__ unsigned char smraw[];
     __shared__ unsigned long long red[33];
@@ -1393,6 +1401,7 @@ int occ_shapes(const FParams& P, size_t smem, int nt, int* occ) {
     if (nt == 1024) return wc ? occ_one<TM, 1024, true, CL>(P, smem, occ) : occ_one<TM, 1024, false, CL>(P, smem, occ);
     if (nt == 256) return wc ? occ_one<TM, 256, true, CL>(P, smem, occ) : occ_one<TM, 256, false, CL>(P, smem, occ);
     if (nt == 128) return wc ? occ_one<TM, 128, true, CL>(P, smem, occ) : occ_one<TM, 128, false, CL>(P, smem, occ);
+    if (nt == 32) return wc ? occ_one<TM, 32, true, CL>(P, smem, occ) : occ_one<TM, 32, false, CL>(P, smem, occ);
     return wc ? occ_one<TM, 512, true, CL>(P, smem, occ) : occ_one<TM, 512, false, CL>(P, smem, occ);
 }
 
@@ -1408,6 +1417,9 @@ void launch_shapes(const FParams& P, int grid, size_t smem, int nt, cudaStream_t
     } else if (nt == 128) {
         if (wc) k_fused<TM, 128, true, CL><<<grid, 128, smem, st>>>(P);
         else k_fused<TM, 128, false, CL><<<grid, 128, smem, st>>>(P);
+    } else if (nt == 32) {
+        if (wc) k_fused<TM, 32, true, CL><<<grid, 32, smem, st>>>(P);
+        else k_fused<TM, 32, false, CL><<<grid, 32, smem, st>>>(P);
     } else {
         if (wc) k_fused<TM, 512, true, CL><<<grid, 512, smem, st>>>(P);
         else k_fused<TM, 512, false, CL><<<grid, 512, smem, st>>>(P);

@@ -398,7 +398,8 @@ int check_cfg(const rich_mlmc_cfg_t* cfg) {
     for (int l = 0; l < NL; ++l) {
         if (cfg->nsamples[l] < 2) return RICH_ERR_INVALID;
         if (cfg->bias_pairs < 0) return RICH_ERR_INVALID;
-        if (cfg->tune_threads[l] != 0 && cfg->tune_threads[l] != 128 && cfg->tune_threads[l] != 256 &&
+        if (cfg->tune_threads[l] != 0 && cfg->tune_threads[l] != 32 && cfg->tune_threads[l] != 128 &&
+            cfg->tune_threads[l] != 256 &&
             cfg->tune_threads[l] != 512 &&
             cfg->tune_threads[l] != 1024)
             return RICH_ERR_INVALID;

@@ -309,9 +309,10 @@ def test_solve_512_fp64_and_mixed_match_oracle(R):
 
 
 def test_block_shape_does_not_change_fp64_results(R):
-    """The 256- and 1024-thread launch shapes give bit-identical FP64 results
-    (they also place different levels' corrections in shared memory); the mixed
-    path with other inner-cycle counts stays within its 1e-6 QoI bound."""
+    """The 32-, 128-, 256- and 1024-thread launch shapes give bit-identical FP64
+    results (they place different levels in shared memory; the one-warp CTA
+    runs every level itself, from its slot); the mixed path with other
+    inner-cycle counts stays within its 1e-6 QoI bound."""
     lk, al = O.sample_fields(32, 32, 10, seed=6)
     dev = torch.device("cuda:0")
     a = (torch.from_numpy(lk).to(dev), torch.from_numpy(al).to(dev))
@@ -320,13 +321,13 @@ def test_block_shape_does_not_change_fp64_results(R):
         R.set_tuning(512, 0)
         q1, p1, s1, _, _ = R.solve_batch(pb, *a, want_p=True)
         ok = s1 == 0
-        for bt in (256, 1024):
+        for bt in (32, 128, 256, 1024):
             R.set_tuning(bt, 0)
             q2, p2, s2, _, _ = R.solve_batch(pb, *a, want_p=True)
             assert torch.equal(s1, s2) and torch.equal(p1, p2)
             assert torch.equal(q1[ok], q2[ok])
         pm = gpu_problem(R, 32, 32, 3, 0.01, precision=R.MIXED)
-        for bt, mi in ((512, 1), (1024, 4), (256, 2)):
+        for bt, mi in ((512, 1), (1024, 4), (256, 2), (32, 3)):
             R.set_tuning(bt, mi)
             qm, _, sm, _, _ = R.solve_batch(pm, *a)
             okm = ok & (sm == 0)

@@ -181,17 +181,17 @@ def test_per_sample_counters_match_oracle(R):
 
 
 def test_vg_w_cycle_block_shapes_bitwise(R):
-    """The van Genuchten W-cycle kernels of all three launch shapes agree bit for bit."""
+    """The van Genuchten W-cycle kernels of all launch shapes agree bit for bit."""
     f = fields(32, 6, 2.0, 1.6, seed=11)
     dev = torch.device("cuda:0")
     g = [torch.from_numpy(x).to(dev) for x in f]
     pb = R.Problem.infiltration(nx=32, nz=32, nsteps=3, dt=1 / 64)
     out = {}
     try:
-        for bt in (256, 512, 1024):
+        for bt in (32, 128, 256, 512, 1024):
             R.set_tuning(bt, 0)
             out[bt] = R.solve_soil(pb, *g, want_p=True)
     finally:
         R.set_tuning(0, 0)
-    for bt in (256, 1024):
+    for bt in (32, 128, 256, 1024):
         assert torch.equal(out[bt][1], out[512][1]) and torch.equal(out[bt][2], out[512][2])
