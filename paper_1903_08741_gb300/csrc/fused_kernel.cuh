@@ -176,10 +176,6 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (nw == 1) {              // one-warp CTA: every lane holds the sum (the
-        __syncwarp();           // second stage would add zeros); the warp
-        return v;               // barrier keeps the CTA barrier's ordering
-    }
     if (lane == 0) red[wid] = v;
     __syncthreads();
     if (wid == 0) {
@@ -198,10 +194,6 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 __device__ __forceinline__ unsigned long long block_max(unsigned long long v, unsigned long long* red) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     v = warp_max_u64(v);
-    if (nw == 1) {
-        __syncwarp();
-        return v;
-    }
     if (lane == 0) red[wid] = v;
     __syncthreads();
     if (wid == 0) {
