@@ -47,8 +47,8 @@ FP64_TFLOPS_NOMINAL = 1.25      # GB300 FP64 (non-tensor) nominal: 152 SMs x 2 F
 # ones captured (fused_sha()).
 TRAFFIC = {
     # (precision, block_threads): (fused_sha() of the captured sources, DRAM bytes per algorithmic byte)
-    ("fp64", 512): ("06f0e930f14ff8a6b70bd5efe0fec7ffca9193b6964b2da20cad31627185dc85", 1.9235),
-    ("mixed", 512): ("06f0e930f14ff8a6b70bd5efe0fec7ffca9193b6964b2da20cad31627185dc85", 0.7079),
+    ("fp64", 512): ("7f22827adec5c407e87fd507ed3f6a2f0b5fd91a9c973c9aa6fea8a4846256e6", 1.9240),
+    ("mixed", 512): ("7f22827adec5c407e87fd507ed3f6a2f0b5fd91a9c973c9aa6fea8a4846256e6", 0.7142),
 }
 
 
@@ -322,6 +322,15 @@ def run_reference(args):
 MLMC_LEVELS = dict(nsamples=(20000, 5000, 1200, 300, 80), n0=16, steps0=5, t_final=0.1)
 
 
+def mlmc_launch_batch(levels, nl):
+    """Samples per solver launch of an MLMC level: the estimator (rich_mlmc_estimate
+    with cfg.batch = 0) solves a level in batches of at most 2^31 / (16 n_L^2)
+    pairs, n_L the finest grid (its field buffers hold that many finest-level
+    fields), so each level is tuned for that launch size, not for N_l."""
+    nL = levels["n0"] << (len(levels["nsamples"]) - 1)
+    return min(nl, max(1, (1 << 31) // (16 * nL * nL)))
+
+
 def mlmc_tuning(R, prec, cycle=1):
     """Per-level launch shapes of the five-level hierarchy from the autotuner."""
     from paper_1903_08741_gb300 import autotune
@@ -330,7 +339,7 @@ def mlmc_tuning(R, prec, cycle=1):
         m = MLMC_LEVELS["n0"] << l
         st_l = MLMC_LEVELS["steps0"] << l
         bt, mi = autotune.tune(R.Problem(nx=m, nz=m, nsteps=st_l, dt=MLMC_LEVELS["t_final"] / st_l,
-                                         precision=prec, cycle=cycle, **PHYS), nl)
+                                         precision=prec, cycle=cycle, **PHYS), mlmc_launch_batch(MLMC_LEVELS, nl))
         tt.append(bt)
         ti.append(mi)
     R.set_tuning(0, 0)
@@ -473,7 +482,8 @@ def run_mlmc_vg(args):
         m = MLMC_VG_LEVELS["n0"] << l
         st_l = MLMC_VG_LEVELS["steps0"] << l
         bt, mi = autotune.tune(R.Problem.infiltration(nx=m, nz=m, nsteps=st_l, dt=MLMC_VG_LEVELS["t_final"] / st_l,
-                                                      precision=prec, cycle=base.cycle), nl)
+                                                      precision=prec, cycle=base.cycle),
+                               mlmc_launch_batch(MLMC_VG_LEVELS, nl))
         tt.append(bt)
         ti.append(mi)
     R.set_tuning(0, 0)
@@ -774,7 +784,7 @@ def run_tunecheck(args):
         for l, nl in enumerate(MLMC_LEVELS["nsamples"]):
             m, st_l = MLMC_LEVELS["n0"] << l, MLMC_LEVELS["steps0"] << l
             cases.append((R.Problem(nx=m, nz=m, nsteps=st_l, dt=MLMC_LEVELS["t_final"] / st_l, precision=prec,
-                                    **PHYS), nl, f"mlmc5 level {l}"))
+                                    **PHYS), mlmc_launch_batch(MLMC_LEVELS, nl), f"mlmc5 level {l}"))
     out = []
     for pb, S, name in cases:
         src = autotune.source(pb, S)
