@@ -322,13 +322,18 @@ def run_reference(args):
 MLMC_LEVELS = dict(nsamples=(20000, 5000, 1200, 300, 80), n0=16, steps0=5, t_final=0.1)
 
 
-def mlmc_launch_batch(levels, nl):
-    """Samples per solver launch of an MLMC level: the estimator (rich_mlmc_estimate
-    with cfg.batch = 0) solves a level in batches of at most 2^31 / (16 n_L^2)
-    pairs, n_L the finest grid (its field buffers hold that many finest-level
-    fields), so each level is tuned for that launch size, not for N_l."""
-    nL = levels["n0"] << (len(levels["nsamples"]) - 1)
-    return min(nl, max(1, (1 << 31) // (16 * nL * nL)))
+def mlmc_launch_batch(levels, nl, level=None):
+    """Pairs per solver launch of an MLMC level: the estimator (rich_mlmc_estimate
+    with cfg.batch = 0) holds B = 2^31 / (16 n_L^2) finest-level fields, n_L the
+    finest grid, and solves level l (grid m) in launches of B (n_L / m)^2
+    pairs, so each level is tuned for that launch size."""
+    L = len(levels["nsamples"]) - 1
+    nL = levels["n0"] << L
+    B = max(1, (1 << 31) // (16 * nL * nL))
+    if level is None:
+        level = list(levels["nsamples"]).index(nl)
+    r = nL // (levels["n0"] << level)
+    return min(nl, B * r * r)
 
 
 def mlmc_tuning(R, prec, cycle=1):
@@ -339,7 +344,7 @@ def mlmc_tuning(R, prec, cycle=1):
         m = MLMC_LEVELS["n0"] << l
         st_l = MLMC_LEVELS["steps0"] << l
         bt, mi = autotune.tune(R.Problem(nx=m, nz=m, nsteps=st_l, dt=MLMC_LEVELS["t_final"] / st_l,
-                                         precision=prec, cycle=cycle, **PHYS), mlmc_launch_batch(MLMC_LEVELS, nl))
+                                         precision=prec, cycle=cycle, **PHYS), mlmc_launch_batch(MLMC_LEVELS, nl, l))
         tt.append(bt)
         ti.append(mi)
     R.set_tuning(0, 0)
@@ -483,7 +488,7 @@ def run_mlmc_vg(args):
         st_l = MLMC_VG_LEVELS["steps0"] << l
         bt, mi = autotune.tune(R.Problem.infiltration(nx=m, nz=m, nsteps=st_l, dt=MLMC_VG_LEVELS["t_final"] / st_l,
                                                       precision=prec, cycle=base.cycle),
-                               mlmc_launch_batch(MLMC_VG_LEVELS, nl))
+                               mlmc_launch_batch(MLMC_VG_LEVELS, nl, l))
         tt.append(bt)
         ti.append(mi)
     R.set_tuning(0, 0)
@@ -784,7 +789,7 @@ def run_tunecheck(args):
         for l, nl in enumerate(MLMC_LEVELS["nsamples"]):
             m, st_l = MLMC_LEVELS["n0"] << l, MLMC_LEVELS["steps0"] << l
             cases.append((R.Problem(nx=m, nz=m, nsteps=st_l, dt=MLMC_LEVELS["t_final"] / st_l, precision=prec,
-                                    **PHYS), mlmc_launch_batch(MLMC_LEVELS, nl), f"mlmc5 level {l}"))
+                                    **PHYS), mlmc_launch_batch(MLMC_LEVELS, nl, l), f"mlmc5 level {l}"))
     out = []
     for pb, S, name in cases:
         src = autotune.source(pb, S)

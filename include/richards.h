@@ -275,7 +275,8 @@ typedef struct {
     int32_t continuation;     /* Gardner: 1 gives alpha_l = alpha (l+1)/(L+1); van Genuchten:
                                  1 gives the additive (d_alpha, d_n) hierarchy below; 0: the
                                  original parameters on every level                       */
-    int32_t batch;            /* samples per batch, 0 = automatic                          */
+    int32_t batch;            /* pairs per launch; 0 = automatic: B = 2^31/(16 n_L^2) on
+                                 the finest level (n_L its grid), B (n_L/n_l)^2 on level l  */
     double eps;               /* RMSE target of the optimal-allocation report              */
     uint32_t key_offset;      /* added to the level in the noise key (independent reruns)  */
     int32_t tune_threads[RICH_MLMC_MAX_LEVELS];  /* per-level launch shape (0: context's)    */

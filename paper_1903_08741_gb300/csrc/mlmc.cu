@@ -101,6 +101,7 @@ int accumulate_shifted(const double* qf, const double* qc, const int32_t* sf, co
 #include <math.h>
 #include <vector>
 #include <algorithm>
+#include <utility>
 
 namespace {
 
@@ -127,6 +128,7 @@ struct MlmcRun {
     rich_ctx* ctx;
     const rich_mlmc_cfg_t* cfg;
     int NL, L, nL, B = 0;
+    long long qcap = 0;                         // pairs the QoI / status buffers hold
     cudaStream_t st = nullptr;
     cudaEvent_t ev[4] = {};
     // the coarse member of each pair is solved at the same time as the fine
@@ -198,8 +200,7 @@ struct MlmcRun {
             return 0;
         };
         if (dalloc(lkf, fine_cells * 8) || dalloc(alf, fine_cells * 8) || dalloc(lkc, fine_cells * 2) ||
-            dalloc(alc, fine_cells * 2) || dalloc(qf, B * 8) || dalloc(qc, B * 8) || dalloc(sf, B * 4) ||
-            dalloc(sc, B * 4) || dalloc(acc, 8 * ACC_W * (NL + 1)))
+            dalloc(alc, fine_cells * 2) || dalloc(acc, 8 * ACC_W * (NL + 1)))
             return RICH_ERR_OOM;
         if (vg && (dalloc(nf, fine_cells * 8) || dalloc(ncb, fine_cells * 2)))
             return RICH_ERR_OOM;
@@ -207,6 +208,32 @@ struct MlmcRun {
                        dalloc(trc, fine_cells * 2)))
             return RICH_ERR_OOM;
         RICH_CUDA(cudaMemsetAsync(acc.p, 0, 8 * ACC_W * (NL + 1), st));
+        return 0;
+    }
+
+    // pairs per launch on level l: the field buffers hold B finest-level
+    // fields, i.e. B (n_L / M)^2 fields of a level on an M x M grid, so a
+    // coarse level runs in few large launches (each launch ends with a tail
+    // in which its last samples finish); cfg->batch > 0 fixes B for all
+    long long level_batch(int l) const {
+        if (cfg->batch > 0) return B;
+        const long long r = nL / grid(l);
+        return (long long)B * r * r;
+    }
+    // QoI and status buffers for n pairs (grown between levels; the previous
+    // batch has completed: batch() ends with a synchronisation)
+    int ensure_q(long long n) {
+        if (n <= qcap) return 0;
+        for (DevBuf* b : {&qf, &qc, &sf, &sc}) {
+            if (b->p) cudaFree(b->p);
+            b->p = nullptr;
+        }
+        qcap = 0;
+        for (auto [b, w] : {std::pair<DevBuf*, size_t>{&qf, 8}, {&qc, 8}, {&sf, 4}, {&sc, 4}}) {
+            cudaError_t e = cudaMalloc(&b->p, std::max<size_t>((size_t)n * w, 256));
+            if (e != cudaSuccess) { cudaGetLastError(); return RICH_ERR_OOM; }
+        }
+        qcap = n;
         return 0;
     }
 
@@ -222,9 +249,11 @@ struct MlmcRun {
         const int save_t = ctx->tune_threads, save_i = ctx->tune_mixed_inner;
         if (cfg->tune_threads[l]) ctx->tune_threads = cfg->tune_threads[l];
         if (cfg->tune_inner[l]) ctx->tune_mixed_inner = cfg->tune_inner[l];
+        const long long Bl = level_batch(l);
+        if (int e = ensure_q(std::min(count, Bl))) return e;
         int rc_all = 0;
-        for (long long b0 = 0; b0 < count && rc_all >= 0; b0 += B) {
-            const int nb = (int)std::min<long long>(B, count - b0);
+        for (long long b0 = 0; b0 < count && rc_all >= 0; b0 += Bl) {
+            const int nb = (int)std::min<long long>(Bl, count - b0);
             const long long s0 = first + b0;
             rc_all = batch(l, s0, nb, M, ndraw, coarsen, pf, pc);
         }
