@@ -341,7 +341,9 @@ int rich_mlmc_estimate(rich_ctx_t ctx, const rich_mlmc_cfg_t* cfg, rich_mlmc_res
  * cfg->eps from the current level variances and the per-sample costs measured
  * so far, and draw the missing samples (continuing each level's sample
  * stream), until no level needs more, max_rounds rounds are done, or a level
- * would exceed nmax[l] (HOST array, may be NULL).  cfg->eps must be > 0. */
+ * would exceed nmax[l] (HOST array, may be NULL).  N_l counts the pairs with
+ * a defined QoI, whose variance the RMSE uses (a failed pair is replaced by
+ * further draws); nmax[l] caps the pairs run.  cfg->eps must be > 0. */
 int rich_mlmc_adaptive(rich_ctx_t ctx, const rich_mlmc_cfg_t* cfg, int32_t max_rounds,
                        const int64_t* nmax, rich_mlmc_result_t* out);
 

@@ -458,7 +458,8 @@ extern "C" int rich_mlmc_estimate(rich_ctx_t ctx, const rich_mlmc_cfg_t* cfg, ri
 
 // Algorithm PC_MLMC (Sec. 5.2): warm-up with N*_l = cfg->nsamples, then repeat
 // {N_l <- optimal allocation (Eq. MLMCSAMP_ch6) from the current V_l and the
-// per-sample costs measured so far; run the missing samples of every level}
+// per-sample costs measured so far; run the missing samples of every level,
+// N_l counting the pairs with a defined QoI}
 // until no level needs more samples, at most max_rounds rounds or until a
 // level would exceed nmax[l] (NULL: no cap).
 extern "C" int rich_mlmc_adaptive(rich_ctx_t ctx, const rich_mlmc_cfg_t* cfg, int32_t max_rounds,
@@ -479,9 +480,12 @@ extern "C" int rich_mlmc_adaptive(rich_ctx_t ctx, const rich_mlmc_cfg_t* cfg, in
         bool more = false;
         std::vector<long long> add(cfg->nlevels, 0);
         for (int l = 0; l < cfg->nlevels; ++l) {
-            long long target = (long long)ceil(out->n_opt[l]);
-            if (nmax) target = std::min<long long>(target, nmax[l]);
-            if (target > run.n_done[l]) { add[l] = target - run.n_done[l]; more = true; }
+            // V_l / N_l counts the pairs with a defined QoI (failed pairs are
+            // excluded), so those must reach the optimal N_l; nmax caps the
+            // pairs run, failed or not
+            long long want = (long long)ceil(out->n_opt[l]) - out->n[l];
+            if (nmax) want = std::min<long long>(want, nmax[l] - run.n_done[l]);
+            if (want > 0) { add[l] = want; more = true; }
         }
         if (!more) break;
         for (int l = 0; l < cfg->nlevels; ++l)

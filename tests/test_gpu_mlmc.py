@@ -174,8 +174,10 @@ def test_mlmc_telescoping_consistency(R):
 
 
 def test_adaptive_pc_mlmc(R):
-    """Algorithm PC_MLMC: the final N_l cover the optimal allocation computed
-    from the final V_l and C_l (so the sampling RMSE is at most eps), and since
+    """Algorithm PC_MLMC: the final N_l (pairs with a defined QoI, the ones the
+    variance counts) cover the optimal allocation computed from the final V_l
+    and C_l, so the sampling RMSE is at most eps whatever the costs measured in
+    this run (they set the allocation); since
     each level continues its own sample stream, the statistics equal a one-shot
     estimate with the final N_l."""
     eps = 0.02
@@ -185,7 +187,7 @@ def test_adaptive_pc_mlmc(R):
     assert a["rounds"] >= 2
     n_final = [n + f for n, f in zip(a["n"], a["failed"])]
     assert all(n >= w for n, w in zip(n_final, (16, 8, 4)))
-    assert all(nf >= np.ceil(no) - 1e-9 for nf, no in zip(n_final, a["n_opt"])) or a["rounds"] == 8
+    assert all(n >= np.ceil(no) - 1e-9 for n, no in zip(a["n"], a["n_opt"])) or a["rounds"] == 8
     assert a["rmse"] <= eps * (1 + 1e-9) or a["rounds"] == 8
     one = R.mlmc_estimate(R.MlmcConfig(nsamples=tuple(n_final), n0=8, steps0=2, t_final=0.04, coupling=2,
                                        eps=eps, problem=R.Problem(**PHYSICS, **SOLVER)))
