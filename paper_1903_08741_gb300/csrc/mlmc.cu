@@ -483,7 +483,10 @@ extern "C" int rich_mlmc_adaptive(rich_ctx_t ctx, const rich_mlmc_cfg_t* cfg, in
             // V_l / N_l counts the pairs with a defined QoI (failed pairs are
             // excluded), so those must reach the optimal N_l; nmax caps the
             // pairs run, failed or not
-            long long want = (long long)ceil(out->n_opt[l]) - out->n[l];
+            // (a level with fewer than two defined pairs has no variance and
+            // every n_opt is NaN: top that level up to two defined pairs first)
+            const double no = out->n_opt[l];
+            long long want = (std::isfinite(no) ? (long long)ceil(no) : 2) - out->n[l];
             if (nmax) want = std::min<long long>(want, nmax[l] - run.n_done[l]);
             if (want > 0) { add[l] = want; more = true; }
         }
